@@ -1,0 +1,187 @@
+/*
+ * libschur — GB300 (sm_103a) solver for the negative Schur complement of distributed optimal
+ * control with a Poisson constraint, applied through its exact complex factorisation.
+ *
+ * Problem (arXiv 1312.5653, Sec. 2): uniform Q1 elements on the unit box [0,1]^d (d = 2 or 3),
+ * nel[a] elements along axis a, homogeneous Dirichlet conditions on the whole boundary.  K is the
+ * stiffness and M the consistent mass (the paper's volume matrix V) on the n = prod(nel[a]-1)
+ * interior nodes.  Vectors are real FP64, one entry per interior node, lexicographic with axis 0
+ * fastest; several right-hand sides are stored column-major with leading dimension ld >= n.
+ * beta is the paper's regularisation phi, gamma = 1/sqrt(beta).
+ *
+ *   S = K M^{-1} K + M / beta                                   (Sec. 3.1, Schur complement)
+ *   S = (K + i gamma M) M^{-1} (K - i gamma M)                  (Sec. 4, exact factorisation)
+ *   S^{-1} b = -Im(z) / gamma,  z = (K + i gamma M)^{-1} b      (b real; follows from Sec. 4:
+ *            A - conj(A) = 2 i gamma M, so S^{-1} = (conj(A)^{-1} - A^{-1}) / (2 i gamma))
+ *
+ * The complex-symmetric factor A = K + i gamma M is solved by a FETI-DP dual iteration (Sec. 5):
+ * non-overlapping subdomains (nsub[a] per axis), primal subdomain corners with a coarse problem,
+ * GMRES on the interface multipliers with the Dirichlet preconditioner, per-subdomain complex
+ * LDL^T factors.  Optional mixed precision runs the FETI-DP solve in complex FP32 and refines
+ * z in FP64 on the residual b - A z (Sec. 3.1 names iterative refinement in higher precision
+ * as the remedy for the accuracy loss of the range-space method).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named *_dev are device pointers owned by the caller (never freed by the library);
+ *     *_host are host pointers (pageable or pinned).
+ *   - Work is ordered on the CUDA stream passed as `stream` (a cudaStream_t; NULL = legacy default
+ *     stream).  Calls return after enqueueing unless the description says they synchronise.
+ *   - Return value: SCHUR_OK (0) or a negative SCHUR_E* code; no C++ exception crosses the ABI.
+ *     schur_last_error() gives a message for the calling thread's most recent failure.
+ *   - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef SCHUR_H
+#define SCHUR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SCHUR_OK 0
+#define SCHUR_EINVAL -1     /* bad argument (mesh, beta, sizes, pointers)                      */
+#define SCHUR_ENOMEM -2     /* device or host allocation failed                                */
+#define SCHUR_ENOTCONV -3   /* tolerance not met within max_iter / max_refine; x still written */
+#define SCHUR_EBREAKDOWN -4 /* zero or non-finite pivot / Krylov breakdown / non-finite data    */
+#define SCHUR_ETIMEOUT -5   /* a bounded device or host wait gave up                           */
+#define SCHUR_ECUDA -6      /* a CUDA runtime call failed                                      */
+#define SCHUR_EBUSY -7      /* serving: admission refused (memory budget or queue full)        */
+
+#define SCHUR_FP64 0   /* FETI-DP solve in complex FP64                                         */
+#define SCHUR_MIXED 1  /* FETI-DP solve in complex FP32, FP64 refinement of z on b - A z        */
+
+#define SCHUR_LOCAL_PER_SUBDOMAIN 0 /* one factor and one set of local operators per subdomain  */
+#define SCHUR_LOCAL_SHARED 1        /* subdomains with identical local matrices share them      */
+
+typedef struct schur_ctx schur_ctx;
+
+typedef struct {
+  int dim;    /* 2 or 3 */
+  int nel[3]; /* elements per axis (entries beyond dim ignored) */
+} schur_mesh;
+
+typedef struct {
+  int nsub[3];       /* subdomains per axis; nel[a] % nsub[a] == 0, nel[a]/nsub[a] >= 2   */
+  int precision;     /* SCHUR_FP64 or SCHUR_MIXED                                         */
+  double tol;        /* outer stop: ||b - A z||_2 / ||b||_2 <= tol for every right-hand side */
+  double inner_tol;  /* GMRES stop: dual residual / initial dual residual (<= 0: default)  */
+  int max_iter;      /* GMRES iterations per inner solve (Krylov basis size, no restart)  */
+  int max_refine;    /* outer refinement steps (each one inner FETI-DP solve)             */
+  int local_mode;    /* SCHUR_LOCAL_PER_SUBDOMAIN or SCHUR_LOCAL_SHARED                   */
+  int reserved[5];   /* must be zero                                                      */
+} schur_opts;
+
+typedef struct {
+  int status;          /* the return code of the call that filled it                      */
+  int outer_steps;     /* refinement steps taken                                           */
+  int iters_total;     /* GMRES iterations summed over steps (max over right-hand sides)   */
+  int iters_first;     /* GMRES iterations of the first step                               */
+  double rel_residual; /* final ||b - A z|| / ||b||, max over right-hand sides (FP64)       */
+  double ms_setup;     /* schur_setup wall time (host clock, includes device sync)         */
+  double ms_solve;     /* this call's wall time, when the call synchronises; else 0        */
+} schur_stats;
+
+typedef struct {
+  long long n;         /* interior dofs                                                    */
+  int n_sub;           /* subdomains                                                       */
+  int n_classes;       /* distinct local operator sets stored                              */
+  int n_lambda;        /* dual unknowns (interface multipliers)                            */
+  int n_coarse;        /* primal corner unknowns                                           */
+  int n_delta;         /* interface slots per subdomain                                    */
+  int n_local;         /* nodes per subdomain grid ((s+1)^d)                               */
+  long long bytes_operators; /* device bytes held by factors and local/coarse operators     */
+} schur_info_t;
+
+/* Defaults: nsub = 4 per axis, FP64, tol 1e-12, inner_tol by precision, max_iter 300,
+ * max_refine 8, per-subdomain local operators. */
+void schur_default_opts(schur_opts* opts);
+
+/* Builds the solver for one mesh and beta: per-subdomain Q1 assembly of K + i gamma M, batched
+ * complex LDL^T (no pivoting; the real and imaginary parts are positive definite) of the
+ * remainder matrices A_rr (subdomain nodes minus corners and Dirichlet nodes, Sec. 5) and of the
+ * interior matrices A_ii, the explicit local dual operators B A_rr^{-1} B^T, the corner coupling,
+ * the Dirichlet-preconditioner Schur complements S_bb (Eq. WS), and the coarse corner problem
+ * (factorised in FP64).  Synchronises `stream` before returning.  *out receives the context.
+ * Errors: EINVAL (mesh/beta/opts), ENOMEM, EBREAKDOWN (zero pivot), ECUDA. */
+int schur_setup(const schur_mesh* mesh, double beta, const schur_opts* opts, void* stream,
+                schur_ctx** out);
+
+/* x = S^{-1} b for nrhs right-hand sides (Sec. 3.1, Eq. schurcomplementsystem with b given):
+ * one complex FETI-DP solve per refinement step, then x = -Im(z)/gamma.  With b = M y_bar the
+ * result is x = beta y* (state of the KKT system of Sec. 2); with b = K y_bar it is lambda*.
+ * b_dev, x_dev: device FP64, n x nrhs, leading dimension ld.  Synchronises `stream` (the host
+ * reads convergence flags).  Returns ENOTCONV with x written if the tolerance is not met.
+ * st may be NULL.  nrhs == 0 is a no-op. */
+int schur_solve(schur_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, int ld, void* stream,
+                schur_stats* st);
+
+/* As schur_solve with host buffers: copies b to the device, solves, copies x back, all on
+ * `stream`; synchronises before returning. */
+int schur_solve_host(schur_ctx* ctx, const double* b_host, double* x_host, int nrhs, int ld,
+                     void* stream, schur_stats* st);
+
+/* z = (K + i gamma M)^{-1} (b_re + i b_im) (one factor of Sec. 4, the factor the shortcut uses).
+ * b_im_dev may be NULL (real right-hand side).  z_dev: interleaved complex FP64 (re, im), n x nrhs
+ * with leading dimension ld complex entries.  Synchronises.  Same refinement and stop rule as
+ * schur_solve. */
+int schur_complex_solve(schur_ctx* ctx, const double* b_re_dev, const double* b_im_dev, double* z_dev,
+                        int nrhs, int ld, void* stream, schur_stats* st);
+
+/* y = M x and y = K x (FP64 matrix-free Q1 stencils).  Asynchronous. */
+int schur_apply_mass(schur_ctx* ctx, const double* x_dev, double* y_dev, int nrhs, int ld, void* stream);
+int schur_apply_stiffness(schur_ctx* ctx, const double* x_dev, double* y_dev, int nrhs, int ld,
+                          void* stream);
+
+/* y = S x = K M^{-1} K x + M x / beta in FP64; M^{-1} by Jacobi-preconditioned conjugate
+ * gradients to a relative residual of 1e-14 (a diagnostic, not on the solve path).
+ * Synchronises. */
+int schur_apply_S(schur_ctx* ctx, const double* x_dev, double* y_dev, int nrhs, int ld, void* stream);
+
+/* Full-space KKT system of Sec. 2 with homogeneous Dirichlet data:
+ *   [M 0 K; 0 beta M -M; K -M 0] (y, u, l).
+ * Vectors hold the three blocks stacked: entries [0,n) = y, [n,2n) = u, [2n,3n) = lambda; ld >= 3n.
+ * schur_kkt_apply: r = KKT v (asynchronous).
+ * schur_kkt_precond_apply: z = P_mgw^{-1} r with P_mgw = diag(M, beta M, S) (Sec. 3.2,
+ *   Eq. murphypreconditioner): M^{-1} by Chebyshev iteration with Jacobi scaling on the Q1 mass
+ *   spectrum bounds (fixed degree, a fixed linear operator), S^{-1} by schur_solve.  Synchronises.
+ * schur_kkt_minres: MINRES on the KKT system preconditioned by P_mgw, FP64 Krylov, stop at
+ *   ||r_k||/||r_0|| <= tol (preconditioned norm); iters receives the iteration count (max over
+ *   right-hand sides).  Synchronises.  ENOTCONV if max_it is reached. */
+int schur_kkt_apply(schur_ctx* ctx, const double* v_dev, double* r_dev, int nrhs, int ld, void* stream);
+int schur_kkt_precond_apply(schur_ctx* ctx, const double* r_dev, double* z_dev, int nrhs, int ld,
+                            void* stream);
+int schur_kkt_minres(schur_ctx* ctx, const double* rhs_dev, double* sol_dev, int nrhs, int ld, double tol,
+                     int max_it, int* iters, void* stream);
+
+/* Host-only (no GPU needed): the FETI-DP partition of Sec. 5 for a mesh and nsub.
+ * schur_partition fills info (bytes_operators = 0) without touching the device.
+ * schur_partition_export copies one index map into out (int32, capacity cap entries):
+ *   which = 0: lambda sides, 2 per multiplier: subdomain*n_delta + slot (+1 side, then -1 side)
+ *           1: interface slot -> local node index                        (n_delta)
+ *           2: subdomain corner -> coarse unknown or -1, 2^dim per subdomain
+ *           3: subdomain -> operator class                               (n_sub)
+ * Returns EINVAL for a bad mesh/nsub or a too small buffer. */
+int schur_partition(const schur_mesh* mesh, const int* nsub, int local_mode, schur_info_t* info);
+int schur_partition_export(const schur_mesh* mesh, const int* nsub, int local_mode, int which, int* out,
+                           long long cap);
+
+int schur_get_info(const schur_ctx* ctx, schur_info_t* info);
+long long schur_ndof(const schur_mesh* mesh);
+void schur_destroy(schur_ctx* ctx);
+const char* schur_strerror(int code);
+const char* schur_last_error(void);
+
+/* Test hook: copies one local operator of class `cls` to host memory as interleaved complex FP64.
+ * which = 0: F  = (A_rr^{-1}) restricted to the interface slots      (n_delta x n_delta)
+ *         1: Frc = (A_rr^{-1} A_rc) on the interface slots           (n_delta x 2^d)
+ *         2: S_bb = A_DD - A_Di A_ii^{-1} A_iD (Dirichlet precond.)  (n_delta x n_delta)
+ *         3: the assembled coarse matrix, dense                      (n_coarse x n_coarse)
+ *         4: the coarse inverse actually applied                     (n_coarse x n_coarse)
+ * Row-major.  `cap` = capacity of out in complex entries.  Synchronises. */
+int schur_debug_operator(schur_ctx* ctx, int which, int cls, double* out_host, long long cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,42 @@
+// Internal layout of the opaque schur_ctx and helpers shared by the C-ABI translation units.
+#pragma once
+#include <string>
+
+#include "../../include/schur.h"
+#include "engine.h"
+#include "maps.h"
+
+
+struct schur_ctx {
+  schur::HostMaps hm;
+  schur::DevMaps dm;
+  schur::EngineBase* eng = nullptr;
+  schur_mesh mesh;
+  schur_opts opts;
+  double beta = 0, gamma = 0, ms_setup = 0;
+  long long launches = 0;  // kernels launched by the most recent solve call
+  // FP64 outer refinement workspace
+  int wsR = 0, nblk = 1;
+  double* z = nullptr;      // complex, n x wsR
+  double* res = nullptr;    // complex, n x wsR
+  double* part = nullptr;   // norm partials
+  double* h_part = nullptr; // pinned host copy
+  // host-buffer entry points
+  double* hb = nullptr;
+  double* hx = nullptr;
+  size_t host_cap = 0;
+  // full-space (KKT) workspace
+  int kkt_R = 0;
+  double* kkt_buf = nullptr;
+  double* kkt_part = nullptr;
+  double* kkt_hpart = nullptr;
+  double* kkt_coef = nullptr;
+};
+
+namespace schur {
+int set_error(int code, const std::string& msg);
+int ctx_ensure_outer(schur_ctx* c, int R);
+int ctx_outer(schur_ctx* c, const double* bre, const double* bim, int ldb, int R, double* x, int ldx, double* zout,
+              int ldz, cudaStream_t st, schur_stats* stats);
+void kkt_free(schur_ctx* c);
+}  // namespace schur

@@ -1,0 +1,54 @@
+// Host interface of the FETI-DP engine (one per context and working precision).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "maps.h"
+
+namespace schur {
+
+// Device copies of the index maps (uploaded once per context).
+struct DevMaps {
+  int* slot_node = nullptr;
+  int* node_slot = nullptr;
+  int* corner_node = nullptr;
+  int* sd_code = nullptr;
+  int* sd_cls = nullptr;
+  int* cls_code = nullptr;
+  int* sd_lam = nullptr;
+  int* lam_side = nullptr;
+  int* sd_corner = nullptr;
+  double* sd_minv = nullptr;
+};
+
+int upload_maps(const HostMaps& hm, DevMaps* dm, std::string* msg);
+void free_maps(DevMaps* dm);
+
+struct InnerResult {
+  int iters = 0;        // GMRES iterations (max over right-hand sides)
+  int converged = 1;    // all right-hand sides met the inner tolerance
+};
+
+class EngineBase {
+ public:
+  virtual ~EngineBase() {}
+  // Builds factors and operators (synchronises `st`).  Returns SCHUR_* code.
+  virtual int setup(cudaStream_t st, std::string* msg) = 0;
+  // One FETI-DP solve of A dz = f for R <= kMaxR columns; f, z interleaved complex FP64 with
+  // leading dimensions ldf, ldz (complex entries); z += dz.  Synchronises `st`.
+  virtual int inner_solve(const double* f, int ldf, double* z, int ldz, int R, double tol, int max_iter,
+                          cudaStream_t st, InnerResult* res, std::string* msg) = 0;
+  virtual long long op_bytes() const = 0;
+  virtual int debug_operator(int which, int cls, double* out, long long cap, cudaStream_t st,
+                             std::string* msg) = 0;
+  // Kernel launches issued by the most recent inner_solve.
+  long long launches = 0;
+};
+
+constexpr int kMaxR = 16;
+
+EngineBase* make_engine_f64(const HostMaps* hm, const DevMaps* dm, double gamma);
+EngineBase* make_engine_f32(const HostMaps* hm, const DevMaps* dm, double gamma);
+
+}  // namespace schur

@@ -1,0 +1,8 @@
+// FP64 instantiation of the FETI-DP engine.
+#include "engine_impl.cuh"
+
+namespace schur {
+EngineBase* make_engine_f64(const HostMaps* hm, const DevMaps* dm, double gamma) {
+  return new Engine<double>(hm, dm, gamma);
+}
+}  // namespace schur

@@ -1,0 +1,578 @@
+// Engine<T>: device storage and host orchestration of one FETI-DP solver for A = K + i gamma M in
+// working precision T.  Included by engine_f64.cu and engine_f32.cu (one instantiation each).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/schur.h"
+#include "engine.h"
+#include "gmres.h"
+#include "kernels.cuh"
+
+namespace schur {
+
+#define ENG_CK(call)                                                                   \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      if (msg) *msg = std::string(#call) + ": " + cudaGetErrorString(e_);              \
+      return e_ == cudaErrorMemoryAllocation ? SCHUR_ENOMEM : SCHUR_ECUDA;             \
+    }                                                                                  \
+  } while (0)
+
+#define ENG_LAUNCH()                                                                   \
+  do {                                                                                 \
+    ++launches;                                                                        \
+    cudaError_t e_ = cudaGetLastError();                                               \
+    if (e_ != cudaSuccess) {                                                           \
+      if (msg) *msg = std::string("kernel launch at line ") + std::to_string(__LINE__) + \
+                      ": " + cudaGetErrorString(e_);                                   \
+      return SCHUR_ECUDA;                                                              \
+    }                                                                                  \
+  } while (0)
+
+template <class T>
+class Engine : public EngineBase {
+ public:
+  Engine(const HostMaps* hm, const DevMaps* dm, double gamma) : hm_(hm), dm_(dm), g_(hm->g), gamma_(gamma) {
+    mv_.slot_node = dm->slot_node;
+    mv_.node_slot = dm->node_slot;
+    mv_.corner_node = dm->corner_node;
+    mv_.sd_cls = dm->sd_cls;
+    mv_.cls_code = dm->cls_code;
+    mv_.sd_lam = dm->sd_lam;
+    mv_.lam_side = dm->lam_side;
+    mv_.sd_corner = dm->sd_corner;
+    mv_.sd_minv = dm->sd_minv;
+    st_ = make_stencil<T>(g_, gamma);
+    ncls_ = hm->ncls;
+    // remainder problem: full local grid, vertices and Dirichlet nodes removed
+    prr_.ly.dim = g_.dim;
+    pii_.ly.dim = g_.dim;
+    for (int a = 0; a < 3; ++a) {
+      prr_.ly.ext[a] = a < g_.dim ? g_.s[a] + 1 : 1;
+      pii_.ly.ext[a] = a < g_.dim ? g_.s[a] - 1 : 1;
+      prr_.s[a] = g_.s[a];
+      pii_.s[a] = g_.s[a];
+    }
+    prr_.ly.b = g_.lb;
+    prr_.ly.L = g_.lL;
+    prr_.st = st_;
+    prr_.off = 0;
+    prr_.masked = 1;
+    prr_.code = 0;
+    pii_.ly.b = g_.ib;
+    pii_.ly.L = g_.iL;
+    pii_.st = st_;
+    pii_.off = 1;
+    pii_.masked = 0;
+    pii_.code = 0;
+    cudaDeviceGetAttribute(&nsm_, cudaDevAttrMultiProcessorCount, 0);
+    if (nsm_ <= 0) nsm_ = 152;
+  }
+
+  ~Engine() override {
+    for (void* p : allocs_) cudaFree(p);
+    if (h_active_) cudaFreeHost(h_active_);
+  }
+
+  long long op_bytes() const override { return op_bytes_; }
+
+  int setup(cudaStream_t st, std::string* msg) override {
+    const Geom& g = g_;
+    const size_t cxT = sizeof(cx<T>);
+    const int bb = g.lb * g.lb;
+    ENG_CK(alloc(&err_, 4 * sizeof(int)));
+    ENG_CK(cudaMemsetAsync(err_, 0, 4 * sizeof(int), st));
+    ENG_CK(alloc(&ones_, kMaxRdev * sizeof(int)));
+    {
+      int h1[kMaxRdev];
+      for (int i = 0; i < kMaxRdev; ++i) h1[i] = 1;
+      ENG_CK(cudaMemcpyAsync(ones_, h1, sizeof(h1), cudaMemcpyHostToDevice, st));
+    }
+    // ---- remainder factors, one per class
+    ENG_CK(alloc(&Dinv_, (size_t)ncls_ * g.lL * bb * cxT));
+    op_bytes_ += (long long)ncls_ * g.lL * bb * cxT;
+    {
+      size_t need = (2 * (size_t)bb + 2 * g.lb) * cxT;
+      int use_smem = need <= 200 * 1024;
+      size_t smem = use_smem ? need : 2 * g.lb * cxT;
+      cx<T>* gws = nullptr;
+      if (!use_smem) ENG_CK(alloc(&gws, (size_t)ncls_ * 2 * bb * cxT));
+      ENG_CK(cudaFuncSetAttribute(k_factor<T, StencilProv<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      int thr = bb >= 1024 ? 512 : 256;
+      k_factor<T, StencilProv<T>><<<ncls_, thr, smem, st>>>(prr_, dm_->cls_code, Dinv_, gws, use_smem, err_);
+      ENG_LAUNCH();
+    }
+    // ---- interior factor (identical for all subdomains)
+    const int ibb = g.ib * g.ib;
+    cx<T>* Dii = nullptr;
+    ENG_CK(alloc(&Dii, (size_t)g.iL * ibb * cxT));
+    {
+      size_t need = (2 * (size_t)ibb + 2 * g.ib) * cxT;
+      int use_smem = need <= 200 * 1024;
+      size_t smem = use_smem ? need : 2 * g.ib * cxT;
+      cx<T>* gws = nullptr;
+      if (!use_smem) ENG_CK(alloc(&gws, 2 * (size_t)ibb * cxT));
+      ENG_CK(cudaFuncSetAttribute(k_factor<T, StencilProv<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_factor<T, StencilProv<T>><<<1, ibb >= 1024 ? 512 : 256, smem, st>>>(pii_, dm_->cls_code, Dii, gws, use_smem, err_ + 1);
+      ENG_LAUNCH();
+    }
+    // ---- local operators
+    ENG_CK(alloc(&F_, (size_t)ncls_ * g.nD * g.nD * cxT));
+    ENG_CK(alloc(&Frc_, (size_t)ncls_ * g.nD * g.nc * cxT));
+    ENG_CK(alloc(&Sd_, (size_t)ncls_ * g.nD * g.nD * cxT));
+    ENG_CK(alloc(&Kcc_, (size_t)ncls_ * g.nc * g.nc * sizeof(cx<double>)));
+    op_bytes_ += (long long)ncls_ * g.nD * (2 * g.nD + g.nc) * cxT;
+    {
+      const int C = 32;
+      const int ncol = g.nD + g.nc, nchunk = (ncol + C - 1) / C;
+      int grid = std::min(ncls_ * nchunk, 8 * nsm_);
+      cx<T>* Xws = nullptr;
+      ENG_CK(alloc(&Xws, (size_t)grid * g.nl * C * cxT));
+      size_t smem = 2 * (size_t)g.lb * C * cxT;
+      ENG_CK(cudaFuncSetAttribute(k_form_rr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_form_rr<T><<<grid, 256, smem, st>>>(prr_, g, mv_, Dinv_, ncls_, C, Xws, F_, Frc_, Kcc_);
+      ENG_LAUNCH();
+      const int nchunk2 = (g.nD + C - 1) / C;
+      cx<T>* Xi = nullptr;
+      cx<T>* Sbase = nullptr;
+      ENG_CK(alloc(&Xi, (size_t)nchunk2 * g.ni * C * cxT));
+      ENG_CK(alloc(&Sbase, (size_t)g.nD * g.nD * cxT));
+      size_t smem2 = 2 * (size_t)g.ib * C * cxT;
+      ENG_CK(cudaFuncSetAttribute(k_form_ii<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+      k_form_ii<T><<<nchunk2, 256, smem2, st>>>(pii_, g, mv_, Dii, C, Xi, Sbase);
+      ENG_LAUNCH();
+      long long tot = (long long)ncls_ * g.nD * g.nD;
+      int gs = (int)std::min<long long>((tot + 255) / 256, 16LL * nsm_);
+      k_mask_S<T><<<gs, 256, 0, st>>>(g, mv_, ncls_, Sbase, Sd_);
+      ENG_LAUNCH();
+      ENG_CK(cudaStreamSynchronize(st));
+      free_one(Xws);
+      free_one(Xi);
+      free_one(Sbase);
+      free_one(Dii);
+    }
+    // ---- coarse problem (FP64 factorisation, inverse stored in T)
+    if (g.ncor > 0) {
+      const int nt = nbr_count(g.dim), cbb = g.cb * g.cb;
+      ENG_CK(alloc(&CA_, (size_t)g.cL * g.cb * nt * sizeof(cx<double>)));
+      ENG_CK(alloc(&CB_, (size_t)std::max(1, g.cL) * g.cb * nt * sizeof(cx<double>)));
+      ENG_CK(cudaMemsetAsync(CA_, 0, (size_t)g.cL * g.cb * nt * sizeof(cx<double>), st));
+      ENG_CK(cudaMemsetAsync(CB_, 0, (size_t)std::max(1, g.cL) * g.cb * nt * sizeof(cx<double>), st));
+      const int noff = g.dim == 2 ? 9 : 27;
+      long long tot = (long long)g.ncor * noff;
+      k_coarse_assemble<<<(int)((tot + 255) / 256), 256, 0, st>>>(g, Kcc_, dm_->sd_cls, CA_, CB_);
+      ENG_LAUNCH();
+      cprov_.ly.dim = g.dim;
+      for (int a = 0; a < 3; ++a) cprov_.ly.ext[a] = a < g.dim ? g.ncg[a] : 1;
+      cprov_.ly.b = g.cb;
+      cprov_.ly.L = g.cL;
+      cprov_.CA = CA_;
+      cprov_.CB = CB_;
+      ENG_CK(alloc(&Dc_, (size_t)g.cL * cbb * sizeof(cx<double>)));
+      size_t need = (2 * (size_t)cbb + 2 * g.cb) * sizeof(cx<double>);
+      int use_smem = need <= 200 * 1024;
+      size_t smem = use_smem ? need : 2 * g.cb * sizeof(cx<double>);
+      cx<double>* gws = nullptr;
+      if (!use_smem) ENG_CK(alloc(&gws, 2 * (size_t)cbb * sizeof(cx<double>)));
+      ENG_CK(cudaFuncSetAttribute(k_factor<double, StoredProv<double>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+      k_factor<double, StoredProv<double>><<<1, 1024, smem, st>>>(cprov_, nullptr, Dc_, gws, use_smem, err_ + 2);
+      ENG_LAUNCH();
+      const int C = 16, nchunk = (g.ncor + C - 1) / C;
+      int grid = std::min(nchunk, 4 * nsm_);
+      cx<double>* Xws = nullptr;
+      ENG_CK(alloc(&Xws, (size_t)grid * g.ncor * C * sizeof(cx<double>)));
+      ENG_CK(alloc(&Kinv_, (size_t)g.ncor * g.ncor * cxT));
+      op_bytes_ += (long long)g.ncor * g.ncor * cxT;
+      size_t smem2 = 2 * (size_t)g.cb * C * sizeof(cx<double>);
+      ENG_CK(cudaFuncSetAttribute(k_coarse_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+      k_coarse_inverse<T><<<grid, 256, smem2, st>>>(cprov_, Dc_, g.ncor, C, Xws, Kinv_);
+      ENG_LAUNCH();
+      ENG_CK(cudaStreamSynchronize(st));
+      free_one(Xws);
+      if (gws) free_one(gws);
+    }
+    ENG_CK(cudaStreamSynchronize(st));
+    int herr[4];
+    ENG_CK(cudaMemcpy(herr, err_, sizeof(herr), cudaMemcpyDeviceToHost));
+    if (herr[0] || herr[1] || herr[2]) {
+      if (msg) *msg = "zero or non-finite pivot in a subdomain or coarse factorisation";
+      return SCHUR_EBREAKDOWN;
+    }
+    return SCHUR_OK;
+  }
+
+  int inner_solve(const double* f, int ldf, double* z, int ldz, int R, double tol, int max_iter, cudaStream_t st,
+                  InnerResult* res, std::string* msg) override {
+    const Geom& g = g_;
+    if (R < 1 || R > kMaxRdev) {
+      if (msg) *msg = "inner_solve: R out of range";
+      return SCHUR_EINVAL;
+    }
+    const int m = std::max(1, std::min(max_iter, kMaxKdev - 1));
+    int rc = ensure_ws(R, m, msg);
+    if (rc) return rc;
+    launches = 0;
+    const cx<double>* fc = reinterpret_cast<const cx<double>*>(f);
+    cx<double>* zc = reinterpret_cast<cx<double>*>(z);
+    const size_t cxT = sizeof(cx<T>);
+    const bool coarse = g.ncor > 0;
+    // ---- local right-hand sides
+    {
+      int thr = std::min(256, ((g.lb * R + 31) / 32) * 32);
+      size_t smem = 2 * (size_t)g.lb * R * cxT;
+      ENG_CK(cudaFuncSetAttribute(k_local_rhs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_local_rhs<T><<<g.nsd, thr, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, R, Xs_, VD_, Tc_);
+      ENG_LAUNCH();
+    }
+    if (coarse) {
+      int tot = R * g.ncor;
+      k_corner_gather<T><<<(tot + 255) / 256, 256, 0, st>>>(g, Tc_, R, fc, ldf, nullptr, T(-1), ftc_);
+      ENG_LAUNCH();
+      rc = coarse_apply(ftc_, R, nullptr, wc_, st, msg);
+      if (rc) return rc;
+    }
+    int iters = 0, conv = 1;
+    if (g.nlam > 0) {
+      long long tot = (long long)R * g.nlam;
+      k_dual_rhs<T><<<(int)((tot + 255) / 256), 256, 0, st>>>(g, mv_, VD_, Frc_, coarse ? wc_ : nullptr, R, d_);
+      ENG_LAUNCH();
+      rc = gmres(R, m, tol, st, &iters, &conv, msg);
+      if (rc) return rc;
+    }
+    // ---- primal recovery
+    if (g.nlam > 0) {
+      rc = local_apply(false, F_, lam_, R, ones_, coarse, st, msg);  // Tc = Frc^T B^T lambda
+      if (rc) return rc;
+    }
+    if (coarse) {
+      int tot = R * g.ncor;
+      if (g.nlam > 0) {
+        k_corner_gather<T><<<(tot + 255) / 256, 256, 0, st>>>(g, Tc_, R, nullptr, 0, ftc_, T(1), gc_);
+        ENG_LAUNCH();
+        rc = coarse_apply(gc_, R, nullptr, uc_, st, msg);
+      } else {
+        rc = coarse_apply(ftc_, R, nullptr, uc_, st, msg);
+      }
+      if (rc) return rc;
+    }
+    {
+      int thr = std::min(256, ((g.lb * R + 31) / 32) * 32);
+      size_t smem = 2 * (size_t)g.lb * R * cxT;
+      ENG_CK(cudaFuncSetAttribute(k_recover<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_recover<T><<<g.nsd, thr, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, g.nlam > 0 ? lam_ : nullptr,
+                                             coarse ? uc_ : nullptr, R, Xs_);
+      ENG_LAUNCH();
+      long long tot = (long long)R * g.n;
+      k_assemble_z<T><<<(int)((tot + 255) / 256), 256, 0, st>>>(g, Xs_, coarse ? uc_ : nullptr, R, zc, ldz);
+      ENG_LAUNCH();
+    }
+    ENG_CK(cudaStreamSynchronize(st));
+    int hb[kMaxRdev];
+    ENG_CK(cudaMemcpy(hb, bad_, sizeof(int) * R, cudaMemcpyDeviceToHost));
+    for (int r = 0; r < R; ++r)
+      if (hb[r]) {
+        if (msg) *msg = "non-finite value in the Krylov iteration";
+        return SCHUR_EBREAKDOWN;
+      }
+    if (res) {
+      res->iters = iters;
+      res->converged = conv;
+    }
+    return SCHUR_OK;
+  }
+
+  int debug_operator(int which, int cls, double* out, long long cap, cudaStream_t st, std::string* msg) override {
+    const Geom& g = g_;
+    ENG_CK(cudaStreamSynchronize(st));
+    std::vector<cx<double>> host;
+    auto fetch = [&](const cx<T>* src, size_t cnt) -> int {
+      std::vector<cx<T>> tmp(cnt);
+      cudaError_t e = cudaMemcpy(tmp.data(), src, cnt * sizeof(cx<T>), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return SCHUR_ECUDA;
+      host.resize(cnt);
+      for (size_t i = 0; i < cnt; ++i) host[i] = ccast<double>(tmp[i]);
+      return 0;
+    };
+    int rc = 0;
+    if (which <= 2 && (cls < 0 || cls >= ncls_)) return SCHUR_EINVAL;
+    if (which == 0) rc = fetch(F_ + (size_t)cls * g.nD * g.nD, (size_t)g.nD * g.nD);
+    else if (which == 1) rc = fetch(Frc_ + (size_t)cls * g.nD * g.nc, (size_t)g.nD * g.nc);
+    else if (which == 2) rc = fetch(Sd_ + (size_t)cls * g.nD * g.nD, (size_t)g.nD * g.nD);
+    else if (which == 3 || which == 4) {
+      if (g.ncor == 0) return SCHUR_EINVAL;
+      if (which == 4) {
+        rc = fetch(Kinv_, (size_t)g.ncor * g.ncor);
+      } else {
+        const int nt = nbr_count(g.dim);
+        std::vector<cx<double>> ca((size_t)g.cL * g.cb * nt), cb((size_t)g.cL * g.cb * nt);
+        if (cudaMemcpy(ca.data(), CA_, ca.size() * sizeof(cx<double>), cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(cb.data(), CB_, cb.size() * sizeof(cx<double>), cudaMemcpyDeviceToHost) != cudaSuccess)
+          return SCHUR_ECUDA;
+        host.assign((size_t)g.ncor * g.ncor, mkc<double>(0, 0));
+        int ext0 = g.ncg[0], ext1 = g.dim == 3 ? g.ncg[1] : 1;
+        for (int K = 0; K < g.cL; ++K)
+          for (int i = 0; i < g.cb; ++i)
+            for (int t = 0; t < nt; ++t) {
+              int d0 = t % 3 - 1, d1 = g.dim == 3 ? t / 3 - 1 : 0;
+              int c0 = i % ext0 + d0, c1 = (g.dim == 3 ? i / ext0 : 0) + d1;
+              if (c0 < 0 || c0 >= ext0 || c1 < 0 || c1 >= ext1) continue;
+              int j = c0 + ext0 * c1;
+              size_t row = (size_t)K * g.cb + i;
+              host[row * g.ncor + (size_t)K * g.cb + j] = ca[((size_t)K * g.cb + i) * nt + t];
+              if (K > 0) {
+                cx<double> v = cb[((size_t)(K - 1) * g.cb + i) * nt + t];
+                size_t col = (size_t)(K - 1) * g.cb + j;
+                host[row * g.ncor + col] = v;
+                host[col * g.ncor + row] = v;
+              }
+            }
+      }
+    } else {
+      return SCHUR_EINVAL;
+    }
+    if (rc) return rc;
+    if ((long long)host.size() > cap) return SCHUR_EINVAL;
+    std::memcpy(out, host.data(), host.size() * sizeof(cx<double>));
+    return SCHUR_OK;
+  }
+
+ private:
+  template <class P>
+  cudaError_t alloc(P** p, size_t bytes) {
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, std::max<size_t>(bytes, 16));
+    if (e == cudaSuccess) {
+      allocs_.push_back(v);
+      *p = reinterpret_cast<P*>(v);
+    }
+    return e;
+  }
+  void free_one(void* p) {
+    auto it = std::find(allocs_.begin(), allocs_.end(), p);
+    if (it != allocs_.end()) {
+      cudaFree(p);
+      allocs_.erase(it);
+    }
+  }
+
+  int ensure_ws(int R, int m, std::string* msg) {
+    if (R <= wsR_ && m <= wsM_) return SCHUR_OK;
+    for (void* p : ws_) free_one(p);
+    ws_.clear();
+    const Geom& g = g_;
+    R = std::max(R, wsR_);
+    m = std::max(m, wsM_);
+    const size_t cxT = sizeof(cx<T>);
+    auto wa = [&](auto** p, size_t bytes) -> cudaError_t {
+      cudaError_t e = alloc(p, bytes);
+      if (e == cudaSuccess) ws_.push_back((void*)*p);
+      return e;
+    };
+    const size_t nl = std::max(1, g.nlam), nco = std::max(1, g.ncor);
+    ENG_CK(wa(&Xs_, (size_t)g.nsd * g.nl * R * cxT));
+    ENG_CK(wa(&VD_, (size_t)g.nsd * R * g.nD * cxT));
+    ENG_CK(wa(&Y_, (size_t)g.nsd * R * g.nD * cxT));
+    ENG_CK(wa(&Tc_, (size_t)g.nsd * R * g.nc * cxT));
+    ENG_CK(wa(&d_, nl * R * cxT));
+    ENG_CK(wa(&zv_, nl * R * cxT));
+    ENG_CK(wa(&lam_, nl * R * cxT));
+    ENG_CK(wa(&V_, nl * R * (m + 1) * cxT));
+    ENG_CK(wa(&ftc_, nco * R * cxT));
+    ENG_CK(wa(&gc_, nco * R * cxT));
+    ENG_CK(wa(&wc_, nco * R * cxT));
+    ENG_CK(wa(&uc_, nco * R * cxT));
+    nblk_ = std::max(1, std::min((int)((nl + 255) / 256), 2 * nsm_));
+    nblk_ = std::max(nblk_, (int)((nl + 2047) / 2048));
+    ENG_CK(wa(&part_, (size_t)kMaxRdev * kMaxKdev * nblk_ * sizeof(cx<double>)));
+    ENG_CK(wa(&H_, (size_t)R * m * (m + 1) * sizeof(cx<double>)));
+    ENG_CK(wa(&hc_, (size_t)kMaxRdev * kMaxKdev * sizeof(cx<double>)));
+    ENG_CK(wa(&gvec_, (size_t)R * (m + 1) * sizeof(cx<double>)));
+    ENG_CK(wa(&cs_s_, (size_t)R * m * sizeof(cx<double>)));
+    ENG_CK(wa(&cs_c_, (size_t)R * m * sizeof(double)));
+    ENG_CK(wa(&y_, (size_t)kMaxRdev * kMaxKdev * sizeof(cx<double>)));
+    ENG_CK(wa(&nrm_part_, (size_t)kMaxRdev * nblk_ * sizeof(double)));
+    ENG_CK(wa(&beta0_, kMaxRdev * sizeof(double)));
+    ENG_CK(wa(&inv_nrm_, kMaxRdev * sizeof(double)));
+    ENG_CK(wa(&resid_, kMaxRdev * sizeof(double)));
+    ENG_CK(wa(&active_, kMaxRdev * sizeof(int)));
+    ENG_CK(wa(&kk_, kMaxRdev * sizeof(int)));
+    ENG_CK(wa(&bad_, kMaxRdev * sizeof(int)));
+    if (!h_active_) ENG_CK(cudaMallocHost(&h_active_, 2 * kMaxRdev * sizeof(int)));
+    wsR_ = R;
+    wsM_ = m;
+    return SCHUR_OK;
+  }
+
+  int coarse_apply(const cx<T>* gv, int R, const int* active, cx<T>* w, cudaStream_t st, std::string* msg) {
+    const int rows_per_block = 8, grid = (g_.ncor + rows_per_block - 1) / rows_per_block;
+    if (R == 1) k_coarse_apply<T, 1><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, gv, R, active, w);
+    else if (R <= 4) k_coarse_apply<T, 4><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, gv, R, active, w);
+    else if (R <= 8) k_coarse_apply<T, 8><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, gv, R, active, w);
+    else k_coarse_apply<T, 16><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, gv, R, active, w);
+    ENG_LAUNCH();
+    return SCHUR_OK;
+  }
+
+  // Y = Op x with x = (scaled) B^T v gathered per subdomain; Tc = Frc^T x when want_tc.
+  int local_apply(bool precond, const cx<T>* Op, const cx<T>* v, int R, const int* active, bool want_tc,
+                  cudaStream_t st, std::string* msg) {
+    const Geom& g = g_;
+    int thr = std::min(512, ((g.nD + 31) / 32) * 32);
+    size_t smem = (size_t)R * g.nD * sizeof(cx<T>);
+    cx<T>* tc = want_tc ? Tc_ : nullptr;
+#define LA_CASE(SC, MR)                                                                                 \
+  do {                                                                                                  \
+    ENG_CK(cudaFuncSetAttribute(k_local_apply<T, SC, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                (int)std::max<size_t>(smem, 1)));                                       \
+    k_local_apply<T, SC, MR><<<g.nsd, thr, smem, st>>>(g, mv_, Op, Frc_, v, R, active, Y_, tc);         \
+  } while (0)
+    if (precond) {
+      if (R == 1) LA_CASE(true, 1);
+      else if (R <= 4) LA_CASE(true, 4);
+      else if (R <= 8) LA_CASE(true, 8);
+      else LA_CASE(true, 16);
+    } else {
+      if (R == 1) LA_CASE(false, 1);
+      else if (R <= 4) LA_CASE(false, 4);
+      else if (R <= 8) LA_CASE(false, 8);
+      else LA_CASE(false, 16);
+    }
+#undef LA_CASE
+    ENG_LAUNCH();
+    return SCHUR_OK;
+  }
+
+  // out = P^{-1} v  (Dirichlet preconditioner)
+  int precond(const cx<T>* v, int R, const int* active, cx<T>* out, cudaStream_t st, std::string* msg) {
+    int rc = local_apply(true, Sd_, v, R, active, false, st, msg);
+    if (rc) return rc;
+    long long tot = (long long)R * g_.nlam;
+    k_scatter<T, true><<<(int)((tot + 255) / 256), 256, 0, st>>>(g_, mv_, Y_, nullptr, nullptr, R, active, out);
+    ENG_LAUNCH();
+    return SCHUR_OK;
+  }
+
+  // out = F_DP v = F_rr v + Frc~ Kcc~^{-1} Frc~^T v
+  int dual_apply(const cx<T>* v, int R, const int* active, cx<T>* out, cudaStream_t st, std::string* msg) {
+    const bool coarse = g_.ncor > 0;
+    int rc = local_apply(false, F_, v, R, active, coarse, st, msg);
+    if (rc) return rc;
+    if (coarse) {
+      int tot = R * g_.ncor;
+      k_corner_gather<T><<<(tot + 255) / 256, 256, 0, st>>>(g_, Tc_, R, nullptr, 0, nullptr, T(1), gc_);
+      ENG_LAUNCH();
+      rc = coarse_apply(gc_, R, active, wc_, st, msg);
+      if (rc) return rc;
+    }
+    long long tot = (long long)R * g_.nlam;
+    k_scatter<T, false><<<(int)((tot + 255) / 256), 256, 0, st>>>(g_, mv_, Y_, Frc_, coarse ? wc_ : nullptr, R, active,
+                                                                  out);
+    ENG_LAUNCH();
+    return SCHUR_OK;
+  }
+
+  int gmres(int R, int m, double tol, cudaStream_t st, int* iters, int* conv, std::string* msg) {
+    const Geom& g = g_;
+    const int nlam = g.nlam, nblk = nblk_;
+    const long long vstride = (long long)R * nlam;
+    const size_t cxT = sizeof(cx<T>);
+    const int gs = std::max(1, std::min((nlam + 255) / 256, 4 * nsm_));
+    ENG_CK(cudaMemsetAsync(H_, 0, (size_t)R * m * (m + 1) * sizeof(cx<double>), st));
+    ENG_CK(cudaMemsetAsync(bad_, 0, kMaxRdev * sizeof(int), st));
+    k_norm2<T><<<dim3(nblk, R), 256, 0, st>>>(d_, nlam, R, nullptr, nblk, nrm_part_);
+    ENG_LAUNCH();
+    ENG_CK(cudaMemcpyAsync(V_, d_, (size_t)R * nlam * cxT, cudaMemcpyDeviceToDevice, st));
+    k_gmres_init<<<1, 32, 0, st>>>(R, nrm_part_, nblk, m, beta0_, gvec_, active_, kk_, inv_nrm_, resid_);
+    ENG_LAUNCH();
+    k_scale_vec<T><<<dim3(gs, R), 256, 0, st>>>(V_, nlam, R, active_, inv_nrm_);
+    ENG_LAUNCH();
+    const int seg = (nlam + nblk - 1) / nblk;
+    const size_t dot_smem = (size_t)seg * cxT;
+    ENG_CK(cudaFuncSetAttribute(k_dots<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dot_smem));
+    const int check_every = 4;
+    int k = 0;
+    for (; k < m; ++k) {
+      cx<T>* vk = V_ + k * vstride;
+      cx<T>* vk1 = V_ + (k + 1) * vstride;
+      int rc = precond(vk, R, active_, zv_, st, msg);
+      if (rc) return rc;
+      rc = dual_apply(zv_, R, active_, vk1, st, msg);
+      if (rc) return rc;
+      for (int pass = 0; pass < 2; ++pass) {
+        k_dots<T><<<dim3(nblk, R), 256, dot_smem, st>>>(V_, vstride, nlam, R, k, vk1, active_, nblk, part_);
+        ENG_LAUNCH();
+        int warps = R * (k + 1);
+        k_dots_reduce<<<(warps * 32 + 255) / 256, 256, 0, st>>>(part_, nblk, R, k, m, active_, H_, hc_);
+        ENG_LAUNCH();
+        k_update<T><<<dim3(gs, R), 256, (k + 1) * cxT, st>>>(V_, vstride, nlam, R, k, hc_, active_, vk1);
+        ENG_LAUNCH();
+      }
+      k_norm2<T><<<dim3(nblk, R), 256, 0, st>>>(vk1, nlam, R, active_, nblk, nrm_part_);
+      ENG_LAUNCH();
+      k_givens<<<1, 32, 0, st>>>(R, k, m, H_, nrm_part_, nblk, cs_c_, cs_s_, gvec_, beta0_, tol, active_, kk_, inv_nrm_,
+                                 resid_, bad_);
+      ENG_LAUNCH();
+      k_scale_vec<T><<<dim3(gs, R), 256, 0, st>>>(vk1, nlam, R, active_, inv_nrm_);
+      ENG_LAUNCH();
+      if ((k + 1) % check_every == 0 || k + 1 == m) {
+        ENG_CK(cudaMemcpyAsync(h_active_, active_, R * sizeof(int), cudaMemcpyDeviceToHost, st));
+        ENG_CK(cudaStreamSynchronize(st));
+        bool any = false;
+        for (int r = 0; r < R; ++r) any = any || h_active_[r];
+        if (!any) break;
+      }
+    }
+    k_hess_solve<<<R, 256, 0, st>>>(m, H_, gvec_, kk_, y_);
+    ENG_LAUNCH();
+    k_combine<T><<<dim3(gs, R), 256, (size_t)m * cxT, st>>>(V_, vstride, nlam, R, y_, kk_, d_);
+    ENG_LAUNCH();
+    int rc = precond(d_, R, ones_, lam_, st, msg);
+    if (rc) return rc;
+    ENG_CK(cudaMemcpyAsync(h_active_, kk_, R * sizeof(int), cudaMemcpyDeviceToHost, st));
+    ENG_CK(cudaMemcpyAsync(h_active_ + kMaxRdev, active_, R * sizeof(int), cudaMemcpyDeviceToHost, st));
+    ENG_CK(cudaStreamSynchronize(st));
+    double hres[kMaxRdev], hb0[kMaxRdev];
+    ENG_CK(cudaMemcpy(hres, resid_, R * sizeof(double), cudaMemcpyDeviceToHost));
+    ENG_CK(cudaMemcpy(hb0, beta0_, R * sizeof(double), cudaMemcpyDeviceToHost));
+    int it = 0, ok = 1;
+    for (int r = 0; r < R; ++r) {
+      it = std::max(it, h_active_[r]);
+      if (hb0[r] > 0 && hres[r] > tol * hb0[r]) ok = 0;
+    }
+    *iters = it;
+    *conv = ok;
+    return SCHUR_OK;
+  }
+
+  const HostMaps* hm_;
+  const DevMaps* dm_;
+  Geom g_;
+  double gamma_;
+  MapsView mv_;
+  Stencil<T> st_;
+  StencilProv<T> prr_, pii_;
+  StoredProv<double> cprov_;
+  int ncls_ = 0, nsm_ = 152, nblk_ = 1;
+  long long op_bytes_ = 0;
+  std::vector<void*> allocs_, ws_;
+  int* err_ = nullptr;
+  int* ones_ = nullptr;
+  cx<T>*Dinv_ = nullptr, *F_ = nullptr, *Frc_ = nullptr, *Sd_ = nullptr, *Kinv_ = nullptr;
+  cx<double>*Kcc_ = nullptr, *CA_ = nullptr, *CB_ = nullptr, *Dc_ = nullptr;
+  int wsR_ = 0, wsM_ = 0;
+  cx<T>*Xs_ = nullptr, *VD_ = nullptr, *Y_ = nullptr, *Tc_ = nullptr, *d_ = nullptr, *zv_ = nullptr, *lam_ = nullptr,
+  *V_ = nullptr, *ftc_ = nullptr, *gc_ = nullptr, *wc_ = nullptr, *uc_ = nullptr;
+  cx<double>*part_ = nullptr, *H_ = nullptr, *hc_ = nullptr, *gvec_ = nullptr, *cs_s_ = nullptr, *y_ = nullptr;
+  double *cs_c_ = nullptr, *nrm_part_ = nullptr, *beta0_ = nullptr, *inv_nrm_ = nullptr, *resid_ = nullptr;
+  int *active_ = nullptr, *kk_ = nullptr, *bad_ = nullptr;
+  int* h_active_ = nullptr;
+};
+
+}  // namespace schur

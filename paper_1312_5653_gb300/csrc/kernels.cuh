@@ -1,0 +1,665 @@
+// FETI-DP kernels for the complex-symmetric factor A = K + i gamma M (Sec. 5 of arXiv 1312.5653),
+// templated on the working precision T (double or float).  Notation follows Sec. 5: subdomain
+// remainder set r (interior and interface nodes minus corners and Dirichlet nodes), corner set c,
+// interface slots Delta, jump operator B, multipliers lambda.
+//   local dual operator     F^s   = (A_rr^{-1})_{Delta,Delta}
+//   corner coupling         Frc^s = (A_rr^{-1} A_rc)_{Delta,c}
+//   corner Schur complement Kcc^s = A_cc - A_cr A_rr^{-1} A_rc
+//   Dirichlet operator      S^s   = A_DD - A_Di A_ii^{-1} A_iD          (Eq. WS, b = Delta)
+// The dual problem (F_rr + Frc~ Kcc~^{-1} Frc~^T) lambda = d_r - Frc~ Kcc~^{-1} f~_c is solved by
+// right-preconditioned GMRES (Sec. 5: GMRES handles the indefinite complex factors) with the
+// Dirichlet preconditioner P^{-1} = sum_s B_D^s S^s B_D^s^T, B_D = B / multiplicity (Eq.
+// dirichletpreconditioner with W = (sum B B^T)^+).
+#pragma once
+#include "layered.cuh"
+
+namespace schur {
+
+struct MapsView {
+  const int* slot_node;
+  const int* node_slot;
+  const int* corner_node;
+  const int* sd_cls;
+  const int* cls_code;
+  const int* sd_lam;
+  const int* lam_side;
+  const int* sd_corner;
+  const double* sd_minv;
+};
+
+__device__ __forceinline__ void local_ext(const Geom& g, int* ext) {
+  ext[0] = g.s[0] + 1;
+  ext[1] = g.s[1] + 1;
+  ext[2] = g.dim == 3 ? g.s[2] + 1 : 1;
+}
+
+// global interior index of global node coordinates G (1..nel-1 per axis)
+__device__ __forceinline__ long long gidx(const Geom& g, const int* G) {
+  long long i = G[0] - 1;
+  long long st = g.nel[0] - 1;
+  i += st * (G[1] - 1);
+  if (g.dim == 3) i += st * (long long)(g.nel[1] - 1) * (G[2] - 1);
+  return i;
+}
+
+template <class T>
+__device__ __forceinline__ cx<T> czero() { return mkc<T>(T(0), T(0)); }
+
+// ================================================================================= setup
+// F, Frc, Kcc of each class: solve A_rr X = [E_Delta, A_rc] column chunk by chunk.
+template <class T>
+__global__ void k_form_rr(StencilProv<T> P, Geom g, MapsView m, const cx<T>* __restrict__ Dinv, int ncls, int C,
+                          cx<T>* Xws, cx<T>* F, cx<T>* Frc, cx<double>* Kcc) {
+  extern __shared__ unsigned char smraw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smraw);
+  const int nD = g.nD, nc = g.nc, ncol = nD + nc, nchunk = (ncol + C - 1) / C;
+  const int b = P.ly.b, L = P.ly.L, dim = g.dim, tid = threadIdx.x, nthr = blockDim.x;
+  cx<T>* X = Xws + (size_t)blockIdx.x * g.nl * C;
+  int ext[3];
+  local_ext(g, ext);
+  for (int w = blockIdx.x; w < ncls * nchunk; w += gridDim.x) {
+    const int q = w / nchunk, col0 = (w % nchunk) * C;
+    P.select(q, m.cls_code);
+    const int code = P.code;
+    auto rhs = [&](int K, int i, int c) -> cx<T> {
+      int col = col0 + c;
+      if (col >= ncol) return czero<T>();
+      int l[3];
+      P.crd(K, i, l);
+      if (P.removed_l(l)) return czero<T>();
+      if (col < nD) return mkc<T>(m.slot_node[col] == K * b + i ? T(1) : T(0), T(0));
+      int lc[3];
+      idx2crd(m.corner_node[col - nD], ext, dim, lc);
+      if (local_dirichlet(code, lc, g.s, dim)) return czero<T>();
+      return q1_entry(P.st, g.s, l, lc);
+    };
+    layered_solve<T>(P, Dinv + (size_t)q * L * b * b, C, rhs, X, C, sm);
+    for (int e = tid; e < nD * C; e += nthr) {
+      int j = e / C, c = e - j * C, col = col0 + c;
+      if (col >= ncol) continue;
+      cx<T> v = X[(size_t)m.slot_node[j] * C + c];
+      if (col < nD) F[((size_t)q * nD + j) * nD + col] = v;
+      else Frc[((size_t)q * nD + j) * nc + (col - nD)] = v;
+    }
+    for (int e = tid; e < nc * C; e += nthr) {
+      int c1 = e / C, c = e - c1 * C, col = col0 + c;
+      if (col < nD || col >= ncol) continue;
+      int c2 = col - nD;
+      int l1[3], l2[3];
+      idx2crd(m.corner_node[c1], ext, dim, l1);
+      idx2crd(m.corner_node[c2], ext, dim, l2);
+      cx<T> v = czero<T>();
+      if (!local_dirichlet(code, l1, g.s, dim) && !local_dirichlet(code, l2, g.s, dim)) {
+        if (c1 == c2) v = q1_entry(P.st, g.s, l1, l1);
+        const int noff = dim == 2 ? 9 : 27;
+        for (int o = 0; o < noff; ++o) {
+          int lp[3] = {l1[0] + o % 3 - 1, l1[1] + (o / 3) % 3 - 1, dim == 3 ? l1[2] + o / 9 - 1 : 0};
+          bool in = true;
+          for (int a = 0; a < dim; ++a) in = in && lp[a] >= 0 && lp[a] <= g.s[a];
+          if (!in || (lp[0] == l1[0] && lp[1] == l1[1] && lp[2] == l1[2])) continue;
+          if (P.removed_l(lp)) continue;
+          cfms(v, q1_entry(P.st, g.s, l1, lp), X[(size_t)crd2idx(lp, ext, dim) * C + c]);
+        }
+      }
+      Kcc[((size_t)q * nc + c1) * nc + c2] = ccast<double>(v);
+    }
+    __syncthreads();
+  }
+}
+
+// S_base = A_DD - A_Di A_ii^{-1} A_iD for all slots (the interior problem is the same for
+// every subdomain); classes mask their Dirichlet slots afterwards.
+template <class T>
+__global__ void k_form_ii(StencilProv<T> P, Geom g, MapsView m, const cx<T>* __restrict__ Dinv, int C, cx<T>* Xws,
+                          cx<T>* Sbase) {
+  extern __shared__ unsigned char smraw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smraw);
+  const int nD = g.nD, nchunk = (nD + C - 1) / C, dim = g.dim, tid = threadIdx.x, nthr = blockDim.x;
+  cx<T>* X = Xws + (size_t)blockIdx.x * g.ni * C;
+  int ext[3], iext[3];
+  local_ext(g, ext);
+  for (int a = 0; a < 3; ++a) iext[a] = a < dim ? g.s[a] - 1 : 1;
+  for (int w = blockIdx.x; w < nchunk; w += gridDim.x) {
+    const int col0 = w * C;
+    auto rhs = [&](int K, int i, int c) -> cx<T> {
+      int col = col0 + c;
+      if (col >= nD) return czero<T>();
+      int l[3], ls[3];
+      P.crd(K, i, l);
+      idx2crd(m.slot_node[col], ext, dim, ls);
+      return q1_entry(P.st, g.s, l, ls);
+    };
+    layered_solve<T>(P, Dinv, C, rhs, X, C, sm);
+    for (int e = tid; e < nD * C; e += nthr) {
+      int j = e / C, c = e - j * C, col = col0 + c;
+      if (col >= nD) continue;
+      int lj[3], lc[3];
+      idx2crd(m.slot_node[j], ext, dim, lj);
+      idx2crd(m.slot_node[col], ext, dim, lc);
+      cx<T> v = q1_entry(P.st, g.s, lj, lc);
+      const int noff = dim == 2 ? 9 : 27;
+      for (int o = 0; o < noff; ++o) {
+        int lp[3] = {lj[0] + o % 3 - 1, lj[1] + (o / 3) % 3 - 1, dim == 3 ? lj[2] + o / 9 - 1 : 0};
+        bool interior = true;
+        for (int a = 0; a < dim; ++a) interior = interior && lp[a] >= 1 && lp[a] <= g.s[a] - 1;
+        if (!interior) continue;
+        int li[3] = {lp[0] - 1, lp[1] - 1, dim == 3 ? lp[2] - 1 : 0};
+        cfms(v, q1_entry(P.st, g.s, lj, lp), X[(size_t)crd2idx(li, iext, dim) * C + c]);
+      }
+      Sbase[(size_t)j * nD + col] = v;
+    }
+    __syncthreads();
+  }
+}
+
+template <class T>
+__global__ void k_mask_S(Geom g, MapsView m, int ncls, const cx<T>* __restrict__ Sbase, cx<T>* Sd) {
+  const long long tot = (long long)ncls * g.nD * g.nD;
+  int ext[3];
+  local_ext(g, ext);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    int q = (int)(e / ((long long)g.nD * g.nD));
+    int r = (int)(e % ((long long)g.nD * g.nD));
+    int j = r / g.nD, k = r % g.nD;
+    int lj[3], lk[3];
+    idx2crd(m.slot_node[j], ext, g.dim, lj);
+    idx2crd(m.slot_node[k], ext, g.dim, lk);
+    int code = m.cls_code[q];
+    bool act = !local_dirichlet(code, lj, g.s, g.dim) && !local_dirichlet(code, lk, g.s, g.dim);
+    Sd[e] = act ? Sbase[r] : czero<T>();
+  }
+}
+
+// Coarse matrix Kcc~ = sum_s B_c^s^T Kcc^s B_c^s in layered storage (CA: in-layer couplings,
+// CB: couplings to the previous layer).  One thread per (coarse node, 3^d offset); each entry
+// sums the subdomains that hold both corners in a fixed order.
+static __global__ void k_coarse_assemble(Geom g, const cx<double>* __restrict__ Kcc, const int* __restrict__ sd_cls,
+                                  cx<double>* CA, cx<double>* CB) {
+  const int dim = g.dim, noff = dim == 2 ? 9 : 27, nt = nbr_count(dim);
+  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)g.ncor * noff) return;
+  int g1 = (int)(e / noff), o = (int)(e % noff);
+  int C1[3], C2[3], d[3] = {o % 3 - 1, (o / 3) % 3 - 1, dim == 3 ? o / 9 - 1 : 0};
+  idx2crd(g1, g.ncg, dim, C1);
+  for (int a = 0; a < 3; ++a) C2[a] = C1[a] + (a < dim ? d[a] : 0);
+  for (int a = 0; a < dim; ++a)
+    if (C2[a] < 0 || C2[a] >= g.ncg[a]) return;
+  if (d[dim - 1] > 0) return;
+  // candidate subdomains per axis: {C1, C1+1} intersect {C2, C2+1}
+  int lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) {
+    if (a < dim) {
+      lo[a] = max(C1[a], C2[a]);
+      hi[a] = min(C1[a], C2[a]) + 1;
+    } else {
+      lo[a] = hi[a] = 0;
+    }
+  }
+  cx<double> sum = mkc<double>(0, 0);
+  for (int s2 = lo[2]; s2 <= hi[2]; ++s2)
+    for (int s1 = lo[1]; s1 <= hi[1]; ++s1)
+      for (int s0 = lo[0]; s0 <= hi[0]; ++s0) {
+        int S[3] = {s0, s1, s2};
+        int sd = crd2idx(S, g.nsub, dim);
+        int c1 = 0, c2 = 0;
+        for (int a = 0; a < dim; ++a) {
+          c1 |= (C1[a] == S[a]) << a;
+          c2 |= (C2[a] == S[a]) << a;
+        }
+        sum = cadd(sum, Kcc[((size_t)sd_cls[sd] * g.nc + c1) * g.nc + c2]);
+      }
+  int K1 = C1[dim - 1];
+  int i1 = dim == 2 ? C1[0] : C1[0] + g.ncg[0] * C1[1];
+  int t = dim == 2 ? d[0] + 1 : (d[0] + 1) + 3 * (d[1] + 1);
+  if (d[dim - 1] == 0) CA[((size_t)K1 * g.cb + i1) * nt + t] = sum;
+  else CB[((size_t)(K1 - 1) * g.cb + i1) * nt + t] = sum;
+}
+
+// Columns of the coarse inverse from the FP64 layered factor; stored in the working precision.
+template <class T>
+__global__ void k_coarse_inverse(StoredProv<double> P, const cx<double>* __restrict__ Dinv, int ncor, int C,
+                                 cx<double>* Xws, cx<T>* Kinv) {
+  extern __shared__ unsigned char smraw[];
+  cx<double>* sm = reinterpret_cast<cx<double>*>(smraw);
+  const int nchunk = (ncor + C - 1) / C, b = P.ly.b;
+  cx<double>* X = Xws + (size_t)blockIdx.x * ncor * C;
+  for (int w = blockIdx.x; w < nchunk; w += gridDim.x) {
+    const int col0 = w * C;
+    auto rhs = [&](int K, int i, int c) -> cx<double> {
+      int col = col0 + c;
+      return mkc<double>((col < ncor && K * b + i == col) ? 1.0 : 0.0, 0.0);
+    };
+    layered_solve<double>(P, Dinv, C, rhs, X, C, sm);
+    for (int e = threadIdx.x; e < ncor * C; e += blockDim.x) {
+      int row = e / C, c = e - row * C, col = col0 + c;
+      if (col < ncor) Kinv[(size_t)col * ncor + row] = ccast<T>(X[e]);
+    }
+    __syncthreads();
+  }
+}
+
+// ================================================================================= solve
+// Local right-hand sides f_r^s (interface entries scaled by 1/multiplicity, corners and
+// Dirichlet nodes removed), v = A_rr^{-1} f_r, and its restrictions: VD = v on the slots (for
+// d_r = sum_s B^s v^s) and Tc = A_cr v (for f~_c = f_c - sum_s B_c^T A_cr A_rr^{-1} f_r).
+template <class T>
+__global__ void k_local_rhs(StencilProv<T> P, Geom g, MapsView m, const cx<T>* __restrict__ Dinv,
+                            const cx<double>* __restrict__ f, int ldf, int R, cx<T>* Xs, cx<T>* VD, cx<T>* Tc) {
+  extern __shared__ unsigned char smraw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smraw);
+  const int sd = blockIdx.x, dim = g.dim, tid = threadIdx.x, nthr = blockDim.x;
+  const int q = m.sd_cls[sd], b = P.ly.b, L = P.ly.L, nD = g.nD, nc = g.nc;
+  P.select(q, m.cls_code);
+  int S[3], ext[3];
+  idx2crd(sd, g.nsub, dim, S);
+  local_ext(g, ext);
+  cx<T>* X = Xs + (size_t)sd * g.nl * R;
+  auto rhs = [&](int K, int i, int c) -> cx<T> {
+    int l[3];
+    P.crd(K, i, l);
+    if (P.removed_l(l)) return czero<T>();
+    int G[3] = {S[0] * g.s[0] + l[0], S[1] * g.s[1] + l[1], dim == 3 ? S[2] * g.s[2] + l[2] : 1};
+    cx<double> v = f[(size_t)c * ldf + gidx(g, G)];
+    int slot = m.node_slot[K * b + i];
+    double sc = slot >= 0 ? m.sd_minv[(size_t)sd * nD + slot] : 1.0;
+    return mkc<T>((T)(v.re * sc), (T)(v.im * sc));
+  };
+  layered_solve<T>(P, Dinv + (size_t)q * L * b * b, R, rhs, X, R, sm);
+  for (int e = tid; e < R * nD; e += nthr) {
+    int c = e / nD, j = e - c * nD;
+    VD[((size_t)sd * R + c) * nD + j] = X[(size_t)m.slot_node[j] * R + c];
+  }
+  for (int e = tid; e < R * nc; e += nthr) {
+    int c = e / nc, cc = e - c * nc;
+    int lc[3];
+    idx2crd(m.corner_node[cc], ext, dim, lc);
+    cx<T> v = czero<T>();
+    if (!local_dirichlet(P.code, lc, g.s, dim)) {
+      const int noff = dim == 2 ? 9 : 27;
+      for (int o = 0; o < noff; ++o) {
+        int lp[3] = {lc[0] + o % 3 - 1, lc[1] + (o / 3) % 3 - 1, dim == 3 ? lc[2] + o / 9 - 1 : 0};
+        bool in = true;
+        for (int a = 0; a < dim; ++a) in = in && lp[a] >= 0 && lp[a] <= g.s[a];
+        if (!in || P.removed_l(lp)) continue;
+        cfma(v, q1_entry(P.st, g.s, lc, lp), X[(size_t)crd2idx(lp, ext, dim) * R + c]);
+      }
+    }
+    Tc[((size_t)sd * R + c) * nc + cc] = v;
+  }
+}
+
+// g[r][C] = (add ? add[r][C] : 0) + sign * sum over subdomains holding corner C of Tc; with
+// f != null also adds f at the corner node (f~_c = f_c - sum A_cr A_rr^{-1} f_r uses sign -1).
+template <class T>
+__global__ void k_corner_gather(Geom g, const cx<T>* __restrict__ Tc, int R, const cx<double>* __restrict__ f, int ldf,
+                                const cx<T>* __restrict__ add, T sign, cx<T>* out) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= R * g.ncor) return;
+  int r = e / g.ncor, cI = e - r * g.ncor, dim = g.dim;
+  int C[3];
+  idx2crd(cI, g.ncg, dim, C);
+  cx<T> sum = czero<T>();
+  const int nb = 1 << dim;
+  for (int bits = 0; bits < nb; ++bits) {
+    // subdomain holding the corner as its vertex `bits` (bit a set: high vertex, S_a = C_a)
+    int S[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) S[a] = C[a] + 1 - ((bits >> a) & 1);
+    int sd = crd2idx(S, g.nsub, dim);
+    sum = cadd(sum, Tc[((size_t)sd * R + r) * g.nc + bits]);
+  }
+  cx<T> v = cscale(sum, sign);
+  if (add) v = cadd(v, add[(size_t)r * g.ncor + cI]);
+  if (f) {
+    int G[3] = {(C[0] + 1) * g.s[0], (C[1] + 1) * g.s[1], dim == 3 ? (C[2] + 1) * g.s[2] : 1};
+    cx<double> fv = f[(size_t)r * ldf + gidx(g, G)];
+    v = cadd(v, mkc<T>((T)fv.re, (T)fv.im));
+  }
+  out[(size_t)r * g.ncor + cI] = v;
+}
+
+// w = Kinv gvec for R columns: one warp per coarse row.
+template <class T, int MR>
+__global__ void k_coarse_apply(const cx<T>* __restrict__ Kinv, int ncor, const cx<T>* __restrict__ gv, int R,
+                               const int* __restrict__ active, cx<T>* w) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (row >= ncor) return;
+  cx<T> acc[MR];
+  for (int r = 0; r < MR; ++r) acc[r] = czero<T>();
+  const cx<T>* Krow = Kinv + (size_t)row * ncor;
+  for (int j = lane; j < ncor; j += 32) {
+    cx<T> a = Krow[j];
+#pragma unroll
+    for (int r = 0; r < MR; ++r)
+      if (r < R) cfma(acc[r], a, gv[(size_t)r * ncor + j]);
+  }
+#pragma unroll
+  for (int r = 0; r < MR; ++r) {
+    if (r >= R) break;
+    T re = acc[r].re, im = acc[r].im;
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0 && (!active || active[r])) w[(size_t)r * ncor + row] = mkc<T>(re, im);
+  }
+}
+
+// Frc^s w_s on slot j of subdomain sd (w: coarse vector of one right-hand side).
+template <class T>
+__device__ __forceinline__ cx<T> frc_corr(const Geom& g, const MapsView& m, const cx<T>* __restrict__ Frc,
+                                          const cx<T>* __restrict__ w, int sd, int j) {
+  cx<T> acc = czero<T>();
+  if (!w) return acc;
+  const int q = m.sd_cls[sd];
+  for (int c = 0; c < g.nc; ++c) {
+    int ci = m.sd_corner[(size_t)sd * g.nc + c];
+    if (ci >= 0) cfma(acc, Frc[((size_t)q * g.nD + j) * g.nc + c], w[ci]);
+  }
+  return acc;
+}
+
+// d = d_r - Frc~ Kcc~^{-1} f~_c:  d_lambda = sum over its two sides sigma (VD - Frc w0).
+template <class T>
+__global__ void k_dual_rhs(Geom g, MapsView m, const cx<T>* __restrict__ VD, const cx<T>* __restrict__ Frc,
+                           const cx<T>* __restrict__ w0, int R, cx<T>* d) {
+  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)R * g.nlam) return;
+  int r = (int)(e / g.nlam), lam = (int)(e % g.nlam);
+  cx<T> v = czero<T>();
+  for (int side = 0; side < 2; ++side) {
+    int code = m.lam_side[2 * lam + side];
+    int sd = code / g.nD, j = code - sd * g.nD;
+    cx<T> t = csub(VD[((size_t)sd * R + r) * g.nD + j], frc_corr(g, m, Frc, w0 ? w0 + (size_t)r * g.ncor : nullptr, sd, j));
+    v = side == 0 ? cadd(v, t) : csub(v, t);
+  }
+  d[(size_t)r * g.nlam + lam] = v;
+}
+
+// Local dense apply per subdomain with the gather of B^T lambda fused in front:
+//   x_j = scale_j * sum_k sign_k lam[idx_k]        (scale = 1/multiplicity for the preconditioner)
+//   Y   = Op[cls] x                                 (Op = F or S, nD x nD, symmetric)
+//   Tc  = Frc[cls]^T x                              (only when Tc != null)
+template <class T, bool SCALE, int MR>
+__global__ void k_local_apply(Geom g, MapsView m, const cx<T>* __restrict__ Op, const cx<T>* __restrict__ Frc,
+                              const cx<T>* __restrict__ lam, int R, const int* __restrict__ active, cx<T>* Y,
+                              cx<T>* Tc) {
+  extern __shared__ unsigned char smraw[];
+  cx<T>* x = reinterpret_cast<cx<T>*>(smraw);
+  const int sd = blockIdx.x, nD = g.nD, tid = threadIdx.x, nthr = blockDim.x, md = g.maxdeg;
+  const int q = m.sd_cls[sd];
+  for (int e = tid; e < R * nD; e += nthr) {
+    int r = e / nD, j = e - r * nD;
+    cx<T> v = czero<T>();
+    if (active[r]) {
+      const int* refs = m.sd_lam + ((size_t)sd * nD + j) * md;
+      for (int k = 0; k < md; ++k) {
+        int ref = refs[k];
+        if (ref > 0) v = cadd(v, lam[(size_t)r * g.nlam + ref - 1]);
+        else if (ref < 0) v = csub(v, lam[(size_t)r * g.nlam - ref - 1]);
+      }
+      if (SCALE) v = cscale(v, (T)m.sd_minv[(size_t)sd * nD + j]);
+    }
+    x[e] = v;
+  }
+  __syncthreads();
+  const cx<T>* A = Op + (size_t)q * nD * nD;
+  for (int j = tid; j < nD; j += nthr) {
+    cx<T> acc[MR];
+    for (int r = 0; r < MR; ++r) acc[r] = czero<T>();
+#pragma unroll 4
+    for (int k = 0; k < nD; ++k) {
+      cx<T> a = A[(size_t)k * nD + j];
+#pragma unroll
+      for (int r = 0; r < MR; ++r)
+        if (r < R) cfma(acc[r], a, x[r * nD + k]);
+    }
+#pragma unroll
+    for (int r = 0; r < MR; ++r)
+      if (r < R) Y[((size_t)sd * R + r) * nD + j] = acc[r];
+  }
+  if (Tc) {
+    for (int e = tid; e < R * g.nc; e += nthr) {
+      int r = e / g.nc, c = e - r * g.nc;
+      cx<T> acc = czero<T>();
+      const cx<T>* Fr = Frc + (size_t)q * nD * g.nc + c;
+      for (int j = 0; j < nD; ++j) cfma(acc, Fr[(size_t)j * g.nc], x[r * nD + j]);
+      Tc[((size_t)sd * R + r) * g.nc + c] = acc;
+    }
+  }
+}
+
+// out_lambda = sum over sides sigma * scale * (Y + Frc wc):  B (Y + Frc wc) for the dual operator,
+// B_D Y for the preconditioner (SCALE, wc = null).
+template <class T, bool SCALE>
+__global__ void k_scatter(Geom g, MapsView m, const cx<T>* __restrict__ Y, const cx<T>* __restrict__ Frc,
+                          const cx<T>* __restrict__ wc, int R, const int* __restrict__ active, cx<T>* out) {
+  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)R * g.nlam) return;
+  int r = (int)(e / g.nlam), lam = (int)(e % g.nlam);
+  if (!active[r]) return;
+  cx<T> v = czero<T>();
+  for (int side = 0; side < 2; ++side) {
+    int code = m.lam_side[2 * lam + side];
+    int sd = code / g.nD, j = code - sd * g.nD;
+    cx<T> t = Y[((size_t)sd * R + r) * g.nD + j];
+    if (wc) t = cadd(t, frc_corr(g, m, Frc, wc + (size_t)r * g.ncor, sd, j));
+    if (SCALE) t = cscale(t, (T)m.sd_minv[(size_t)sd * g.nD + j]);
+    v = side == 0 ? cadd(v, t) : csub(v, t);
+  }
+  out[(size_t)r * g.nlam + lam] = v;
+}
+
+// ------------------------------------------------------------------------------- GMRES
+// Block partial dot products h_j = <V_j, w> (conjugate-linear in V_j) for j = 0..k of right-hand
+// side r = blockIdx.y; the block's segment of w is staged in shared memory, one warp per j.
+// Products in the working precision, accumulation in FP64.
+template <class T>
+__global__ void k_dots(const cx<T>* __restrict__ V, long long vstride, int nlam, int R, int k,
+                       const cx<T>* __restrict__ w, const int* __restrict__ active, int nblk, cx<double>* part) {
+  extern __shared__ unsigned char smraw[];
+  cx<T>* ws = reinterpret_cast<cx<T>*>(smraw);
+  const int r = blockIdx.y;
+  if (!active[r]) return;
+  const int seg = (nlam + nblk - 1) / nblk, lo = blockIdx.x * seg, hi = min(nlam, lo + seg);
+  const int n = max(0, hi - lo);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) ws[i] = w[(size_t)r * nlam + lo + i];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = warp; j <= k; j += nw) {
+    const cx<T>* vj = V + j * vstride + (size_t)r * nlam + lo;
+    double re = 0, im = 0;
+    for (int i = lane; i < n; i += 32) {
+      cx<T> a = vj[i], b = ws[i];
+      re += (double)(a.re * b.re + a.im * b.im);
+      im += (double)(a.re * b.im - a.im * b.re);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) part[((size_t)r * kMaxKdev + j) * nblk + blockIdx.x] = mkc<double>(re, im);
+  }
+}
+
+// h_j = sum of the block partials (fixed order); H[r][j][k] += h_j; hc[r][j] = h_j.
+__global__ void k_dots_reduce(const cx<double>* __restrict__ part, int nblk, int R, int k, int m,
+                              const int* __restrict__ active, cx<double>* H, cx<double>* hc);
+
+template <class T>
+__global__ void k_update(cx<T>* V, long long vstride, int nlam, int R, int k, const cx<double>* __restrict__ hc,
+                         const int* __restrict__ active, cx<T>* w) {
+  extern __shared__ unsigned char smraw[];
+  cx<T>* h = reinterpret_cast<cx<T>*>(smraw);
+  const int r = blockIdx.y;
+  if (!active[r]) return;
+  for (int j = threadIdx.x; j <= k; j += blockDim.x) h[j] = ccast<T>(hc[(size_t)r * kMaxKdev + j]);
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nlam; i += (long long)gridDim.x * blockDim.x) {
+    cx<T> acc = w[(size_t)r * nlam + i];
+    for (int j = 0; j <= k; ++j) cfms(acc, h[j], V[j * vstride + (size_t)r * nlam + i]);
+    w[(size_t)r * nlam + i] = acc;
+  }
+}
+
+// Block partial sums of |w|^2 (FP64 accumulation) per right-hand side.
+template <class T>
+__global__ void k_norm2(const cx<T>* __restrict__ w, int nlam, int R, const int* __restrict__ active, int nblk,
+                        double* part) {
+  __shared__ double red[32];
+  const int r = blockIdx.y;
+  if (active && !active[r]) return;
+  double s = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nlam; i += (long long)nblk * blockDim.x) {
+    cx<T> a = w[(size_t)r * nlam + i];
+    s += (double)a.re * (double)a.re + (double)a.im * (double)a.im;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) part[(size_t)r * nblk + blockIdx.x] = s;
+  }
+}
+
+template <class T>
+__global__ void k_scale_vec(cx<T>* w, int nlam, int R, const int* __restrict__ active, const double* __restrict__ sc) {
+  const int r = blockIdx.y;
+  if (!active[r]) return;
+  T s = (T)sc[r];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nlam; i += (long long)gridDim.x * blockDim.x)
+    w[(size_t)r * nlam + i] = cscale(w[(size_t)r * nlam + i], s);
+}
+
+// u = sum_{j < kk[r]} y_j V_j
+template <class T>
+__global__ void k_combine(const cx<T>* __restrict__ V, long long vstride, int nlam, int R,
+                          const cx<double>* __restrict__ y, const int* __restrict__ kk, cx<T>* u) {
+  extern __shared__ unsigned char smraw[];
+  cx<T>* ys = reinterpret_cast<cx<T>*>(smraw);
+  const int r = blockIdx.y, nk = kk[r];
+  for (int j = threadIdx.x; j < nk; j += blockDim.x) ys[j] = ccast<T>(y[(size_t)r * kMaxKdev + j]);
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nlam; i += (long long)gridDim.x * blockDim.x) {
+    cx<T> acc = czero<T>();
+    for (int j = 0; j < nk; ++j) cfma(acc, ys[j], V[j * vstride + (size_t)r * nlam + i]);
+    u[(size_t)r * nlam + i] = acc;
+  }
+}
+
+// ------------------------------------------------------------------------------- recovery
+// u_r^s = A_rr^{-1} (f_r - B_r^T lambda - A_rc u_c)
+template <class T>
+__global__ void k_recover(StencilProv<T> P, Geom g, MapsView m, const cx<T>* __restrict__ Dinv,
+                          const cx<double>* __restrict__ f, int ldf, const cx<T>* __restrict__ lam,
+                          const cx<T>* __restrict__ uc, int R, cx<T>* Xs) {
+  extern __shared__ unsigned char smraw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smraw);
+  const int sd = blockIdx.x, dim = g.dim;
+  const int q = m.sd_cls[sd], b = P.ly.b, L = P.ly.L, nD = g.nD, md = g.maxdeg;
+  P.select(q, m.cls_code);
+  int S[3], ext[3];
+  idx2crd(sd, g.nsub, dim, S);
+  local_ext(g, ext);
+  cx<T>* X = Xs + (size_t)sd * g.nl * R;
+  auto rhs = [&](int K, int i, int c) -> cx<T> {
+    int l[3];
+    P.crd(K, i, l);
+    if (P.removed_l(l)) return czero<T>();
+    int G[3] = {S[0] * g.s[0] + l[0], S[1] * g.s[1] + l[1], dim == 3 ? S[2] * g.s[2] + l[2] : 1};
+    cx<double> fv = f[(size_t)c * ldf + gidx(g, G)];
+    int slot = m.node_slot[K * b + i];
+    double sc = 1.0;
+    cx<T> v;
+    if (slot >= 0) {
+      sc = m.sd_minv[(size_t)sd * nD + slot];
+      v = mkc<T>((T)(fv.re * sc), (T)(fv.im * sc));
+      if (lam) {
+        const int* refs = m.sd_lam + ((size_t)sd * nD + slot) * md;
+        for (int k = 0; k < md; ++k) {
+          int ref = refs[k];
+          if (ref > 0) v = csub(v, lam[(size_t)c * g.nlam + ref - 1]);
+          else if (ref < 0) v = cadd(v, lam[(size_t)c * g.nlam - ref - 1]);
+        }
+      }
+    } else {
+      v = mkc<T>((T)fv.re, (T)fv.im);
+    }
+    if (uc) {
+      for (int cc = 0; cc < g.nc; ++cc) {
+        int ci = m.sd_corner[(size_t)sd * g.nc + cc];
+        if (ci < 0) continue;
+        int lc[3];
+        idx2crd(m.corner_node[cc], ext, dim, lc);
+        cfms(v, q1_entry(P.st, g.s, l, lc), uc[(size_t)c * g.ncor + ci]);
+      }
+    }
+    return v;
+  };
+  layered_solve<T>(P, Dinv + (size_t)q * L * b * b, R, rhs, X, R, sm);
+}
+
+// z[gi][r] += value of node gi: the coarse unknown at corners, else the mean of its subdomain
+// copies (equal at convergence).
+template <class T>
+__global__ void k_assemble_z(Geom g, const cx<T>* __restrict__ Xs, const cx<T>* __restrict__ uc, int R,
+                             cx<double>* z, int ldz) {
+  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)R * g.n) return;
+  const int dim = g.dim;
+  int r = (int)(e / g.n);
+  long long gi = e % g.n;
+  int G[3] = {0, 0, 0};
+  long long t = gi;
+  G[0] = (int)(t % (g.nel[0] - 1)) + 1;
+  t /= (g.nel[0] - 1);
+  if (dim == 2) {
+    G[1] = (int)t + 1;
+  } else {
+    G[1] = (int)(t % (g.nel[1] - 1)) + 1;
+    G[2] = (int)(t / (g.nel[1] - 1)) + 1;
+  }
+  int S0[3], L0[3], twin[3], nshared = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (a < dim) {
+      S0[a] = G[a] / g.s[a];
+      L0[a] = G[a] - S0[a] * g.s[a];
+      twin[a] = L0[a] == 0;
+      nshared += twin[a];
+    } else {
+      S0[a] = 0;
+      L0[a] = 0;
+      twin[a] = 0;
+    }
+  }
+  cx<double> val;
+  if (nshared == dim) {
+    int C[3] = {S0[0] - 1, S0[1] - 1, dim == 3 ? S0[2] - 1 : 0};
+    val = uc ? ccast<double>(uc[(size_t)r * g.ncor + crd2idx(C, g.ncg, dim)]) : mkc<double>(0, 0);
+  } else {
+    int ext[3] = {g.s[0] + 1, g.s[1] + 1, dim == 3 ? g.s[2] + 1 : 1};
+    cx<double> sum = mkc<double>(0, 0);
+    int cnt = 0;
+    for (int mask = 0; mask < (1 << dim); ++mask) {
+      bool ok = true;
+      int S[3], l[3];
+      for (int a = 0; a < 3; ++a) {
+        int bit = a < dim ? (mask >> a) & 1 : 0;
+        if (bit && !twin[a]) ok = false;
+        S[a] = S0[a] - bit;
+        l[a] = bit ? g.s[a] : L0[a];
+      }
+      if (!ok) continue;
+      int sd = crd2idx(S, g.nsub, dim);
+      sum = cadd(sum, ccast<double>(Xs[((size_t)sd * g.nl + crd2idx(l, ext, dim)) * R + r]));
+      ++cnt;
+    }
+    val = cscale(sum, 1.0 / cnt);
+  }
+  cx<double>& zz = z[(size_t)r * ldz + gi];
+  zz = cadd(zz, val);
+}
+
+}  // namespace schur

@@ -1,0 +1,269 @@
+// Block LDL^T of complex-symmetric matrices on box grids, layered along the last axis.
+//
+// A box problem with ext[a] nodes per axis, numbered lexicographically (axis 0 fastest), has a
+// block-tridiagonal matrix when grouped by layers of the last axis: b = prod_{a<dim-1} ext[a]
+// nodes per layer, L = ext[dim-1] layers, and every node couples only to in-layer offsets in
+// {-1,0,1}^(dim-1) of its own and the two adjacent layers (Q1 stencil).  The block LDL^T
+//   D_0 = A_00,  D_{K+1} = A_{K+1,K+1} - A_{K+1,K} D_K^{-1} A_{K,K+1}
+// is computed with explicit, symmetrised D_K^{-1} (Gauss-Jordan without pivoting).  For the
+// subdomain matrices A_rr = K_rr + i gamma M_rr the real and imaginary parts are positive
+// definite, a class closed under Schur complements, so every D_K has positive definite real and
+// imaginary parts and no pivot vanishes.  The solve needs only D_K^{-1} and the sparse A blocks:
+//   forward   E_K = D_K^{-1} (b_K - A_{K,K-1} E_{K-1})
+//   backward  X_K = E_K - D_K^{-1} A_{K,K+1} X_{K+1}
+// (the unit lower factor is A_{K+1,K} D_K^{-1}; its products are re-associated above).
+#pragma once
+#include "common.cuh"
+
+namespace schur {
+
+struct Layer {
+  int dim;
+  int ext[3];
+  int b, L;
+};
+
+__host__ __device__ __forceinline__ int nbr_count(int dim) { return dim == 2 ? 3 : 9; }
+
+// In-layer neighbour t of in-layer node i (offset digit a = (t / 3^a) % 3 - 1), or -1.
+__device__ __forceinline__ int nbr_of(const Layer& ly, int i, int t) {
+  int c0 = i % ly.ext[0];
+  int n0 = c0 + (t % 3) - 1;
+  if (n0 < 0 || n0 >= ly.ext[0]) return -1;
+  if (ly.dim == 2) return n0;
+  int c1 = i / ly.ext[0];
+  int n1 = c1 + (t / 3) - 1;
+  if (n1 < 0 || n1 >= ly.ext[1]) return -1;
+  return n0 + ly.ext[0] * n1;
+}
+// Slot t with nbr_of(i, t) == j, or -1 if j is not an in-layer neighbour of i.
+__device__ __forceinline__ int nbr_slot(const Layer& ly, int i, int j) {
+  int d0 = j % ly.ext[0] - i % ly.ext[0];
+  if (d0 < -1 || d0 > 1) return -1;
+  if (ly.dim == 2) return d0 + 1;
+  int d1 = j / ly.ext[0] - i / ly.ext[0];
+  if (d1 < -1 || d1 > 1) return -1;
+  return (d0 + 1) + 3 * (d1 + 1);
+}
+
+// Entries of a subdomain problem from the closed-form Q1 stencil.  Node (K, i) has subdomain-
+// local coordinates off + (in-layer coords, K).  masked: remainder problem, whose subdomain
+// vertices and Dirichlet nodes are replaced by identity rows and columns.
+template <class T>
+struct StencilProv {
+  Layer ly;
+  Stencil<T> st;
+  int s[3];
+  int off;
+  int masked;
+  int code;
+  __device__ __forceinline__ void select(int q, const int* codes) { code = masked ? codes[q] : 0; }
+  __device__ __forceinline__ void crd(int K, int i, int* l) const {
+    l[0] = i % ly.ext[0] + off;
+    if (ly.dim == 3) {
+      l[1] = i / ly.ext[0] + off;
+      l[2] = K + off;
+    } else {
+      l[1] = K + off;
+      l[2] = 0;
+    }
+  }
+  __device__ __forceinline__ bool removed_l(const int* l) const {
+    return masked && (local_vertex(l, s, ly.dim) || local_dirichlet(code, l, s, ly.dim));
+  }
+  __device__ __forceinline__ cx<T> entry(int K1, int i, int K2, int j) const {
+    int p[3], q[3];
+    crd(K1, i, p);
+    crd(K2, j, q);
+    if (removed_l(p) || removed_l(q)) return mkc<T>((K1 == K2 && i == j) ? T(1) : T(0), T(0));
+    return q1_entry(st, s, p, q);
+  }
+  __device__ __forceinline__ cx<T> Ad(int K, int i, int t) const {
+    int j = nbr_of(ly, i, t);
+    return j < 0 ? mkc<T>(0, 0) : entry(K, i, K, j);
+  }
+  // A(K+1, i ; K, nbr(i, t))
+  __device__ __forceinline__ cx<T> Al(int K, int i, int t) const {
+    int j = nbr_of(ly, i, t);
+    return j < 0 ? mkc<T>(0, 0) : entry(K + 1, i, K, j);
+  }
+};
+
+// Entries stored per (layer, node, neighbour slot): CA = diagonal blocks, CB = A_{K+1,K}.
+template <class T>
+struct StoredProv {
+  Layer ly;
+  const cx<T>* CA;
+  const cx<T>* CB;
+  __device__ __forceinline__ void select(int, const int*) {}
+  __device__ __forceinline__ cx<T> Ad(int K, int i, int t) const {
+    return CA[((size_t)K * ly.b + i) * nbr_count(ly.dim) + t];
+  }
+  __device__ __forceinline__ cx<T> Al(int K, int i, int t) const {
+    return CB[((size_t)K * ly.b + i) * nbr_count(ly.dim) + t];
+  }
+};
+
+template <class T>
+__device__ __forceinline__ bool finite_nonzero(cx<T> p) {
+  return isfinite(p.re) && isfinite(p.im) && (p.re != T(0) || p.im != T(0));
+}
+
+// In-place Gauss-Jordan inversion without pivoting of the b x b matrix A (whole block).
+// rc: 2b scratch entries.  Sets *err on a zero or non-finite pivot.
+template <class T>
+__device__ void gj_invert(cx<T>* A, int b, cx<T>* rc, int* err) {
+  const int nt = blockDim.x, tid = threadIdx.x, bb = b * b;
+  for (int k = 0; k < b; ++k) {
+    cx<T> p = A[k * b + k];
+    cx<T> piv = cinv(p);
+    if (tid == 0 && !finite_nonzero(p)) atomicExch(err, 1);
+    for (int j = tid; j < b; j += nt) {
+      rc[j] = cmul(A[k * b + j], piv);
+      rc[b + j] = A[j * b + k];
+    }
+    __syncthreads();
+    for (int e = tid; e < bb; e += nt) {
+      int i = e / b, j = e - i * b;
+      if (i == k) {
+        A[e] = (j == k) ? piv : rc[j];
+      } else if (j == k) {
+        cx<T> v = cmul(rc[b + i], piv);
+        A[e] = mkc<T>(-v.re, -v.im);
+      } else {
+        cfms(A[e], rc[b + i], rc[j]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Block LDL^T of one layered problem per block (blockIdx.x = problem).  Writes the L explicit
+// inverses D_K^{-1} (b x b, symmetric) to Dinv + q*L*b*b.  Workspace: 2 b^2 + 2 b entries in
+// shared memory when use_smem, else the (2 b^2 per block) global buffer gws (+2b in shared).
+template <class T, class Prov>
+__global__ void k_factor(Prov P, const int* codes, cx<T>* Dinv, cx<T>* gws, int use_smem, int* err) {
+  const int q = blockIdx.x;
+  P.select(q, codes);
+  const int b = P.ly.b, L = P.ly.L, bb = b * b, nt = nbr_count(P.ly.dim);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  extern __shared__ unsigned char smraw[];
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smraw);
+  cx<T>*Dt, *W, *rc;
+  if (use_smem) {
+    Dt = sm;
+    W = sm + bb;
+    rc = sm + 2 * bb;
+  } else {
+    Dt = gws + (size_t)q * 2 * bb;
+    W = Dt + bb;
+    rc = sm;
+  }
+  cx<T>* out = Dinv + (size_t)q * L * bb;
+  for (int e = tid; e < bb; e += nthr) Dt[e] = mkc<T>(0, 0);
+  __syncthreads();
+  for (int e = tid; e < b * nt; e += nthr) {
+    int i = e / nt, t = e - i * nt;
+    int j = nbr_of(P.ly, i, t);
+    if (j >= 0) Dt[i * b + j] = P.Ad(0, i, t);
+  }
+  __syncthreads();
+  for (int K = 0; K < L; ++K) {
+    gj_invert(Dt, b, rc, err);
+    for (int e = tid; e < bb; e += nthr) {
+      int i = e / b, j = e - i * b;
+      cx<T> v = cadd(Dt[i * b + j], Dt[j * b + i]);
+      W[e] = cscale(v, T(0.5));
+    }
+    __syncthreads();
+    for (int e = tid; e < bb; e += nthr) {
+      Dt[e] = W[e];
+      out[(size_t)K * bb + e] = W[e];
+    }
+    __syncthreads();
+    if (K + 1 == L) break;
+    // W = D_K^{-1} A_{K,K+1}:  W[k][j] = sum_t Dt[k][nbr(j,t)] A(K+1, j ; K, nbr(j,t))
+    for (int e = tid; e < bb; e += nthr) {
+      int k = e / b, j = e - k * b;
+      cx<T> acc = mkc<T>(0, 0);
+      for (int t = 0; t < nt; ++t) {
+        int m = nbr_of(P.ly, j, t);
+        if (m >= 0) cfma(acc, Dt[k * b + m], P.Al(K, j, t));
+      }
+      W[e] = acc;
+    }
+    __syncthreads();
+    // D_{K+1} = A_{K+1,K+1} - A_{K+1,K} W
+    for (int e = tid; e < bb; e += nthr) {
+      int i = e / b, j = e - i * b;
+      int tj = nbr_slot(P.ly, i, j);
+      cx<T> acc = tj >= 0 ? P.Ad(K + 1, i, tj) : mkc<T>(0, 0);
+      for (int t = 0; t < nt; ++t) {
+        int k = nbr_of(P.ly, i, t);
+        if (k >= 0) cfms(acc, P.Al(K, i, t), W[k * b + j]);
+      }
+      Dt[e] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// Multi-column solve with a layered factor, executed by one whole block.
+//   rhs(K, i, c)   right-hand side entry of node (K, i), column c (must be 0 on removed nodes)
+//   X              solution, X[(K*b + i) * ldx + c] (global memory, written here)
+//   sm             2 * b * C shared entries
+template <class T, class Prov, class RhsF>
+__device__ void layered_solve(const Prov& P, const cx<T>* __restrict__ Dinv, int C, RhsF rhs, cx<T>* X,
+                              int ldx, cx<T>* sm) {
+  const int b = P.ly.b, L = P.ly.L, bb = b * b, nt = nbr_count(P.ly.dim);
+  const int tid = threadIdx.x, nthr = blockDim.x, bc = b * C;
+  cx<T>* Tb = sm;
+  cx<T>* Ep = sm + bc;
+  for (int K = 0; K < L; ++K) {
+    for (int e = tid; e < bc; e += nthr) {
+      int i = e / C, c = e - i * C;
+      cx<T> t = rhs(K, i, c);
+      if (K > 0)
+        for (int tt = 0; tt < nt; ++tt) {
+          int k = nbr_of(P.ly, i, tt);
+          if (k >= 0) cfms(t, P.Al(K - 1, i, tt), Ep[k * C + c]);
+        }
+      Tb[e] = t;
+    }
+    __syncthreads();
+    const cx<T>* D = Dinv + (size_t)K * bb;
+    for (int e = tid; e < bc; e += nthr) {
+      int i = e / C, c = e - i * C;
+      cx<T> acc = mkc<T>(0, 0);
+      for (int m = 0; m < b; ++m) cfma(acc, D[m * b + i], Tb[m * C + c]);
+      Ep[e] = acc;
+      X[(size_t)(K * b + i) * ldx + c] = acc;
+    }
+    __syncthreads();
+  }
+  for (int K = L - 1; K >= 0; --K) {
+    for (int e = tid; e < bc; e += nthr) {
+      int i = e / C, c = e - i * C;
+      cx<T> u = mkc<T>(0, 0);
+      if (K < L - 1)
+        for (int tt = 0; tt < nt; ++tt) {
+          int k = nbr_of(P.ly, i, tt);
+          // A(K, i ; K+1, k) = A(K+1, k ; K, i) = Al(K, k, reverse slot)
+          if (k >= 0) cfma(u, P.Al(K, k, nt - 1 - tt), Ep[k * C + c]);
+        }
+      Tb[e] = u;
+    }
+    __syncthreads();
+    const cx<T>* D = Dinv + (size_t)K * bb;
+    for (int e = tid; e < bc; e += nthr) {
+      int i = e / C, c = e - i * C;
+      cx<T> x = X[(size_t)(K * b + i) * ldx + c];
+      for (int m = 0; m < b; ++m) cfms(x, D[m * b + i], Tb[m * C + c]);
+      X[(size_t)(K * b + i) * ldx + c] = x;
+      Ep[e] = x;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace schur
