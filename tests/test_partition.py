@@ -106,7 +106,11 @@ def test_setup_rejects_bad_arguments_before_touching_the_device():
     assert setup(2, 32, 0.0, nsub=4) == S.SCHUR_EINVAL         # beta must be positive
     assert setup(2, 32, float("nan"), nsub=4) == S.SCHUR_EINVAL
     assert setup(2, 32, 1e-4, nsub=32) == S.SCHUR_EINVAL       # one element per subdomain
-    assert setup(4, 32, 1e-4, nsub=4) == S.SCHUR_EINVAL        # dim
+    bad = S.make_mesh(3, 32)
+    bad.dim = 4
+    ctx = ctypes.c_void_p()
+    assert lib.schur_setup(ctypes.byref(bad), 1e-4, ctypes.byref(S.default_opts()), None,
+                           ctypes.byref(ctx)) == S.SCHUR_EINVAL
     assert setup(2, 32, 1e-4, nsub=4, precision=7) == S.SCHUR_EINVAL
     assert setup(2, 32, 1e-4, nsub=4, max_iter=0) == S.SCHUR_EINVAL
     assert setup(2, 32, 1e-4, nsub=4, max_iter=512) == S.SCHUR_EINVAL
