@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark of the factored Schur complement solve (arXiv 1312.5653, Sec. 3.1 + Sec. 4 + Sec. 5).
+
+Workload: 2D unit square, 1024 x 1024 Q1 elements (1,046,529 interior dofs), homogeneous
+Dirichlet boundary, 64 x 64 subdomains of 16 x 16 elements, beta cycling over
+{1e-2, 1e-4, 1e-6, 1e-8}, one right-hand side b = M y_bar per step with y_bar = seeded i.i.d.
+N(0,1) nodal values smoothed by 3 damped Jacobi sweeps (synthetic; the paper's targets are
+analytic, no dataset).
+
+One step = the whole path for one (beta, b): schur_setup (assembly, batched subdomain LDL^T,
+local operators, coarse factorisation) + schur_solve (FETI-DP GMRES with FP64 refinement and the
+-Im(z)/gamma shortcut) + schur_destroy.  Headline = mixed precision (complex FP32 FETI-DP, FP64
+refinement); the plain FP64 form and the cached-factor solve rate are reported beside it.
+L2 is flushed (256 MB write) between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_EL, N_SUB, BETAS = 1024, 64, (1e-2, 1e-4, 1e-6, 1e-8)
+WORKLOAD = "2d-q1-1024x1024-dirichlet-64x64sub-16x16el-smoothed-noise-beta-sweep"
+METRIC = "MDoF/s (S-solves at relerr<=1e-8, setup+solve per solve)"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=8)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+class Clocks:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [t.strip() for t in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_solve(b, beta):
+    import oracle
+    t0 = time.perf_counter()
+    x = oracle.fd_schur_solve(2, N_EL, beta, b)
+    return x, time.perf_counter() - t0
+
+
+def run_reference(args, rank, world):
+    """The oracle (FP64 fast diagonalisation, single-threaded C) on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1312_5653_gb300 import inputs
+    oracle.build()
+    yb = inputs.smoothed_noise(2, N_EL, seed=1)
+    b = oracle.apply_M(2, N_EL, yb)
+    n = b.size
+    for i in range(args.warmup):
+        cpu_oracle_solve(b, BETAS[i % 4])
+    ts = []
+    for i in range(args.steps):
+        ts.append(cpu_oracle_solve(b, BETAS[i % 4])[1])
+    t = float(np.sum(ts))
+    val = n * args.steps / t / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "MDoF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_dofs": n, "beta": list(BETAS), "nrhs_per_step": 1},
+            "cpu_baseline": {"value": val, "unit": "MDoF/s", "cores": 1, "kind": "oracle",
+                             "sample": "one full-size right-hand side per step, fast-diagonalisation oracle "
+                                       "(dense sine transforms), single thread"},
+            "e2e": {"value": val, "unit": "MDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+# algorithmic traffic / work per launch of each kernel category (documented in the design doc)
+def algorithmic(cat, info, prec_bytes):
+    nsd, nD, nc, nlam, nco = info["n_sub"], info["n_delta"], 4, info["n_lambda"], info["n_coarse"]
+    cb = 2 * prec_bytes  # complex entry
+    if cat == "apply_F":
+        byts = nsd * (nD * nD + nD * nc) * cb + nlam * cb + nsd * (nD + nc) * cb
+        return "hbm", byts
+    if cat == "apply_S":
+        byts = nsd * nD * nD * cb + nlam * cb + nsd * nD * cb
+        return "hbm", byts
+    if cat == "coarse_apply":
+        return "hbm", nco * nco * cb + 2 * nco * cb
+    if cat == "scatter":
+        return "hbm", nlam * cb + 2 * nlam * cb
+    return None, None
+
+
+def main():
+    args = parse()
+    rank, local_rank, world = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    import torch
+    from paper_1312_5653_gb300 import inputs
+    from paper_1312_5653_gb300 import schur as S
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream(dev)
+    lib = S.load()
+    n = S.schur_ndof(2, N_EL)
+    # each rank solves its own seeded right-hand side (independent problems: weak scaling)
+    yb = inputs.smoothed_noise(2, N_EL, seed=1 + rank)
+    ybd = torch.from_numpy(yb).to(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def make(beta, prec):
+        return S.Solver(2, N_EL, beta, nsub=N_SUB, precision=prec)
+
+    # b = M y_bar on the device (library mass apply)
+    s0 = make(BETAS[0], S.SCHUR_FP64)
+    b = s0.schur_apply_mass(ybd)
+    s0.close()
+    x = torch.empty_like(b)
+    torch.cuda.synchronize()
+
+    def step(i, prec):
+        sol = make(BETAS[i % 4], prec)
+        sol.schur_solve(b, x)
+        st = sol.last_stats
+        nl = lib.schur_launch_count(sol.ctx)
+        sol.close()
+        return st, nl
+
+    def timed(prec, steps, warmup, profile_mask=0):
+        for i in range(warmup):
+            step(i, prec)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        if profile_mask:
+            lib.schur_profile_begin(profile_mask)
+        times, stats, launches = [], [], 0
+        for i in range(steps):
+            flush_l2(flush)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, nl = step(i, prec)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            stats.append(st)
+            launches += nl
+        torch.cuda.synchronize()
+        prof = None
+        if profile_mask:
+            import ctypes
+            arr = (S_kernel_time * 16)()
+            cnt = ctypes.c_int(0)
+            lib.schur_profile_end(arr, 16, ctypes.byref(cnt))
+            prof = {lib.schur_kernel_category_name(arr[k].category).decode(): (arr[k].launches, arr[k].total_ms)
+                    for k in range(cnt.value)}
+        if world > 1:
+            torch.distributed.barrier()
+        total = float(np.sum(times))
+        if world > 1:
+            t = torch.tensor([total], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total = float(t.item())
+        return total, times, stats, launches, prof
+
+    import ctypes
+
+    class S_kernel_time(ctypes.Structure):
+        _fields_ = [("category", ctypes.c_int), ("launches", ctypes.c_longlong), ("total_ms", ctypes.c_double)]
+
+    lib.schur_profile_end.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    lib.schur_profile_begin.argtypes = [ctypes.c_uint]
+    lib.schur_kernel_category_name.restype = ctypes.c_char_p
+    lib.schur_launch_count.restype = ctypes.c_longlong
+    lib.schur_launch_count.argtypes = [ctypes.c_void_p]
+
+    # untimed profiling pass over one step per beta: find the dominant kernel category
+    _, _, _, _, prof_all = timed(S.SCHUR_MIXED, 4, 0, profile_mask=0xFFFF)
+    dom = max(prof_all.items(), key=lambda kv: kv[1][1])[0] if prof_all else None
+    names = ["factor", "form", "coarse_setup", "local_rhs", "apply_F", "apply_S", "scatter", "coarse_apply",
+             "corner", "gmres_dots", "gmres_update", "gmres_other", "recover", "assemble_z", "residual", "other"]
+    dom_mask = (1 << names.index(dom)) if dom in names else 0
+
+    # headline: mixed precision, timed region
+    with Clocks(local_rank) as clk:
+        total, times, stats, launches, prof = timed(S.SCHUR_MIXED, args.steps, args.warmup, profile_mask=dom_mask)
+    ms_step = total / args.steps
+    value = world * n * args.steps / (total / 1e3) / 1e6
+
+    # accuracy of the timed path vs the oracle on one step (rank 0)
+    relerr = None
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        bh = b.cpu().numpy()
+        xref, tcpu = cpu_oracle_solve(bh, BETAS[(args.steps - 1) % 4])
+        sol = make(BETAS[(args.steps - 1) % 4], S.SCHUR_MIXED)
+        xg = sol.schur_solve(b).cpu().numpy()
+        sol.close()
+        relerr = float(np.linalg.norm(xg - xref) / np.linalg.norm(xref))
+        cpu = {"value": n / tcpu / 1e6, "unit": "MDoF/s", "cores": 1, "kind": "oracle",
+               "sample": "one full-size right-hand side (1,046,529 dofs), fast-diagonalisation oracle, "
+                         "single thread, %.1f s" % tcpu}
+
+    # cached-factor solve rate (factorisation reused across right-hand sides, as the server does)
+    cached = {}
+    for prec, key in ((S.SCHUR_MIXED, "mixed"), (S.SCHUR_FP64, "fp64")):
+        if prec == S.SCHUR_FP64 and args.no_fp64:
+            continue
+        ts, its = [], []
+        for beta in BETAS:
+            sol = make(beta, prec)
+            sol.schur_solve(b, x)
+            flush_l2(flush)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sol.schur_solve(b, x)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            its.append(sol.last_stats)
+            sol.close()
+        cached[key] = {"ms_per_solve": float(np.mean(ts)), "mdof_s": n / (np.mean(ts) / 1e3) / 1e6,
+                       "solves_s": 1e3 / float(np.mean(ts)),
+                       "per_beta": [{"beta": bb, "ms": t, "outer_steps": s["outer_steps"],
+                                     "gmres_iters": s["iters_total"], "ms_setup": s["ms_setup"]}
+                                    for bb, t, s in zip(BETAS, ts, its)]}
+
+    # plain FP64 form, same steps (setup + solve), one per beta
+    fp64 = None
+    if not args.no_fp64:
+        t64, tt64, st64, _, _ = timed(S.SCHUR_FP64, 4, 1)
+        fp64 = {"value": n * 4 / (t64 / 1e3) / 1e6, "unit": "MDoF/s", "ms_per_step": t64 / 4,
+                "gmres_iters": [s["iters_total"] for s in st64], "outer_steps": [s["outer_steps"] for s in st64]}
+
+    # end to end through the host-buffer entry point (pinned host b, host x), setup included
+    bh_pin = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    bh_pin.copy_(b.cpu())
+    xh_pin = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    e2e_t = []
+    for i in range(max(2, args.steps // 2)):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sol = make(BETAS[i % 4], S.SCHUR_MIXED)
+        st = S.schur_stats()
+        rc = lib.schur_solve_host(sol.ctx, ctypes.c_void_p(bh_pin.data_ptr()), ctypes.c_void_p(xh_pin.data_ptr()), 1,
+                                  n, S._stream_ptr(stream), ctypes.byref(st))
+        assert rc == 0, S.last_error()
+        sol.close()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e = {"value": world * n * len(e2e_t) / float(np.sum(e2e_t)) / 1e6, "unit": "MDoF/s",
+           "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
+
+    # roofline of the dominant kernel category (event-timed inside the timed region)
+    roof = None
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    if prof and dom in prof:
+        nl_, tot_ms = prof[dom]
+        sol = make(BETAS[0], S.SCHUR_MIXED)
+        info = sol.info()
+        sol.close()
+        bound, algo = algorithmic(dom, info, 4)
+        avg_s = tot_ms / nl_ / 1e3
+        if bound == "hbm":
+            peak = peaks.get("hbm_gbs", 6800.0)
+            ach = algo / avg_s / 1e9
+            roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                    "traffic": None, "launches": nl_, "avg_us": avg_s * 1e6, "algorithmic_bytes": algo,
+                    "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+        else:
+            roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+                    "traffic": None, "launches": nl_, "avg_us": avg_s * 1e6}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MDoF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_dofs": n, "subdomains": N_SUB * N_SUB, "beta": list(BETAS),
+                       "nrhs_per_step": 1, "step": "schur_setup + schur_solve + schur_destroy",
+                       "precision": "complex FP32 FETI-DP, FP64 refinement to ||b-Az||/||b||<=1e-12",
+                       "l2": "flushed (256 MB write) between timed steps"},
+            "solves_per_s": world * args.steps / (total / 1e3),
+            "relerr_vs_oracle": relerr,
+            "gmres_iters": [s["iters_total"] for s in stats], "outer_steps": [s["outer_steps"] for s in stats],
+            "ms_setup": [s["ms_setup"] for s in stats],
+            "cached_factor_solve": cached, "fp64": fp64,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "profile_ms_by_kernel": {k: v[1] for k, v in (prof_all or {}).items()},
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -166,6 +166,24 @@ int schur_partition(const schur_mesh* mesh, const int* nsub, int local_mode, sch
 int schur_partition_export(const schur_mesh* mesh, const int* nsub, int local_mode, int which, int* out,
                            long long cap);
 
+/* Kernel timing for measurement (not needed to solve).  schur_profile_begin enables, for every
+ * category whose bit is set in mask, a CUDA event pair recorded on the launching stream around
+ * each launch.  schur_profile_end synchronises the device, writes per-category launch counts and
+ * summed event times (ms) into out (up to cap entries; *count = categories seen) and disables
+ * timing.  Categories: 0 factor, 1 form, 2 coarse_setup, 3 local_rhs, 4 apply_F, 5 apply_S,
+ * 6 scatter, 7 coarse_apply, 8 corner, 9 gmres_dots, 10 gmres_update, 11 gmres_other,
+ * 12 recover, 13 assemble_z, 14 residual, 15 other.
+ * schur_launch_count: kernels launched through ctx since schur_setup (setup included). */
+typedef struct {
+  int category;
+  long long launches;
+  double total_ms;
+} schur_kernel_time;
+int schur_profile_begin(unsigned mask);
+int schur_profile_end(schur_kernel_time* out, int cap, int* count);
+const char* schur_kernel_category_name(int category);
+long long schur_launch_count(const schur_ctx* ctx);
+
 int schur_get_info(const schur_ctx* ctx, schur_info_t* info);
 long long schur_ndof(const schur_mesh* mesh);
 void schur_destroy(schur_ctx* ctx);

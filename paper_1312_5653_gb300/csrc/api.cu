@@ -14,6 +14,7 @@
 #include "engine.h"
 #include "outer.h"
 #include "api_internal.h"
+#include "prof.h"
 
 namespace {
 thread_local std::string g_last_error;
@@ -96,10 +97,13 @@ int ctx_ensure_outer(schur_ctx* c, int R) {
 int ctx_residual(schur_ctx* c, const double* bre, const double* bim, int ldb, int R, cudaStream_t st, double* rel) {
   const Geom& g = c->hm.g;
   Stencil<double> sten = make_stencil<double>(g, c->gamma);
+  prof_start(KC_RESIDUAL, st);
   k_residual<<<dim3(c->nblk, R), 256, 0, st>>>(g, sten, bre, bim, ldb, reinterpret_cast<const cx<double>*>(c->z),
                                                (int)g.n, R, reinterpret_cast<cx<double>*>(c->res), c->part, c->nblk);
+  prof_stop(KC_RESIDUAL, st);
   API_CK(cudaGetLastError());
   ++c->launches;
+  ++c->total_launches;
   API_CK(cudaMemcpyAsync(c->h_part, c->part, (size_t)R * c->nblk * 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   API_CK(cudaStreamSynchronize(st));
   for (int r = 0; r < R; ++r) {
@@ -149,16 +153,20 @@ int ctx_outer(schur_ctx* c, const double* bre, const double* bim, int ldb, int R
     std::string msg;
     rc = c->eng->inner_solve(c->res, (int)g.n, c->z, (int)g.n, R, inner_tol, c->opts.max_iter, st, &ir, &msg);
     c->launches += c->eng->launches;
+    c->total_launches += c->eng->launches;
     if (rc) return set_error(rc, msg);
     ++steps;
     iters_total += ir.iters;
     if (iters_first < 0) iters_first = ir.iters;
   }
   if (x) {
+    prof_start(KC_RESIDUAL, st);
     k_shortcut<<<dim3(std::max(1, (int)std::min<long long>((g.n + 255) / 256, 4 * 152)), R), 256, 0, st>>>(
         g.n, reinterpret_cast<const cx<double>*>(c->z), (int)g.n, R, 1.0 / c->gamma, x, ldx);
+    prof_stop(KC_RESIDUAL, st);
     API_CK(cudaGetLastError());
     ++c->launches;
+    ++c->total_launches;
   }
   if (zout) {
     k_split_complex<<<dim3(std::max(1, (int)std::min<long long>((g.n + 255) / 256, 4 * 152)), R), 256, 0, st>>>(
@@ -260,6 +268,7 @@ int schur_setup(const schur_mesh* mesh, double beta, const schur_opts* opts, voi
     return set_error(rc, msg);
   }
   c->ms_setup = now_ms() - t0;
+  c->total_launches = c->eng->launches;
   *out = c;
   return SCHUR_OK;
 }
@@ -369,6 +378,8 @@ int schur_apply_mass(schur_ctx* c, const double* x, double* y, int nrhs, int ld,
 int schur_apply_stiffness(schur_ctx* c, const double* x, double* y, int nrhs, int ld, void* stream) {
   return apply_real(c, 1, x, y, nrhs, ld, stream);
 }
+
+long long schur_launch_count(const schur_ctx* c) { return c ? c->total_launches : -1; }
 
 int schur_get_info(const schur_ctx* c, schur_info_t* info) {
   if (!c || !info) return set_error(SCHUR_EINVAL, "NULL argument");

@@ -14,7 +14,8 @@ struct schur_ctx {
   schur_mesh mesh;
   schur_opts opts;
   double beta = 0, gamma = 0, ms_setup = 0;
-  long long launches = 0;  // kernels launched by the most recent solve call
+  long long launches = 0;        // kernels launched by the most recent solve call
+  long long total_launches = 0;  // kernels launched through this context since setup
   // FP64 outer refinement workspace
   int wsR = 0, nblk = 1;
   double* z = nullptr;      // complex, n x wsR

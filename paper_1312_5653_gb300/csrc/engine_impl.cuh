@@ -12,6 +12,7 @@
 #include "engine.h"
 #include "gmres.h"
 #include "kernels.cuh"
+#include "prof.h"
 
 namespace schur {
 
@@ -105,7 +106,9 @@ class Engine : public EngineBase {
       if (!use_smem) ENG_CK(alloc(&gws, (size_t)ncls_ * 2 * bb * cxT));
       ENG_CK(cudaFuncSetAttribute(k_factor<T, StencilProv<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       int thr = bb >= 1024 ? 512 : 256;
+      prof_start(KC_FACTOR, st);
       k_factor<T, StencilProv<T>><<<ncls_, thr, smem, st>>>(prr_, dm_->cls_code, Dinv_, gws, use_smem, err_);
+      prof_stop(KC_FACTOR, st);
       ENG_LAUNCH();
     }
     // ---- interior factor (identical for all subdomains)
@@ -119,7 +122,9 @@ class Engine : public EngineBase {
       cx<T>* gws = nullptr;
       if (!use_smem) ENG_CK(alloc(&gws, 2 * (size_t)ibb * cxT));
       ENG_CK(cudaFuncSetAttribute(k_factor<T, StencilProv<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      prof_start(KC_FACTOR, st);
       k_factor<T, StencilProv<T>><<<1, ibb >= 1024 ? 512 : 256, smem, st>>>(pii_, dm_->cls_code, Dii, gws, use_smem, err_ + 1);
+      prof_stop(KC_FACTOR, st);
       ENG_LAUNCH();
     }
     // ---- local operators
@@ -136,7 +141,9 @@ class Engine : public EngineBase {
       ENG_CK(alloc(&Xws, (size_t)grid * g.nl * C * cxT));
       size_t smem = 2 * (size_t)g.lb * C * cxT;
       ENG_CK(cudaFuncSetAttribute(k_form_rr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      prof_start(KC_FORM, st);
       k_form_rr<T><<<grid, 256, smem, st>>>(prr_, g, mv_, Dinv_, ncls_, C, Xws, F_, Frc_, Kcc_);
+      prof_stop(KC_FORM, st);
       ENG_LAUNCH();
       const int nchunk2 = (g.nD + C - 1) / C;
       cx<T>* Xi = nullptr;
@@ -145,11 +152,15 @@ class Engine : public EngineBase {
       ENG_CK(alloc(&Sbase, (size_t)g.nD * g.nD * cxT));
       size_t smem2 = 2 * (size_t)g.ib * C * cxT;
       ENG_CK(cudaFuncSetAttribute(k_form_ii<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+      prof_start(KC_FORM, st);
       k_form_ii<T><<<nchunk2, 256, smem2, st>>>(pii_, g, mv_, Dii, C, Xi, Sbase);
+      prof_stop(KC_FORM, st);
       ENG_LAUNCH();
       long long tot = (long long)ncls_ * g.nD * g.nD;
       int gs = (int)std::min<long long>((tot + 255) / 256, 16LL * nsm_);
+      prof_start(KC_FORM, st);
       k_mask_S<T><<<gs, 256, 0, st>>>(g, mv_, ncls_, Sbase, Sd_);
+      prof_stop(KC_FORM, st);
       ENG_LAUNCH();
       ENG_CK(cudaStreamSynchronize(st));
       free_one(Xws);
@@ -166,7 +177,9 @@ class Engine : public EngineBase {
       ENG_CK(cudaMemsetAsync(CB_, 0, (size_t)std::max(1, g.cL) * g.cb * nt * sizeof(cx<double>), st));
       const int noff = g.dim == 2 ? 9 : 27;
       long long tot = (long long)g.ncor * noff;
+      prof_start(KC_COARSE_SETUP, st);
       k_coarse_assemble<<<(int)((tot + 255) / 256), 256, 0, st>>>(g, Kcc_, dm_->sd_cls, CA_, CB_);
+      prof_stop(KC_COARSE_SETUP, st);
       ENG_LAUNCH();
       cprov_.ly.dim = g.dim;
       for (int a = 0; a < 3; ++a) cprov_.ly.ext[a] = a < g.dim ? g.ncg[a] : 1;
@@ -182,7 +195,9 @@ class Engine : public EngineBase {
       if (!use_smem) ENG_CK(alloc(&gws, 2 * (size_t)cbb * sizeof(cx<double>)));
       ENG_CK(cudaFuncSetAttribute(k_factor<double, StoredProv<double>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
+      prof_start(KC_COARSE_SETUP, st);
       k_factor<double, StoredProv<double>><<<1, 1024, smem, st>>>(cprov_, nullptr, Dc_, gws, use_smem, err_ + 2);
+      prof_stop(KC_COARSE_SETUP, st);
       ENG_LAUNCH();
       const int C = 16, nchunk = (g.ncor + C - 1) / C;
       int grid = std::min(nchunk, 4 * nsm_);
@@ -192,7 +207,9 @@ class Engine : public EngineBase {
       op_bytes_ += (long long)g.ncor * g.ncor * cxT;
       size_t smem2 = 2 * (size_t)g.cb * C * sizeof(cx<double>);
       ENG_CK(cudaFuncSetAttribute(k_coarse_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+      prof_start(KC_COARSE_SETUP, st);
       k_coarse_inverse<T><<<grid, 256, smem2, st>>>(cprov_, Dc_, g.ncor, C, Xws, Kinv_);
+      prof_stop(KC_COARSE_SETUP, st);
       ENG_LAUNCH();
       ENG_CK(cudaStreamSynchronize(st));
       free_one(Xws);
@@ -228,12 +245,16 @@ class Engine : public EngineBase {
       int thr = std::min(256, ((g.lb * R + 31) / 32) * 32);
       size_t smem = 2 * (size_t)g.lb * R * cxT;
       ENG_CK(cudaFuncSetAttribute(k_local_rhs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      prof_start(KC_LOCAL_RHS, st);
       k_local_rhs<T><<<g.nsd, thr, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, R, Xs_, VD_, Tc_);
+      prof_stop(KC_LOCAL_RHS, st);
       ENG_LAUNCH();
     }
     if (coarse) {
       int tot = R * g.ncor;
+      prof_start(KC_CORNER, st);
       k_corner_gather<T><<<(tot + 255) / 256, 256, 0, st>>>(g, Tc_, R, fc, ldf, nullptr, T(-1), ftc_);
+      prof_stop(KC_CORNER, st);
       ENG_LAUNCH();
       rc = coarse_apply(ftc_, R, nullptr, wc_, st, msg);
       if (rc) return rc;
@@ -241,7 +262,9 @@ class Engine : public EngineBase {
     int iters = 0, conv = 1;
     if (g.nlam > 0) {
       long long tot = (long long)R * g.nlam;
+      prof_start(KC_SCATTER, st);
       k_dual_rhs<T><<<(int)((tot + 255) / 256), 256, 0, st>>>(g, mv_, VD_, Frc_, coarse ? wc_ : nullptr, R, d_);
+      prof_stop(KC_SCATTER, st);
       ENG_LAUNCH();
       rc = gmres(R, m, tol, st, &iters, &conv, msg);
       if (rc) return rc;
@@ -254,7 +277,9 @@ class Engine : public EngineBase {
     if (coarse) {
       int tot = R * g.ncor;
       if (g.nlam > 0) {
+        prof_start(KC_CORNER, st);
         k_corner_gather<T><<<(tot + 255) / 256, 256, 0, st>>>(g, Tc_, R, nullptr, 0, ftc_, T(1), gc_);
+        prof_stop(KC_CORNER, st);
         ENG_LAUNCH();
         rc = coarse_apply(gc_, R, nullptr, uc_, st, msg);
       } else {
@@ -266,11 +291,15 @@ class Engine : public EngineBase {
       int thr = std::min(256, ((g.lb * R + 31) / 32) * 32);
       size_t smem = 2 * (size_t)g.lb * R * cxT;
       ENG_CK(cudaFuncSetAttribute(k_recover<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      prof_start(KC_RECOVER, st);
       k_recover<T><<<g.nsd, thr, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, g.nlam > 0 ? lam_ : nullptr,
                                              coarse ? uc_ : nullptr, R, Xs_);
+      prof_stop(KC_RECOVER, st);
       ENG_LAUNCH();
       long long tot = (long long)R * g.n;
+      prof_start(KC_ASSEMBLE, st);
       k_assemble_z<T><<<(int)((tot + 255) / 256), 256, 0, st>>>(g, Xs_, coarse ? uc_ : nullptr, R, zc, ldz);
+      prof_stop(KC_ASSEMBLE, st);
       ENG_LAUNCH();
     }
     ENG_CK(cudaStreamSynchronize(st));
@@ -412,11 +441,14 @@ class Engine : public EngineBase {
 
   int coarse_apply(const cx<T>* gv, int R, const int* active, cx<T>* w, cudaStream_t st, std::string* msg) {
     const int rows_per_block = 8, grid = (g_.ncor + rows_per_block - 1) / rows_per_block;
+    prof_start(KC_COARSE_APPLY, st);
     if (R == 1) k_coarse_apply<T, 1><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, gv, R, active, w);
     else if (R <= 4) k_coarse_apply<T, 4><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, gv, R, active, w);
     else if (R <= 8) k_coarse_apply<T, 8><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, gv, R, active, w);
-    else k_coarse_apply<T, 16><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, gv, R, active, w);
-    ENG_LAUNCH();
+    else prof_start(KC_COARSE_APPLY, st);
+ k_coarse_apply<T, 16><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, gv, R, active, w);
+ prof_stop(KC_COARSE_APPLY, st);
+ ENG_LAUNCH();
     return SCHUR_OK;
   }
 
@@ -431,7 +463,9 @@ class Engine : public EngineBase {
   do {                                                                                                  \
     ENG_CK(cudaFuncSetAttribute(k_local_apply<T, SC, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                 (int)std::max<size_t>(smem, 1)));                                       \
+    prof_start(SC ? KC_APPLY_S : KC_APPLY_F, st);                                                      \
     k_local_apply<T, SC, MR><<<g.nsd, thr, smem, st>>>(g, mv_, Op, Frc_, v, R, active, Y_, tc);         \
+    prof_stop(SC ? KC_APPLY_S : KC_APPLY_F, st);                                                       \
   } while (0)
     if (precond) {
       if (R == 1) LA_CASE(true, 1);
@@ -454,7 +488,9 @@ class Engine : public EngineBase {
     int rc = local_apply(true, Sd_, v, R, active, false, st, msg);
     if (rc) return rc;
     long long tot = (long long)R * g_.nlam;
+    prof_start(KC_SCATTER, st);
     k_scatter<T, true><<<(int)((tot + 255) / 256), 256, 0, st>>>(g_, mv_, Y_, nullptr, nullptr, R, active, out);
+    prof_stop(KC_SCATTER, st);
     ENG_LAUNCH();
     return SCHUR_OK;
   }
@@ -466,14 +502,18 @@ class Engine : public EngineBase {
     if (rc) return rc;
     if (coarse) {
       int tot = R * g_.ncor;
+      prof_start(KC_CORNER, st);
       k_corner_gather<T><<<(tot + 255) / 256, 256, 0, st>>>(g_, Tc_, R, nullptr, 0, nullptr, T(1), gc_);
+      prof_stop(KC_CORNER, st);
       ENG_LAUNCH();
       rc = coarse_apply(gc_, R, active, wc_, st, msg);
       if (rc) return rc;
     }
     long long tot = (long long)R * g_.nlam;
+    prof_start(KC_SCATTER, st);
     k_scatter<T, false><<<(int)((tot + 255) / 256), 256, 0, st>>>(g_, mv_, Y_, Frc_, coarse ? wc_ : nullptr, R, active,
                                                                   out);
+    prof_stop(KC_SCATTER, st);
     ENG_LAUNCH();
     return SCHUR_OK;
   }
@@ -486,12 +526,18 @@ class Engine : public EngineBase {
     const int gs = std::max(1, std::min((nlam + 255) / 256, 4 * nsm_));
     ENG_CK(cudaMemsetAsync(H_, 0, (size_t)R * m * (m + 1) * sizeof(cx<double>), st));
     ENG_CK(cudaMemsetAsync(bad_, 0, kMaxRdev * sizeof(int), st));
+    prof_start(KC_GMRES_OTHER, st);
     k_norm2<T><<<dim3(nblk, R), 256, 0, st>>>(d_, nlam, R, nullptr, nblk, nrm_part_);
+    prof_stop(KC_GMRES_OTHER, st);
     ENG_LAUNCH();
     ENG_CK(cudaMemcpyAsync(V_, d_, (size_t)R * nlam * cxT, cudaMemcpyDeviceToDevice, st));
+    prof_start(KC_GMRES_OTHER, st);
     k_gmres_init<<<1, 32, 0, st>>>(R, nrm_part_, nblk, m, beta0_, gvec_, active_, kk_, inv_nrm_, resid_);
+    prof_stop(KC_GMRES_OTHER, st);
     ENG_LAUNCH();
+    prof_start(KC_GMRES_OTHER, st);
     k_scale_vec<T><<<dim3(gs, R), 256, 0, st>>>(V_, nlam, R, active_, inv_nrm_);
+    prof_stop(KC_GMRES_OTHER, st);
     ENG_LAUNCH();
     const int seg = (nlam + nblk - 1) / nblk;
     const size_t dot_smem = (size_t)seg * cxT;
@@ -506,20 +552,32 @@ class Engine : public EngineBase {
       rc = dual_apply(zv_, R, active_, vk1, st, msg);
       if (rc) return rc;
       for (int pass = 0; pass < 2; ++pass) {
+        prof_start(KC_GMRES_DOTS, st);
         k_dots<T><<<dim3(nblk, R), 256, dot_smem, st>>>(V_, vstride, nlam, R, k, vk1, active_, nblk, part_);
+        prof_stop(KC_GMRES_DOTS, st);
         ENG_LAUNCH();
         int warps = R * (k + 1);
+        prof_start(KC_GMRES_DOTS, st);
         k_dots_reduce<<<(warps * 32 + 255) / 256, 256, 0, st>>>(part_, nblk, R, k, m, active_, H_, hc_);
+        prof_stop(KC_GMRES_DOTS, st);
         ENG_LAUNCH();
+        prof_start(KC_GMRES_UPDATE, st);
         k_update<T><<<dim3(gs, R), 256, (k + 1) * cxT, st>>>(V_, vstride, nlam, R, k, hc_, active_, vk1);
+        prof_stop(KC_GMRES_UPDATE, st);
         ENG_LAUNCH();
       }
+      prof_start(KC_GMRES_OTHER, st);
       k_norm2<T><<<dim3(nblk, R), 256, 0, st>>>(vk1, nlam, R, active_, nblk, nrm_part_);
+      prof_stop(KC_GMRES_OTHER, st);
       ENG_LAUNCH();
+      prof_start(KC_GMRES_OTHER, st);
       k_givens<<<1, 32, 0, st>>>(R, k, m, H_, nrm_part_, nblk, cs_c_, cs_s_, gvec_, beta0_, tol, active_, kk_, inv_nrm_,
                                  resid_, bad_);
+      prof_stop(KC_GMRES_OTHER, st);
       ENG_LAUNCH();
+      prof_start(KC_GMRES_OTHER, st);
       k_scale_vec<T><<<dim3(gs, R), 256, 0, st>>>(vk1, nlam, R, active_, inv_nrm_);
+      prof_stop(KC_GMRES_OTHER, st);
       ENG_LAUNCH();
       if ((k + 1) % check_every == 0 || k + 1 == m) {
         ENG_CK(cudaMemcpyAsync(h_active_, active_, R * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -529,9 +587,13 @@ class Engine : public EngineBase {
         if (!any) break;
       }
     }
+    prof_start(KC_GMRES_OTHER, st);
     k_hess_solve<<<R, 256, 0, st>>>(m, H_, gvec_, kk_, y_);
+    prof_stop(KC_GMRES_OTHER, st);
     ENG_LAUNCH();
+    prof_start(KC_GMRES_OTHER, st);
     k_combine<T><<<dim3(gs, R), 256, (size_t)m * cxT, st>>>(V_, vstride, nlam, R, y_, kk_, d_);
+    prof_stop(KC_GMRES_OTHER, st);
     ENG_LAUNCH();
     int rc = precond(d_, R, ones_, lam_, st, msg);
     if (rc) return rc;
