@@ -219,14 +219,7 @@ def main():
             stats.append(st)
             launches += nl
         torch.cuda.synchronize()
-        prof = None
-        if profile_mask:
-            import ctypes
-            arr = (S_kernel_time * 16)()
-            cnt = ctypes.c_int(0)
-            lib.schur_profile_end(arr, 16, ctypes.byref(cnt))
-            prof = {lib.schur_kernel_category_name(arr[k].category).decode(): (arr[k].launches, arr[k].total_ms)
-                    for k in range(cnt.value)}
+        prof = S.schur_profile_end() if profile_mask else None
         if world > 1:
             torch.distributed.barrier()
         total = float(np.sum(times))
@@ -237,15 +230,6 @@ def main():
         return total, times, stats, launches, prof
 
     import ctypes
-
-    class S_kernel_time(ctypes.Structure):
-        _fields_ = [("category", ctypes.c_int), ("launches", ctypes.c_longlong), ("total_ms", ctypes.c_double)]
-
-    lib.schur_profile_end.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
-    lib.schur_profile_begin.argtypes = [ctypes.c_uint]
-    lib.schur_kernel_category_name.restype = ctypes.c_char_p
-    lib.schur_launch_count.restype = ctypes.c_longlong
-    lib.schur_launch_count.argtypes = [ctypes.c_void_p]
 
     # untimed profiling pass over one step per beta: find the dominant kernel category
     _, _, _, _, prof_all = timed(S.SCHUR_MIXED, 4, 0, profile_mask=0xFFFF)

@@ -52,6 +52,10 @@ class schur_info_t(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class schur_kernel_time(ctypes.Structure):
+    _fields_ = [("category", ctypes.c_int), ("launches", ctypes.c_longlong), ("total_ms", ctypes.c_double)]
+
+
 class SchurError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
@@ -63,7 +67,8 @@ EXPORTS = [
     "schur_default_opts", "schur_setup", "schur_solve", "schur_solve_host", "schur_complex_solve",
     "schur_apply_mass", "schur_apply_stiffness", "schur_apply_S", "schur_kkt_apply", "schur_kkt_precond_apply",
     "schur_kkt_minres", "schur_partition", "schur_partition_export", "schur_get_info", "schur_ndof",
-    "schur_destroy", "schur_strerror", "schur_last_error", "schur_debug_operator",
+    "schur_destroy", "schur_strerror", "schur_last_error", "schur_debug_operator", "schur_profile_begin",
+    "schur_profile_end", "schur_kernel_category_name", "schur_launch_count",
 ]
 
 
@@ -103,6 +108,10 @@ def load(build_if_missing=True):
         "schur_strerror": (ctypes.c_char_p, [I]),
         "schur_last_error": (ctypes.c_char_p, []),
         "schur_debug_operator": (I, [P, I, I, P, LL]),
+        "schur_profile_begin": (I, [ctypes.c_uint]),
+        "schur_profile_end": (I, [P, I, ctypes.POINTER(I)]),
+        "schur_kernel_category_name": (ctypes.c_char_p, [I]),
+        "schur_launch_count": (LL, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -124,6 +133,19 @@ def _check(code, where, allow=()):
     if code != SCHUR_OK and code not in allow:
         raise SchurError(code, where)
     return code
+
+
+def schur_profile_begin(mask=0xFFFF):
+    _check(load().schur_profile_begin(mask), "schur_profile_begin")
+
+
+def schur_profile_end():
+    """{category name: (launches, total ms)} since schur_profile_begin (synchronises)."""
+    arr = (schur_kernel_time * 16)()
+    cnt = ctypes.c_int(0)
+    _check(load().schur_profile_end(arr, 16, ctypes.byref(cnt)), "schur_profile_end")
+    return {load().schur_kernel_category_name(arr[k].category).decode(): (arr[k].launches, arr[k].total_ms)
+            for k in range(cnt.value)}
 
 
 def make_mesh(dim, nel):
