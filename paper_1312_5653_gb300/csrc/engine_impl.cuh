@@ -12,7 +12,9 @@
 #include "engine.h"
 #include "gmres.h"
 #include "kernels.cuh"
+#include "warp.cuh"
 #include "prof.h"
+#include "coarse.h"
 
 namespace schur {
 
@@ -98,7 +100,15 @@ class Engine : public EngineBase {
     // ---- remainder factors, one per class
     ENG_CK(alloc(&Dinv_, (size_t)ncls_ * g.lL * bb * cxT));
     op_bytes_ += (long long)ncls_ * g.lL * bb * cxT;
-    {
+    if (g.lb <= 32) {
+      const int wpb = 8;
+      size_t smem = (size_t)wpb * (2 * bb + 2 * g.lb) * cxT;
+      ENG_CK(cudaFuncSetAttribute(k_factor_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      prof_start(KC_FACTOR, st);
+      k_factor_warp<T><<<(ncls_ + wpb - 1) / wpb, 32 * wpb, smem, st>>>(prr_, dm_->cls_code, ncls_, Dinv_, err_);
+      prof_stop(KC_FACTOR, st);
+      ENG_LAUNCH();
+    } else {
       size_t need = (2 * (size_t)bb + 2 * g.lb) * cxT;
       int use_smem = need <= 200 * 1024;
       size_t smem = use_smem ? need : 2 * g.lb * cxT;
@@ -135,16 +145,29 @@ class Engine : public EngineBase {
     op_bytes_ += (long long)ncls_ * g.nD * (2 * g.nD + g.nc) * cxT;
     {
       const int C = 32;
-      const int ncol = g.nD + g.nc, nchunk = (ncol + C - 1) / C;
-      int grid = std::min(ncls_ * nchunk, 8 * nsm_);
       cx<T>* Xws = nullptr;
-      ENG_CK(alloc(&Xws, (size_t)grid * g.nl * C * cxT));
-      size_t smem = 2 * (size_t)g.lb * C * cxT;
-      ENG_CK(cudaFuncSetAttribute(k_form_rr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      prof_start(KC_FORM, st);
-      k_form_rr<T><<<grid, 256, smem, st>>>(prr_, g, mv_, Dinv_, ncls_, C, Xws, F_, Frc_, Kcc_);
-      prof_stop(KC_FORM, st);
-      ENG_LAUNCH();
+      if (g.lb <= 32) {
+        constexpr int CW = sizeof(T) == 4 ? 16 : 8;
+        const int ncol = g.nD + g.nc, nchunk = (ncol + CW - 1) / CW, nwork = ncls_ * nchunk;
+        const size_t per_warp = (size_t)g.nl * CW * cxT;
+        const int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (160 * 1024) / per_warp));
+        size_t smem = per_warp * wpb;
+        ENG_CK(cudaFuncSetAttribute(k_form_rr_warp<T, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        prof_start(KC_FORM, st);
+        k_form_rr_warp<T, CW><<<(nwork + wpb - 1) / wpb, 32 * wpb, smem, st>>>(prr_, g, mv_, Dinv_, ncls_, F_, Frc_, Kcc_);
+        prof_stop(KC_FORM, st);
+        ENG_LAUNCH();
+      } else {
+        const int ncol = g.nD + g.nc, nchunk = (ncol + C - 1) / C;
+        int grid = std::min(ncls_ * nchunk, 8 * nsm_);
+        ENG_CK(alloc(&Xws, (size_t)grid * g.nl * C * cxT));
+        size_t smem = 2 * (size_t)g.lb * C * cxT;
+        ENG_CK(cudaFuncSetAttribute(k_form_rr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        prof_start(KC_FORM, st);
+        k_form_rr<T><<<grid, 256, smem, st>>>(prr_, g, mv_, Dinv_, ncls_, C, Xws, F_, Frc_, Kcc_);
+        prof_stop(KC_FORM, st);
+        ENG_LAUNCH();
+      }
       const int nchunk2 = (g.nD + C - 1) / C;
       cx<T>* Xi = nullptr;
       cx<T>* Sbase = nullptr;
@@ -163,7 +186,7 @@ class Engine : public EngineBase {
       prof_stop(KC_FORM, st);
       ENG_LAUNCH();
       ENG_CK(cudaStreamSynchronize(st));
-      free_one(Xws);
+      if (Xws) free_one(Xws);
       free_one(Xi);
       free_one(Sbase);
       free_one(Dii);
@@ -188,32 +211,72 @@ class Engine : public EngineBase {
       cprov_.CA = CA_;
       cprov_.CB = CB_;
       ENG_CK(alloc(&Dc_, (size_t)g.cL * cbb * sizeof(cx<double>)));
-      size_t need = (2 * (size_t)cbb + 2 * g.cb) * sizeof(cx<double>);
-      int use_smem = need <= 200 * 1024;
-      size_t smem = use_smem ? need : 2 * g.cb * sizeof(cx<double>);
-      cx<double>* gws = nullptr;
-      if (!use_smem) ENG_CK(alloc(&gws, 2 * (size_t)cbb * sizeof(cx<double>)));
-      ENG_CK(cudaFuncSetAttribute(k_factor<double, StoredProv<double>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
       prof_start(KC_COARSE_SETUP, st);
-      k_factor<double, StoredProv<double>><<<1, 1024, smem, st>>>(cprov_, nullptr, Dc_, gws, use_smem, err_ + 2);
+      cudaError_t ce = coarse_factor_cluster(cprov_, Dc_, err_ + 2, st, &coarse_cluster_);
       prof_stop(KC_COARSE_SETUP, st);
+      if (ce != cudaSuccess) {
+        // no cluster launch available: one CTA does the whole factorisation
+        coarse_cluster_ = 0;
+        size_t need = (2 * (size_t)cbb + 2 * g.cb) * sizeof(cx<double>);
+        int use_smem = need <= 200 * 1024;
+        size_t smem = use_smem ? need : 2 * g.cb * sizeof(cx<double>);
+        cx<double>* gws = nullptr;
+        if (!use_smem) ENG_CK(alloc(&gws, 2 * (size_t)cbb * sizeof(cx<double>)));
+        ENG_CK(cudaFuncSetAttribute(k_factor<double, StoredProv<double>>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        prof_start(KC_COARSE_SETUP, st);
+        k_factor<double, StoredProv<double>><<<1, 1024, smem, st>>>(cprov_, nullptr, Dc_, gws, use_smem, err_ + 2);
+        prof_stop(KC_COARSE_SETUP, st);
+      }
       ENG_LAUNCH();
-      const int C = 16, nchunk = (g.ncor + C - 1) / C;
-      int grid = std::min(nchunk, 4 * nsm_);
-      cx<double>* Xws = nullptr;
-      ENG_CK(alloc(&Xws, (size_t)grid * g.ncor * C * sizeof(cx<double>)));
       ENG_CK(alloc(&Kinv_, (size_t)g.ncor * g.ncor * cxT));
       op_bytes_ += (long long)g.ncor * g.ncor * cxT;
-      size_t smem2 = 2 * (size_t)g.cb * C * sizeof(cx<double>);
-      ENG_CK(cudaFuncSetAttribute(k_coarse_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
-      prof_start(KC_COARSE_SETUP, st);
-      k_coarse_inverse<T><<<grid, 256, smem2, st>>>(cprov_, Dc_, g.ncor, C, Xws, Kinv_);
-      prof_stop(KC_COARSE_SETUP, st);
-      ENG_LAUNCH();
-      ENG_CK(cudaStreamSynchronize(st));
-      free_one(Xws);
-      if (gws) free_one(gws);
+      const int C = 16, nchunk = (g.ncor + C - 1) / C;
+      int grid = std::min(nchunk, 4 * nsm_);
+      if (sizeof(T) == sizeof(double)) {
+        cx<double>* Xws = nullptr;
+        ENG_CK(alloc(&Xws, (size_t)grid * g.ncor * C * sizeof(cx<double>)));
+        size_t smem2 = 2 * (size_t)g.cb * C * sizeof(cx<double>);
+        ENG_CK(cudaFuncSetAttribute(k_coarse_inverse<T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem2));
+        prof_start(KC_COARSE_SETUP, st);
+        k_coarse_inverse<T, double><<<grid, 256, smem2, st>>>(cprov_, Dc_, g.ncor, C, Xws, Kinv_);
+        prof_stop(KC_COARSE_SETUP, st);
+        ENG_LAUNCH();
+        ENG_CK(cudaStreamSynchronize(st));
+        free_one(Xws);
+      } else {
+        // FP32 copies of the FP64 factor and coupling blocks; columns of the inverse in FP32
+        const long long nD = (long long)g.cL * cbb, nA = (long long)g.cL * g.cb * nt;
+        cx<float>*Df = nullptr, *CAf = nullptr, *CBf = nullptr, *Xws = nullptr;
+        ENG_CK(alloc(&Df, nD * sizeof(cx<float>)));
+        ENG_CK(alloc(&CAf, nA * sizeof(cx<float>)));
+        ENG_CK(alloc(&CBf, nA * sizeof(cx<float>)));
+        prof_start(KC_COARSE_SETUP, st);
+        k_convert<float, double><<<std::min<long long>((nD + 255) / 256, 4 * nsm_), 256, 0, st>>>(Dc_, Df, nD);
+        k_convert<float, double><<<std::min<long long>((nA + 255) / 256, 4 * nsm_), 256, 0, st>>>(CA_, CAf, nA);
+        k_convert<float, double><<<std::min<long long>((nA + 255) / 256, 4 * nsm_), 256, 0, st>>>(CB_, CBf, nA);
+        prof_stop(KC_COARSE_SETUP, st);
+        ENG_LAUNCH();
+        StoredProv<float> pf;
+        pf.ly = cprov_.ly;
+        pf.CA = CAf;
+        pf.CB = CBf;
+        ENG_CK(alloc(&Xws, (size_t)grid * g.ncor * C * sizeof(cx<float>)));
+        size_t smem2 = 2 * (size_t)g.cb * C * sizeof(cx<float>);
+        ENG_CK(cudaFuncSetAttribute(k_coarse_inverse<T, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem2));
+        prof_start(KC_COARSE_SETUP, st);
+        k_coarse_inverse<T, float><<<grid, 256, smem2, st>>>(pf, Df, g.ncor, C, Xws, Kinv_);
+        prof_stop(KC_COARSE_SETUP, st);
+        ENG_LAUNCH();
+        ENG_CK(cudaStreamSynchronize(st));
+        free_one(Xws);
+        free_one(Df);
+        free_one(CAf);
+        free_one(CBf);
+      }
+
     }
     ENG_CK(cudaStreamSynchronize(st));
     int herr[4];
@@ -241,15 +304,8 @@ class Engine : public EngineBase {
     const size_t cxT = sizeof(cx<T>);
     const bool coarse = g.ncor > 0;
     // ---- local right-hand sides
-    {
-      int thr = std::min(256, ((g.lb * R + 31) / 32) * 32);
-      size_t smem = 2 * (size_t)g.lb * R * cxT;
-      ENG_CK(cudaFuncSetAttribute(k_local_rhs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      prof_start(KC_LOCAL_RHS, st);
-      k_local_rhs<T><<<g.nsd, thr, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, R, Xs_, VD_, Tc_);
-      prof_stop(KC_LOCAL_RHS, st);
-      ENG_LAUNCH();
-    }
+    rc = local_solves(fc, ldf, nullptr, nullptr, R, true, st, msg);
+    if (rc) return rc;
     if (coarse) {
       int tot = R * g.ncor;
       prof_start(KC_CORNER, st);
@@ -288,14 +344,8 @@ class Engine : public EngineBase {
       if (rc) return rc;
     }
     {
-      int thr = std::min(256, ((g.lb * R + 31) / 32) * 32);
-      size_t smem = 2 * (size_t)g.lb * R * cxT;
-      ENG_CK(cudaFuncSetAttribute(k_recover<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      prof_start(KC_RECOVER, st);
-      k_recover<T><<<g.nsd, thr, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, g.nlam > 0 ? lam_ : nullptr,
-                                             coarse ? uc_ : nullptr, R, Xs_);
-      prof_stop(KC_RECOVER, st);
-      ENG_LAUNCH();
+      rc = local_solves(fc, ldf, g.nlam > 0 ? lam_ : nullptr, coarse ? uc_ : nullptr, R, false, st, msg);
+      if (rc) return rc;
       long long tot = (long long)R * g.n;
       prof_start(KC_ASSEMBLE, st);
       k_assemble_z<T><<<(int)((tot + 255) / 256), 256, 0, st>>>(g, Xs_, coarse ? uc_ : nullptr, R, zc, ldz);
@@ -439,16 +489,52 @@ class Engine : public EngineBase {
     return SCHUR_OK;
   }
 
+  // Local remainder solves of every subdomain: the right-hand-side split (rhs_split: VD, Tc) or the
+  // primal recovery (lam, uc given; solution left in Xs).
+  int local_solves(const cx<double>* fc, int ldf, const cx<T>* lam, const cx<T>* uc, int R, bool rhs_split,
+                   cudaStream_t st, std::string* msg) {
+    const Geom& g = g_;
+    const int cat = rhs_split ? KC_LOCAL_RHS : KC_RECOVER;
+    if (g.lb <= 32) {
+      const int wpb = 4, grid = (g.nsd + wpb - 1) / wpb;
+      cx<T>* vd = rhs_split ? VD_ : nullptr;
+      cx<T>* tc = rhs_split ? Tc_ : nullptr;
+      prof_start(cat, st);
+      if (R == 1) k_local_solve_warp<T, 1><<<grid, 32 * wpb, 0, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc);
+      else if (R == 2) k_local_solve_warp<T, 2><<<grid, 32 * wpb, 0, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc);
+      else if (R <= 4) k_local_solve_warp<T, 4><<<grid, 32 * wpb, 0, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc);
+      else if (R <= 8) k_local_solve_warp<T, 8><<<grid, 32 * wpb, 0, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc);
+      else k_local_solve_warp<T, 16><<<grid, 32 * wpb, 0, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc);
+      prof_stop(cat, st);
+      ENG_LAUNCH();
+      return SCHUR_OK;
+    }
+    int thr = std::min(256, ((g.lb * R + 31) / 32) * 32);
+    size_t smem = 2 * (size_t)g.lb * R * sizeof(cx<T>);
+    if (rhs_split) {
+      ENG_CK(cudaFuncSetAttribute(k_local_rhs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      prof_start(cat, st);
+      k_local_rhs<T><<<g.nsd, thr, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, R, Xs_, VD_, Tc_);
+      prof_stop(cat, st);
+    } else {
+      ENG_CK(cudaFuncSetAttribute(k_recover<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      prof_start(cat, st);
+      k_recover<T><<<g.nsd, thr, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_);
+      prof_stop(cat, st);
+    }
+    ENG_LAUNCH();
+    return SCHUR_OK;
+  }
+
   int coarse_apply(const cx<T>* gv, int R, const int* active, cx<T>* w, cudaStream_t st, std::string* msg) {
     const int rows_per_block = 8, grid = (g_.ncor + rows_per_block - 1) / rows_per_block;
     prof_start(KC_COARSE_APPLY, st);
     if (R == 1) k_coarse_apply<T, 1><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, gv, R, active, w);
     else if (R <= 4) k_coarse_apply<T, 4><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, gv, R, active, w);
     else if (R <= 8) k_coarse_apply<T, 8><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, gv, R, active, w);
-    else prof_start(KC_COARSE_APPLY, st);
- k_coarse_apply<T, 16><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, gv, R, active, w);
- prof_stop(KC_COARSE_APPLY, st);
- ENG_LAUNCH();
+    else k_coarse_apply<T, 16><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, gv, R, active, w);
+    prof_stop(KC_COARSE_APPLY, st);
+    ENG_LAUNCH();
     return SCHUR_OK;
   }
 
@@ -621,7 +707,7 @@ class Engine : public EngineBase {
   Stencil<T> st_;
   StencilProv<T> prr_, pii_;
   StoredProv<double> cprov_;
-  int ncls_ = 0, nsm_ = 152, nblk_ = 1;
+  int ncls_ = 0, nsm_ = 152, nblk_ = 1, coarse_cluster_ = 0;
   long long op_bytes_ = 0;
   std::vector<void*> allocs_, ws_;
   int* err_ = nullptr;

@@ -215,27 +215,34 @@ static __global__ void k_coarse_assemble(Geom g, const cx<double>* __restrict__ 
   else CB[((size_t)(K1 - 1) * g.cb + i1) * nt + t] = sum;
 }
 
-// Columns of the coarse inverse from the FP64 layered factor; stored in the working precision.
-template <class T>
-__global__ void k_coarse_inverse(StoredProv<double> P, const cx<double>* __restrict__ Dinv, int ncor, int C,
-                                 cx<double>* Xws, cx<T>* Kinv) {
+// Columns of the coarse inverse from the layered factor of the coarse matrix, solved in precision
+// S (FP64 for the FP64 path; FP32 copies of the FP64 factor for the mixed path), stored as T.
+template <class T, class S>
+__global__ void k_coarse_inverse(StoredProv<S> P, const cx<S>* __restrict__ Dinv, int ncor, int C, cx<S>* Xws,
+                                 cx<T>* Kinv) {
   extern __shared__ unsigned char smraw[];
-  cx<double>* sm = reinterpret_cast<cx<double>*>(smraw);
+  cx<S>* sm = reinterpret_cast<cx<S>*>(smraw);
   const int nchunk = (ncor + C - 1) / C, b = P.ly.b;
-  cx<double>* X = Xws + (size_t)blockIdx.x * ncor * C;
+  cx<S>* X = Xws + (size_t)blockIdx.x * ncor * C;
   for (int w = blockIdx.x; w < nchunk; w += gridDim.x) {
     const int col0 = w * C;
-    auto rhs = [&](int K, int i, int c) -> cx<double> {
+    auto rhs = [&](int K, int i, int c) -> cx<S> {
       int col = col0 + c;
-      return mkc<double>((col < ncor && K * b + i == col) ? 1.0 : 0.0, 0.0);
+      return mkc<S>((col < ncor && K * b + i == col) ? S(1) : S(0), S(0));
     };
-    layered_solve<double>(P, Dinv, C, rhs, X, C, sm);
+    layered_solve<S>(P, Dinv, C, rhs, X, C, sm);
     for (int e = threadIdx.x; e < ncor * C; e += blockDim.x) {
       int row = e / C, c = e - row * C, col = col0 + c;
       if (col < ncor) Kinv[(size_t)col * ncor + row] = ccast<T>(X[e]);
     }
     __syncthreads();
   }
+}
+
+template <class T, class S>
+__global__ void k_convert(const cx<S>* __restrict__ in, cx<T>* out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = ccast<T>(in[i]);
 }
 
 // ================================================================================= solve
@@ -419,12 +426,26 @@ __global__ void k_local_apply(Geom g, MapsView m, const cx<T>* __restrict__ Op, 
       if (r < R) Y[((size_t)sd * R + r) * nD + j] = acc[r];
   }
   if (Tc) {
-    for (int e = tid; e < R * g.nc; e += nthr) {
-      int r = e / g.nc, c = e - r * g.nc;
-      cx<T> acc = czero<T>();
-      const cx<T>* Fr = Frc + (size_t)q * nD * g.nc + c;
-      for (int j = 0; j < nD; ++j) cfma(acc, Fr[(size_t)j * g.nc], x[r * nD + j]);
-      Tc[((size_t)sd * R + r) * g.nc + c] = acc;
+    // Tc[r][c] = sum_j Frc[j][c] x[r][j]: per-thread partials over j, warp shuffles, then warps
+    __shared__ cx<T> red[32];
+    const int lane = tid & 31, warp = tid >> 5, nw = (nthr + 31) >> 5;
+    const cx<T>* Fr = Frc + (size_t)q * nD * g.nc;
+    for (int rc = 0; rc < R * g.nc; ++rc) {
+      const int r = rc / g.nc, c = rc - r * g.nc;
+      cx<T> p = czero<T>();
+      for (int j = tid; j < nD; j += nthr) cfma(p, Fr[(size_t)j * g.nc + c], x[r * nD + j]);
+      for (int o = 16; o > 0; o >>= 1) {
+        p.re += __shfl_xor_sync(0xffffffffu, p.re, o);
+        p.im += __shfl_xor_sync(0xffffffffu, p.im, o);
+      }
+      __syncthreads();
+      if (lane == 0) red[warp] = p;
+      __syncthreads();
+      if (tid == 0) {
+        cx<T> s = czero<T>();
+        for (int w = 0; w < nw; ++w) s = cadd(s, red[w]);
+        Tc[((size_t)sd * R + r) * g.nc + c] = s;
+      }
     }
   }
 }
