@@ -96,7 +96,7 @@ int ctx_ensure_outer(schur_ctx* c, int R) {
 // Relative residuals ||f - A z|| / ||f|| for R columns (synchronises).  Leaves res = f - A z.
 int ctx_residual(schur_ctx* c, const double* bre, const double* bim, int ldb, int R, cudaStream_t st, double* rel) {
   const Geom& g = c->hm.g;
-  Stencil<double> sten = make_stencil<double>(g, c->gamma);
+  Coef27 sten = make_coef(g, c->gamma);
   prof_start(KC_RESIDUAL, st);
   k_residual<<<dim3(c->nblk, R), 256, 0, st>>>(g, sten, bre, bim, ldb, reinterpret_cast<const cx<double>*>(c->z),
                                                (int)g.n, R, reinterpret_cast<cx<double>*>(c->res), c->part, c->nblk);
@@ -364,7 +364,7 @@ static int apply_real(schur_ctx* c, int mode, const double* x, double* y, int nr
   int rc = check_vec_args(c, x, y, nrhs, ld, 1);
   if (rc || nrhs == 0) return rc;
   const Geom& g = c->hm.g;
-  Stencil<double> sten = make_stencil<double>(g, 1.0);
+  Coef27 sten = make_coef(g, 1.0);
   int grid = std::max(1, (int)std::min<long long>((g.n + 255) / 256, 8 * 152));
   k_apply_real<<<dim3(grid, nrhs), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(g, sten, mode, x, ld, y, ld, nrhs,
                                                                                        1.0, 0.0);

@@ -97,6 +97,26 @@ class Engine : public EngineBase {
       for (int i = 0; i < kMaxRdev; ++i) h1[i] = 1;
       ENG_CK(cudaMemcpyAsync(ones_, h1, sizeof(h1), cudaMemcpyHostToDevice, st));
     }
+    // ---- stencil tables of the remainder and interior problems
+    {
+      const int nt = nbr_count(g.dim);
+      StencilProv<T>* probs[2] = {&prr_, &pii_};
+      for (StencilProv<T>* P : probs) {
+        const size_t ne = (size_t)P->ly.L * P->ly.b * nt;
+        cx<T>*tad = nullptr, *tal = nullptr;
+        unsigned char* fl = nullptr;
+        ENG_CK(alloc(&tad, ne * cxT));
+        ENG_CK(alloc(&tal, ne * cxT));
+        ENG_CK(alloc(&fl, (size_t)P->ly.L * P->ly.b));
+        P->tad = tad;
+        P->tal = tal;
+        P->flags = fl;
+        prof_start(KC_FACTOR, st);
+        k_stencil_tables<T><<<(int)std::min<size_t>((ne + 255) / 256, 1024), 256, 0, st>>>(*P, tad, tal, fl);
+        prof_stop(KC_FACTOR, st);
+        ENG_LAUNCH();
+      }
+    }
     // ---- remainder factors, one per class
     ENG_CK(alloc(&Dinv_, (size_t)ncls_ * g.lL * bb * cxT));
     op_bytes_ += (long long)ncls_ * g.lL * bb * cxT;

@@ -76,7 +76,7 @@ static int mass_inverse(schur_ctx* c, const double* t, int ldt, double* w, int l
   double* r = scr;
   double* d = scr + (size_t)n * R;
   double* Ad = scr + 2 * (size_t)n * R;
-  Stencil<double> sten = make_stencil<double>(g, 1.0);
+  Coef27 sten = make_coef(g, 1.0);
   const int gs = grid_for(n);
   k_copy_cols<<<dim3(gs, R), 256, 0, st>>>(n, R, t, ldt, r, (int)n, 1.0);
   KKT_CK(cudaGetLastError());
@@ -150,7 +150,7 @@ static int dots(schur_ctx* c, long long len, const double* x, int ldx, const dou
 static int kkt_apply_impl(schur_ctx* c, const double* v, double* r, int R, int ld, cudaStream_t st) {
   const Geom& g = c->hm.g;
   const long long n = g.n;
-  Stencil<double> sten = make_stencil<double>(g, 1.0);
+  Coef27 sten = make_coef(g, 1.0);
   const int gs = grid_for(n);
   for (int col = 0; col < R; ++col) {
     const double* y = v + (size_t)col * ld;
@@ -242,7 +242,7 @@ int schur_apply_S(schur_ctx* c, const double* x, double* y, int nrhs, int ld, vo
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const Geom& g = c->hm.g;
   const long long n = g.n;
-  Stencil<double> sten = make_stencil<double>(g, 1.0);
+  Coef27 sten = make_coef(g, 1.0);
   const int gs = grid_for(n);
   const int deg = cheb_degree(g.dim, 1e-15);
   for (int r0 = 0; r0 < nrhs; r0 += kMaxR) {

@@ -46,9 +46,12 @@ __device__ __forceinline__ int nbr_slot(const Layer& ly, int i, int j) {
   return (d0 + 1) + 3 * (d1 + 1);
 }
 
-// Entries of a subdomain problem from the closed-form Q1 stencil.  Node (K, i) has subdomain-
-// local coordinates off + (in-layer coords, K).  masked: remainder problem, whose subdomain
-// vertices and Dirichlet nodes are replaced by identity rows and columns.
+// Entries of a subdomain problem.  Node (K, i) has subdomain-local coordinates off + (in-layer
+// coords, K).  The unmasked Neumann entries are read from tables built once per problem from the
+// closed-form Q1 stencil (tad: in-layer couplings, tal: couplings to the previous layer, both
+// [(K*b + i)*nt + t]); flags[K*b + i] marks subdomain vertices (bit 7) and the faces a node lies on
+// (bit 2a: low face of axis a, bit 2a+1: high face).  masked: remainder problem, whose vertices
+// and Dirichlet nodes (face bit set in the subdomain's boundary code) become identity rows.
 template <class T>
 struct StencilProv {
   Layer ly;
@@ -57,6 +60,9 @@ struct StencilProv {
   int off;
   int masked;
   int code;
+  const cx<T>* tad;
+  const cx<T>* tal;
+  const unsigned char* flags;
   __device__ __forceinline__ void select(int q, const int* codes) { code = masked ? codes[q] : 0; }
   __device__ __forceinline__ void crd(int K, int i, int* l) const {
     l[0] = i % ly.ext[0] + off;
@@ -68,26 +74,59 @@ struct StencilProv {
       l[2] = 0;
     }
   }
+  __device__ __forceinline__ bool removed_node(int K, int i) const {
+    if (!masked) return false;
+    unsigned f = flags[K * ly.b + i];
+    return (f & 0x80u) || (f & (unsigned)code);
+  }
   __device__ __forceinline__ bool removed_l(const int* l) const {
     return masked && (local_vertex(l, s, ly.dim) || local_dirichlet(code, l, s, ly.dim));
   }
-  __device__ __forceinline__ cx<T> entry(int K1, int i, int K2, int j) const {
-    int p[3], q[3];
-    crd(K1, i, p);
-    crd(K2, j, q);
-    if (removed_l(p) || removed_l(q)) return mkc<T>((K1 == K2 && i == j) ? T(1) : T(0), T(0));
-    return q1_entry(st, s, p, q);
-  }
   __device__ __forceinline__ cx<T> Ad(int K, int i, int t) const {
     int j = nbr_of(ly, i, t);
-    return j < 0 ? mkc<T>(0, 0) : entry(K, i, K, j);
+    if (j < 0) return mkc<T>(0, 0);
+    if (removed_node(K, i) || removed_node(K, j)) return mkc<T>(i == j ? T(1) : T(0), T(0));
+    return tad[((size_t)K * ly.b + i) * nbr_count(ly.dim) + t];
   }
   // A(K+1, i ; K, nbr(i, t))
   __device__ __forceinline__ cx<T> Al(int K, int i, int t) const {
     int j = nbr_of(ly, i, t);
-    return j < 0 ? mkc<T>(0, 0) : entry(K + 1, i, K, j);
+    if (j < 0 || removed_node(K + 1, i) || removed_node(K, j)) return mkc<T>(0, 0);
+    return tal[((size_t)K * ly.b + i) * nbr_count(ly.dim) + t];
   }
 };
+
+// Builds tad, tal and flags of a box problem from the closed-form Q1 stencil (no masking).
+template <class T>
+__global__ void k_stencil_tables(StencilProv<T> P, cx<T>* tad, cx<T>* tal, unsigned char* flags) {
+  const int b = P.ly.b, L = P.ly.L, nt = nbr_count(P.ly.dim), dim = P.ly.dim;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < L * b * nt; e += gridDim.x * blockDim.x) {
+    int t = e % nt, i = (e / nt) % b, K = e / (nt * b);
+    int j = nbr_of(P.ly, i, t);
+    int p[3], q[3];
+    P.crd(K, i, p);
+    cx<T> ad = mkc<T>(0, 0), al = mkc<T>(0, 0);
+    if (j >= 0) {
+      P.crd(K, j, q);
+      ad = q1_entry(P.st, P.s, p, q);
+      if (K + 1 < L) {
+        int p1[3];
+        P.crd(K + 1, i, p1);
+        al = q1_entry(P.st, P.s, p1, q);
+      }
+    }
+    tad[e] = ad;
+    tal[e] = al;
+    if (t == 0) {
+      unsigned f = local_vertex(p, P.s, dim) ? 0x80u : 0u;
+      for (int a = 0; a < dim; ++a) {
+        if (p[a] == 0) f |= 1u << (2 * a);
+        if (p[a] == P.s[a]) f |= 1u << (2 * a + 1);
+      }
+      flags[K * b + i] = (unsigned char)f;
+    }
+  }
+}
 
 // Entries stored per (layer, node, neighbour slot): CA = diagonal blocks, CB = A_{K+1,K}.
 template <class T>

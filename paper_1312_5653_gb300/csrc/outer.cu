@@ -18,7 +18,20 @@ __device__ __forceinline__ void node_crd(const Geom& g, long long gi, int* G) {
   }
 }
 
-// sum over interior neighbours G' of coef(G, G') * x(G'), coef from the assembled stencil
+Coef27 make_coef(const Geom& g, double gamma) {
+  // every interior node has two elements per axis, so the assembled coefficient of a neighbour
+  // depends only on the offset
+  Stencil<double> st = make_stencil<double>(g, gamma);
+  Coef27 cf;
+  int G[3] = {1, 1, 1};
+  for (int o = 0; o < 27; ++o) {
+    int Q[3] = {1 + o % 3 - 1, 1 + (o / 3) % 3 - 1, 1 + o / 9 - 1};
+    cf.c[o] = q1_entry(st, g.nel, G, Q);
+  }
+  return cf;
+}
+
+// calls fn(offset index o, neighbour index) for the interior neighbours of interior node G
 template <class F>
 __device__ __forceinline__ void for_neighbours(const Geom& g, const int* G, F fn) {
   const int noff = g.dim == 2 ? 9 : 27;
@@ -29,11 +42,11 @@ __device__ __forceinline__ void for_neighbours(const Geom& g, const int* G, F fn
     for (int a = 0; a < g.dim; ++a) in = in && Q[a] >= 1 && Q[a] <= g.nel[a] - 1;
     if (!in) continue;
     long long qi = (Q[0] - 1) + s1 * (Q[1] - 1) + (g.dim == 3 ? s2 * (Q[2] - 1) : 0);
-    fn(Q, qi);
+    fn(o, qi);
   }
 }
 
-__global__ void k_residual(Geom g, Stencil<double> st, const double* __restrict__ bre, const double* __restrict__ bim,
+__global__ void k_residual(Geom g, Coef27 cf, const double* __restrict__ bre, const double* __restrict__ bim,
                            int ldb, const cx<double>* __restrict__ z, int ldz, int R, cx<double>* res,
                            double* part, int nblk) {
   __shared__ double red[2][32];
@@ -44,7 +57,7 @@ __global__ void k_residual(Geom g, Stencil<double> st, const double* __restrict_
     node_crd(g, i, G);
     cx<double> acc = mkc<double>(0, 0);
     const cx<double>* zr = z + (size_t)r * ldz;
-    for_neighbours(g, G, [&](const int* Q, long long qi) { cfma(acc, q1_entry(st, g.nel, G, Q), zr[qi]); });
+    for_neighbours(g, G, [&](int o, long long qi) { cfma(acc, cf.c[o], zr[qi]); });
     double br = bre[(size_t)r * ldb + i], bi = bim ? bim[(size_t)r * ldb + i] : 0.0;
     cx<double> rr = mkc<double>(br - acc.re, bi - acc.im);
     res[(size_t)r * g.n + i] = rr;
@@ -92,7 +105,7 @@ __global__ void k_split_complex(long long n, const cx<double>* __restrict__ z, i
 }
 
 // y = alpha * Op x + beta * y, Op = M (mode 0), K (mode 1), real FP64
-__global__ void k_apply_real(Geom g, Stencil<double> st, int mode, const double* __restrict__ x, int ldx, double* y,
+__global__ void k_apply_real(Geom g, Coef27 cf, int mode, const double* __restrict__ x, int ldx, double* y,
                              int ldy, int R, double alpha, double beta) {
   const int r = blockIdx.y;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.n; i += (long long)gridDim.x * blockDim.x) {
@@ -100,10 +113,7 @@ __global__ void k_apply_real(Geom g, Stencil<double> st, int mode, const double*
     node_crd(g, i, G);
     double acc = 0;
     const double* xr = x + (size_t)r * ldx;
-    for_neighbours(g, G, [&](const int* Q, long long qi) {
-      cx<double> c = q1_entry(st, g.nel, G, Q);
-      acc += (mode == 0 ? c.im : c.re) * xr[qi];
-    });
+    for_neighbours(g, G, [&](int o, long long qi) { acc += (mode == 0 ? cf.c[o].im : cf.c[o].re) * xr[qi]; });
     double* yy = y + (size_t)r * ldy + i;
     *yy = alpha * acc + (beta == 0.0 ? 0.0 : beta * *yy);
   }

@@ -13,11 +13,11 @@ __device__ __forceinline__ cx<T> shfl_cx(cx<T> v, int src) {
 }
 
 // X = A^{-1} B for up to C columns (runtime R <= C used), B given by rhs(K, i, c).
-// X (per warp, any address space) holds [(K*b + i) * ldx + c]; forward results are overwritten
-// by the solution in the backward sweep.
+// X (per warp, any address space) holds entry (node K*b + i, column c) at (K*b + i)*rs + c*cs;
+// forward results are overwritten by the solution in the backward sweep.
 template <class T, int C, class Prov, class RhsF>
 __device__ __forceinline__ void warp_layered_solve(const Prov& P, const cx<T>* __restrict__ Dinv, int R, RhsF rhs,
-                                                   cx<T>* X, int ldx) {
+                                                   cx<T>* X, int rs, int cs) {
   const int lane = threadIdx.x & 31, b = P.ly.b, L = P.ly.L, nt = nbr_count(P.ly.dim), bb = b * b;
   const bool act = lane < b;
   cx<T> prev[C];
@@ -48,7 +48,7 @@ __device__ __forceinline__ void warp_layered_solve(const Prov& P, const cx<T>* _
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       prev[c] = acc[c];
-      if (act && c < R) X[(size_t)(K * b + lane) * ldx + c] = acc[c];
+      if (act && c < R) X[(size_t)(K * b + lane) * rs + (size_t)c * cs] = acc[c];
     }
   }
   // backward: prev = E_{L-1} = X_{L-1}
@@ -65,7 +65,7 @@ __device__ __forceinline__ void warp_layered_solve(const Prov& P, const cx<T>* _
     }
     cx<T> x[C];
 #pragma unroll
-    for (int c = 0; c < C; ++c) x[c] = (act && c < R) ? X[(size_t)(K * b + lane) * ldx + c] : czero<T>();
+    for (int c = 0; c < C; ++c) x[c] = (act && c < R) ? X[(size_t)(K * b + lane) * rs + (size_t)c * cs] : czero<T>();
     const cx<T>* D = Dinv + (size_t)K * bb;
     for (int mm = 0; mm < b; ++mm) {
       cx<T> d = act ? D[mm * b + lane] : czero<T>();
@@ -75,7 +75,7 @@ __device__ __forceinline__ void warp_layered_solve(const Prov& P, const cx<T>* _
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       prev[c] = x[c];
-      if (act && c < R) X[(size_t)(K * b + lane) * ldx + c] = x[c];
+      if (act && c < R) X[(size_t)(K * b + lane) * rs + (size_t)c * cs] = x[c];
     }
   }
 }
@@ -166,9 +166,9 @@ __device__ __forceinline__ cx<T> remainder_rhs(const StencilProv<T>& P, const Ge
                                                const cx<T>* __restrict__ lam, const cx<T>* __restrict__ uc, int K,
                                                int i, int c) {
   const int dim = g.dim;
+  if (P.removed_node(K, i)) return czero<T>();
   int l[3];
   P.crd(K, i, l);
-  if (P.removed_l(l)) return czero<T>();
   int G[3] = {S[0] * g.s[0] + l[0], S[1] * g.s[1] + l[1], dim == 3 ? S[2] * g.s[2] + l[2] : 1};
   cx<double> fv = f[(size_t)c * ldf + gidx(g, G)];
   int slot = m.node_slot[K * P.ly.b + i];
@@ -217,7 +217,7 @@ __global__ void k_local_solve_warp(StencilProv<T> P, Geom g, MapsView m, const c
   local_ext(g, ext);
   cx<T>* X = Xs + (size_t)sd * g.nl * R;
   auto rhs = [&](int K, int i, int c) -> cx<T> { return remainder_rhs(P, g, m, sd, S, f, ldf, lam, uc, K, i, c); };
-  warp_layered_solve<T, C>(P, Dinv + (size_t)q * L * b * b, R, rhs, X, R);
+  warp_layered_solve<T, C>(P, Dinv + (size_t)q * L * b * b, R, rhs, X, R, 1);
   if (!VD) return;
   __syncwarp();
   for (int e = lane; e < R * nD; e += 32) {
@@ -271,12 +271,12 @@ __global__ void k_form_rr_warp(StencilProv<T> P, Geom g, MapsView m, const cx<T>
     if (local_dirichlet(code, lc, g.s, dim)) return czero<T>();
     return q1_entry(P.st, g.s, l, lc);
   };
-  warp_layered_solve<T, C>(P, Dinv + (size_t)q * L * b * b, C, rhs, X, C);
+  warp_layered_solve<T, C>(P, Dinv + (size_t)q * L * b * b, C, rhs, X, 1, g.nl);
   __syncwarp();
   for (int e = lane; e < nD * C; e += 32) {
     int j = e / C, c = e - j * C, col = col0 + c;
     if (col >= ncol) continue;
-    cx<T> v = X[(size_t)m.slot_node[j] * C + c];
+    cx<T> v = X[(size_t)m.slot_node[j] + (size_t)c * g.nl];
     if (col < nD) F[((size_t)q * nD + j) * nD + col] = v;
     else Frc[((size_t)q * nD + j) * nc + (col - nD)] = v;
   }
@@ -297,7 +297,7 @@ __global__ void k_form_rr_warp(StencilProv<T> P, Geom g, MapsView m, const cx<T>
         for (int a = 0; a < dim; ++a) in = in && lp[a] >= 0 && lp[a] <= g.s[a];
         if (!in || (lp[0] == l1[0] && lp[1] == l1[1] && lp[2] == l1[2])) continue;
         if (P.removed_l(lp)) continue;
-        cfms(v, q1_entry(P.st, g.s, l1, lp), X[(size_t)crd2idx(lp, ext, dim) * C + c]);
+        cfms(v, q1_entry(P.st, g.s, l1, lp), X[(size_t)crd2idx(lp, ext, dim) + (size_t)c * g.nl]);
       }
     }
     Kcc[((size_t)q * nc + c1) * nc + c2] = ccast<double>(v);
