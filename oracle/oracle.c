@@ -139,20 +139,46 @@ static void band_matvec(long n, int w, const double* band, const double* x, doub
   }
 }
 
+/* Matrix-free products by the element loop: y = sum_e P_e^T A_e P_e x (memory O(n), any mesh). */
 int or_apply_KM(int dim, const int* nel, int nrhs, const double* x, double* Kx, double* Mx) {
   if (check_mesh(dim, nel) || nrhs < 0) return -1;
   long n = or_ndof(dim, nel);
-  int w = or_bandwidth(dim, nel);
-  double* Kb = (double*)malloc(sizeof(double) * n * (w + 1));
-  double* Mb = (double*)malloc(sizeof(double) * n * (w + 1));
-  if (!Kb || !Mb) { free(Kb); free(Mb); return -2; }
-  or_assemble(dim, nel, Kb, Mb);
+  double h[3] = {1.0, 1.0, 1.0};
+  for (int a = 0; a < dim; ++a) h[a] = 1.0 / nel[a];
+  double Ke[64], Me[64];
+  or_element(dim, h, Ke, Me);
+  int nn = 1 << dim;
   for (int r = 0; r < nrhs; ++r) {
-    if (Kx) band_matvec(n, w, Kb, x + (long)r * n, Kx + (long)r * n);
-    if (Mx) band_matvec(n, w, Mb, x + (long)r * n, Mx + (long)r * n);
+    const double* xr = x + (long)r * n;
+    double* kr = Kx ? Kx + (long)r * n : NULL;
+    double* mr = Mx ? Mx + (long)r * n : NULL;
+    if (kr) memset(kr, 0, sizeof(double) * n);
+    if (mr) memset(mr, 0, sizeof(double) * n);
+    int e[3] = {0, 0, 0};
+    int ez = dim == 3 ? nel[2] : 1;
+    for (e[2] = 0; e[2] < ez; ++e[2])
+      for (e[1] = 0; e[1] < nel[1]; ++e[1])
+        for (e[0] = 0; e[0] < nel[0]; ++e[0]) {
+          long idx[8];
+          double xe[8];
+          for (int p = 0; p < nn; ++p) {
+            int gp[3];
+            for (int a = 0; a < dim; ++a) gp[a] = e[a] + ((p >> a) & 1);
+            idx[p] = node_index(dim, nel, gp);
+            xe[p] = idx[p] >= 0 ? xr[idx[p]] : 0.0;
+          }
+          for (int p = 0; p < nn; ++p) {
+            if (idx[p] < 0) continue;
+            double sk = 0.0, sm = 0.0;
+            for (int q = 0; q < nn; ++q) {
+              sk += Ke[p * nn + q] * xe[q];
+              sm += Me[p * nn + q] * xe[q];
+            }
+            if (kr) kr[idx[p]] += sk;
+            if (mr) mr[idx[p]] += sm;
+          }
+        }
   }
-  free(Kb);
-  free(Mb);
   return 0;
 }
 
