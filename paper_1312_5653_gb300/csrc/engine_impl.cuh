@@ -259,9 +259,9 @@ class Engine : public EngineBase {
         size_t smem2 = 2 * (size_t)g.cb * C * sizeof(cx<double>);
         ENG_CK(cudaFuncSetAttribute(k_coarse_inverse<T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem2));
-        prof_start(KC_COARSE_SETUP, st);
+        prof_start(KC_COARSE_INV, st);
         k_coarse_inverse<T, double><<<grid, 256, smem2, st>>>(cprov_, Dc_, g.ncor, C, Xws, Kinv_);
-        prof_stop(KC_COARSE_SETUP, st);
+        prof_stop(KC_COARSE_INV, st);
         ENG_LAUNCH();
         ENG_CK(cudaStreamSynchronize(st));
         free_one(Xws);
@@ -272,11 +272,11 @@ class Engine : public EngineBase {
         ENG_CK(alloc(&Df, nD * sizeof(cx<float>)));
         ENG_CK(alloc(&CAf, nA * sizeof(cx<float>)));
         ENG_CK(alloc(&CBf, nA * sizeof(cx<float>)));
-        prof_start(KC_COARSE_SETUP, st);
+        prof_start(KC_COARSE_INV, st);
         k_convert<float, double><<<std::min<long long>((nD + 255) / 256, 4 * nsm_), 256, 0, st>>>(Dc_, Df, nD);
         k_convert<float, double><<<std::min<long long>((nA + 255) / 256, 4 * nsm_), 256, 0, st>>>(CA_, CAf, nA);
         k_convert<float, double><<<std::min<long long>((nA + 255) / 256, 4 * nsm_), 256, 0, st>>>(CB_, CBf, nA);
-        prof_stop(KC_COARSE_SETUP, st);
+        prof_stop(KC_COARSE_INV, st);
         ENG_LAUNCH();
         StoredProv<float> pf;
         pf.ly = cprov_.ly;
@@ -286,9 +286,9 @@ class Engine : public EngineBase {
         size_t smem2 = 2 * (size_t)g.cb * C * sizeof(cx<float>);
         ENG_CK(cudaFuncSetAttribute(k_coarse_inverse<T, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem2));
-        prof_start(KC_COARSE_SETUP, st);
+        prof_start(KC_COARSE_INV, st);
         k_coarse_inverse<T, float><<<grid, 256, smem2, st>>>(pf, Df, g.ncor, C, Xws, Kinv_);
-        prof_stop(KC_COARSE_SETUP, st);
+        prof_stop(KC_COARSE_INV, st);
         ENG_LAUNCH();
         ENG_CK(cudaStreamSynchronize(st));
         free_one(Xws);

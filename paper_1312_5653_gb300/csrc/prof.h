@@ -20,7 +20,7 @@ enum KCat {
   KC_RECOVER = 12,    // primal recovery solves
   KC_ASSEMBLE = 13,   // z assembly
   KC_RESIDUAL = 14,   // FP64 refinement residual and shortcut
-  KC_OTHER = 15,
+  KC_COARSE_INV = 15,  // coarse inverse columns (and precision conversion)
   KC_N = 16
 };
 
