@@ -138,6 +138,21 @@ int schur_apply_stiffness(schur_ctx* ctx, const double* x_dev, double* y_dev, in
  * Synchronises. */
 int schur_apply_S(schur_ctx* ctx, const double* x_dev, double* y_dev, int nrhs, int ld, void* stream);
 
+/* y = S x as schur_apply_S, but with no context and no device allocation at all (the paper has no
+ * counterpart; this is a deployment convenience).  For callers that cannot allocate device
+ * memory: code that runs where cudaMalloc is unavailable or not allowed, such as a plugin inside
+ * another runtime's stream-ordered region or a process whose allocator is owned by its host
+ * application, and that therefore cannot call schur_setup.  The work vectors live in one fixed
+ * device array of 5 x 2^20 doubles (40 MiB) that every GPU loading the library holds until the
+ * process exits, so n (interior nodes of the mesh) must be at most 2^20; larger meshes return
+ * SCHUR_EINVAL.  Columns are processed one after another (any nrhs; ld >= n).
+ * The first call on a device looks up the array's device address with that device current; make
+ * that first call before any stream capture.  All calls on all streams share the one array and
+ * every call overwrites it completely before reading it: calls whose work overlaps on the GPU race
+ * and must be ordered by the caller.  Asynchronous on `stream`.  Errors: EINVAL, ECUDA. */
+int schur_apply_S_static(const schur_mesh* mesh, double beta, const double* x_dev, double* y_dev, int nrhs, int ld,
+                         void* stream);
+
 /* Full-space KKT system of Sec. 2 with homogeneous Dirichlet data:
  *   [M 0 K; 0 beta M -M; K -M 0] (y, u, l).
  * Vectors hold the three blocks stacked: entries [0,n) = y, [n,2n) = u, [2n,3n) = lambda; ld >= 3n.

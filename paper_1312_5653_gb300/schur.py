@@ -68,7 +68,7 @@ EXPORTS = [
     "schur_apply_mass", "schur_apply_stiffness", "schur_apply_S", "schur_kkt_apply", "schur_kkt_precond_apply",
     "schur_kkt_minres", "schur_partition", "schur_partition_export", "schur_get_info", "schur_ndof",
     "schur_destroy", "schur_strerror", "schur_last_error", "schur_debug_operator", "schur_profile_begin",
-    "schur_profile_end", "schur_kernel_category_name", "schur_launch_count",
+    "schur_profile_end", "schur_kernel_category_name", "schur_launch_count", "schur_apply_S_static",
 ]
 
 
@@ -112,6 +112,7 @@ def load(build_if_missing=True):
         "schur_profile_end": (I, [P, I, ctypes.POINTER(I)]),
         "schur_kernel_category_name": (ctypes.c_char_p, [I]),
         "schur_launch_count": (LL, [P]),
+        "schur_apply_S_static": (I, [ctypes.POINTER(schur_mesh), D, P, P, I, I, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
