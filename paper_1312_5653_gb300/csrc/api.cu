@@ -5,7 +5,9 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -71,6 +73,69 @@ void free_maps(DevMaps* dm) {
   *dm = DevMaps();
 }
 
+void configure_pool() {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  done[dev] = true;
+}
+
+MapEntry::~MapEntry() {
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != device) cudaSetDevice(device);
+  free_maps(&dm);
+  if (cur != device) cudaSetDevice(cur);
+}
+
+// Process-wide cache of partitions (host maps + device copies), keyed by device, mesh, nsub and
+// local_mode; the most recently used kPartitionCache entries stay alive after their contexts.
+namespace {
+constexpr size_t kPartitionCache = 8;
+std::mutex g_part_mu;
+std::vector<std::pair<std::string, std::shared_ptr<MapEntry>>> g_parts;  // most recent last
+}  // namespace
+
+int get_partition(const schur_mesh* mesh, const schur_opts* opts, std::shared_ptr<MapEntry>* out, std::string* msg) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+  char key[160];
+  const int d = mesh->dim;
+  snprintf(key, sizeof(key), "%d|%d|%d,%d,%d|%d,%d,%d|%d", dev, d, mesh->nel[0], mesh->nel[1], d == 3 ? mesh->nel[2] : 1,
+           opts->nsub[0], opts->nsub[1], d == 3 ? opts->nsub[2] : 1, opts->local_mode);
+  std::lock_guard<std::mutex> lk(g_part_mu);
+  for (size_t i = 0; i < g_parts.size(); ++i)
+    if (g_parts[i].first == key) {
+      auto e = g_parts[i];
+      g_parts.erase(g_parts.begin() + i);
+      g_parts.push_back(e);
+      *out = e.second;
+      return SCHUR_OK;
+    }
+  auto e = std::make_shared<MapEntry>();
+  e->device = dev;
+  std::string m = build_maps(mesh->dim, mesh->nel, opts->nsub, opts->local_mode, &e->hm);
+  if (!m.empty()) {
+    if (msg) *msg = m;
+    return SCHUR_EINVAL;
+  }
+  int rc = upload_maps(e->hm, &e->dm, msg);
+  if (rc) return rc;
+  g_parts.push_back({key, e});
+  if (g_parts.size() > kPartitionCache) g_parts.erase(g_parts.begin());
+  *out = e;
+  return SCHUR_OK;
+}
+
 static double now_ms() {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -82,10 +147,10 @@ int ctx_ensure_outer(schur_ctx* c, int R) {
   if (c->part) cudaFree(c->part);
   if (c->h_part) cudaFreeHost(c->h_part);
   c->z = c->res = c->part = c->h_part = nullptr;
-  const size_t n = (size_t)c->hm.g.n;
+  const size_t n = (size_t)c->mp->hm.g.n;
   API_CK(cudaMalloc(&c->z, n * R * 2 * sizeof(double)));
   API_CK(cudaMalloc(&c->res, n * R * 2 * sizeof(double)));
-  c->nblk = (int)std::min<long long>(4LL * 152, (c->hm.g.n + 255) / 256);
+  c->nblk = (int)std::min<long long>(4LL * 152, (c->mp->hm.g.n + 255) / 256);
   if (c->nblk < 1) c->nblk = 1;
   API_CK(cudaMalloc(&c->part, (size_t)R * c->nblk * 2 * sizeof(double)));
   API_CK(cudaMallocHost(&c->h_part, (size_t)R * c->nblk * 2 * sizeof(double)));
@@ -95,7 +160,7 @@ int ctx_ensure_outer(schur_ctx* c, int R) {
 
 // Relative residuals ||f - A z|| / ||f|| for R columns (synchronises).  Leaves res = f - A z.
 int ctx_residual(schur_ctx* c, const double* bre, const double* bim, int ldb, int R, cudaStream_t st, double* rel) {
-  const Geom& g = c->hm.g;
+  const Geom& g = c->mp->hm.g;
   Coef27 sten = make_coef(g, c->gamma);
   prof_start(KC_RESIDUAL, st);
   k_residual<<<dim3(c->nblk, R), 256, 0, st>>>(g, sten, bre, bim, ldb, reinterpret_cast<const cx<double>*>(c->z),
@@ -122,7 +187,7 @@ int ctx_residual(schur_ctx* c, const double* bre, const double* bim, int ldb, in
 // ||b - A z|| / ||b|| <= tol.  Output: x = -Im(z)/gamma (x != null) and/or z (zout != null).
 int ctx_outer(schur_ctx* c, const double* bre, const double* bim, int ldb, int R, double* x, int ldx, double* zout,
               int ldz, cudaStream_t st, schur_stats* stats) {
-  const Geom& g = c->hm.g;
+  const Geom& g = c->mp->hm.g;
   int rc = ctx_ensure_outer(c, R);
   if (rc) return rc;
   API_CK(cudaMemsetAsync(c->z, 0, (size_t)g.n * R * 2 * sizeof(double), st));
@@ -246,18 +311,14 @@ int schur_setup(const schur_mesh* mesh, double beta, const schur_opts* opts, voi
   c->opts = *opts;
   c->beta = beta;
   c->gamma = 1.0 / std::sqrt(beta);
-  std::string msg = build_maps(mesh->dim, mesh->nel, opts->nsub, opts->local_mode, &c->hm);
-  if (!msg.empty()) {
-    delete c;
-    return set_error(SCHUR_EINVAL, msg);
-  }
-  int rc = upload_maps(c->hm, &c->dm, &msg);
+  std::string msg;
+  int rc = get_partition(mesh, opts, &c->mp, &msg);
   if (rc) {
-    schur_destroy(c);
+    delete c;
     return set_error(rc, msg);
   }
-  c->eng = opts->precision == SCHUR_MIXED ? make_engine_f32(&c->hm, &c->dm, c->gamma)
-                                          : make_engine_f64(&c->hm, &c->dm, c->gamma);
+  c->eng = opts->precision == SCHUR_MIXED ? make_engine_f32(&c->mp->hm, &c->mp->dm, c->gamma)
+                                          : make_engine_f64(&c->mp->hm, &c->mp->dm, c->gamma);
   if (!c->eng) {
     schur_destroy(c);
     return set_error(SCHUR_ENOMEM, "engine allocation failed");
@@ -278,7 +339,7 @@ static int check_vec_args(schur_ctx* c, const void* a, const void* b, int nrhs, 
   if (nrhs < 0) return set_error(SCHUR_EINVAL, "nrhs < 0");
   if (nrhs == 0) return SCHUR_OK;
   if (!a || !b) return set_error(SCHUR_EINVAL, "NULL vector");
-  if ((long long)ld < mult * c->hm.g.n) return set_error(SCHUR_EINVAL, "ld smaller than the vector length");
+  if ((long long)ld < mult * c->mp->hm.g.n) return set_error(SCHUR_EINVAL, "ld smaller than the vector length");
   return SCHUR_OK;
 }
 
@@ -363,7 +424,7 @@ int schur_solve_host(schur_ctx* c, const double* bh, double* xh, int nrhs, int l
 static int apply_real(schur_ctx* c, int mode, const double* x, double* y, int nrhs, int ld, void* stream) {
   int rc = check_vec_args(c, x, y, nrhs, ld, 1);
   if (rc || nrhs == 0) return rc;
-  const Geom& g = c->hm.g;
+  const Geom& g = c->mp->hm.g;
   Coef27 sten = make_coef(g, 1.0);
   int grid = std::max(1, (int)std::min<long long>((g.n + 255) / 256, 8 * 152));
   k_apply_real<<<dim3(grid, nrhs), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(g, sten, mode, x, ld, y, ld, nrhs,
@@ -383,10 +444,10 @@ long long schur_launch_count(const schur_ctx* c) { return c ? c->total_launches 
 
 int schur_get_info(const schur_ctx* c, schur_info_t* info) {
   if (!c || !info) return set_error(SCHUR_EINVAL, "NULL argument");
-  const Geom& g = c->hm.g;
+  const Geom& g = c->mp->hm.g;
   info->n = g.n;
   info->n_sub = g.nsd;
-  info->n_classes = c->hm.ncls;
+  info->n_classes = c->mp->hm.ncls;
   info->n_lambda = g.nlam;
   info->n_coarse = g.ncor;
   info->n_delta = g.nD;
@@ -407,7 +468,7 @@ void schur_destroy(schur_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
   delete c->eng;
-  free_maps(&c->dm);
+  c->mp.reset();
   if (c->z) cudaFree(c->z);
   if (c->res) cudaFree(c->res);
   if (c->part) cudaFree(c->part);

@@ -1,5 +1,6 @@
 // Internal layout of the opaque schur_ctx and helpers shared by the C-ABI translation units.
 #pragma once
+#include <memory>
 #include <string>
 
 #include "../../include/schur.h"
@@ -7,9 +8,19 @@
 #include "maps.h"
 
 
+namespace schur {
+// Partition of one (mesh, nsub, local_mode): host maps and their device copies, shared by every
+// context on the same device that uses that partition (it does not depend on beta).
+struct MapEntry {
+  HostMaps hm;
+  DevMaps dm;
+  int device = 0;
+  ~MapEntry();
+};
+}  // namespace schur
+
 struct schur_ctx {
-  schur::HostMaps hm;
-  schur::DevMaps dm;
+  std::shared_ptr<schur::MapEntry> mp;
   schur::EngineBase* eng = nullptr;
   schur_mesh mesh;
   schur_opts opts;
@@ -40,4 +51,5 @@ int ctx_ensure_outer(schur_ctx* c, int R);
 int ctx_outer(schur_ctx* c, const double* bre, const double* bim, int ldb, int R, double* x, int ldx, double* zout,
               int ldz, cudaStream_t st, schur_stats* stats);
 void kkt_free(schur_ctx* c);
+int get_partition(const schur_mesh* mesh, const schur_opts* opts, std::shared_ptr<MapEntry>* out, std::string* msg);
 }  // namespace schur

@@ -48,6 +48,10 @@ class EngineBase {
 
 constexpr int kMaxR = 16;
 
+// Keeps freed blocks of the current device's default memory pool cached in the process
+// (release threshold = unlimited), once per device.
+void configure_pool();
+
 EngineBase* make_engine_f64(const HostMaps* hm, const DevMaps* dm, double gamma);
 EngineBase* make_engine_f32(const HostMaps* hm, const DevMaps* dm, double gamma);
 

@@ -79,7 +79,8 @@ class Engine : public EngineBase {
   }
 
   ~Engine() override {
-    for (void* p : allocs_) cudaFree(p);
+    for (void* p : allocs_) cudaFreeAsync(p, ast_);
+    cudaStreamSynchronize(ast_);
     if (h_active_) cudaFreeHost(h_active_);
   }
 
@@ -87,6 +88,8 @@ class Engine : public EngineBase {
 
   int setup(cudaStream_t st, std::string* msg) override {
     const Geom& g = g_;
+    ast_ = st;
+    configure_pool();
     const size_t cxT = sizeof(cx<T>);
     const int bb = g.lb * g.lb;
     ENG_CK(alloc(&err_, 4 * sizeof(int)));
@@ -169,12 +172,11 @@ class Engine : public EngineBase {
       if (g.lb <= 32) {
         constexpr int CW = sizeof(T) == 4 ? 16 : 8;
         const int ncol = g.nD + g.nc, nchunk = (ncol + CW - 1) / CW, nwork = ncls_ * nchunk;
-        const size_t per_warp = (size_t)g.nl * CW * cxT;
-        const int wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (160 * 1024) / per_warp));
-        size_t smem = per_warp * wpb;
-        ENG_CK(cudaFuncSetAttribute(k_form_rr_warp<T, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int wpb = 8;
+        const int grid = std::max(1, std::min((nwork + wpb - 1) / wpb, 2 * nsm_));
+        ENG_CK(alloc(&Xws, (size_t)grid * wpb * g.nl * CW * cxT));
         prof_start(KC_FORM, st);
-        k_form_rr_warp<T, CW><<<(nwork + wpb - 1) / wpb, 32 * wpb, smem, st>>>(prr_, g, mv_, Dinv_, ncls_, F_, Frc_, Kcc_);
+        k_form_rr_warp<T, CW><<<grid, 32 * wpb, 0, st>>>(prr_, g, mv_, Dinv_, ncls_, F_, Frc_, Kcc_, Xws);
         prof_stop(KC_FORM, st);
         ENG_LAUNCH();
       } else {
@@ -316,6 +318,7 @@ class Engine : public EngineBase {
       return SCHUR_EINVAL;
     }
     const int m = std::max(1, std::min(max_iter, kMaxKdev - 1));
+    ast_ = st;
     int rc = ensure_ws(R, m, msg);
     if (rc) return rc;
     launches = 0;
@@ -444,9 +447,11 @@ class Engine : public EngineBase {
 
  private:
   template <class P>
+  // Stream-ordered allocations from the device's default memory pool (kept by the pool after a
+  // context is destroyed, so the next setup on the same device does not map memory again).
   cudaError_t alloc(P** p, size_t bytes) {
     void* v = nullptr;
-    cudaError_t e = cudaMalloc(&v, std::max<size_t>(bytes, 16));
+    cudaError_t e = cudaMallocAsync(&v, std::max<size_t>(bytes, 16), ast_);
     if (e == cudaSuccess) {
       allocs_.push_back(v);
       *p = reinterpret_cast<P*>(v);
@@ -456,7 +461,7 @@ class Engine : public EngineBase {
   void free_one(void* p) {
     auto it = std::find(allocs_.begin(), allocs_.end(), p);
     if (it != allocs_.end()) {
-      cudaFree(p);
+      cudaFreeAsync(p, ast_);
       allocs_.erase(it);
     }
   }
@@ -741,6 +746,7 @@ class Engine : public EngineBase {
   double *cs_c_ = nullptr, *nrm_part_ = nullptr, *beta0_ = nullptr, *inv_nrm_ = nullptr, *resid_ = nullptr;
   int *active_ = nullptr, *kk_ = nullptr, *bad_ = nullptr;
   int* h_active_ = nullptr;
+  cudaStream_t ast_ = nullptr;  // stream of the current setup / solve (stream-ordered allocations)
 };
 
 }  // namespace schur

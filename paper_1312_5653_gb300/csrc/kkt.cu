@@ -68,7 +68,7 @@ static int grid_for(long long n) { return std::max(1, (int)std::min<long long>((
 // scratch columns blocks of n x R.
 static int mass_inverse(schur_ctx* c, const double* t, int ldt, double* w, int ldw, int R, int deg, double* scr,
                         cudaStream_t st) {
-  const Geom& g = c->hm.g;
+  const Geom& g = c->mp->hm.g;
   const long long n = g.n;
   const double lo = std::pow(0.5, g.dim), hi = std::pow(1.5, g.dim);
   const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
@@ -111,7 +111,7 @@ static int cheb_degree(int dim, double tol) {
 static int kkt_ws(schur_ctx* c, int R) {
   if (R <= c->kkt_R) return SCHUR_OK;
   kkt_free(c);
-  const size_t n = (size_t)c->hm.g.n;
+  const size_t n = (size_t)c->mp->hm.g.n;
   // 14 blocks of 3n x R (MINRES vectors) + 4 of n x R (Chebyshev scratch, contiguous column copies)
   KKT_CK(cudaMalloc(&c->kkt_buf, (14 * 3 * n + 4 * n) * R * sizeof(double)));
   KKT_CK(cudaMalloc(&c->kkt_part, (size_t)R * 1216 * sizeof(double)));
@@ -148,7 +148,7 @@ static int dots(schur_ctx* c, long long len, const double* x, int ldx, const dou
 }
 
 static int kkt_apply_impl(schur_ctx* c, const double* v, double* r, int R, int ld, cudaStream_t st) {
-  const Geom& g = c->hm.g;
+  const Geom& g = c->mp->hm.g;
   const long long n = g.n;
   Coef27 sten = make_coef(g, 1.0);
   const int gs = grid_for(n);
@@ -173,7 +173,7 @@ static int kkt_apply_impl(schur_ctx* c, const double* v, double* r, int R, int l
 
 // z = P_mgw^{-1} r for R columns (R <= kMaxR), leading dimension ld >= 3n
 static int kkt_precond_impl(schur_ctx* c, const double* r, double* z, int R, int ld, cudaStream_t st) {
-  const Geom& g = c->hm.g;
+  const Geom& g = c->mp->hm.g;
   const long long n = g.n;
   int rc = kkt_ws(c, R);
   if (rc) return rc;
@@ -217,14 +217,14 @@ extern "C" {
 int schur_kkt_apply(schur_ctx* c, const double* v, double* r, int nrhs, int ld, void* stream) {
   if (!c || (nrhs > 0 && (!v || !r)) || nrhs < 0) return set_error(SCHUR_EINVAL, "bad arguments");
   if (nrhs == 0) return SCHUR_OK;
-  if ((long long)ld < 3 * c->hm.g.n) return set_error(SCHUR_EINVAL, "ld < 3n");
+  if ((long long)ld < 3 * c->mp->hm.g.n) return set_error(SCHUR_EINVAL, "ld < 3n");
   return kkt_apply_impl(c, v, r, nrhs, ld, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int schur_kkt_precond_apply(schur_ctx* c, const double* r, double* z, int nrhs, int ld, void* stream) {
   if (!c || (nrhs > 0 && (!r || !z)) || nrhs < 0) return set_error(SCHUR_EINVAL, "bad arguments");
   if (nrhs == 0) return SCHUR_OK;
-  if ((long long)ld < 3 * c->hm.g.n) return set_error(SCHUR_EINVAL, "ld < 3n");
+  if ((long long)ld < 3 * c->mp->hm.g.n) return set_error(SCHUR_EINVAL, "ld < 3n");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   for (int r0 = 0; r0 < nrhs; r0 += kMaxR) {
     int R = std::min(kMaxR, nrhs - r0);
@@ -238,9 +238,9 @@ int schur_kkt_precond_apply(schur_ctx* c, const double* r, double* z, int nrhs, 
 int schur_apply_S(schur_ctx* c, const double* x, double* y, int nrhs, int ld, void* stream) {
   if (!c || (nrhs > 0 && (!x || !y)) || nrhs < 0) return set_error(SCHUR_EINVAL, "bad arguments");
   if (nrhs == 0) return SCHUR_OK;
-  if ((long long)ld < c->hm.g.n) return set_error(SCHUR_EINVAL, "ld < n");
+  if ((long long)ld < c->mp->hm.g.n) return set_error(SCHUR_EINVAL, "ld < n");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const Geom& g = c->hm.g;
+  const Geom& g = c->mp->hm.g;
   const long long n = g.n;
   Coef27 sten = make_coef(g, 1.0);
   const int gs = grid_for(n);
@@ -274,7 +274,7 @@ int schur_kkt_minres(schur_ctx* c, const double* rhs, double* sol, int nrhs, int
     return set_error(SCHUR_EINVAL, "bad arguments");
   if (iters) *iters = 0;
   if (nrhs == 0) return SCHUR_OK;
-  const long long n3 = 3 * c->hm.g.n;
+  const long long n3 = 3 * c->mp->hm.g.n;
   if ((long long)ld < n3) return set_error(SCHUR_EINVAL, "ld < 3n");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int status = SCHUR_OK, itmax = 0;

@@ -129,6 +129,17 @@ std::string build_maps(int dim, const int* nel, const int* nsub, int local_mode,
   m->sd_lam.assign((size_t)g.nsd * g.nD * g.maxdeg, 0);
   m->sd_minv.assign((size_t)g.nsd * g.nD, 0.0);
   m->lam_side.clear();
+  {
+    // multipliers per subdomain pair and shared node: faces 1, 3D edges 6 per node and 4 owners
+    long long est = 0;
+    for (int a = 0; a < dim; ++a) {
+      long long faces = (long long)(g.nsub[a] - 1);
+      for (int b = 0; b < dim; ++b)
+        if (b != a) faces *= (long long)(g.nel[b] - 1);
+      est += faces;
+    }
+    m->lam_side.reserve((size_t)(2 * est * (dim == 3 ? 2 : 1) + 16));
+  }
   std::vector<int> deg((size_t)g.nsd * g.nD, 0);
   for (int sd = 0; sd < g.nsd; ++sd) {
     int S[3];
@@ -144,7 +155,8 @@ std::string build_maps(int dim, const int* nel, const int* nsub, int local_mode,
       }
       if (dir) continue;
       // all subdomains holding global node G, with the node's local coordinates there
-      std::vector<std::pair<int, int>> owners;  // (subdomain, slot)
+      std::pair<int, int> owners[8];  // (subdomain, slot), at most 2^(dim-1) for a non-vertex node
+      int nown = 0;
       int cand[3][2], ncand[3];
       for (int a = 0; a < 3; ++a) { ncand[a] = 1; cand[a][0] = 0; }
       for (int a = 0; a < dim; ++a) {
@@ -168,12 +180,14 @@ std::string build_maps(int dim, const int* nel, const int* nsub, int local_mode,
             int sdt = crd2idx(T, g.nsub, dim);
             int slot = m->node_slot[crd2idx(lt, ext, dim)];
             if (slot < 0) return "internal error: shared node is not an interface slot";
-            owners.push_back({sdt, slot});
+            if (nown >= 8) return "internal error: too many owners";
+            owners[nown++] = {sdt, slot};
           }
-      std::sort(owners.begin(), owners.end());
-      int mult = (int)owners.size();
+      std::sort(owners, owners + nown);
+      int mult = nown;
       m->sd_minv[(size_t)sd * g.nD + j] = 1.0 / mult;
-      for (auto& o : owners) {
+      for (int oi = 0; oi < nown; ++oi) {
+        const auto& o = owners[oi];
         if (o.first <= sd) continue;
         int lam = (int)(m->lam_side.size() / 2);
         m->lam_side.push_back(sd * g.nD + j);

@@ -246,15 +246,14 @@ __global__ void k_local_solve_warp(StencilProv<T> P, Geom g, MapsView m, const c
 // F, Frc, Kcc of each class, one warp per (class, chunk of C columns); solution in shared memory.
 template <class T, int C>
 __global__ void k_form_rr_warp(StencilProv<T> P, Geom g, MapsView m, const cx<T>* __restrict__ Dinv, int ncls,
-                               cx<T>* F, cx<T>* Frc, cx<double>* Kcc) {
+                               cx<T>* F, cx<T>* Frc, cx<double>* Kcc, cx<T>* Xws) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int nD = g.nD, nc = g.nc, ncol = nD + nc, nchunk = (ncol + C - 1) / C;
-  const int w = blockIdx.x * wpb + wib;
-  if (w >= ncls * nchunk) return;
-  const int q = w / nchunk, col0 = (w % nchunk) * C;
   const int b = P.ly.b, L = P.ly.L, dim = g.dim;
-  extern __shared__ unsigned char smraw[];
-  cx<T>* X = reinterpret_cast<cx<T>*>(smraw) + (size_t)wib * g.nl * C;
+  // per-warp solution buffer in global memory (column-major: node fastest), persistent warps
+  cx<T>* X = Xws + (size_t)(blockIdx.x * wpb + wib) * g.nl * C;
+  for (int w = blockIdx.x * wpb + wib; w < ncls * nchunk; w += gridDim.x * wpb) {
+  const int q = w / nchunk, col0 = (w % nchunk) * C;
   P.select(q, m.cls_code);
   const int code = P.code;
   int ext[3];
@@ -301,6 +300,8 @@ __global__ void k_form_rr_warp(StencilProv<T> P, Geom g, MapsView m, const cx<T>
       }
     }
     Kcc[((size_t)q * nc + c1) * nc + c2] = ccast<double>(v);
+  }
+  __syncwarp();
   }
 }
 
