@@ -199,6 +199,46 @@ int schur_profile_end(schur_kernel_time* out, int cap, int* count);
 const char* schur_kernel_category_name(int category);
 long long schur_launch_count(const schur_ctx* ctx);
 
+/* ---------------------------------------------------------------------------------------------
+ * Serving.  A server owns worker threads (one CUDA stream each, on the device current at
+ * creation) and a device-resident cache of contexts keyed by (mesh, beta) with the server's
+ * precision, evicted least-recently-used when a new context would exceed device_mem_budget.
+ * Subdomains are 16 elements per side in 2D and 8 in 3D (or the nearest divisor of nel).
+ * schur_submit queues a request (host buffers b, x of n x nrhs, column-major, ld = n; both must
+ * stay valid until the request completes).  A request is admitted when its context is cached or
+ * memory for a new one can be freed; queued requests with the same (mesh, beta) are solved
+ * together as one multi-RHS solve of up to max_batch_rhs columns (requests arriving while other
+ * work runs join the next batch of their key); batches of different keys run concurrently on the
+ * worker streams.  Results equal those of separate schur_solve calls within the solver
+ * tolerance (each column is refined until every column of the batch meets tol).
+ * schur_poll: 0 done (st filled; st->ms_solve = submit-to-completion latency in ms), 1 pending,
+ * <0 the request's error.  schur_wait: the same after waiting at most timeout_ms
+ * (SCHUR_ETIMEOUT if still pending).  schur_submit returns SCHUR_EBUSY when the request can never
+ * fit the budget.  No paper counterpart (Sec. 4 notes that multiple right-hand sides favour reusing
+ * factorisations). */
+typedef struct schur_server schur_server;
+typedef struct {
+  size_t device_mem_budget; /* bytes of device memory the cache and workspaces may hold        */
+  int workers;              /* worker threads / streams (concurrent batches)                   */
+  int precision;            /* SCHUR_FP64 or SCHUR_MIXED                                       */
+  double tol;               /* outer tolerance of every solve                                  */
+  int max_batch_rhs;        /* columns per batched solve                                       */
+  int max_iter;             /* GMRES iterations per inner solve                                */
+  int reserved[4];
+} schur_server_opts;
+typedef struct {
+  int cached_contexts, queued;
+  long long completed, bytes_reserved;
+} schur_server_info_t;
+void schur_server_default_opts(schur_server_opts* opts);
+int schur_server_create(const schur_server_opts* opts, schur_server** out);
+int schur_submit(schur_server* srv, const schur_mesh* mesh, double beta, const double* b_host, int nrhs,
+                 double* x_host, long long* ticket);
+int schur_poll(schur_server* srv, long long ticket, schur_stats* st);
+int schur_wait(schur_server* srv, long long ticket, double timeout_ms, schur_stats* st);
+int schur_server_info(schur_server* srv, schur_server_info_t* info);
+void schur_server_destroy(schur_server* srv);
+
 int schur_get_info(const schur_ctx* ctx, schur_info_t* info);
 long long schur_ndof(const schur_mesh* mesh);
 void schur_destroy(schur_ctx* ctx);

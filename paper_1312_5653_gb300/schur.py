@@ -69,6 +69,8 @@ EXPORTS = [
     "schur_kkt_minres", "schur_partition", "schur_partition_export", "schur_get_info", "schur_ndof",
     "schur_destroy", "schur_strerror", "schur_last_error", "schur_debug_operator", "schur_profile_begin",
     "schur_profile_end", "schur_kernel_category_name", "schur_launch_count", "schur_apply_S_static",
+    "schur_server_default_opts", "schur_server_create", "schur_submit", "schur_poll", "schur_wait",
+    "schur_server_info", "schur_server_destroy",
 ]
 
 
@@ -326,3 +328,99 @@ class Solver:
         _check(self.lib.schur_debug_operator(self.ctx, which, cls, out.ctypes.data_as(ctypes.c_void_p),
                                              out.size // 2), "schur_debug_operator")
         return out[..., 0] + 1j * out[..., 1]
+
+
+class schur_server_opts(ctypes.Structure):
+    _fields_ = [("device_mem_budget", ctypes.c_size_t), ("workers", ctypes.c_int), ("precision", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_batch_rhs", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
+
+
+class schur_server_info_t(ctypes.Structure):
+    _fields_ = [("cached_contexts", ctypes.c_int), ("queued", ctypes.c_int), ("completed", ctypes.c_longlong),
+                ("bytes_reserved", ctypes.c_longlong)]
+
+
+def _load_server_syms(lib):
+    if getattr(lib, "_server_bound", False):
+        return lib
+    P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    lib.schur_server_default_opts.restype = None
+    lib.schur_server_default_opts.argtypes = [ctypes.POINTER(schur_server_opts)]
+    lib.schur_server_create.restype = I
+    lib.schur_server_create.argtypes = [ctypes.POINTER(schur_server_opts), ctypes.POINTER(P)]
+    lib.schur_submit.restype = I
+    lib.schur_submit.argtypes = [P, ctypes.POINTER(schur_mesh), D, P, I, P, ctypes.POINTER(LL)]
+    lib.schur_poll.restype = I
+    lib.schur_poll.argtypes = [P, LL, ctypes.POINTER(schur_stats)]
+    lib.schur_wait.restype = I
+    lib.schur_wait.argtypes = [P, LL, D, ctypes.POINTER(schur_stats)]
+    lib.schur_server_info.restype = I
+    lib.schur_server_info.argtypes = [P, ctypes.POINTER(schur_server_info_t)]
+    lib.schur_server_destroy.restype = None
+    lib.schur_server_destroy.argtypes = [P]
+    lib._server_bound = True
+    return lib
+
+
+class Server:
+    """schur_server: submit host right-hand sides, poll or wait for host results."""
+
+    def __init__(self, budget_bytes=16 << 30, workers=4, precision=SCHUR_MIXED, tol=1e-10, max_batch_rhs=16,
+                 max_iter=300):
+        self.lib = _load_server_syms(load())
+        o = schur_server_opts()
+        self.lib.schur_server_default_opts(ctypes.byref(o))
+        o.device_mem_budget = int(budget_bytes)
+        o.workers = workers
+        o.precision = precision
+        o.tol = tol
+        o.max_batch_rhs = max_batch_rhs
+        o.max_iter = max_iter
+        self.srv = ctypes.c_void_p()
+        _check(self.lib.schur_server_create(ctypes.byref(o), ctypes.byref(self.srv)), "schur_server_create")
+        self._bufs = {}
+
+    def submit(self, dim, nel, beta, b):
+        """b: float64 host array (n,) or (nrhs, n); returns a ticket."""
+        import numpy as np
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.empty_like(b)
+        nrhs = 1 if b.ndim == 1 else b.shape[0]
+        t = ctypes.c_longlong(0)
+        rc = self.lib.schur_submit(self.srv, ctypes.byref(make_mesh(dim, nel)), float(beta),
+                                   b.ctypes.data_as(ctypes.c_void_p), nrhs, x.ctypes.data_as(ctypes.c_void_p),
+                                   ctypes.byref(t))
+        _check(rc, "schur_submit")
+        self._bufs[t.value] = (b, x)
+        return t.value
+
+    def poll(self, ticket):
+        """(done, x or None, stats)"""
+        st = schur_stats()
+        rc = self.lib.schur_poll(self.srv, ticket, ctypes.byref(st))
+        if rc == 1:
+            return False, None, None
+        _check(rc, "schur_poll")
+        return True, self._bufs.pop(ticket)[1], st.as_dict()
+
+    def wait(self, ticket, timeout_ms=600000.0):
+        st = schur_stats()
+        _check(self.lib.schur_wait(self.srv, ticket, float(timeout_ms), ctypes.byref(st)), "schur_wait")
+        return self._bufs.pop(ticket)[1], st.as_dict()
+
+    def info(self):
+        i = schur_server_info_t()
+        _check(self.lib.schur_server_info(self.srv, ctypes.byref(i)), "schur_server_info")
+        return {k: getattr(i, k) for k, _ in i._fields_}
+
+    def close(self):
+        if self.srv:
+            self.lib.schur_server_destroy(self.srv)
+            self.srv = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
