@@ -284,6 +284,17 @@ class Engine : public EngineBase {
         pf.ly = cprov_.ly;
         pf.CA = CAf;
         pf.CB = CBf;
+        const size_t staged = ((size_t)cbb + 2 * (size_t)g.cb * 32) * sizeof(cx<float>);
+        if (g.cb <= 128 && staged <= 200 * 1024) {
+          const int grid_s = std::max(1, std::min((g.ncor + 31) / 32, 2 * nsm_));
+          ENG_CK(alloc(&Xws, (size_t)grid_s * g.ncor * 32 * sizeof(cx<float>)));
+          ENG_CK(cudaFuncSetAttribute(k_coarse_inverse_staged<T, float>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)staged));
+          prof_start(KC_COARSE_INV, st);
+          k_coarse_inverse_staged<T, float><<<grid_s, 256, staged, st>>>(pf, Df, g.ncor, Xws, Kinv_);
+          prof_stop(KC_COARSE_INV, st);
+          ENG_LAUNCH();
+        } else {
         ENG_CK(alloc(&Xws, (size_t)grid * g.ncor * C * sizeof(cx<float>)));
         size_t smem2 = 2 * (size_t)g.cb * C * sizeof(cx<float>);
         ENG_CK(cudaFuncSetAttribute(k_coarse_inverse<T, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -292,6 +303,7 @@ class Engine : public EngineBase {
         k_coarse_inverse<T, float><<<grid, 256, smem2, st>>>(pf, Df, g.ncor, C, Xws, Kinv_);
         prof_stop(KC_COARSE_INV, st);
         ENG_LAUNCH();
+        }
         ENG_CK(cudaStreamSynchronize(st));
         free_one(Xws);
         free_one(Df);

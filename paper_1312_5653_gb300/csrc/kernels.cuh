@@ -239,6 +239,98 @@ __global__ void k_coarse_inverse(StoredProv<S> P, const cx<S>* __restrict__ Dinv
   }
 }
 
+// The same columns with each layer block D_K^{-1} staged in shared memory (layer size b <= 128):
+// a CTA solves 32 columns; thread (row i, group of 8 columns) keeps 8 accumulators, so every
+// staged D entry feeds 8 complex multiply-adds.
+template <class T, class S>
+__global__ void __launch_bounds__(256) k_coarse_inverse_staged(StoredProv<S> P, const cx<S>* __restrict__ Dinv,
+                                                               int ncor, cx<S>* Xws, cx<T>* Kinv) {
+  constexpr int CS = 32, CG = 8;
+  extern __shared__ unsigned char smraw[];
+  const int b = P.ly.b, L = P.ly.L, bb = b * b, nt = nbr_count(P.ly.dim), tid = threadIdx.x;
+  cx<S>* Dsm = reinterpret_cast<cx<S>*>(smraw);
+  cx<S>* Tb = Dsm + bb;
+  cx<S>* Ep = Tb + b * CS;
+  cx<S>* X = Xws + (size_t)blockIdx.x * ncor * CS;
+  const int nchunk = (ncor + CS - 1) / CS;
+  const int ri = tid & 63, cg = tid >> 6;  // 4 groups of 8 columns
+  for (int w = blockIdx.x; w < nchunk; w += gridDim.x) {
+    const int col0 = w * CS;
+    for (int K = 0; K < L; ++K) {
+      for (int e = tid; e < bb; e += 256) Dsm[e] = Dinv[(size_t)K * bb + e];
+      for (int e = tid; e < b * CS; e += 256) {
+        int i = e / CS, c = e - i * CS, col = col0 + c;
+        cx<S> t = mkc<S>((col < ncor && K * b + i == col) ? S(1) : S(0), S(0));
+        if (K > 0)
+          for (int tt = 0; tt < nt; ++tt) {
+            int k = nbr_of(P.ly, i, tt);
+            if (k >= 0) cfms(t, P.Al(K - 1, i, tt), Ep[k * CS + c]);
+          }
+        Tb[e] = t;
+      }
+      __syncthreads();
+      for (int i0 = 0; i0 < b; i0 += 64) {
+        const int i = i0 + ri;
+        cx<S> acc[CG];
+#pragma unroll
+        for (int j = 0; j < CG; ++j) acc[j] = mkc<S>(0, 0);
+        if (i < b)
+          for (int mm = 0; mm < b; ++mm) {
+            const cx<S> d = Dsm[mm * b + i];
+#pragma unroll
+            for (int j = 0; j < CG; ++j) cfma(acc[j], d, Tb[mm * CS + cg * CG + j]);
+          }
+        __syncthreads();  // all reads of Ep (coupling) are done before it is overwritten
+        if (i < b)
+#pragma unroll
+          for (int j = 0; j < CG; ++j) {
+            Ep[i * CS + cg * CG + j] = acc[j];
+            X[(size_t)(K * b + i) * CS + cg * CG + j] = acc[j];
+          }
+      }
+      __syncthreads();
+    }
+    for (int K = L - 2; K >= 0; --K) {
+      for (int e = tid; e < bb; e += 256) Dsm[e] = Dinv[(size_t)K * bb + e];
+      for (int e = tid; e < b * CS; e += 256) {
+        int i = e / CS, c = e - i * CS;
+        cx<S> u = mkc<S>(0, 0);
+        for (int tt = 0; tt < nt; ++tt) {
+          int k = nbr_of(P.ly, i, tt);
+          if (k >= 0) cfma(u, P.Al(K, k, nt - 1 - tt), Ep[k * CS + c]);
+        }
+        Tb[e] = u;
+      }
+      __syncthreads();
+      for (int i0 = 0; i0 < b; i0 += 64) {
+        const int i = i0 + ri;
+        cx<S> acc[CG];
+#pragma unroll
+        for (int j = 0; j < CG; ++j) acc[j] = i < b ? X[(size_t)(K * b + i) * CS + cg * CG + j] : mkc<S>(0, 0);
+        if (i < b)
+          for (int mm = 0; mm < b; ++mm) {
+            const cx<S> d = Dsm[mm * b + i];
+#pragma unroll
+            for (int j = 0; j < CG; ++j) cfms(acc[j], d, Tb[mm * CS + cg * CG + j]);
+          }
+        __syncthreads();
+        if (i < b)
+#pragma unroll
+          for (int j = 0; j < CG; ++j) {
+            Ep[i * CS + cg * CG + j] = acc[j];
+            X[(size_t)(K * b + i) * CS + cg * CG + j] = acc[j];
+          }
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < ncor * CS; e += 256) {
+      int row = e / CS, c = e - row * CS, col = col0 + c;
+      if (col < ncor) Kinv[(size_t)col * ncor + row] = ccast<T>(X[e]);
+    }
+    __syncthreads();
+  }
+}
+
 template <class T, class S>
 __global__ void k_convert(const cx<S>* __restrict__ in, cx<T>* out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -334,6 +426,7 @@ __global__ void k_coarse_apply(const cx<T>* __restrict__ Kinv, int ncor, const c
   cx<T> acc[MR];
   for (int r = 0; r < MR; ++r) acc[r] = czero<T>();
   const cx<T>* Krow = Kinv + (size_t)row * ncor;
+#pragma unroll 4
   for (int j = lane; j < ncor; j += 32) {
     cx<T> a = Krow[j];
 #pragma unroll
