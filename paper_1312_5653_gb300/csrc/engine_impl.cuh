@@ -232,85 +232,12 @@ class Engine : public EngineBase {
       cprov_.ly.L = g.cL;
       cprov_.CA = CA_;
       cprov_.CB = CB_;
-      ENG_CK(alloc(&Dc_, (size_t)g.cL * cbb * sizeof(cx<double>)));
-      prof_start(KC_COARSE_SETUP, st);
-      cudaError_t ce = coarse_factor_cluster(cprov_, Dc_, err_ + 2, st, &coarse_cluster_);
-      prof_stop(KC_COARSE_SETUP, st);
-      if (ce != cudaSuccess) {
-        // no cluster launch available: one CTA does the whole factorisation
-        coarse_cluster_ = 0;
-        size_t need = (2 * (size_t)cbb + 2 * g.cb) * sizeof(cx<double>);
-        int use_smem = need <= 200 * 1024;
-        size_t smem = use_smem ? need : 2 * g.cb * sizeof(cx<double>);
-        cx<double>* gws = nullptr;
-        if (!use_smem) ENG_CK(alloc(&gws, 2 * (size_t)cbb * sizeof(cx<double>)));
-        ENG_CK(cudaFuncSetAttribute(k_factor<double, StoredProv<double>>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        prof_start(KC_COARSE_SETUP, st);
-        k_factor<double, StoredProv<double>><<<1, 1024, smem, st>>>(cprov_, nullptr, Dc_, gws, use_smem, err_ + 2);
-        prof_stop(KC_COARSE_SETUP, st);
-      }
-      ENG_LAUNCH();
+      // FP64 block cyclic reduction over the coarse layers, explicit inverse in precision T
       ENG_CK(alloc(&Kinv_, (size_t)g.ncor * g.ncor * cxT));
       op_bytes_ += (long long)g.ncor * g.ncor * cxT;
-      const int C = 16, nchunk = (g.ncor + C - 1) / C;
-      int grid = std::min(nchunk, 4 * nsm_);
-      if (sizeof(T) == sizeof(double)) {
-        cx<double>* Xws = nullptr;
-        ENG_CK(alloc(&Xws, (size_t)grid * g.ncor * C * sizeof(cx<double>)));
-        size_t smem2 = 2 * (size_t)g.cb * C * sizeof(cx<double>);
-        ENG_CK(cudaFuncSetAttribute(k_coarse_inverse<T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem2));
-        prof_start(KC_COARSE_INV, st);
-        k_coarse_inverse<T, double><<<grid, 256, smem2, st>>>(cprov_, Dc_, g.ncor, C, Xws, Kinv_);
-        prof_stop(KC_COARSE_INV, st);
-        ENG_LAUNCH();
-        ENG_CK(cudaStreamSynchronize(st));
-        free_one(Xws);
-      } else {
-        // FP32 copies of the FP64 factor and coupling blocks; columns of the inverse in FP32
-        const long long nD = (long long)g.cL * cbb, nA = (long long)g.cL * g.cb * nt;
-        cx<float>*Df = nullptr, *CAf = nullptr, *CBf = nullptr, *Xws = nullptr;
-        ENG_CK(alloc(&Df, nD * sizeof(cx<float>)));
-        ENG_CK(alloc(&CAf, nA * sizeof(cx<float>)));
-        ENG_CK(alloc(&CBf, nA * sizeof(cx<float>)));
-        prof_start(KC_COARSE_INV, st);
-        k_convert<float, double><<<std::min<long long>((nD + 255) / 256, 4 * nsm_), 256, 0, st>>>(Dc_, Df, nD);
-        k_convert<float, double><<<std::min<long long>((nA + 255) / 256, 4 * nsm_), 256, 0, st>>>(CA_, CAf, nA);
-        k_convert<float, double><<<std::min<long long>((nA + 255) / 256, 4 * nsm_), 256, 0, st>>>(CB_, CBf, nA);
-        prof_stop(KC_COARSE_INV, st);
-        ENG_LAUNCH();
-        StoredProv<float> pf;
-        pf.ly = cprov_.ly;
-        pf.CA = CAf;
-        pf.CB = CBf;
-        const size_t staged = ((size_t)cbb + 2 * (size_t)g.cb * 32) * sizeof(cx<float>);
-        if (g.cb <= 128 && staged <= 200 * 1024) {
-          const int grid_s = std::max(1, std::min((g.ncor + 31) / 32, 2 * nsm_));
-          ENG_CK(alloc(&Xws, (size_t)grid_s * g.ncor * 32 * sizeof(cx<float>)));
-          ENG_CK(cudaFuncSetAttribute(k_coarse_inverse_staged<T, float>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)staged));
-          prof_start(KC_COARSE_INV, st);
-          k_coarse_inverse_staged<T, float><<<grid_s, 256, staged, st>>>(pf, Df, g.ncor, Xws, Kinv_);
-          prof_stop(KC_COARSE_INV, st);
-          ENG_LAUNCH();
-        } else {
-        ENG_CK(alloc(&Xws, (size_t)grid * g.ncor * C * sizeof(cx<float>)));
-        size_t smem2 = 2 * (size_t)g.cb * C * sizeof(cx<float>);
-        ENG_CK(cudaFuncSetAttribute(k_coarse_inverse<T, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem2));
-        prof_start(KC_COARSE_INV, st);
-        k_coarse_inverse<T, float><<<grid, 256, smem2, st>>>(pf, Df, g.ncor, C, Xws, Kinv_);
-        prof_stop(KC_COARSE_INV, st);
-        ENG_LAUNCH();
-        }
-        ENG_CK(cudaStreamSynchronize(st));
-        free_one(Xws);
-        free_one(Df);
-        free_one(CAf);
-        free_one(CBf);
-      }
-
+      (void)cbb;
+      int crc = coarse_bcr<T>(cprov_, Kinv_, err_ + 2, st, msg, &launches);
+      if (crc) return crc;
     }
     ENG_CK(cudaStreamSynchronize(st));
     int herr[4];
