@@ -73,6 +73,22 @@ void free_maps(DevMaps* dm) {
   *dm = DevMaps();
 }
 
+cudaError_t smem_attr(const void* func, int bytes) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, int>> set;  // (kernel, limit set so far)
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto& kv : set)
+    if (kv.first == func) {
+      if (kv.second >= bytes) return cudaSuccess;
+      cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+      if (e == cudaSuccess) kv.second = bytes;
+      return e;
+    }
+  cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) set.push_back({func, bytes});
+  return e;
+}
+
 void configure_pool() {
   static std::mutex mu;
   static bool done[64] = {false};

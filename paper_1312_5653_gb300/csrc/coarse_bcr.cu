@@ -214,7 +214,7 @@ static cudaError_t launch_gj_batch(const cx<double>* Din, cx<double>* Dout, cons
     if (CL > 1 && nblk * CL > 4 * 152 && CL > 4) continue;  // keep many clusters resident at once
     size_t smem = bcr_gj_smem(b, CL);
     if (smem > 200 * 1024) continue;
-    cudaError_t e = cudaFuncSetAttribute(k_gj_batch_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_attr((const void*)k_gj_batch_cluster, (int)smem);
     if (e == cudaSuccess && CL > 8)
       e = cudaFuncSetAttribute(k_gj_batch_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) {

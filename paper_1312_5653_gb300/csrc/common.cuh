@@ -8,6 +8,11 @@
 
 namespace schur {
 
+// Raises the dynamic shared-memory limit of kernel `func` to at least `bytes`.  The limit is a
+// per-process attribute shared by every thread, so it only ever grows (under a lock): a thread
+// configuring a smaller launch never undercuts a concurrent larger one.
+cudaError_t smem_attr(const void* func, int bytes);
+
 constexpr int kMaxRdev = 16;   // right-hand sides per FETI-DP solve
 constexpr int kMaxKdev = 512;  // Krylov basis size bound (max_iter < kMaxKdev)
 

@@ -126,7 +126,7 @@ class Engine : public EngineBase {
     if (g.lb <= 32) {
       const int wpb = 8;
       size_t smem = (size_t)wpb * (2 * bb + 2 * g.lb) * cxT;
-      ENG_CK(cudaFuncSetAttribute(k_factor_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      ENG_CK(smem_attr((const void*)k_factor_warp<T>, (int)smem));
       prof_start(KC_FACTOR, st);
       k_factor_warp<T><<<(ncls_ + wpb - 1) / wpb, 32 * wpb, smem, st>>>(prr_, dm_->cls_code, ncls_, Dinv_, err_);
       prof_stop(KC_FACTOR, st);
@@ -137,7 +137,7 @@ class Engine : public EngineBase {
       size_t smem = use_smem ? need : 2 * g.lb * cxT;
       cx<T>* gws = nullptr;
       if (!use_smem) ENG_CK(alloc(&gws, (size_t)ncls_ * 2 * bb * cxT));
-      ENG_CK(cudaFuncSetAttribute(k_factor<T, StencilProv<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      ENG_CK(smem_attr((const void*)k_factor<T, StencilProv<T>>, (int)smem));
       int thr = bb >= 1024 ? 512 : 256;
       prof_start(KC_FACTOR, st);
       k_factor<T, StencilProv<T>><<<ncls_, thr, smem, st>>>(prr_, dm_->cls_code, Dinv_, gws, use_smem, err_);
@@ -154,7 +154,7 @@ class Engine : public EngineBase {
       size_t smem = use_smem ? need : 2 * g.ib * cxT;
       cx<T>* gws = nullptr;
       if (!use_smem) ENG_CK(alloc(&gws, 2 * (size_t)ibb * cxT));
-      ENG_CK(cudaFuncSetAttribute(k_factor<T, StencilProv<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      ENG_CK(smem_attr((const void*)k_factor<T, StencilProv<T>>, (int)smem));
       prof_start(KC_FACTOR, st);
       k_factor<T, StencilProv<T>><<<1, ibb >= 1024 ? 512 : 256, smem, st>>>(pii_, dm_->cls_code, Dii, gws, use_smem, err_ + 1);
       prof_stop(KC_FACTOR, st);
@@ -184,7 +184,7 @@ class Engine : public EngineBase {
         int grid = std::min(ncls_ * nchunk, 8 * nsm_);
         ENG_CK(alloc(&Xws, (size_t)grid * g.nl * C * cxT));
         size_t smem = 2 * (size_t)g.lb * C * cxT;
-        ENG_CK(cudaFuncSetAttribute(k_form_rr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ENG_CK(smem_attr((const void*)k_form_rr<T>, (int)smem));
         prof_start(KC_FORM, st);
         k_form_rr<T><<<grid, 256, smem, st>>>(prr_, g, mv_, Dinv_, ncls_, C, Xws, F_, Frc_, Kcc_);
         prof_stop(KC_FORM, st);
@@ -196,7 +196,7 @@ class Engine : public EngineBase {
       ENG_CK(alloc(&Xi, (size_t)nchunk2 * g.ni * C * cxT));
       ENG_CK(alloc(&Sbase, (size_t)g.nD * g.nD * cxT));
       size_t smem2 = 2 * (size_t)g.ib * C * cxT;
-      ENG_CK(cudaFuncSetAttribute(k_form_ii<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+      ENG_CK(smem_attr((const void*)k_form_ii<T>, (int)smem2));
       prof_start(KC_FORM, st);
       k_form_ii<T><<<nchunk2, 256, smem2, st>>>(pii_, g, mv_, Dii, C, Xi, Sbase);
       prof_stop(KC_FORM, st);
@@ -476,12 +476,12 @@ class Engine : public EngineBase {
     int thr = std::min(256, ((g.lb * R + 31) / 32) * 32);
     size_t smem = 2 * (size_t)g.lb * R * sizeof(cx<T>);
     if (rhs_split) {
-      ENG_CK(cudaFuncSetAttribute(k_local_rhs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      ENG_CK(smem_attr((const void*)k_local_rhs<T>, (int)smem));
       prof_start(cat, st);
       k_local_rhs<T><<<g.nsd, thr, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, R, Xs_, VD_, Tc_);
       prof_stop(cat, st);
     } else {
-      ENG_CK(cudaFuncSetAttribute(k_recover<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      ENG_CK(smem_attr((const void*)k_recover<T>, (int)smem));
       prof_start(cat, st);
       k_recover<T><<<g.nsd, thr, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_);
       prof_stop(cat, st);
@@ -511,7 +511,7 @@ class Engine : public EngineBase {
     cx<T>* tc = want_tc ? Tc_ : nullptr;
 #define LA_CASE(SC, MR)                                                                                 \
   do {                                                                                                  \
-    ENG_CK(cudaFuncSetAttribute(k_local_apply<T, SC, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+    ENG_CK(smem_attr((const void*)k_local_apply<T, SC, MR>,                                       \
                                 (int)std::max<size_t>(smem, 1)));                                       \
     prof_start(SC ? KC_APPLY_S : KC_APPLY_F, st);                                                      \
     k_local_apply<T, SC, MR><<<g.nsd, thr, smem, st>>>(g, mv_, Op, Frc_, v, R, active, Y_, tc);         \
@@ -591,7 +591,7 @@ class Engine : public EngineBase {
     ENG_LAUNCH();
     const int seg = (nlam + nblk - 1) / nblk;
     const size_t dot_smem = (size_t)seg * cxT;
-    ENG_CK(cudaFuncSetAttribute(k_dots<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dot_smem));
+    ENG_CK(smem_attr((const void*)k_dots<T>, (int)dot_smem));
     const int check_every = 4;
     int k = 0;
     for (; k < m; ++k) {

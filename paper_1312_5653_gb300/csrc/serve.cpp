@@ -9,6 +9,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -243,6 +244,9 @@ struct schur_server {
           }
         }
       }
+      if (rc != SCHUR_OK && rc != SCHUR_ENOTCONV)
+        fprintf(stderr, "schur_server: batch of %d request(s) failed: %s: %s\n", (int)batch.size(), schur_strerror(rc),
+                schur_last_error());
       lk.lock();
       auto it = cache.find(key);
       if (it != cache.end()) {

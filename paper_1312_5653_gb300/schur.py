@@ -380,6 +380,7 @@ class Server:
         self.srv = ctypes.c_void_p()
         _check(self.lib.schur_server_create(ctypes.byref(o), ctypes.byref(self.srv)), "schur_server_create")
         self._bufs = {}
+        _live_servers.add(self)
 
     def submit(self, dim, nel, beta, b):
         """b: float64 host array (n,) or (nrhs, n); returns a ticket."""
@@ -422,5 +423,22 @@ class Server:
     def __del__(self):
         try:
             self.close()
+        except Exception:
+            pass
+
+
+# Servers own worker threads that call CUDA; close any still open before the interpreter (and then
+# the CUDA runtime) shuts down.
+import atexit as _atexit
+import weakref as _weakref
+
+_live_servers = _weakref.WeakSet()
+
+
+@_atexit.register
+def _close_live_servers():
+    for s in list(_live_servers):
+        try:
+            s.close()
         except Exception:
             pass

@@ -43,14 +43,16 @@ def test_mixed_stream_matches_solo_and_oracle():
             dim, N, beta, b = reqs[i]
             tickets[i] = srv.submit(dim, N, beta, b)
 
-    threads = [threading.Thread(target=producer, args=(list(range(k, len(reqs), 3)),)) for k in range(3)]
-    for t in threads:
-        t.start()
-    for t in threads:
-        t.join()
-    results = [srv.wait(t) for t in tickets]
-    info = srv.info()
-    srv.close()
+    try:
+        threads = [threading.Thread(target=producer, args=(list(range(k, len(reqs), 3)),)) for k in range(3)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        results = [srv.wait(t) for t in tickets]
+        info = srv.info()
+    finally:
+        srv.close()
     assert info["completed"] == len(reqs)
     lat = [st["ms_solve"] for _, st in results]
     print("served", len(reqs), "p50 %.1f ms p99 %.1f ms" % (np.percentile(lat, 50), np.percentile(lat, 99)), info)
@@ -71,6 +73,13 @@ def test_mixed_stream_matches_solo_and_oracle():
 def test_budget_admission_eviction_and_rejection():
     one_key = 600 << 20  # fits one 256^2 context at a time
     srv = S.Server(budget_bytes=one_key, workers=2, precision=S.SCHUR_MIXED, tol=1e-10)
+    try:
+        _budget_body(srv)
+    finally:
+        srv.close()
+
+
+def _budget_body(srv):
     b1 = make_rhs(2, 256, 1, 7)
     b2 = make_rhs(2, 256, 1, 8)
     t1 = srv.submit(2, 256, 1e-3, b1)
@@ -83,4 +92,3 @@ def test_budget_admission_eviction_and_rejection():
     with pytest.raises(S.SchurError) as e:
         srv.submit(2, 1024, 1e-3, np.zeros(1023 * 1023))
     assert e.value.code == S.SCHUR_EBUSY
-    srv.close()
