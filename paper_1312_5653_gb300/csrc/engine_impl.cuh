@@ -78,9 +78,11 @@ class Engine : public EngineBase {
     if (nsm_ <= 0) nsm_ = 152;
   }
 
+  // The stream of the last call may no longer exist (a server worker that created the context can
+  // have exited); schur_destroy synchronises the device first, so free on the default stream.
   ~Engine() override {
-    for (void* p : allocs_) cudaFreeAsync(p, ast_);
-    cudaStreamSynchronize(ast_);
+    for (void* p : allocs_) cudaFreeAsync(p, nullptr);
+    cudaStreamSynchronize(nullptr);
     if (h_active_) cudaFreeHost(h_active_);
   }
 
