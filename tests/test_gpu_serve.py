@@ -70,9 +70,24 @@ def test_mixed_stream_matches_solo_and_oracle():
         s.close()
 
 
+def _reservation_of_one_key():
+    """Bytes the server reserves for one 256^2 context (its own admission estimate)."""
+    srv = S.Server(budget_bytes=8 << 30, workers=1, precision=S.SCHUR_MIXED, tol=1e-10)
+    try:
+        b = make_rhs(2, 256, 1, 6)
+        srv.wait(srv.submit(2, 256, 1e-3, b))
+        info = srv.info()
+        assert info["cached_contexts"] == 1
+        return info["bytes_reserved"]
+    finally:
+        srv.close()
+
+
 def test_budget_admission_eviction_and_rejection():
-    one_key = 600 << 20  # fits one 256^2 context at a time
-    srv = S.Server(budget_bytes=one_key, workers=2, precision=S.SCHUR_MIXED, tol=1e-10)
+    one_key = _reservation_of_one_key()
+    assert one_key > 0
+    # room for one 256^2 context, not two: the second key must evict the first
+    srv = S.Server(budget_bytes=one_key * 3 // 2, workers=2, precision=S.SCHUR_MIXED, tol=1e-10)
     try:
         _budget_body(srv)
     finally:
@@ -89,6 +104,7 @@ def _budget_body(srv):
     assert rel(x1, oracle.fd_schur_solve(2, 256, 1e-3, b1)) <= 1e-8
     assert rel(x2, oracle.fd_schur_solve(2, 256, 1e-6, b2)) <= 1e-8
     assert srv.info()["cached_contexts"] == 1
+    # a mesh whose estimate exceeds the whole budget is refused at submission
     with pytest.raises(S.SchurError) as e:
         srv.submit(2, 1024, 1e-3, np.zeros(1023 * 1023))
     assert e.value.code == S.SCHUR_EBUSY
