@@ -1,12 +1,12 @@
-// Coarse corner problem: FP64 block cyclic reduction and its explicit inverse (coarse_bcr.cu).
+// Coarse corner problem: block cyclic reduction and its explicit inverse (coarse_bcr.cu).
 #pragma once
 #include <string>
 
 #include "layered.cuh"
 
 namespace schur {
-// Block cyclic reduction of the coarse matrix (FP64 factor) and its explicit inverse in precision
-// T written to Kinv (n_c x n_c).  Returns SCHUR_* code; *launches counts kernel launches.
+// Block cyclic reduction of the coarse matrix (assembled in FP64) and its explicit inverse, both in
+// precision T; the inverse is written to Kinv (n_c x n_c).  Returns SCHUR_* code; *launches counts kernel launches.
 template <class T>
 int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int* err, cudaStream_t st, std::string* msg,
                long long* launches);

@@ -4,9 +4,10 @@
 // the sequential layer recursion, every level eliminates every other remaining layer j at once:
 //   Dinv_j = D_j^{-1},  Lp = A_pj Dinv_j,  Lq = A_qj Dinv_j,
 //   D_p -= Lp A_jp,  D_q -= Lq A_jq,  A_pq = -Lp A_jq          (p, q: remaining neighbours of j)
-// so the critical path is log2(L) levels of batched dense work.  All factor arithmetic is FP64.
-// The explicit inverse is then formed by a cyclic-reduction solve with the identity as right-hand
-// side, in the working precision of the solver (FP64 or FP32 copies of the FP64 factor).
+// so the critical path is log2(L) levels of batched dense work.  The factor and the explicit
+// inverse (a cyclic-reduction solve with the identity as right-hand side) are computed in the
+// working precision of the solver: FP64, or FP32 for the inner solver of the mixed form, whose
+// outer FP64 refinement absorbs the rounding of the coarse problem like that of the local ones.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -22,26 +23,28 @@ namespace schur {
 
 // ------------------------------------------------------------------ batched dense kernels
 // Dense layer blocks from the stored sparse coarse blocks: D_K = A_KK, U_K = A_{K,K+1}.
-__global__ void k_bcr_densify(StoredProv<double> P, cx<double>* D, cx<double>* U) {
+template <class S>
+__global__ void k_bcr_densify(StoredProv<double> P, cx<S>* D, cx<S>* U) {
   const int b = P.ly.b, L = P.ly.L, nt = nbr_count(P.ly.dim);
   const size_t bb = (size_t)b * b;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)L * bb; e += (size_t)gridDim.x * blockDim.x) {
     int K = (int)(e / bb), r = (int)(e % bb), i = r / b, j = r % b;
     int t = nbr_slot(P.ly, i, j);
-    D[e] = t >= 0 ? P.Ad(K, i, t) : mkc<double>(0, 0);
+    D[e] = ccast<S>(t >= 0 ? P.Ad(K, i, t) : mkc<double>(0, 0));
     // A_{K,K+1}[i][j] = A(K, i ; K+1, j) = A(K+1, j ; K, i) = CB[K][j][slot of i from j]
     cx<double> u = mkc<double>(0, 0);
     if (K + 1 < L) {
       int tj = nbr_slot(P.ly, j, i);
       if (tj >= 0) u = P.Al(K, j, tj);
     }
-    U[e] = u;
+    U[e] = ccast<S>(u);
   }
 }
 
-// Gauss-Jordan inversion of a batch of dense b x b FP64 blocks, one thread-block cluster per
+// Gauss-Jordan inversion of a batch of dense b x b blocks, one thread-block cluster per
 // block; columns distributed over the cluster, pivot column broadcast through DSMEM.
-__global__ void __launch_bounds__(256) k_gj_batch_cluster(const cx<double>* __restrict__ Din, cx<double>* Dout,
+template <class S>
+__global__ void __launch_bounds__(256) k_gj_batch_cluster(const cx<S>* __restrict__ Din, cx<S>* Dout,
                                                           const int* __restrict__ list, int b, int* err) {
   cg::cluster_group cluster = cg::this_cluster();
   const int CL = (int)cluster.num_blocks(), me = (int)cluster.block_rank();
@@ -49,40 +52,40 @@ __global__ void __launch_bounds__(256) k_gj_batch_cluster(const cx<double>* __re
   const int cw = (b + CL - 1) / CL, c0 = me * cw, c1 = min(b, c0 + cw), ncol = max(0, c1 - c0);
   const int tid = threadIdx.x, nthr = blockDim.x;
   extern __shared__ unsigned char smraw[];
-  cx<double>* Dl = reinterpret_cast<cx<double>*>(smraw);  // b x cw
-  cx<double>* colk = Dl + (size_t)b * cw;                  // b
-  cx<double>* bcast = colk + b;                            // 2 x b
-  cx<double>* rowk = bcast + 2 * b;                        // cw
+  cx<S>* Dl = reinterpret_cast<cx<S>*>(smraw);  // b x cw
+  cx<S>* colk = Dl + (size_t)b * cw;                  // b
+  cx<S>* bcast = colk + b;                            // 2 x b
+  cx<S>* rowk = bcast + 2 * b;                        // cw
   const size_t bb = (size_t)b * b;
-  const cx<double>* src = Din + (size_t)which * bb;
+  const cx<S>* src = Din + (size_t)which * bb;
   for (int e = tid; e < b * cw; e += nthr) {
     int i = e / cw, jl = e - i * cw;
-    Dl[e] = jl < ncol ? src[(size_t)i * b + c0 + jl] : mkc<double>(0, 0);
+    Dl[e] = jl < ncol ? src[(size_t)i * b + c0 + jl] : mkc<S>(0, 0);
   }
   __syncthreads();
   for (int k = 0; k < b; ++k) {
     const int owner = k / cw;
-    cx<double>* pub = bcast + (k & 1) * b;
+    cx<S>* pub = bcast + (k & 1) * b;
     if (me == owner)
       for (int i = tid; i < b; i += nthr) pub[i] = Dl[i * cw + (k - c0)];
     cluster.sync();
-    const cx<double>* rs = cluster.map_shared_rank(pub, owner);
+    const cx<S>* rs = cluster.map_shared_rank(pub, owner);
     for (int i = tid; i < b; i += nthr) colk[i] = rs[i];
     __syncthreads();
-    const cx<double> p = colk[k];
-    const cx<double> piv = cinv(p);
+    const cx<S> p = colk[k];
+    const cx<S> piv = cinv(p);
     if (tid == 0 && me == 0 && !finite_nonzero(p)) atomicExch(err, 1);
     for (int jl = tid; jl < ncol; jl += nthr) rowk[jl] = cmul(Dl[k * cw + jl], piv);
     __syncthreads();
     for (int e = tid; e < b * ncol; e += nthr) {
       int i = e / ncol, jl = e - i * ncol, j = c0 + jl;
-      cx<double>& a = Dl[i * cw + jl];
+      cx<S>& a = Dl[i * cw + jl];
       if (j == k) {
         if (i == k) {
           a = piv;
         } else {
-          cx<double> v = cmul(colk[i], piv);
-          a = mkc<double>(-v.re, -v.im);
+          cx<S> v = cmul(colk[i], piv);
+          a = mkc<S>(-v.re, -v.im);
         }
       } else if (i == k) {
         a = rowk[jl];
@@ -92,7 +95,7 @@ __global__ void __launch_bounds__(256) k_gj_batch_cluster(const cx<double>* __re
     }
     __syncthreads();
   }
-  cx<double>* dst = Dout + (size_t)which * bb;
+  cx<S>* dst = Dout + (size_t)which * bb;
   for (int e = tid; e < b * ncol; e += nthr) {
     int i = e / ncol, jl = e - i * ncol;
     dst[(size_t)i * b + c0 + jl] = Dl[i * cw + jl];
@@ -113,23 +116,30 @@ struct GemmTask {
   int accumulate;
 };
 
-// C[M x N] (+)= alpha * A[M x Kd] * B[Kd x N]  (B^T when transB), 64 x 64 output tiles per CTA,
-// 16 x 16 threads with 4 x 4 outputs each, K in steps of 16 staged in shared memory.
+// C[M x N] (+)= alpha * A[M x Kd] * B[Kd x N]  (B^T when transB), TM x TM output tiles per CTA,
+// 16 x 16 threads with (TM/16)^2 outputs each, K in steps of 16 staged in shared memory.  FP64 uses
+// 32 x 32 tiles: its per-SM rate is low, so more CTAs per b x b task keep more SMs busy.
 template <class S>
+struct GemmTile {
+  static constexpr int TM = sizeof(S) == 8 ? 32 : 64;
+};
+
+template <class S, int TM>
 __global__ void __launch_bounds__(256) k_gemm_batch(const GemmTask<S>* __restrict__ tasks, int M, int N, int Kd) {
+  constexpr int Q = TM / 16;
   const GemmTask<S> t = tasks[blockIdx.z];
-  const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
+  const int row0 = blockIdx.y * TM, col0 = blockIdx.x * TM;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  __shared__ cx<S> As[16][64 + 1];
-  __shared__ cx<S> Bs[16][64 + 1];
-  cx<S> acc[4][4];
+  __shared__ cx<S> As[16][TM + 1];
+  __shared__ cx<S> Bs[16][TM + 1];
+  cx<S> acc[Q][Q];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < Q; ++a)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[a][c] = mkc<S>(0, 0);
+    for (int c = 0; c < Q; ++c) acc[a][c] = mkc<S>(0, 0);
   for (int k0 = 0; k0 < Kd; k0 += 16) {
-    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
-      int kk = e / 64, r = e % 64;
+    for (int e = threadIdx.x; e < 16 * TM; e += 256) {
+      int kk = e / TM, r = e % TM;
       int gr = row0 + r, gk = k0 + kk;
       As[kk][r] = (gr < M && gk < Kd) ? t.A[(size_t)gr * t.lda + gk] : mkc<S>(0, 0);
       int gc = col0 + r;
@@ -140,23 +150,23 @@ __global__ void __launch_bounds__(256) k_gemm_batch(const GemmTask<S>* __restric
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < 16; ++kk) {
-      cx<S> a[4], bq[4];
+      cx<S> a[Q], bq[Q];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < Q; ++q) {
         a[q] = As[kk][ty + 16 * q];
         bq[q] = Bs[kk][tx + 16 * q];
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+      for (int q = 0; q < Q; ++q)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) cfma(acc[q][c], a[q], bq[c]);
+        for (int c = 0; c < Q; ++c) cfma(acc[q][c], a[q], bq[c]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+  for (int q = 0; q < Q; ++q)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < Q; ++c) {
       int gr = row0 + ty + 16 * q, gc = col0 + tx + 16 * c;
       if (gr < M && gc < N) {
         cx<S>& o = t.C[(size_t)gr * t.ldc + gc];
@@ -172,8 +182,9 @@ static cudaError_t launch_gemms(const std::vector<GemmTask<S>>& tasks, GemmTask<
   if (tasks.empty()) return cudaSuccess;
   cudaError_t e = cudaMemcpyAsync(dtasks, tasks.data(), tasks.size() * sizeof(GemmTask<S>), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
-  dim3 grid((N + 63) / 64, (M + 63) / 64, (unsigned)tasks.size());
-  k_gemm_batch<S><<<grid, 256, 0, st>>>(dtasks, M, N, Kd);
+  constexpr int TM = GemmTile<S>::TM;
+  dim3 grid((N + TM - 1) / TM, (M + TM - 1) / TM, (unsigned)tasks.size());
+  k_gemm_batch<S, TM><<<grid, 256, 0, st>>>(dtasks, M, N, Kd);
   return cudaGetLastError();
 }
 
@@ -201,22 +212,24 @@ static void bcr_schedule(int L, std::vector<std::vector<int>>* lev_j, std::vecto
   }
 }
 
-size_t bcr_gj_smem(int b, int CL) {
+template <class S>
+static size_t bcr_gj_smem(int b, int CL) {
   int cw = (b + CL - 1) / CL;
-  return ((size_t)b * cw + 3 * (size_t)b + cw) * sizeof(cx<double>);
+  return ((size_t)b * cw + 3 * (size_t)b + cw) * sizeof(cx<S>);
 }
 
-static cudaError_t launch_gj_batch(const cx<double>* Din, cx<double>* Dout, const int* dlist, int nblk, int b, int* err,
+template <class S>
+static cudaError_t launch_gj_batch(const cx<S>* Din, cx<S>* Dout, const int* dlist, int nblk, int b, int* err,
                                    cudaStream_t st) {
   static const int sizes[] = {16, 8, 4, 2, 1};
   cudaError_t last = cudaErrorInvalidConfiguration;
   for (int CL : sizes) {
     if (CL > 1 && nblk * CL > 4 * 152 && CL > 4) continue;  // keep many clusters resident at once
-    size_t smem = bcr_gj_smem(b, CL);
+    size_t smem = bcr_gj_smem<S>(b, CL);
     if (smem > 200 * 1024) continue;
-    cudaError_t e = smem_attr((const void*)k_gj_batch_cluster, (int)smem);
+    cudaError_t e = smem_attr((const void*)k_gj_batch_cluster<S>, (int)smem);
     if (e == cudaSuccess && CL > 8)
-      e = cudaFuncSetAttribute(k_gj_batch_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      e = cudaFuncSetAttribute(k_gj_batch_cluster<S>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) {
       cudaGetLastError();
       last = e;
@@ -235,24 +248,18 @@ static cudaError_t launch_gj_batch(const cx<double>* Din, cx<double>* Dout, cons
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int ncl = 0;
-    e = cudaOccupancyMaxActiveClusters(&ncl, k_gj_batch_cluster, &cfg);
+    e = cudaOccupancyMaxActiveClusters(&ncl, k_gj_batch_cluster<S>, &cfg);
     if (e != cudaSuccess || ncl < 1) {
       cudaGetLastError();
       last = e != cudaSuccess ? e : cudaErrorInvalidConfiguration;
       continue;
     }
-    e = cudaLaunchKernelEx(&cfg, k_gj_batch_cluster, Din, Dout, dlist, b, err);
+    e = cudaLaunchKernelEx(&cfg, k_gj_batch_cluster<S>, Din, Dout, dlist, b, err);
     if (e == cudaSuccess) return cudaSuccess;
     cudaGetLastError();
     last = e;
   }
   return last;
-}
-
-template <class S>
-__global__ void k_bcr_convert(const cx<double>* __restrict__ in, cx<S>* out, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    out[i] = ccast<S>(in[i]);
 }
 
 template <class T>
@@ -322,10 +329,10 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int* err, cudaStream_t 
   const size_t bb = (size_t)b * b, n = (size_t)b * L;
   std::vector<std::vector<int>> lj, lp, lq;
   bcr_schedule(L, &lj, &lp, &lq);
-  cx<double>*D = nullptr, *Ucur = nullptr, *Dinv = nullptr, *UP = nullptr, *UQ = nullptr, *Lp = nullptr,
-             *Lq = nullptr, *Unew = nullptr;
+  cx<T>*D = nullptr, *Ucur = nullptr, *Dinv = nullptr, *UP = nullptr, *UQ = nullptr, *Lp = nullptr, *Lq = nullptr,
+        *Unew = nullptr;
   int* dlist = nullptr;
-  GemmTask<double>* dt64 = nullptr;
+  GemmTask<T>* dtT = nullptr;
   auto fail = [&](cudaError_t e, const char* where) {
     if (msg) *msg = std::string("coarse reduction (") + where + "): " + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? SCHUR_ENOMEM : SCHUR_ECUDA;
@@ -348,111 +355,94 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int* err, cudaStream_t 
       for (void* p : *m) cudaFreeAsync(p, s);
     }
   } guard{&mem, st};
-  BCR_CK(mal(&D, L * bb * sizeof(cx<double>)), "alloc");
-  BCR_CK(mal(&Ucur, L * bb * sizeof(cx<double>)), "alloc");
-  BCR_CK(mal(&Dinv, L * bb * sizeof(cx<double>)), "alloc");
-  BCR_CK(mal(&UP, 2 * L * bb * sizeof(cx<double>)), "alloc");  // UP_j, then its transposes
-  BCR_CK(mal(&UQ, 2 * L * bb * sizeof(cx<double>)), "alloc");  // UQ_j, then its transposes
-  BCR_CK(mal(&Lp, L * bb * sizeof(cx<double>)), "alloc");
-  BCR_CK(mal(&Lq, L * bb * sizeof(cx<double>)), "alloc");
-  BCR_CK(mal(&Unew, L * bb * sizeof(cx<double>)), "alloc");
+  BCR_CK(mal(&D, L * bb * sizeof(cx<T>)), "alloc");
+  BCR_CK(mal(&Ucur, L * bb * sizeof(cx<T>)), "alloc");
+  BCR_CK(mal(&Dinv, L * bb * sizeof(cx<T>)), "alloc");
+  BCR_CK(mal(&UP, 2 * L * bb * sizeof(cx<T>)), "alloc");  // UP_j, then its transposes
+  BCR_CK(mal(&UQ, 2 * L * bb * sizeof(cx<T>)), "alloc");  // UQ_j, then its transposes
+  BCR_CK(mal(&Lp, L * bb * sizeof(cx<T>)), "alloc");
+  BCR_CK(mal(&Lq, L * bb * sizeof(cx<T>)), "alloc");
+  BCR_CK(mal(&Unew, L * bb * sizeof(cx<T>)), "alloc");
   BCR_CK(mal(&dlist, (size_t)L * sizeof(int)), "alloc");
-  BCR_CK(mal(&dt64, (size_t)4 * L * sizeof(GemmTask<double>)), "alloc");
-  BCR_CK(cudaMemsetAsync(UP, 0, 2 * L * bb * sizeof(cx<double>), st), "memset");
-  BCR_CK(cudaMemsetAsync(UQ, 0, 2 * L * bb * sizeof(cx<double>), st), "memset");
+  BCR_CK(mal(&dtT, (size_t)4 * L * sizeof(GemmTask<T>)), "alloc");
+  BCR_CK(cudaMemsetAsync(UP, 0, 2 * L * bb * sizeof(cx<T>), st), "memset");
+  BCR_CK(cudaMemsetAsync(UQ, 0, 2 * L * bb * sizeof(cx<T>), st), "memset");
   const int gs = (int)std::min<size_t>((L * bb + 255) / 256, 4096);
-  k_bcr_densify<<<gs, 256, 0, st>>>(P, D, Ucur);
+  k_bcr_densify<T><<<gs, 256, 0, st>>>(P, D, Ucur);
   BCR_CK(cudaGetLastError(), "densify");
   ++*launches;
-  // ---- factorisation (FP64)
+  // ---- factorisation
   prof_start(KC_COARSE_SETUP, st);
   for (size_t lv = 0; lv < lj.size(); ++lv) {
     const std::vector<int>& J = lj[lv];
     BCR_CK(cudaMemcpyAsync(dlist, J.data(), J.size() * sizeof(int), cudaMemcpyHostToDevice, st), "list");
-    BCR_CK(launch_gj_batch(D, Dinv, dlist, (int)J.size(), b, err, st), "inversion");
+    BCR_CK(launch_gj_batch<T>(D, Dinv, dlist, (int)J.size(), b, err, st), "inversion");
     ++*launches;
-    std::vector<GemmTask<double>> t1, t2;
+    std::vector<GemmTask<T>> t1;
     for (size_t k = 0; k < J.size(); ++k) {
       int j = J[k], p = lp[lv][k], q = lq[lv][k];
       if (p >= 0) {
         // UP_j = A_pj = Ucur_p ; Lp_j = UP_j Dinv_j
-        BCR_CK(cudaMemcpyAsync(UP + j * bb, Ucur + p * bb, bb * sizeof(cx<double>), cudaMemcpyDeviceToDevice, st), "copy");
-        t1.push_back({Ucur + p * bb, Dinv + j * bb, Lp + j * bb, b, b, b, 0, 1.0, 0});
+        BCR_CK(cudaMemcpyAsync(UP + j * bb, Ucur + p * bb, bb * sizeof(cx<T>), cudaMemcpyDeviceToDevice, st), "copy");
+        t1.push_back({Ucur + p * bb, Dinv + j * bb, Lp + j * bb, b, b, b, 0, T(1), 0});
       }
       if (q >= 0) {
         // UQ_j = A_jq = Ucur_j ; Lq_j = A_qj Dinv_j = UQ_j^T Dinv_j  -> computed as (Dinv_j UQ_j)^T:
         // Dinv_j is symmetric, so Lq_j^T = Dinv_j UQ_j; store W = Dinv_j UQ_j and use its transpose
-        BCR_CK(cudaMemcpyAsync(UQ + j * bb, Ucur + j * bb, bb * sizeof(cx<double>), cudaMemcpyDeviceToDevice, st), "copy");
-        t1.push_back({Dinv + j * bb, Ucur + j * bb, Lq + j * bb, b, b, b, 0, 1.0, 0});  // Lq holds Dinv_j A_jq
+        BCR_CK(cudaMemcpyAsync(UQ + j * bb, Ucur + j * bb, bb * sizeof(cx<T>), cudaMemcpyDeviceToDevice, st), "copy");
+        t1.push_back({Dinv + j * bb, Ucur + j * bb, Lq + j * bb, b, b, b, 0, T(1), 0});  // Lq holds Dinv_j A_jq
       }
     }
-    BCR_CK(launch_gemms(t1, dt64, b, b, b, st), "gemm L");
+    BCR_CK(launch_gemms(t1, dtT, b, b, b, st), "gemm L");
     ++*launches;
     // D_p -= Lp_j A_jp = Lp_j UP_j^T ; D_q -= A_qj Dinv_j A_jq = UQ_j^T (Dinv_j UQ_j) = UQ_j^T Lq_j
     // A_pq (new coupling from p) = -Lp_j A_jq = -Lp_j UQ_j
     // Launch 1: updates from the right neighbour j of p (D_p, Unew_p); launch 2: from the left
     // neighbour j' of q (D_q).  No two tasks of one launch write the same block.
-    std::vector<GemmTask<double>> ta, tb;
+    std::vector<GemmTask<T>> ta, tb;
     for (size_t k = 0; k < J.size(); ++k) {
       int j = J[k], p = lp[lv][k], q = lq[lv][k];
       if (p >= 0) {
-        ta.push_back({Lp + j * bb, UP + j * bb, D + p * bb, b, b, b, 1, -1.0, 1});
-        if (q >= 0) tb.push_back({Lp + j * bb, UQ + j * bb, Unew + p * bb, b, b, b, 0, -1.0, 0});
+        ta.push_back({Lp + j * bb, UP + j * bb, D + p * bb, b, b, b, 1, T(-1), 1});
+        if (q >= 0) tb.push_back({Lp + j * bb, UQ + j * bb, Unew + p * bb, b, b, b, 0, T(-1), 0});
       }
     }
-    BCR_CK(launch_gemms(ta, dt64, b, b, b, st), "gemm Dp");
-    BCR_CK(launch_gemms(tb, dt64 + ta.size(), b, b, b, st), "gemm Upq");
+    BCR_CK(launch_gemms(ta, dtT, b, b, b, st), "gemm Dp");
+    BCR_CK(launch_gemms(tb, dtT + ta.size(), b, b, b, st), "gemm Upq");
     // D_q -= UQ_j^T Lq_j: transpose UQ_j into UQ + L*bb, then a plain GEMM
-    k_bcr_transpose<double><<<gs, 256, 0, st>>>(UQ, UQ + (size_t)L * bb, b, L);
+    k_bcr_transpose<T><<<gs, 256, 0, st>>>(UQ, UQ + (size_t)L * bb, b, L);
     BCR_CK(cudaGetLastError(), "transpose");
-    std::vector<GemmTask<double>> tc;
+    std::vector<GemmTask<T>> tc;
     for (size_t k = 0; k < J.size(); ++k) {
       int j = J[k], q = lq[lv][k];
-      if (q >= 0) tc.push_back({UQ + (size_t)L * bb + j * bb, Lq + j * bb, D + q * bb, b, b, b, 0, -1.0, 1});
+      if (q >= 0) tc.push_back({UQ + (size_t)L * bb + j * bb, Lq + j * bb, D + q * bb, b, b, b, 0, T(-1), 1});
     }
-    BCR_CK(launch_gemms(tc, dt64 + ta.size() + tb.size(), b, b, b, st), "gemm Dq");
+    BCR_CK(launch_gemms(tc, dtT + ta.size() + tb.size(), b, b, b, st), "gemm Dq");
     *launches += 4;
     // remaining p whose right neighbour j was eliminated now couples to q
     for (size_t k = 0; k < J.size(); ++k) {
       int p = lp[lv][k], q = lq[lv][k];
       if (p >= 0) {
         if (q >= 0)
-          BCR_CK(cudaMemcpyAsync(Ucur + p * bb, Unew + p * bb, bb * sizeof(cx<double>), cudaMemcpyDeviceToDevice, st), "copy");
+          BCR_CK(cudaMemcpyAsync(Ucur + p * bb, Unew + p * bb, bb * sizeof(cx<T>), cudaMemcpyDeviceToDevice, st), "copy");
         else
-          BCR_CK(cudaMemsetAsync(Ucur + p * bb, 0, bb * sizeof(cx<double>), st), "memset");
+          BCR_CK(cudaMemsetAsync(Ucur + p * bb, 0, bb * sizeof(cx<T>), st), "memset");
       }
     }
   }
   // transposes of UP (for back substitution) and UQ (forward), kept behind the originals
-  k_bcr_transpose<double><<<gs, 256, 0, st>>>(UP, UP + (size_t)L * bb, b, L);
-  k_bcr_transpose<double><<<gs, 256, 0, st>>>(UQ, UQ + (size_t)L * bb, b, L);
+  k_bcr_transpose<T><<<gs, 256, 0, st>>>(UP, UP + (size_t)L * bb, b, L);
+  k_bcr_transpose<T><<<gs, 256, 0, st>>>(UQ, UQ + (size_t)L * bb, b, L);
   BCR_CK(cudaGetLastError(), "transpose");
   prof_stop(KC_COARSE_SETUP, st);
-  // ---- explicit inverse: solve with the identity in precision T
+  // ---- explicit inverse: solve with the identity
   prof_start(KC_COARSE_INV, st);
-  cx<T>*Df = nullptr, *UPf = nullptr, *UQf = nullptr, *X = nullptr, *Tmp = nullptr;
-  GemmTask<T>* dtT = nullptr;
-  BCR_CK(mal(&X, n * n * sizeof(cx<T>)), "alloc");
+  // solved in place in Kinv; the inverse is symmetric, so its rows are the solution columns
+  cx<T>* Tmp = nullptr;
   BCR_CK(mal(&Tmp, n * n * sizeof(cx<T>)), "alloc");
-  BCR_CK(mal(&dtT, (size_t)4 * L * sizeof(GemmTask<T>)), "alloc");
-  if (sizeof(T) == sizeof(double)) {
-    Df = reinterpret_cast<cx<T>*>(Dinv);
-    UPf = reinterpret_cast<cx<T>*>(UP);
-    UQf = reinterpret_cast<cx<T>*>(UQ);
-  } else {
-    BCR_CK(mal(&Df, L * bb * sizeof(cx<T>)), "alloc");
-    BCR_CK(mal(&UPf, 2 * L * bb * sizeof(cx<T>)), "alloc");
-    BCR_CK(mal(&UQf, 2 * L * bb * sizeof(cx<T>)), "alloc");
-    k_bcr_convert<T><<<gs, 256, 0, st>>>(Dinv, Df, L * bb);
-    k_bcr_convert<T><<<gs, 256, 0, st>>>(UP, UPf, 2 * L * bb);
-    k_bcr_convert<T><<<gs, 256, 0, st>>>(UQ, UQf, 2 * L * bb);
-    BCR_CK(cudaGetLastError(), "convert");
-  }
-  k_bcr_identity<T><<<(int)std::min<size_t>((n * n + 255) / 256, 8192), 256, 0, st>>>(X, (int)n);
+  k_bcr_identity<T><<<(int)std::min<size_t>((n * n + 255) / 256, 8192), 256, 0, st>>>(Kinv, (int)n);
   BCR_CK(cudaGetLastError(), "identity");
-  BCR_CK(bcr_solve<T>(Df, UPf, UQf, b, L, lj, lp, lq, X, Tmp, (int)n, dtT, st), "solve");
-  // the inverse is symmetric: its rows are the solution columns
-  BCR_CK(cudaMemcpyAsync(Kinv, X, n * n * sizeof(cx<T>), cudaMemcpyDeviceToDevice, st), "copy");
+  BCR_CK(bcr_solve<T>(Dinv, UP, UQ, b, L, lj, lp, lq, Kinv, Tmp, (int)n, dtT, st), "solve");
   prof_stop(KC_COARSE_INV, st);
   BCR_CK(cudaStreamSynchronize(st), "sync");
   *launches += 8;

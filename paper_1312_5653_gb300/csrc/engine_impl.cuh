@@ -172,13 +172,15 @@ class Engine : public EngineBase {
       const int C = 32;
       cx<T>* Xws = nullptr;
       if (g.lb <= 32) {
-        constexpr int CW = sizeof(T) == 4 ? 16 : 8;
+        constexpr int CW = 4;
         const int ncol = g.nD + g.nc, nchunk = (ncol + CW - 1) / CW, nwork = ncls_ * nchunk;
-        const int wpb = 8;
-        const int grid = std::max(1, std::min((nwork + wpb - 1) / wpb, 2 * nsm_));
+        const int wpb = 4;
+        const int grid = std::max(1, std::min((nwork + wpb - 1) / wpb, 4 * nsm_));
+        const size_t smem = wpb * warp_solve_smem<T>(g.lb);
         ENG_CK(alloc(&Xws, (size_t)grid * wpb * g.nl * CW * cxT));
+        ENG_CK(smem_attr((const void*)k_form_rr_warp<T, CW>, (int)smem));
         prof_start(KC_FORM, st);
-        k_form_rr_warp<T, CW><<<grid, 32 * wpb, 0, st>>>(prr_, g, mv_, Dinv_, ncls_, F_, Frc_, Kcc_, Xws);
+        k_form_rr_warp<T, CW><<<grid, 32 * wpb, smem, st>>>(prr_, g, mv_, Dinv_, ncls_, F_, Frc_, Kcc_, Xws);
         prof_stop(KC_FORM, st);
         ENG_LAUNCH();
       } else {
@@ -463,14 +465,22 @@ class Engine : public EngineBase {
     const int cat = rhs_split ? KC_LOCAL_RHS : KC_RECOVER;
     if (g.lb <= 32) {
       const int wpb = 4, grid = (g.nsd + wpb - 1) / wpb;
+      const size_t smem = wpb * warp_solve_smem<T>(g.lb);
       cx<T>* vd = rhs_split ? VD_ : nullptr;
       cx<T>* tc = rhs_split ? Tc_ : nullptr;
+#define LS_ATTR(C) ENG_CK(smem_attr((const void*)k_local_solve_warp<T, C>, (int)smem))
+      if (R == 1) LS_ATTR(1);
+      else if (R == 2) LS_ATTR(2);
+      else if (R <= 4) LS_ATTR(4);
+      else if (R <= 8) LS_ATTR(8);
+      else LS_ATTR(16);
+#undef LS_ATTR
       prof_start(cat, st);
-      if (R == 1) k_local_solve_warp<T, 1><<<grid, 32 * wpb, 0, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc);
-      else if (R == 2) k_local_solve_warp<T, 2><<<grid, 32 * wpb, 0, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc);
-      else if (R <= 4) k_local_solve_warp<T, 4><<<grid, 32 * wpb, 0, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc);
-      else if (R <= 8) k_local_solve_warp<T, 8><<<grid, 32 * wpb, 0, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc);
-      else k_local_solve_warp<T, 16><<<grid, 32 * wpb, 0, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc);
+      if (R == 1) k_local_solve_warp<T, 1><<<grid, 32 * wpb, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc);
+      else if (R == 2) k_local_solve_warp<T, 2><<<grid, 32 * wpb, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc);
+      else if (R <= 4) k_local_solve_warp<T, 4><<<grid, 32 * wpb, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc);
+      else if (R <= 8) k_local_solve_warp<T, 8><<<grid, 32 * wpb, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc);
+      else k_local_solve_warp<T, 16><<<grid, 32 * wpb, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc);
       prof_stop(cat, st);
       ENG_LAUNCH();
       return SCHUR_OK;
@@ -584,7 +594,7 @@ class Engine : public EngineBase {
     ENG_LAUNCH();
     ENG_CK(cudaMemcpyAsync(V_, d_, (size_t)R * nlam * cxT, cudaMemcpyDeviceToDevice, st));
     prof_start(KC_GMRES_OTHER, st);
-    k_gmres_init<<<1, 32, 0, st>>>(R, nrm_part_, nblk, m, beta0_, gvec_, active_, kk_, inv_nrm_, resid_);
+    k_gmres_init<<<R, 32, 0, st>>>(R, nrm_part_, nblk, m, beta0_, gvec_, active_, kk_, inv_nrm_, resid_);
     prof_stop(KC_GMRES_OTHER, st);
     ENG_LAUNCH();
     prof_start(KC_GMRES_OTHER, st);
@@ -623,7 +633,7 @@ class Engine : public EngineBase {
       prof_stop(KC_GMRES_OTHER, st);
       ENG_LAUNCH();
       prof_start(KC_GMRES_OTHER, st);
-      k_givens<<<1, 32, 0, st>>>(R, k, m, H_, nrm_part_, nblk, cs_c_, cs_s_, gvec_, beta0_, tol, active_, kk_, inv_nrm_,
+      k_givens<<<R, 32, 0, st>>>(R, k, m, H_, nrm_part_, nblk, cs_c_, cs_s_, gvec_, beta0_, tol, active_, kk_, inv_nrm_,
                                  resid_, bad_);
       prof_stop(KC_GMRES_OTHER, st);
       ENG_LAUNCH();

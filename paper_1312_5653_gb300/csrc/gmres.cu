@@ -29,12 +29,21 @@ __global__ void k_dots_reduce(const cx<double>* __restrict__ part, int nblk, int
   }
 }
 
+// Sum of the nblk partial sums of right-hand side r, by the whole warp (result in every lane).
+__device__ __forceinline__ double warp_sum_parts(const double* __restrict__ part, int nblk) {
+  double s = 0;
+  for (int b = threadIdx.x; b < nblk; b += 32) s += part[b];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// One warp per right-hand side (grid R x 32 threads).
 __global__ void k_gmres_init(int R, const double* __restrict__ nrm_part, int nblk, int m, double* beta0,
                              cx<double>* gvec, int* active, int* kk, double* inv_nrm, double* resid) {
-  const int r = threadIdx.x;
+  const int r = blockIdx.x;
   if (r >= R) return;
-  double s = 0;
-  for (int b = 0; b < nblk; ++b) s += nrm_part[(size_t)r * nblk + b];
+  const double s = warp_sum_parts(nrm_part + (size_t)r * nblk, nblk);
+  if (threadIdx.x != 0) return;
   double b0 = sqrt(s);
   beta0[r] = b0;
   for (int j = 0; j <= m; ++j) gvec[(size_t)r * (m + 1) + j] = mkc<double>(0, 0);
@@ -49,10 +58,10 @@ __global__ void k_gmres_init(int R, const double* __restrict__ nrm_part, int nbl
 __global__ void k_givens(int R, int k, int m, cx<double>* H, const double* __restrict__ nrm_part, int nblk,
                          double* cs_c, cx<double>* cs_s, cx<double>* gvec, const double* __restrict__ beta0,
                          double tol, int* active, int* kk, double* inv_nrm, double* resid, int* bad) {
-  const int r = threadIdx.x;
+  const int r = blockIdx.x;  // one warp per right-hand side
   if (r >= R || !active[r]) return;
-  double s2 = 0;
-  for (int b = 0; b < nblk; ++b) s2 += nrm_part[(size_t)r * nblk + b];
+  const double s2 = warp_sum_parts(nrm_part + (size_t)r * nblk, nblk);
+  if (threadIdx.x != 0) return;
   const double hk1 = sqrt(s2);
   cx<double>* col = H + ((size_t)r * m + k) * (m + 1);
   for (int i = 0; i < k; ++i) {

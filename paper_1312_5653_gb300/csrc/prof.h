@@ -7,7 +7,7 @@ namespace schur {
 enum KCat {
   KC_FACTOR = 0,      // batched block LDL^T of subdomain matrices
   KC_FORM = 1,        // local operator formation (multi-RHS layered solves)
-  KC_COARSE_SETUP = 2,// coarse assembly, FP64 factorisation, inverse
+  KC_COARSE_SETUP = 2,// coarse assembly and block cyclic reduction
   KC_LOCAL_RHS = 3,   // local right-hand-side solves
   KC_APPLY_F = 4,     // local dual operator apply (gather fused)
   KC_APPLY_S = 5,     // local Dirichlet operator apply (gather fused)

@@ -12,36 +12,78 @@ __device__ __forceinline__ cx<T> shfl_cx(cx<T> v, int src) {
   return mkc<T>(__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src));
 }
 
+// Asynchronous global -> shared copies (cp.async, L1-allocating), one complex entry per lane.
+template <class T>
+__device__ __forceinline__ void cp_async_cx(cx<T>* smem, const cx<T>* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (sizeof(cx<T>) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Warp-wide asynchronous copy of one b x b layer block into shared memory.
+template <class T>
+__device__ __forceinline__ void warp_stage_block(cx<T>* dst, const cx<T>* __restrict__ src, int bb) {
+  for (int e = threadIdx.x & 31; e < bb; e += 32) cp_async_cx(dst + e, src + e);
+}
+
+// Shared memory per warp of warp_layered_solve: two b x b blocks (double buffer).
+template <class T>
+__host__ __device__ constexpr size_t warp_solve_smem(int b) {
+  return 2 * (size_t)b * b * sizeof(cx<T>);
+}
+
 // X = A^{-1} B for up to C columns (runtime R <= C used), B given by rhs(K, i, c).
 // X (per warp, any address space) holds entry (node K*b + i, column c) at (K*b + i)*rs + c*cs;
-// forward results are overwritten by the solution in the backward sweep.
+// forward results are overwritten by the solution in the backward sweep.  Ds: this warp's
+// shared buffer (warp_solve_smem bytes); the D_K^{-1} block of the next layer is copied into it
+// asynchronously while the current layer is processed, and the neighbour couplings and right-hand
+// side of a layer are loaded before the wait, so one global latency is exposed per layer.
 template <class T, int C, class Prov, class RhsF>
 __device__ __forceinline__ void warp_layered_solve(const Prov& P, const cx<T>* __restrict__ Dinv, int R, RhsF rhs,
-                                                   cx<T>* X, int rs, int cs) {
+                                                   cx<T>* X, int rs, int cs, cx<T>* Ds) {
+  constexpr int kMaxNt = 9;
   const int lane = threadIdx.x & 31, b = P.ly.b, L = P.ly.L, nt = nbr_count(P.ly.dim), bb = b * b;
   const bool act = lane < b;
   cx<T> prev[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) prev[c] = czero<T>();
+  warp_stage_block(Ds, Dinv, bb);
+  cp_async_commit();
   for (int K = 0; K < L; ++K) {
+    const cx<T>* Dk = Ds + (size_t)(K & 1) * bb;
+    if (K + 1 < L) warp_stage_block(Ds + (size_t)((K + 1) & 1) * bb, Dinv + (size_t)(K + 1) * bb, bb);
+    cp_async_commit();
     cx<T> t[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) t[c] = (act && c < R) ? rhs(K, lane, c) : czero<T>();
     if (K > 0) {
-      for (int tt = 0; tt < nt; ++tt) {
-        int k = act ? nbr_of(P.ly, lane, tt) : -1;
-        cx<T> a = k >= 0 ? P.Al(K - 1, lane, tt) : czero<T>();
-        int src = k >= 0 ? k : lane;
+      cx<T> al[kMaxNt];
+      int src[kMaxNt];
 #pragma unroll
-        for (int c = 0; c < C; ++c) cfms(t[c], a, shfl_cx(prev[c], src));
+      for (int tt = 0; tt < kMaxNt; ++tt) {
+        int k = (act && tt < nt) ? nbr_of(P.ly, lane, tt) : -1;
+        al[tt] = k >= 0 ? P.Al(K - 1, lane, tt) : czero<T>();
+        src[tt] = k >= 0 ? k : lane;
+      }
+#pragma unroll
+      for (int tt = 0; tt < kMaxNt; ++tt) {
+        if (tt >= nt) break;
+#pragma unroll
+        for (int c = 0; c < C; ++c) cfms(t[c], al[tt], shfl_cx(prev[c], src[tt]));
       }
     }
-    const cx<T>* D = Dinv + (size_t)K * bb;
+    cp_async_wait<1>();
+    __syncwarp();
     cx<T> acc[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) acc[c] = czero<T>();
     for (int mm = 0; mm < b; ++mm) {
-      cx<T> d = act ? D[mm * b + lane] : czero<T>();
+      cx<T> d = act ? Dk[mm * b + lane] : czero<T>();
 #pragma unroll
       for (int c = 0; c < C; ++c) cfma(acc[c], d, shfl_cx(t[c], mm));
     }
@@ -50,25 +92,39 @@ __device__ __forceinline__ void warp_layered_solve(const Prov& P, const cx<T>* _
       prev[c] = acc[c];
       if (act && c < R) X[(size_t)(K * b + lane) * rs + (size_t)c * cs] = acc[c];
     }
+    __syncwarp();
   }
   // backward: prev = E_{L-1} = X_{L-1}
-  for (int K = L - 2; K >= 0; --K) {
-    cx<T> u[C];
+  if (L >= 2) warp_stage_block(Ds, Dinv + (size_t)(L - 2) * bb, bb);
+  cp_async_commit();
+  for (int K = L - 2, it = 0; K >= 0; --K, ++it) {
+    const cx<T>* Dk = Ds + (size_t)(it & 1) * bb;
+    if (K >= 1) warp_stage_block(Ds + (size_t)((it + 1) & 1) * bb, Dinv + (size_t)(K - 1) * bb, bb);
+    cp_async_commit();
+    cx<T> al[kMaxNt];
+    int src[kMaxNt];
 #pragma unroll
-    for (int c = 0; c < C; ++c) u[c] = czero<T>();
-    for (int tt = 0; tt < nt; ++tt) {
-      int k = act ? nbr_of(P.ly, lane, tt) : -1;
-      cx<T> a = k >= 0 ? P.Al(K, k, nt - 1 - tt) : czero<T>();
-      int src = k >= 0 ? k : lane;
-#pragma unroll
-      for (int c = 0; c < C; ++c) cfma(u[c], a, shfl_cx(prev[c], src));
+    for (int tt = 0; tt < kMaxNt; ++tt) {
+      int k = (act && tt < nt) ? nbr_of(P.ly, lane, tt) : -1;
+      al[tt] = k >= 0 ? P.Al(K, k, nt - 1 - tt) : czero<T>();
+      src[tt] = k >= 0 ? k : lane;
     }
     cx<T> x[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) x[c] = (act && c < R) ? X[(size_t)(K * b + lane) * rs + (size_t)c * cs] : czero<T>();
-    const cx<T>* D = Dinv + (size_t)K * bb;
+    cx<T> u[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) u[c] = czero<T>();
+#pragma unroll
+    for (int tt = 0; tt < kMaxNt; ++tt) {
+      if (tt >= nt) break;
+#pragma unroll
+      for (int c = 0; c < C; ++c) cfma(u[c], al[tt], shfl_cx(prev[c], src[tt]));
+    }
+    cp_async_wait<1>();
+    __syncwarp();
     for (int mm = 0; mm < b; ++mm) {
-      cx<T> d = act ? D[mm * b + lane] : czero<T>();
+      cx<T> d = act ? Dk[mm * b + lane] : czero<T>();
 #pragma unroll
       for (int c = 0; c < C; ++c) cfms(x[c], d, shfl_cx(u[c], mm));
     }
@@ -77,7 +133,10 @@ __device__ __forceinline__ void warp_layered_solve(const Prov& P, const cx<T>* _
       prev[c] = x[c];
       if (act && c < R) X[(size_t)(K * b + lane) * rs + (size_t)c * cs] = x[c];
     }
+    __syncwarp();
   }
+  cp_async_wait<0>();
+  __syncwarp();
 }
 
 // Block LDL^T, one warp per problem (b <= 32): the same steps as k_factor with warp barriers.
@@ -216,8 +275,10 @@ __global__ void k_local_solve_warp(StencilProv<T> P, Geom g, MapsView m, const c
   idx2crd(sd, g.nsub, dim, S);
   local_ext(g, ext);
   cx<T>* X = Xs + (size_t)sd * g.nl * R;
+  extern __shared__ unsigned char smraw[];
+  cx<T>* Ds = reinterpret_cast<cx<T>*>(smraw) + (size_t)(threadIdx.x >> 5) * 2 * b * b;
   auto rhs = [&](int K, int i, int c) -> cx<T> { return remainder_rhs(P, g, m, sd, S, f, ldf, lam, uc, K, i, c); };
-  warp_layered_solve<T, C>(P, Dinv + (size_t)q * L * b * b, R, rhs, X, R, 1);
+  warp_layered_solve<T, C>(P, Dinv + (size_t)q * L * b * b, R, rhs, X, R, 1, Ds);
   if (!VD) return;
   __syncwarp();
   for (int e = lane; e < R * nD; e += 32) {
@@ -250,8 +311,11 @@ __global__ void k_form_rr_warp(StencilProv<T> P, Geom g, MapsView m, const cx<T>
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int nD = g.nD, nc = g.nc, ncol = nD + nc, nchunk = (ncol + C - 1) / C;
   const int b = P.ly.b, L = P.ly.L, dim = g.dim;
-  // per-warp solution buffer in global memory (column-major: node fastest), persistent warps
+  // per-warp solution buffer in global memory (column-major: node fastest), persistent warps;
+  // per-warp staging buffer of the layer blocks in shared memory
   cx<T>* X = Xws + (size_t)(blockIdx.x * wpb + wib) * g.nl * C;
+  extern __shared__ unsigned char smraw[];
+  cx<T>* Ds = reinterpret_cast<cx<T>*>(smraw) + (size_t)wib * 2 * P.ly.b * P.ly.b;
   for (int w = blockIdx.x * wpb + wib; w < ncls * nchunk; w += gridDim.x * wpb) {
   const int q = w / nchunk, col0 = (w % nchunk) * C;
   P.select(q, m.cls_code);
@@ -270,7 +334,7 @@ __global__ void k_form_rr_warp(StencilProv<T> P, Geom g, MapsView m, const cx<T>
     if (local_dirichlet(code, lc, g.s, dim)) return czero<T>();
     return q1_entry(P.st, g.s, l, lc);
   };
-  warp_layered_solve<T, C>(P, Dinv + (size_t)q * L * b * b, C, rhs, X, 1, g.nl);
+  warp_layered_solve<T, C>(P, Dinv + (size_t)q * L * b * b, C, rhs, X, 1, g.nl, Ds);
   __syncwarp();
   for (int e = lane; e < nD * C; e += 32) {
     int j = e / C, c = e - j * C, col = col0 + c;
