@@ -38,6 +38,18 @@ namespace schur {
     }                                                                                  \
   } while (0)
 
+// Launch of the column-per-thread local operator formation (2D, layer size b <= B).
+template <class T, int B>
+static cudaError_t launch_form_cols(const StencilProv<T>& P, const Geom& g, const MapsView& mv, const cx<T>* Dinv,
+                                    int ncls, cx<T>* F, cx<T>* Frc, cx<double>* Kcc, cx<T>* Ews, int grid, int ldE,
+                                    cudaStream_t st) {
+  const size_t smem = form_cols_smem<T, B>(g.lb, g.lL);
+  cudaError_t e = smem_attr((const void*)k_form_rr_cols<T, B>, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_form_rr_cols<T, B><<<grid, ldE, smem, st>>>(P, g, mv, Dinv, ncls, F, Frc, Kcc, Ews, ldE);
+  return cudaGetLastError();
+}
+
 template <class T>
 class Engine : public EngineBase {
  public:
@@ -171,7 +183,37 @@ class Engine : public EngineBase {
     {
       const int C = 32;
       cx<T>* Xws = nullptr;
-      if (g.lb <= 32) {
+      bool formed = false;
+      if constexpr (sizeof(T) == 4) {
+        const int ncol = g.nD + g.nc, ldE = ((ncol + 31) / 32) * 32;
+        if (g.dim == 2 && g.lb <= 32 && ldE <= 128) {
+          const int Bp = g.lb == 9 ? 9 : g.lb == 17 ? 17 : ((g.lb + 7) / 8) * 8;
+          const size_t per_cta = (size_t)g.lL * Bp * ldE * cxT;
+          int grid = std::min(ncls_, 8 * nsm_);
+          grid = std::max(1, (int)std::min<size_t>((size_t)grid, ((size_t)256 << 20) / per_cta));
+          ENG_CK(alloc(&Xws, (size_t)grid * per_cta));
+          prof_start(KC_FORM, st);
+          cudaError_t fe = cudaErrorInvalidValue;
+#define FC_CASE(BV) \
+  case BV: fe = launch_form_cols<T, BV>(prr_, g, mv_, Dinv_, ncls_, F_, Frc_, Kcc_, Xws, grid, ldE, st); break
+          switch (Bp) {
+            FC_CASE(8);
+            FC_CASE(9);
+            FC_CASE(16);
+            FC_CASE(17);
+            FC_CASE(24);
+            FC_CASE(32);
+            default: break;
+          }
+#undef FC_CASE
+          ENG_CK(fe);
+          prof_stop(KC_FORM, st);
+          ENG_LAUNCH();
+          formed = true;
+        }
+      }
+      if (formed) {
+      } else if (g.lb <= 32) {
         constexpr int CW = 4;
         const int ncol = g.nD + g.nc, nchunk = (ncol + CW - 1) / CW, nwork = ncls_ * nchunk;
         const int wpb = 4;

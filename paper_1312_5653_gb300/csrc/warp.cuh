@@ -139,6 +139,247 @@ __device__ __forceinline__ void warp_layered_solve(const Prov& P, const cx<T>* _
   __syncwarp();
 }
 
+// Local operators F, Frc, Kcc of each class on 2D remainder problems (layer size b <= B), one CTA
+// per class and one thread per right-hand-side column c of [E_Delta, A_rc]: the thread keeps its
+// column of the current layer in registers (rows unrolled at compile time), the layer block
+// D_K^{-1} and the neighbour couplings are staged in shared memory and read as broadcasts, so each
+// row update of E_K = D_K^{-1} (b_K - A_{K,K-1} E_{K-1}) is B complex FMAs per loaded entry pair.
+// Forward results E_K go to a per-CTA global buffer (layer, row, column; column fastest) and are
+// read back by the same thread in the backward sweep X_K = E_K - D_K^{-1} A_{K,K+1} X_{K+1}.
+// Outputs: rows of X on the interface slots (F, Frc) and, for the corner columns, the corner
+// Schur complement Kcc = A_cc - A_cr X_rc accumulated while the sweep passes the corner layers.
+template <int B>
+struct ColsLayout {
+  static constexpr int SB = (B + 1) & ~1;  // row stride of the staged blocks: 16-byte aligned rows
+};
+
+template <class T, int B>
+__host__ __device__ constexpr size_t form_cols_smem(int b, int L) {
+  return (2 * (size_t)B * ColsLayout<B>::SB + 3 * (size_t)B + 12 * (size_t)B) * sizeof(cx<T>) +
+         ((size_t)L * b + 12) * sizeof(int);
+}
+
+template <class T, int SB>
+__device__ __forceinline__ void load_pair(const cx<T>* p, cx<T>& a, cx<T>& b2) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = mkc<T>(v.x, v.y);
+    b2 = mkc<T>(v.z, v.w);
+  } else {
+    a = p[0];
+    b2 = p[1];
+  }
+}
+
+template <class T, int B>
+__global__ void __launch_bounds__(128) k_form_rr_cols(StencilProv<T> P, Geom g, MapsView m, const cx<T>* __restrict__ Dinv,
+                                                      int ncls, cx<T>* F, cx<T>* Frc, cx<double>* Kcc, cx<T>* Ews,
+                                                      int ldE) {
+  constexpr int SB = ColsLayout<B>::SB, NT = 3;
+  const int b = P.ly.b, L = P.ly.L, nD = g.nD, nc = g.nc, ncol = nD + nc, bb = b * b;
+  const int c = threadIdx.x, nthr = blockDim.x;
+  extern __shared__ __align__(16) unsigned char smcols[];
+  cx<T>* Db = reinterpret_cast<cx<T>*>(smcols);  // 2 x B x SB
+  cx<T>* cf = Db + 2 * B * SB;                  // B x 3 couplings of the current layer
+  cx<T>* ct = cf + 3 * B;                       // 4 corners x 3 layers x B: A(node, corner)
+  int* slot_s = reinterpret_cast<int*>(ct + 12 * B);  // L x b: interface slot of node or -1
+  int* cK = slot_s + L * b;                           // corner layer, row, Dirichlet flag
+  int* cI = cK + 4;
+  int* cDir = cI + 4;
+  for (int e = c; e < 2 * B * SB; e += nthr) Db[e] = czero<T>();
+  for (int e = c; e < L * b; e += nthr) slot_s[e] = m.node_slot[e];
+  cx<T>* E = Ews + (size_t)blockIdx.x * L * B * ldE;
+  const bool is_unit = c < nD, is_corner = c >= nD && c < ncol;
+  const int cc = c - nD;
+  for (int q = blockIdx.x; q < ncls; q += gridDim.x) {
+    P.select(q, m.cls_code);
+    if (c < nc) {
+      const int node = m.corner_node[c];
+      cK[c] = node / b;
+      cI[c] = node % b;
+      int lc[3];
+      P.crd(node / b, node % b, lc);
+      cDir[c] = local_dirichlet(P.code, lc, g.s, 2) ? 1 : 0;
+    }
+    __syncthreads();
+    for (int e = c; e < 12 * B; e += nthr) {
+      const int c1 = e / (3 * B), d = (e / B) % 3, i = e % B;
+      const int K = cK[c1] - 1 + d;
+      cx<T> v = czero<T>();
+      if (c1 < nc && !cDir[c1] && i < b && K >= 0 && K < L && abs(i - cI[c1]) <= 1 && !P.removed_node(K, i)) {
+        int l[3], lc[3];
+        P.crd(K, i, l);
+        P.crd(cK[c1], cI[c1], lc);
+        v = q1_entry(P.st, g.s, l, lc);
+      }
+      ct[e] = v;
+    }
+    int Ku = -1, iu = -1;
+    if (is_unit) {
+      const int node = m.slot_node[c];
+      if (!P.removed_node(node / b, node % b)) {
+        Ku = node / b;
+        iu = node % b;
+      }
+    }
+    auto stage = [&](int K, int buf) {
+      const cx<T>* src = Dinv + ((size_t)q * L + K) * bb;
+      cx<T>* dst = Db + buf * B * SB;
+      for (int e = c; e < bb; e += nthr) {
+        const int mm = e / b, i = e - mm * b;
+        cp_async_cx(dst + mm * SB + i, src + e);
+      }
+    };
+    cx<T> prev[B], kacc[4];
+#pragma unroll
+    for (int i = 0; i < B; ++i) prev[i] = czero<T>();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) kacc[k] = czero<T>();
+    auto emit = [&](int K, const cx<T>* x) {
+      if (is_unit || is_corner) {
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+          if (i < b) {
+            const int j = slot_s[K * b + i];
+            if (j >= 0) {
+              if (is_unit) F[((size_t)q * nD + j) * nD + c] = x[i];
+              else Frc[((size_t)q * nD + j) * nc + cc] = x[i];
+            }
+          }
+        }
+      }
+      if (is_corner) {
+#pragma unroll
+        for (int c1 = 0; c1 < 4; ++c1) {
+          const int d = K - cK[c1] + 1;
+          if (c1 < nc && d >= 0 && d < 3) {
+            const cx<T>* a = ct + (c1 * 3 + d) * B;
+#pragma unroll
+            for (int i = 0; i < B; ++i) cfms(kacc[c1], a[i], x[i]);
+          }
+        }
+      }
+    };
+    __syncthreads();  // corner tables and cleared blocks visible; previous class fully consumed
+    // ---- forward sweep
+    stage(0, 0);
+    cp_async_commit();
+    for (int K = 0; K < L; ++K) {
+      if (K + 1 < L) stage(K + 1, (K + 1) & 1);
+      cp_async_commit();
+      if (K > 0)
+        for (int e = c; e < b * NT; e += nthr) cf[e] = P.Al(K - 1, e / NT, e % NT);
+      cx<T> t[B];
+#pragma unroll
+      for (int i = 0; i < B; ++i) t[i] = czero<T>();
+      if (K == Ku) {
+#pragma unroll
+        for (int i = 0; i < B; ++i)
+          if (i == iu) t[i] = mkc<T>(T(1), T(0));
+      }
+      if (is_corner) {
+        const int d = K - cK[cc] + 1;
+        if (d >= 0 && d < 3) {
+#pragma unroll
+          for (int i = 0; i < B; ++i) t[i] = ct[(cc * 3 + d) * B + i];
+        }
+      }
+      cp_async_wait<1>();
+      __syncthreads();
+      if (K > 0) {
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+          if (i < b) {
+            if (i > 0) cfms(t[i], cf[i * NT], prev[i - 1]);
+            cfms(t[i], cf[i * NT + 1], prev[i]);
+            if (i + 1 < B) cfms(t[i], cf[i * NT + 2], prev[i + 1]);
+          }
+        }
+      }
+      const cx<T>* Dk = Db + (K & 1) * B * SB;
+#pragma unroll
+      for (int i = 0; i < B; ++i) prev[i] = czero<T>();
+#pragma unroll
+      for (int mm = 0; mm < B; ++mm) {
+        const cx<T> tm = t[mm];
+#pragma unroll
+        for (int i = 0; i + 1 < B; i += 2) {
+          cx<T> d0, d1;
+          load_pair<T, SB>(Dk + mm * SB + i, d0, d1);
+          cfma(prev[i], d0, tm);
+          cfma(prev[i + 1], d1, tm);
+        }
+        if (B & 1) cfma(prev[B - 1], Dk[mm * SB + B - 1], tm);
+      }
+      if (c < ldE) {
+#pragma unroll
+        for (int i = 0; i < B; ++i)
+          if (i < b) E[((size_t)K * B + i) * ldE + c] = prev[i];
+      }
+      __syncthreads();
+    }
+    emit(L - 1, prev);
+    // ---- backward sweep: prev = X_{K+1}
+    if (L >= 2) stage(L - 2, 0);
+    cp_async_commit();
+    for (int K = L - 2, it = 0; K >= 0; --K, ++it) {
+      if (K >= 1) stage(K - 1, (it + 1) & 1);
+      cp_async_commit();
+      for (int e = c; e < b * NT; e += nthr) {
+        const int i = e / NT, tt = e - i * NT, k = i + tt - 1;
+        cf[e] = (k >= 0 && k < b) ? P.Al(K, k, NT - 1 - tt) : czero<T>();
+      }
+      cx<T> x[B];
+#pragma unroll
+      for (int i = 0; i < B; ++i) x[i] = (c < ldE && i < b) ? E[((size_t)K * B + i) * ldE + c] : czero<T>();
+      cp_async_wait<1>();
+      __syncthreads();
+      cx<T> u[B];
+#pragma unroll
+      for (int i = 0; i < B; ++i) {
+        u[i] = czero<T>();
+        if (i < b) {
+          if (i > 0) cfma(u[i], cf[i * NT], prev[i - 1]);
+          cfma(u[i], cf[i * NT + 1], prev[i]);
+          if (i + 1 < B) cfma(u[i], cf[i * NT + 2], prev[i + 1]);
+        }
+      }
+      const cx<T>* Dk = Db + (it & 1) * B * SB;
+#pragma unroll
+      for (int mm = 0; mm < B; ++mm) {
+        const cx<T> um = u[mm];
+#pragma unroll
+        for (int i = 0; i + 1 < B; i += 2) {
+          cx<T> d0, d1;
+          load_pair<T, SB>(Dk + mm * SB + i, d0, d1);
+          cfms(x[i], d0, um);
+          cfms(x[i + 1], d1, um);
+        }
+        if (B & 1) cfms(x[B - 1], Dk[mm * SB + B - 1], um);
+      }
+      emit(K, x);
+#pragma unroll
+      for (int i = 0; i < B; ++i) prev[i] = x[i];
+      __syncthreads();
+    }
+    cp_async_wait<0>();
+    if (is_corner) {
+      int lc2[3];
+      P.crd(cK[cc], cI[cc], lc2);
+#pragma unroll
+      for (int c1 = 0; c1 < 4; ++c1) {
+        if (c1 < nc) {
+          cx<T> v = kacc[c1];
+          if (c1 == cc) v = cadd(v, q1_entry(P.st, g.s, lc2, lc2));
+          if (cDir[c1] || cDir[cc]) v = czero<T>();
+          Kcc[((size_t)q * nc + c1) * nc + cc] = ccast<double>(v);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Block LDL^T, one warp per problem (b <= 32): the same steps as k_factor with warp barriers.
 template <class T>
 __global__ void k_factor_warp(StencilProv<T> P, const int* codes, int nprob, cx<T>* Dinv, int* err) {

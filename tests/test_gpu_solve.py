@@ -29,7 +29,10 @@ def gpu(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(DEV)
 
 
-@pytest.mark.parametrize("dim,N,P,beta", [(2, 8, 2, 1e-4), (2, 12, 3, 1e-2), (3, 6, 3, 1e-6)])
+# 2D layer sizes b = s + 1 of 5, 9, 14, 17 and 32 cover the exact (9, 17) and padded (8, 16, 32)
+# register-tile widths of the column-per-thread formation kernel.
+@pytest.mark.parametrize("dim,N,P,beta", [(2, 8, 2, 1e-4), (2, 12, 3, 1e-2), (3, 6, 3, 1e-6), (2, 16, 2, 1e-6),
+                                          (2, 26, 2, 1e-3), (2, 32, 2, 1e-4), (2, 62, 2, 1e-2)])
 @pytest.mark.parametrize("prec", PRECS)
 def test_local_operators_match_dense_definitions(dim, N, P, beta, prec):
     sol = S.Solver(dim, N, beta, nsub=P, precision=prec)
@@ -107,7 +110,7 @@ def test_multi_rhs_chunks_and_zero(prec):
 
 
 @pytest.mark.parametrize("nel,nsub", [((12, 8), (3, 2)), ((8, 8), (2, 1)), ((6, 6), (1, 1)), ((6, 8, 4), (3, 2, 2)),
-                                      ((20, 20), (10, 10))])
+                                      ((20, 20), (10, 10)), ((24, 16), (2, 2))])
 @pytest.mark.parametrize("prec", PRECS)
 def test_ragged_and_degenerate_partitions(nel, nsub, prec):
     """Anisotropic grids, no primal corners (nsub = 1 on an axis), a single subdomain (no
