@@ -138,8 +138,9 @@ class Engine : public EngineBase {
     ENG_CK(alloc(&Dinv_, (size_t)ncls_ * g.lL * bb * cxT));
     op_bytes_ += (long long)ncls_ * g.lL * bb * cxT;
     if (g.lb <= 32) {
-      const int wpb = 8;
-      size_t smem = (size_t)wpb * (2 * bb + 2 * g.lb) * cxT;
+      const size_t per_warp = (2 * (size_t)bb + 2 * g.lb) * cxT;
+      const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, ((size_t)160 << 10) / per_warp));
+      size_t smem = (size_t)wpb * per_warp;
       ENG_CK(smem_attr((const void*)k_factor_warp<T>, (int)smem));
       prof_start(KC_FACTOR, st);
       k_factor_warp<T><<<(ncls_ + wpb - 1) / wpb, 32 * wpb, smem, st>>>(prr_, dm_->cls_code, ncls_, Dinv_, err_);
