@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(256) k_gj_batch_cluster(const cx<S>* __restric
   cluster.sync();
 }
 
-// One batched complex GEMM task: C (+)= alpha * A * op(B), all b x b (or b x N for the solve),
+// One batched complex GEMM task: C (+)= alpha * A * op(B), A b x b, B and C b x N (N per task),
 // row-major with leading dimensions; transB: use B^T.
 template <class S>
 struct GemmTask {
@@ -114,6 +114,17 @@ struct GemmTask {
   int transB;
   S alpha;  // real scale (+1 / -1)
   int accumulate;
+  int N;
+};
+
+// One block copy: dst = src (count entries), src^T for a b x b block when transpose, zero when
+// src is null.
+template <class S>
+struct CopyTask {
+  const cx<S>* src;
+  cx<S>* dst;
+  long long count;
+  int transpose;
 };
 
 // C[M x N] (+)= alpha * A[M x Kd] * B[Kd x N]  (B^T when transB), TM x TM output tiles per CTA,
@@ -125,10 +136,12 @@ struct GemmTile {
 };
 
 template <class S, int TM>
-__global__ void __launch_bounds__(256) k_gemm_batch(const GemmTask<S>* __restrict__ tasks, int M, int N, int Kd) {
+__global__ void __launch_bounds__(256) k_gemm_batch(const GemmTask<S>* __restrict__ tasks, int M, int Kd) {
   constexpr int Q = TM / 16;
   const GemmTask<S> t = tasks[blockIdx.z];
+  const int N = t.N;
   const int row0 = blockIdx.y * TM, col0 = blockIdx.x * TM;
+  if (col0 >= N) return;  // tasks narrower than the grid
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   __shared__ cx<S> As[16][TM + 1];
   __shared__ cx<S> Bs[16][TM + 1];
@@ -176,40 +189,74 @@ __global__ void __launch_bounds__(256) k_gemm_batch(const GemmTask<S>* __restric
     }
 }
 
+// Batched block copies, grid (chunks, tasks).  Transposed copies are b x b blocks (count = b*b).
 template <class S>
-static cudaError_t launch_gemms(const std::vector<GemmTask<S>>& tasks, GemmTask<S>* dtasks, int M, int N, int Kd,
-                                cudaStream_t st) {
-  if (tasks.empty()) return cudaSuccess;
-  cudaError_t e = cudaMemcpyAsync(dtasks, tasks.data(), tasks.size() * sizeof(GemmTask<S>), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return e;
-  constexpr int TM = GemmTile<S>::TM;
-  dim3 grid((N + TM - 1) / TM, (M + TM - 1) / TM, (unsigned)tasks.size());
-  k_gemm_batch<S, TM><<<grid, 256, 0, st>>>(dtasks, M, N, Kd);
-  return cudaGetLastError();
-}
-
-// ------------------------------------------------------------------ host orchestration
-// Levels: lists of (j, p, q) with p, q = remaining neighbours of j (-1 if none).
-static void bcr_schedule(int L, std::vector<std::vector<int>>* lev_j, std::vector<std::vector<int>>* lev_p,
-                         std::vector<std::vector<int>>* lev_q) {
-  std::vector<int> rem(L);
-  for (int i = 0; i < L; ++i) rem[i] = i;
-  while (!rem.empty()) {
-    std::vector<int> J, Pp, Q, next;
-    for (size_t t = 0; t < rem.size(); ++t) {
-      if (t % 2 == 0) {
-        J.push_back(rem[t]);
-        Pp.push_back(t > 0 ? rem[t - 1] : -1);
-        Q.push_back(t + 1 < rem.size() ? rem[t + 1] : -1);
+__global__ void k_copy_blocks(const CopyTask<S>* __restrict__ tasks, int b) {
+  const CopyTask<S> t = tasks[blockIdx.y];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < t.count; e += (long long)gridDim.x * blockDim.x) {
+    cx<S> v = mkc<S>(0, 0);
+    if (t.src) {
+      if (t.transpose) {
+        const int i = (int)(e / b), j = (int)(e - (long long)i * b);
+        v = t.src[(size_t)j * b + i];
       } else {
-        next.push_back(rem[t]);
+        v = t.src[e];
       }
     }
-    lev_j->push_back(J);
-    lev_p->push_back(Pp);
-    lev_q->push_back(Q);
-    rem.swap(next);
+    t.dst[e] = v;
   }
+}
+
+// Gauss-Jordan inversion of a batch of dense b x b blocks, one CTA per block with the block in
+// shared memory: threads (tx, ty) of a 32 x 8 grid sweep columns j = tx + 32 c and rows
+// i = ty + 8 r, so no index division is needed; two barriers per pivot.
+template <class S>
+__global__ void __launch_bounds__(256) k_gj_block(const cx<S>* __restrict__ Din, cx<S>* Dout,
+                                                  const int* __restrict__ list, int b, int* err) {
+  extern __shared__ __align__(16) unsigned char smgj[];
+  cx<S>* A = reinterpret_cast<cx<S>*>(smgj);  // b x b
+  cx<S>* rowk = A + (size_t)b * b;            // b
+  cx<S>* colk = rowk + b;                     // b
+  const int which = list[blockIdx.x];
+  const size_t bb = (size_t)b * b;
+  const cx<S>* src = Din + (size_t)which * bb;
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  for (int e = tid; e < (int)bb; e += 256) A[e] = src[e];
+  __syncthreads();
+  for (int k = 0; k < b; ++k) {
+    const cx<S> p = A[k * b + k];
+    const cx<S> piv = cinv(p);
+    if (tid == 0 && !finite_nonzero(p)) atomicExch(err, 1);
+    for (int j = tid; j < b; j += 256) {
+      rowk[j] = cmul(A[k * b + j], piv);
+      colk[j] = A[j * b + k];
+    }
+    __syncthreads();
+    for (int i = ty; i < b; i += 8) {
+      const cx<S> ci = colk[i];
+      cx<S>* Ai = A + (size_t)i * b;
+      if (i == k) {
+        for (int j = tx; j < b; j += 32) Ai[j] = (j == k) ? piv : rowk[j];
+      } else {
+        for (int j = tx; j < b; j += 32) {
+          if (j == k) {
+            const cx<S> v = cmul(ci, piv);
+            Ai[j] = mkc<S>(-v.re, -v.im);
+          } else {
+            cfms(Ai[j], ci, rowk[j]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  cx<S>* dst = Dout + (size_t)which * bb;
+  for (int e = tid; e < (int)bb; e += 256) dst[e] = A[e];
+}
+
+template <class S>
+static size_t gj_block_smem(int b) {
+  return ((size_t)b * b + 2 * (size_t)b) * sizeof(cx<S>);
 }
 
 template <class S>
@@ -218,9 +265,18 @@ static size_t bcr_gj_smem(int b, int CL) {
   return ((size_t)b * cw + 3 * (size_t)b + cw) * sizeof(cx<S>);
 }
 
+// Inversion of the listed blocks: one CTA per block when the block fits in shared memory, else
+// one thread-block cluster per block with the columns distributed over its CTAs.
 template <class S>
 static cudaError_t launch_gj_batch(const cx<S>* Din, cx<S>* Dout, const int* dlist, int nblk, int b, int* err,
                                    cudaStream_t st) {
+  if (gj_block_smem<S>(b) <= 200 * 1024) {
+    const size_t smem = gj_block_smem<S>(b);
+    cudaError_t e = smem_attr((const void*)k_gj_block<S>, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gj_block<S><<<nblk, 256, smem, st>>>(Din, Dout, dlist, b, err);
+    return cudaGetLastError();
+  }
   static const int sizes[] = {16, 8, 4, 2, 1};
   cudaError_t last = cudaErrorInvalidConfiguration;
   for (int CL : sizes) {
@@ -268,59 +324,68 @@ __global__ void k_bcr_identity(cx<T>* X, int n) {
     X[e] = mkc<T>((e / n) == (e % n) ? T(1) : T(0), T(0));
 }
 
-// Solve with the reduction factors for the right-hand side X (n_c x N, row-major, rows grouped by
-// layer), in place.  Dinv_j, UP_j = A_pj and UQ_j = A_jq in precision S; UP + L*b*b and
-// UQ + L*b*b hold their transposes.  Updates of one block by two neighbours go to separate
-// launches, so no launch has two tasks writing the same block.
-template <class S>
-static cudaError_t bcr_solve(const cx<S>* Dinv, const cx<S>* UP, const cx<S>* UQ, int b, int L,
-                             const std::vector<std::vector<int>>& lj, const std::vector<std::vector<int>>& lp,
-                             const std::vector<std::vector<int>>& lq, cx<S>* X, cx<S>* Tmp, int N,
-                             GemmTask<S>* dt, cudaStream_t st) {
-  const size_t bb = (size_t)b * b, bN = (size_t)b * N;
-  const cx<S>* UPT = UP + (size_t)L * bb;
-  const cx<S>* UQT = UQ + (size_t)L * bb;
-  cudaError_t e = cudaSuccess;
-  for (size_t lv = 0; lv < lj.size() && e == cudaSuccess; ++lv) {
-    std::vector<GemmTask<S>> t1, ta, tb;
-    for (size_t k = 0; k < lj[lv].size(); ++k) {
-      const int j = lj[lv][k], p = lp[lv][k], q = lq[lv][k];
-      t1.push_back({Dinv + j * bb, X + j * bN, Tmp + j * bN, b, N, N, 0, S(1), 0});  // Tmp_j = Dinv_j X_j
-      if (p >= 0) ta.push_back({UP + j * bb, Tmp + j * bN, X + p * bN, b, N, N, 0, S(-1), 1});   // X_p -= A_pj Tmp_j
-      if (q >= 0) tb.push_back({UQT + j * bb, Tmp + j * bN, X + q * bN, b, N, N, 0, S(-1), 1});  // X_q -= A_qj Tmp_j
+// ------------------------------------------------------------------ host orchestration
+// Levels: lists of (j, p, q) with p, q = remaining neighbours of j (-1 if none).
+static void bcr_schedule(int L, std::vector<std::vector<int>>* lev_j, std::vector<std::vector<int>>* lev_p,
+                         std::vector<std::vector<int>>* lev_q) {
+  std::vector<int> rem(L);
+  for (int i = 0; i < L; ++i) rem[i] = i;
+  while (!rem.empty()) {
+    std::vector<int> J, Pp, Q, next;
+    for (size_t t = 0; t < rem.size(); ++t) {
+      if (t % 2 == 0) {
+        J.push_back(rem[t]);
+        Pp.push_back(t > 0 ? rem[t - 1] : -1);
+        Q.push_back(t + 1 < rem.size() ? rem[t + 1] : -1);
+      } else {
+        next.push_back(rem[t]);
+      }
     }
-    e = launch_gemms(t1, dt, b, N, b, st);
-    if (e == cudaSuccess) e = launch_gemms(ta, dt + t1.size(), b, N, b, st);
-    if (e == cudaSuccess) e = launch_gemms(tb, dt + t1.size() + ta.size(), b, N, b, st);
+    lev_j->push_back(J);
+    lev_p->push_back(Pp);
+    lev_q->push_back(Q);
+    rem.swap(next);
   }
-  for (int lv = (int)lj.size() - 1; lv >= 0 && e == cudaSuccess; --lv) {
-    std::vector<GemmTask<S>> ta, tb, t2;
-    for (size_t k = 0; k < lj[lv].size(); ++k) {
-      const int j = lj[lv][k], p = lp[lv][k], q = lq[lv][k];
-      if (p >= 0) ta.push_back({UPT + j * bb, X + p * bN, X + j * bN, b, N, N, 0, S(-1), 1});  // X_j -= A_jp X_p
-      if (q >= 0) tb.push_back({UQ + j * bb, X + q * bN, X + j * bN, b, N, N, 0, S(-1), 1});   // X_j -= A_jq X_q
-      t2.push_back({Dinv + j * bb, X + j * bN, Tmp + j * bN, b, N, N, 0, S(1), 0});
-    }
-    e = launch_gemms(ta, dt, b, N, b, st);
-    if (e == cudaSuccess) e = launch_gemms(tb, dt + ta.size(), b, N, b, st);
-    if (e == cudaSuccess) e = launch_gemms(t2, dt + ta.size() + tb.size(), b, N, b, st);
-    for (size_t k = 0; k < lj[lv].size() && e == cudaSuccess; ++k) {
-      const int j = lj[lv][k];
-      e = cudaMemcpyAsync(X + j * bN, Tmp + j * bN, bN * sizeof(cx<S>), cudaMemcpyDeviceToDevice, st);
-    }
-  }
-  return e;
 }
 
-template <class S>
-__global__ void k_bcr_transpose(const cx<S>* __restrict__ in, cx<S>* out, int b, int L) {
-  const size_t bb = (size_t)b * b;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)L * bb; e += (size_t)gridDim.x * blockDim.x) {
-    size_t K = e / bb, r = e % bb;
-    int i = (int)(r / b), j = (int)(r % b);
-    out[K * bb + (size_t)j * b + i] = in[e];
+// The whole reduction as a list of launches over task arrays that are built on the host and
+// uploaded once.
+enum BcrOpKind { OP_GJ, OP_GEMM, OP_COPY };
+struct BcrOp {
+  BcrOpKind kind;
+  size_t off;  // first task (GEMM, COPY) or list entry (GJ)
+  int count;
+  int maxN;      // GEMM: widest task; COPY: longest copy
+  bool timed_inverse;  // first op of the inverse phase (profiling boundary)
+};
+
+template <class T>
+struct BcrPlan {
+  std::vector<GemmTask<T>> gemm;
+  std::vector<CopyTask<T>> copy;
+  std::vector<int> list;
+  std::vector<BcrOp> ops;
+  void add_gemm(std::vector<GemmTask<T>>& ts) {
+    if (ts.empty()) return;
+    int mx = 0;
+    for (auto& t : ts) mx = std::max(mx, t.N);
+    ops.push_back({OP_GEMM, gemm.size(), (int)ts.size(), mx, false});
+    gemm.insert(gemm.end(), ts.begin(), ts.end());
+    ts.clear();
   }
-}
+  void add_copy(std::vector<CopyTask<T>>& ts) {
+    if (ts.empty()) return;
+    long long mx = 0;
+    for (auto& t : ts) mx = std::max(mx, t.count);
+    ops.push_back({OP_COPY, copy.size(), (int)ts.size(), (int)std::min<long long>(mx, 1 << 30), false});
+    copy.insert(copy.end(), ts.begin(), ts.end());
+    ts.clear();
+  }
+  void add_gj(const std::vector<int>& J) {
+    ops.push_back({OP_GJ, list.size(), (int)J.size(), 0, false});
+    list.insert(list.end(), J.begin(), J.end());
+  }
+};
 
 template <class T>
 int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int* err, cudaStream_t st, std::string* msg,
@@ -329,17 +394,13 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int* err, cudaStream_t 
   const size_t bb = (size_t)b * b, n = (size_t)b * L;
   std::vector<std::vector<int>> lj, lp, lq;
   bcr_schedule(L, &lj, &lp, &lq);
-  cx<T>*D = nullptr, *Ucur = nullptr, *Dinv = nullptr, *UP = nullptr, *UQ = nullptr, *Lp = nullptr, *Lq = nullptr,
-        *Unew = nullptr;
-  int* dlist = nullptr;
-  GemmTask<T>* dtT = nullptr;
   auto fail = [&](cudaError_t e, const char* where) {
     if (msg) *msg = std::string("coarse reduction (") + where + "): " + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? SCHUR_ENOMEM : SCHUR_ECUDA;
   };
-#define BCR_CK(x, where)                    \
-  do {                                      \
-    cudaError_t e_ = (x);                   \
+#define BCR_CK(x, where)                           \
+  do {                                             \
+    cudaError_t e_ = (x);                          \
     if (e_ != cudaSuccess) return fail(e_, where); \
   } while (0)
   std::vector<void*> mem;
@@ -355,97 +416,171 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int* err, cudaStream_t 
       for (void* p : *m) cudaFreeAsync(p, s);
     }
   } guard{&mem, st};
+  cx<T>*D = nullptr, *Ucur = nullptr, *Dinv = nullptr, *UP = nullptr, *UQ = nullptr, *Lp = nullptr, *Lq = nullptr,
+        *Unew = nullptr, *Tmp = nullptr;
   BCR_CK(mal(&D, L * bb * sizeof(cx<T>)), "alloc");
   BCR_CK(mal(&Ucur, L * bb * sizeof(cx<T>)), "alloc");
   BCR_CK(mal(&Dinv, L * bb * sizeof(cx<T>)), "alloc");
-  BCR_CK(mal(&UP, 2 * L * bb * sizeof(cx<T>)), "alloc");  // UP_j, then its transposes
-  BCR_CK(mal(&UQ, 2 * L * bb * sizeof(cx<T>)), "alloc");  // UQ_j, then its transposes
+  BCR_CK(mal(&UP, 2 * L * bb * sizeof(cx<T>)), "alloc");  // UP_j = A_pj, then the transposes
+  BCR_CK(mal(&UQ, 2 * L * bb * sizeof(cx<T>)), "alloc");  // UQ_j = A_jq, then the transposes
   BCR_CK(mal(&Lp, L * bb * sizeof(cx<T>)), "alloc");
   BCR_CK(mal(&Lq, L * bb * sizeof(cx<T>)), "alloc");
   BCR_CK(mal(&Unew, L * bb * sizeof(cx<T>)), "alloc");
-  BCR_CK(mal(&dlist, (size_t)L * sizeof(int)), "alloc");
-  BCR_CK(mal(&dtT, (size_t)4 * L * sizeof(GemmTask<T>)), "alloc");
-  BCR_CK(cudaMemsetAsync(UP, 0, 2 * L * bb * sizeof(cx<T>), st), "memset");
-  BCR_CK(cudaMemsetAsync(UQ, 0, 2 * L * bb * sizeof(cx<T>), st), "memset");
-  const int gs = (int)std::min<size_t>((L * bb + 255) / 256, 4096);
-  k_bcr_densify<T><<<gs, 256, 0, st>>>(P, D, Ucur);
-  BCR_CK(cudaGetLastError(), "densify");
-  ++*launches;
-  // ---- factorisation
-  prof_start(KC_COARSE_SETUP, st);
+  BCR_CK(mal(&Tmp, n * n * sizeof(cx<T>)), "alloc");
+  cx<T>* UPT = UP + (size_t)L * bb;
+  cx<T>* UQT = UQ + (size_t)L * bb;
+
+  // ---- plan: factorisation
+  BcrPlan<T> plan;
+  std::vector<GemmTask<T>> ts;
+  std::vector<CopyTask<T>> cs;
+  const long long lbb = (long long)bb;
   for (size_t lv = 0; lv < lj.size(); ++lv) {
     const std::vector<int>& J = lj[lv];
-    BCR_CK(cudaMemcpyAsync(dlist, J.data(), J.size() * sizeof(int), cudaMemcpyHostToDevice, st), "list");
-    BCR_CK(launch_gj_batch<T>(D, Dinv, dlist, (int)J.size(), b, err, st), "inversion");
-    ++*launches;
-    std::vector<GemmTask<T>> t1;
+    plan.add_gj(J);  // Dinv_j = D_j^{-1}
     for (size_t k = 0; k < J.size(); ++k) {
-      int j = J[k], p = lp[lv][k], q = lq[lv][k];
+      const int j = J[k], p = lp[lv][k], q = lq[lv][k];
+      if (p >= 0) cs.push_back({Ucur + p * bb, UP + j * bb, lbb, 0});  // UP_j = A_pj
+      if (q >= 0) cs.push_back({Ucur + j * bb, UQ + j * bb, lbb, 0});  // UQ_j = A_jq
+      if (q >= 0) cs.push_back({Ucur + j * bb, UQT + j * bb, lbb, 1});  // UQ_j^T
+    }
+    plan.add_copy(cs);
+    for (size_t k = 0; k < J.size(); ++k) {
+      const int j = J[k], p = lp[lv][k], q = lq[lv][k];
+      // Lp_j = A_pj Dinv_j ; Lq_j = Dinv_j A_jq (= (A_qj Dinv_j)^T, Dinv_j symmetric)
+      if (p >= 0) ts.push_back({Ucur + p * bb, Dinv + j * bb, Lp + j * bb, b, b, b, 0, T(1), 0, b});
+      if (q >= 0) ts.push_back({Dinv + j * bb, Ucur + j * bb, Lq + j * bb, b, b, b, 0, T(1), 0, b});
+    }
+    plan.add_gemm(ts);
+    // D_p -= Lp_j A_jp = Lp_j UP_j^T ; A_pq (new coupling of p) = -Lp_j UQ_j.  A separate launch
+    // for D_q -= A_qj Dinv_j A_jq = UQ_j^T Lq_j: no two tasks of one launch write the same block.
+    for (size_t k = 0; k < J.size(); ++k) {
+      const int j = J[k], p = lp[lv][k], q = lq[lv][k];
       if (p >= 0) {
-        // UP_j = A_pj = Ucur_p ; Lp_j = UP_j Dinv_j
-        BCR_CK(cudaMemcpyAsync(UP + j * bb, Ucur + p * bb, bb * sizeof(cx<T>), cudaMemcpyDeviceToDevice, st), "copy");
-        t1.push_back({Ucur + p * bb, Dinv + j * bb, Lp + j * bb, b, b, b, 0, T(1), 0});
+        ts.push_back({Lp + j * bb, UP + j * bb, D + p * bb, b, b, b, 1, T(-1), 1, b});
+        if (q >= 0) ts.push_back({Lp + j * bb, UQ + j * bb, Unew + p * bb, b, b, b, 0, T(-1), 0, b});
+      }
+    }
+    plan.add_gemm(ts);
+    for (size_t k = 0; k < J.size(); ++k) {
+      const int j = J[k], q = lq[lv][k];
+      if (q >= 0) ts.push_back({UQT + j * bb, Lq + j * bb, D + q * bb, b, b, b, 0, T(-1), 1, b});
+    }
+    plan.add_gemm(ts);
+    // a remaining p whose right neighbour j was eliminated now couples to q (or to nothing)
+    for (size_t k = 0; k < J.size(); ++k) {
+      const int p = lp[lv][k], q = lq[lv][k];
+      if (p >= 0) cs.push_back({q >= 0 ? Unew + p * bb : nullptr, Ucur + p * bb, lbb, 0});
+    }
+    plan.add_copy(cs);
+  }
+  // transposes of UP for the back substitution
+  for (size_t lv = 0; lv < lj.size(); ++lv)
+    for (size_t k = 0; k < lj[lv].size(); ++k)
+      if (lp[lv][k] >= 0) cs.push_back({UP + lj[lv][k] * bb, UPT + lj[lv][k] * bb, lbb, 1});
+  plan.add_copy(cs);
+  const size_t inv_begin = plan.ops.size();
+
+  // ---- plan: explicit inverse, a cyclic-reduction solve with X = I (in place in Kinv).  Forward
+  // products only touch the block columns where row block j can be nonzero: [lo_j, hi_j], which
+  // starts as {j} and grows by the ranges of the eliminated neighbours.
+  const size_t bN = (size_t)b * n;
+  const int N = (int)n;
+  std::vector<int> lo(L), hi(L);
+  for (int i = 0; i < L; ++i) lo[i] = hi[i] = i;
+  auto sub = [&](const cx<T>* base, int blockrow, int c0) { return base + (size_t)blockrow * bN + (size_t)c0 * b; };
+  for (size_t lv = 0; lv < lj.size(); ++lv) {
+    std::vector<GemmTask<T>> ta, tb;
+    for (size_t k = 0; k < lj[lv].size(); ++k) {
+      const int j = lj[lv][k], p = lp[lv][k], q = lq[lv][k];
+      const int c0 = lo[j], w = (hi[j] - lo[j] + 1) * b;
+      // Tmp_j = Dinv_j X_j ; X_p -= A_pj Tmp_j ; X_q -= A_qj Tmp_j  (on the columns of j)
+      ts.push_back({Dinv + j * bb, sub(Kinv, j, c0), const_cast<cx<T>*>(sub(Tmp, j, c0)), b, N, N, 0, T(1), 0, w});
+      if (p >= 0)
+        ta.push_back({UP + j * bb, sub(Tmp, j, c0), const_cast<cx<T>*>(sub(Kinv, p, c0)), b, N, N, 0, T(-1), 1, w});
+      if (q >= 0)
+        tb.push_back({UQT + j * bb, sub(Tmp, j, c0), const_cast<cx<T>*>(sub(Kinv, q, c0)), b, N, N, 0, T(-1), 1, w});
+    }
+    plan.add_gemm(ts);
+    plan.add_gemm(ta);
+    plan.add_gemm(tb);
+    for (size_t k = 0; k < lj[lv].size(); ++k) {
+      const int j = lj[lv][k], p = lp[lv][k], q = lq[lv][k];
+      if (p >= 0) {
+        lo[p] = std::min(lo[p], lo[j]);
+        hi[p] = std::max(hi[p], hi[j]);
       }
       if (q >= 0) {
-        // UQ_j = A_jq = Ucur_j ; Lq_j = A_qj Dinv_j = UQ_j^T Dinv_j  -> computed as (Dinv_j UQ_j)^T:
-        // Dinv_j is symmetric, so Lq_j^T = Dinv_j UQ_j; store W = Dinv_j UQ_j and use its transpose
-        BCR_CK(cudaMemcpyAsync(UQ + j * bb, Ucur + j * bb, bb * sizeof(cx<T>), cudaMemcpyDeviceToDevice, st), "copy");
-        t1.push_back({Dinv + j * bb, Ucur + j * bb, Lq + j * bb, b, b, b, 0, T(1), 0});  // Lq holds Dinv_j A_jq
-      }
-    }
-    BCR_CK(launch_gemms(t1, dtT, b, b, b, st), "gemm L");
-    ++*launches;
-    // D_p -= Lp_j A_jp = Lp_j UP_j^T ; D_q -= A_qj Dinv_j A_jq = UQ_j^T (Dinv_j UQ_j) = UQ_j^T Lq_j
-    // A_pq (new coupling from p) = -Lp_j A_jq = -Lp_j UQ_j
-    // Launch 1: updates from the right neighbour j of p (D_p, Unew_p); launch 2: from the left
-    // neighbour j' of q (D_q).  No two tasks of one launch write the same block.
-    std::vector<GemmTask<T>> ta, tb;
-    for (size_t k = 0; k < J.size(); ++k) {
-      int j = J[k], p = lp[lv][k], q = lq[lv][k];
-      if (p >= 0) {
-        ta.push_back({Lp + j * bb, UP + j * bb, D + p * bb, b, b, b, 1, T(-1), 1});
-        if (q >= 0) tb.push_back({Lp + j * bb, UQ + j * bb, Unew + p * bb, b, b, b, 0, T(-1), 0});
-      }
-    }
-    BCR_CK(launch_gemms(ta, dtT, b, b, b, st), "gemm Dp");
-    BCR_CK(launch_gemms(tb, dtT + ta.size(), b, b, b, st), "gemm Upq");
-    // D_q -= UQ_j^T Lq_j: transpose UQ_j into UQ + L*bb, then a plain GEMM
-    k_bcr_transpose<T><<<gs, 256, 0, st>>>(UQ, UQ + (size_t)L * bb, b, L);
-    BCR_CK(cudaGetLastError(), "transpose");
-    std::vector<GemmTask<T>> tc;
-    for (size_t k = 0; k < J.size(); ++k) {
-      int j = J[k], q = lq[lv][k];
-      if (q >= 0) tc.push_back({UQ + (size_t)L * bb + j * bb, Lq + j * bb, D + q * bb, b, b, b, 0, T(-1), 1});
-    }
-    BCR_CK(launch_gemms(tc, dtT + ta.size() + tb.size(), b, b, b, st), "gemm Dq");
-    *launches += 4;
-    // remaining p whose right neighbour j was eliminated now couples to q
-    for (size_t k = 0; k < J.size(); ++k) {
-      int p = lp[lv][k], q = lq[lv][k];
-      if (p >= 0) {
-        if (q >= 0)
-          BCR_CK(cudaMemcpyAsync(Ucur + p * bb, Unew + p * bb, bb * sizeof(cx<T>), cudaMemcpyDeviceToDevice, st), "copy");
-        else
-          BCR_CK(cudaMemsetAsync(Ucur + p * bb, 0, bb * sizeof(cx<T>), st), "memset");
+        lo[q] = std::min(lo[q], lo[j]);
+        hi[q] = std::max(hi[q], hi[j]);
       }
     }
   }
-  // transposes of UP (for back substitution) and UQ (forward), kept behind the originals
-  k_bcr_transpose<T><<<gs, 256, 0, st>>>(UP, UP + (size_t)L * bb, b, L);
-  k_bcr_transpose<T><<<gs, 256, 0, st>>>(UQ, UQ + (size_t)L * bb, b, L);
-  BCR_CK(cudaGetLastError(), "transpose");
-  prof_stop(KC_COARSE_SETUP, st);
-  // ---- explicit inverse: solve with the identity
-  prof_start(KC_COARSE_INV, st);
-  // solved in place in Kinv; the inverse is symmetric, so its rows are the solution columns
-  cx<T>* Tmp = nullptr;
-  BCR_CK(mal(&Tmp, n * n * sizeof(cx<T>)), "alloc");
-  k_bcr_identity<T><<<(int)std::min<size_t>((n * n + 255) / 256, 8192), 256, 0, st>>>(Kinv, (int)n);
-  BCR_CK(cudaGetLastError(), "identity");
-  BCR_CK(bcr_solve<T>(Dinv, UP, UQ, b, L, lj, lp, lq, Kinv, Tmp, (int)n, dtT, st), "solve");
-  prof_stop(KC_COARSE_INV, st);
+  for (int lv = (int)lj.size() - 1; lv >= 0; --lv) {
+    std::vector<GemmTask<T>> ta, tb;
+    for (size_t k = 0; k < lj[lv].size(); ++k) {
+      const int j = lj[lv][k], p = lp[lv][k], q = lq[lv][k];
+      // X_j -= A_jp X_p ; X_j -= A_jq X_q ; X_j = Dinv_j X_j (through Tmp_j)
+      if (p >= 0) ta.push_back({UPT + j * bb, sub(Kinv, p, 0), const_cast<cx<T>*>(sub(Kinv, j, 0)), b, N, N, 0, T(-1), 1, N});
+      if (q >= 0) tb.push_back({UQ + j * bb, sub(Kinv, q, 0), const_cast<cx<T>*>(sub(Kinv, j, 0)), b, N, N, 0, T(-1), 1, N});
+      ts.push_back({Dinv + j * bb, sub(Kinv, j, 0), const_cast<cx<T>*>(sub(Tmp, j, 0)), b, N, N, 0, T(1), 0, N});
+      cs.push_back({sub(Tmp, j, 0), const_cast<cx<T>*>(sub(Kinv, j, 0)), (long long)bN, 0});
+    }
+    plan.add_gemm(ta);
+    plan.add_gemm(tb);
+    plan.add_gemm(ts);
+    plan.add_copy(cs);
+  }
+  if (inv_begin < plan.ops.size()) plan.ops[inv_begin].timed_inverse = true;
+
+  // ---- upload the task arrays once
+  GemmTask<T>* dG = nullptr;
+  CopyTask<T>* dC = nullptr;
+  int* dL = nullptr;
+  BCR_CK(mal(&dG, plan.gemm.size() * sizeof(GemmTask<T>)), "alloc");
+  BCR_CK(mal(&dC, plan.copy.size() * sizeof(CopyTask<T>)), "alloc");
+  BCR_CK(mal(&dL, plan.list.size() * sizeof(int)), "alloc");
+  if (!plan.gemm.empty())
+    BCR_CK(cudaMemcpyAsync(dG, plan.gemm.data(), plan.gemm.size() * sizeof(GemmTask<T>), cudaMemcpyHostToDevice, st), "upload");
+  if (!plan.copy.empty())
+    BCR_CK(cudaMemcpyAsync(dC, plan.copy.data(), plan.copy.size() * sizeof(CopyTask<T>), cudaMemcpyHostToDevice, st), "upload");
+  if (!plan.list.empty())
+    BCR_CK(cudaMemcpyAsync(dL, plan.list.data(), plan.list.size() * sizeof(int), cudaMemcpyHostToDevice, st), "upload");
+
+  // ---- run
+  BCR_CK(cudaMemsetAsync(UP, 0, 2 * L * bb * sizeof(cx<T>), st), "memset");
+  BCR_CK(cudaMemsetAsync(UQ, 0, 2 * L * bb * sizeof(cx<T>), st), "memset");
+  const int gs = (int)std::min<size_t>((L * bb + 255) / 256, 4096);
+  prof_start(KC_COARSE_SETUP, st);
+  k_bcr_densify<T><<<gs, 256, 0, st>>>(P, D, Ucur);
+  BCR_CK(cudaGetLastError(), "densify");
+  ++*launches;
+  constexpr int TM = GemmTile<T>::TM;
+  bool in_inverse = false;
+  for (const BcrOp& op : plan.ops) {
+    if (op.timed_inverse) {
+      prof_stop(KC_COARSE_SETUP, st);
+      prof_start(KC_COARSE_INV, st);
+      in_inverse = true;
+      k_bcr_identity<T><<<(int)std::min<size_t>((n * n + 255) / 256, 8192), 256, 0, st>>>(Kinv, (int)n);
+      BCR_CK(cudaGetLastError(), "identity");
+      ++*launches;
+    }
+    if (op.kind == OP_GJ) {
+      BCR_CK(launch_gj_batch<T>(D, Dinv, dL + op.off, op.count, b, err, st), "inversion");
+    } else if (op.kind == OP_GEMM) {
+      dim3 grid((op.maxN + TM - 1) / TM, (b + TM - 1) / TM, (unsigned)op.count);
+      k_gemm_batch<T, TM><<<grid, 256, 0, st>>>(dG + op.off, b, b);
+      BCR_CK(cudaGetLastError(), "gemm");
+    } else {
+      const int chunks = (int)std::min<long long>(((long long)op.maxN + 255) / 256, 256);
+      k_copy_blocks<T><<<dim3(chunks, op.count), 256, 0, st>>>(dC + op.off, b);
+      BCR_CK(cudaGetLastError(), "copy");
+    }
+    ++*launches;
+  }
+  prof_stop(in_inverse ? KC_COARSE_INV : KC_COARSE_SETUP, st);
   BCR_CK(cudaStreamSynchronize(st), "sync");
-  *launches += 8;
   return SCHUR_OK;
 #undef BCR_CK
 }

@@ -50,6 +50,24 @@ def test_local_operators_match_dense_definitions(dim, N, P, beta, prec):
     sol.close()
 
 
+# Coarse grids of 17 x 17 (five reduction levels, odd counts), 9 x 9, 15 x 15 and 5 x 5 x 5 (3D
+# layers of 25): the cyclic-reduction inverse against the assembled coarse matrix.
+@pytest.mark.parametrize("dim,N,P,beta", [(2, 36, 18, 1e-3), (2, 40, 10, 1e-6), (2, 64, 16, 1e-2), (3, 12, 6, 1e-4)])
+@pytest.mark.parametrize("prec", PRECS)
+def test_coarse_inverse_multilevel(dim, N, P, beta, prec):
+    sol = S.Solver(dim, N, beta, nsub=P, precision=prec)
+    K = sol.schur_debug_operator(3)
+    inv = sol.schur_debug_operator(4)
+    nc = (P - 1) ** dim
+    assert K.shape == (nc, nc) and inv.shape == (nc, nc)
+    assert np.abs(K - K.T).max() <= 1e-12 * np.abs(K).max()
+    ref = np.linalg.inv(K)
+    err = np.abs(inv - ref).max() / np.abs(ref).max()
+    # FP32: unit roundoff 6e-8 times the growth of the reduction on these coarse grids
+    assert err <= (1e-11 if prec == S.SCHUR_FP64 else 1e-4), err
+    sol.close()
+
+
 @pytest.mark.parametrize("dim,N,P,beta", [(2, 12, 3, 1e-2), (2, 16, 4, 1e-8), (3, 6, 3, 1e-6), (3, 8, 2, 1e-4)])
 @pytest.mark.parametrize("prec", PRECS)
 def test_complex_factor_solve(dim, N, P, beta, prec):
