@@ -60,7 +60,8 @@ def test_coarse_inverse_multilevel(dim, N, P, beta, prec):
     inv = sol.schur_debug_operator(4)
     nc = (P - 1) ** dim
     assert K.shape == (nc, nc) and inv.shape == (nc, nc)
-    assert np.abs(K - K.T).max() <= 1e-12 * np.abs(K).max()
+    # the mixed form assembles the coarse matrix from FP32 local operators: symmetric to FP32 rounding
+    assert np.abs(K - K.T).max() <= (1e-12 if prec == S.SCHUR_FP64 else 1e-6) * np.abs(K).max()
     ref = np.linalg.inv(K)
     err = np.abs(inv - ref).max() / np.abs(ref).max()
     # FP32: unit roundoff 6e-8 times the growth of the reduction on these coarse grids
