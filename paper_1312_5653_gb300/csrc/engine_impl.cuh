@@ -50,6 +50,18 @@ static cudaError_t launch_form_cols(const StencilProv<T>& P, const Geom& g, cons
   return cudaGetLastError();
 }
 
+// Launch of the column-per-lane layered factorisation (2D, layer size b <= B), 4 warps per block.
+template <class T, int B>
+static cudaError_t launch_factor_cols(const StencilProv<T>& P, const int* codes, int nprob, cx<T>* Dinv, int* err,
+                                      cudaStream_t st) {
+  const int wpb = 4;
+  const size_t smem = wpb * factor_cols_smem_per_warp<T, B>();
+  cudaError_t e = smem_attr((const void*)k_factor_cols<T, B>, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_factor_cols<T, B><<<(nprob + wpb - 1) / wpb, 32 * wpb, smem, st>>>(P, codes, nprob, Dinv, err);
+  return cudaGetLastError();
+}
+
 template <class T>
 class Engine : public EngineBase {
  public:
@@ -137,7 +149,32 @@ class Engine : public EngineBase {
     // ---- remainder factors, one per class
     ENG_CK(alloc(&Dinv_, (size_t)ncls_ * g.lL * bb * cxT));
     op_bytes_ += (long long)ncls_ * g.lL * bb * cxT;
-    if (g.lb <= 32) {
+    bool factored = false;
+    if constexpr (sizeof(T) == 4) {
+      if (g.dim == 2 && g.lb <= 32) {
+        const int Bp = g.lb == 9 ? 9 : g.lb == 17 ? 17 : ((g.lb + 7) / 8) * 8;
+        prof_start(KC_FACTOR, st);
+        cudaError_t fe = cudaErrorInvalidValue;
+#define FK_CASE(BV) \
+  case BV: fe = launch_factor_cols<T, BV>(prr_, dm_->cls_code, ncls_, Dinv_, err_, st); break
+        switch (Bp) {
+          FK_CASE(8);
+          FK_CASE(9);
+          FK_CASE(16);
+          FK_CASE(17);
+          FK_CASE(24);
+          FK_CASE(32);
+          default: break;
+        }
+#undef FK_CASE
+        ENG_CK(fe);
+        prof_stop(KC_FACTOR, st);
+        ENG_LAUNCH();
+        factored = true;
+      }
+    }
+    if (factored) {
+    } else if (g.lb <= 32) {
       const size_t per_warp = (2 * (size_t)bb + 2 * g.lb) * cxT;
       const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, ((size_t)160 << 10) / per_warp));
       size_t smem = (size_t)wpb * per_warp;
@@ -163,7 +200,31 @@ class Engine : public EngineBase {
     const int ibb = g.ib * g.ib;
     cx<T>* Dii = nullptr;
     ENG_CK(alloc(&Dii, (size_t)g.iL * ibb * cxT));
-    {
+    bool ifactored = false;
+    if constexpr (sizeof(T) == 4) {
+      if (g.dim == 2 && g.ib <= 32) {
+        const int Bp = g.ib == 9 ? 9 : g.ib == 17 ? 17 : ((g.ib + 7) / 8) * 8;
+        prof_start(KC_FACTOR, st);
+        cudaError_t fe = cudaErrorInvalidValue;
+#define FK_CASE(BV) \
+  case BV: fe = launch_factor_cols<T, BV>(pii_, dm_->cls_code, 1, Dii, err_ + 1, st); break
+        switch (Bp) {
+          FK_CASE(8);
+          FK_CASE(9);
+          FK_CASE(16);
+          FK_CASE(17);
+          FK_CASE(24);
+          FK_CASE(32);
+          default: break;
+        }
+#undef FK_CASE
+        ENG_CK(fe);
+        prof_stop(KC_FACTOR, st);
+        ENG_LAUNCH();
+        ifactored = true;
+      }
+    }
+    if (!ifactored) {
       size_t need = (2 * (size_t)ibb + 2 * g.ib) * cxT;
       int use_smem = need <= 200 * 1024;
       size_t smem = use_smem ? need : 2 * g.ib * cxT;

@@ -380,6 +380,126 @@ __global__ void __launch_bounds__(128) k_form_rr_cols(StencilProv<T> P, Geom g, 
   }
 }
 
+// Block LDL^T of 2D remainder problems (layer size b <= B), one warp per problem: lane j holds
+// column j of the current pivot block in registers (rows unrolled at compile time).  Gauss-Jordan
+// pivots broadcast the pivot column by shuffles; the product with the tridiagonal layer coupling
+// takes the neighbouring columns by uniform shuffles up / down; the transpose for the symmetric
+// average goes through a padded per-warp shared tile.  Same steps as k_factor_warp.
+template <int B>
+struct FacLayout {
+  static constexpr int TS = B | 1;  // odd row stride: conflict-free column reads of 8-byte entries
+};
+
+template <class T, int B>
+__host__ __device__ constexpr size_t factor_cols_smem_per_warp() {
+  return ((size_t)B * FacLayout<B>::TS + 3 * (size_t)B) * sizeof(cx<T>);
+}
+
+template <class T>
+__device__ __forceinline__ cx<T> shfl_up_cx(cx<T> v, int d) {
+  return mkc<T>(__shfl_up_sync(0xffffffffu, v.re, d), __shfl_up_sync(0xffffffffu, v.im, d));
+}
+template <class T>
+__device__ __forceinline__ cx<T> shfl_down_cx(cx<T> v, int d) {
+  return mkc<T>(__shfl_down_sync(0xffffffffu, v.re, d), __shfl_down_sync(0xffffffffu, v.im, d));
+}
+
+template <class T, int B>
+__global__ void __launch_bounds__(128) k_factor_cols(StencilProv<T> P, const int* codes, int nprob, cx<T>* Dinv,
+                                                     int* err) {
+  constexpr int TS = FacLayout<B>::TS, NT = 3;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const int q = blockIdx.x * wpb + wib;
+  if (q >= nprob) return;
+  P.select(q, codes);
+  const int b = P.ly.b, L = P.ly.L, bb = b * b;
+  extern __shared__ __align__(16) unsigned char smfac[];
+  cx<T>* Tr = reinterpret_cast<cx<T>*>(smfac) + (size_t)wib * (B * TS + 3 * B);  // B x TS tile
+  cx<T>* cf = Tr + B * TS;                                                        // B x 3 couplings
+  const bool act = lane < b;
+  cx<T>* out = Dinv + (size_t)q * L * bb;
+  cx<T> d[B];
+  // pivot block of layer K from the stencil: column j has rows j-1, j, j+1
+  auto diag_block = [&](int K) {
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+      const int dl = i - lane;
+      d[i] = (act && i < b && dl >= -1 && dl <= 1) ? P.Ad(K, i, 1 - dl) : czero<T>();
+    }
+  };
+  diag_block(0);
+  for (int K = 0; K < L; ++K) {
+    // ---- explicit inverse of the pivot block (Gauss-Jordan, no pivoting)
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      if (k < b) {
+        const cx<T> p = shfl_cx(d[k], k);
+        const cx<T> piv = cinv(p);
+        if (lane == 0 && !finite_nonzero(p)) atomicExch(err, 1);
+        const cx<T> rk = cmul(d[k], piv);
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+          const cx<T> ci = shfl_cx(d[i], k);
+          if (i == k) {
+            d[i] = (lane == k) ? piv : rk;
+          } else if (lane == k) {
+            const cx<T> v = cmul(ci, piv);
+            d[i] = mkc<T>(-v.re, -v.im);
+          } else {
+            cfms(d[i], ci, rk);
+          }
+        }
+      }
+    }
+    // ---- symmetric average (D + D^T) / 2 through the shared tile; store D_K^{-1}
+    if (lane < B) {
+#pragma unroll
+      for (int i = 0; i < B; ++i) Tr[i * TS + lane] = d[i];
+    }
+    __syncwarp();
+    if (act) {
+#pragma unroll
+      for (int i = 0; i < B; ++i) {
+        const cx<T> t = Tr[lane * TS + i];
+        d[i] = cscale(cadd(d[i], t), T(0.5));
+      }
+    }
+    if (act) {
+#pragma unroll
+      for (int i = 0; i < B; ++i)
+        if (i < b) out[(size_t)K * bb + (size_t)i * b + lane] = d[i];
+    }
+    __syncwarp();
+    if (K + 1 == L) break;
+    // ---- W = D_K^{-1} A_{K,K+1}: column j = sum_t Al(K, j, t) * (column j + t - 1 of D_K^{-1})
+    const cx<T> a0 = act ? P.Al(K, lane, 0) : czero<T>();
+    const cx<T> a1 = act ? P.Al(K, lane, 1) : czero<T>();
+    const cx<T> a2 = act ? P.Al(K, lane, 2) : czero<T>();
+    for (int e = lane; e < b * NT; e += 32) cf[e] = P.Al(K, e / NT, e % NT);
+    cx<T> w[B];
+#pragma unroll
+    for (int m = 0; m < B; ++m) {
+      const cx<T> left = shfl_up_cx(d[m], 1), right = shfl_down_cx(d[m], 1);
+      cx<T> v = cmul(a1, d[m]);
+      if (lane > 0) cfma(v, a0, left);
+      if (lane + 1 < 32) cfma(v, a2, right);
+      w[m] = v;
+    }
+    __syncwarp();
+    // ---- D_{K+1} = A_{K+1,K+1} - A_{K+1,K} W: row i couples to rows i-1, i, i+1 of W
+    diag_block(K + 1);
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+      if (i < b) {
+        if (i > 0) cfms(d[i], cf[i * NT], w[i - 1]);
+        cfms(d[i], cf[i * NT + 1], w[i]);
+        if (i + 1 < B) cfms(d[i], cf[i * NT + 2], w[i + 1]);
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // Block LDL^T, one warp per problem (b <= 32): the same steps as k_factor with warp barriers.
 template <class T>
 __global__ void k_factor_warp(StencilProv<T> P, const int* codes, int nprob, cx<T>* Dinv, int* err) {
