@@ -555,6 +555,8 @@ class Engine : public EngineBase {
     ENG_CK(wa(&active_, kMaxRdev * sizeof(int)));
     ENG_CK(wa(&kk_, kMaxRdev * sizeof(int)));
     ENG_CK(wa(&bad_, kMaxRdev * sizeof(int)));
+    ENG_CK(wa(&cnt_, kMaxRdev * sizeof(int)));
+    ENG_CK(cudaMemsetAsync(cnt_, 0, kMaxRdev * sizeof(int), ast_));  // tickets of the fused reductions
     if (!h_active_) ENG_CK(cudaMallocHost(&h_active_, 2 * kMaxRdev * sizeof(int)));
     wsR_ = R;
     wsM_ = m;
@@ -706,8 +708,31 @@ class Engine : public EngineBase {
     prof_stop(KC_GMRES_OTHER, st);
     ENG_LAUNCH();
     const int seg = (nlam + nblk - 1) / nblk;
-    const size_t dot_smem = (size_t)seg * cxT;
-    ENG_CK(smem_attr((const void*)k_dots<T>, (int)dot_smem));
+    const size_t dot_smem = (size_t)seg * cxT, upd_smem = (size_t)(seg + m + 1) * cxT;
+    ENG_CK(smem_attr((const void*)k_orth_dots<T>, (int)dot_smem));
+    ENG_CK(smem_attr((const void*)k_orth_update_dots<T>, (int)upd_smem));
+    ENG_CK(smem_attr((const void*)k_orth_update_norm<T>, (int)upd_smem));
+    OrthArgs oa;
+    oa.vstride = vstride;
+    oa.nlam = nlam;
+    oa.m = m;
+    oa.nblk = nblk;
+    oa.active = active_;
+    oa.part = part_;
+    oa.nrm_part = nrm_part_;
+    oa.cnt = cnt_;
+    oa.H = H_;
+    oa.hc = hc_;
+    oa.cs_c = cs_c_;
+    oa.cs_s = cs_s_;
+    oa.gvec = gvec_;
+    oa.beta0 = beta0_;
+    oa.tol = tol;
+    oa.active_w = active_;
+    oa.kk = kk_;
+    oa.inv_nrm = inv_nrm_;
+    oa.resid = resid_;
+    oa.bad = bad_;
     const int check_every = 4;
     int k = 0;
     for (; k < m; ++k) {
@@ -717,28 +742,18 @@ class Engine : public EngineBase {
       if (rc) return rc;
       rc = dual_apply(zv_, R, active_, vk1, st, msg);
       if (rc) return rc;
-      for (int pass = 0; pass < 2; ++pass) {
-        prof_start(KC_GMRES_DOTS, st);
-        k_dots<T><<<dim3(nblk, R), 256, dot_smem, st>>>(V_, vstride, nlam, R, k, vk1, active_, nblk, part_);
-        prof_stop(KC_GMRES_DOTS, st);
-        ENG_LAUNCH();
-        int warps = R * (k + 1);
-        prof_start(KC_GMRES_DOTS, st);
-        k_dots_reduce<<<(warps * 32 + 255) / 256, 256, 0, st>>>(part_, nblk, R, k, m, active_, H_, hc_);
-        prof_stop(KC_GMRES_DOTS, st);
-        ENG_LAUNCH();
-        prof_start(KC_GMRES_UPDATE, st);
-        k_update<T><<<dim3(gs, R), 256, (k + 1) * cxT, st>>>(V_, vstride, nlam, R, k, hc_, active_, vk1);
-        prof_stop(KC_GMRES_UPDATE, st);
-        ENG_LAUNCH();
-      }
-      prof_start(KC_GMRES_OTHER, st);
-      k_norm2<T><<<dim3(nblk, R), 256, 0, st>>>(vk1, nlam, R, active_, nblk, nrm_part_);
-      prof_stop(KC_GMRES_OTHER, st);
+      oa.k = k;
+      const dim3 og(nblk, R);
+      prof_start(KC_GMRES_DOTS, st);
+      k_orth_dots<T><<<og, 256, dot_smem, st>>>(V_, vk1, oa);
+      prof_stop(KC_GMRES_DOTS, st);
+      ENG_LAUNCH();
+      prof_start(KC_GMRES_UPDATE, st);
+      k_orth_update_dots<T><<<og, 256, upd_smem, st>>>(V_, vk1, oa);
+      prof_stop(KC_GMRES_UPDATE, st);
       ENG_LAUNCH();
       prof_start(KC_GMRES_OTHER, st);
-      k_givens<<<R, 32, 0, st>>>(R, k, m, H_, nrm_part_, nblk, cs_c_, cs_s_, gvec_, beta0_, tol, active_, kk_, inv_nrm_,
-                                 resid_, bad_);
+      k_orth_update_norm<T><<<og, 256, upd_smem, st>>>(V_, vk1, oa);
       prof_stop(KC_GMRES_OTHER, st);
       ENG_LAUNCH();
       prof_start(KC_GMRES_OTHER, st);
@@ -799,7 +814,7 @@ class Engine : public EngineBase {
   *V_ = nullptr, *ftc_ = nullptr, *gc_ = nullptr, *wc_ = nullptr, *uc_ = nullptr;
   cx<double>*part_ = nullptr, *H_ = nullptr, *hc_ = nullptr, *gvec_ = nullptr, *cs_s_ = nullptr, *y_ = nullptr;
   double *cs_c_ = nullptr, *nrm_part_ = nullptr, *beta0_ = nullptr, *inv_nrm_ = nullptr, *resid_ = nullptr;
-  int *active_ = nullptr, *kk_ = nullptr, *bad_ = nullptr;
+  int *active_ = nullptr, *kk_ = nullptr, *bad_ = nullptr, *cnt_ = nullptr;
   int* h_active_ = nullptr;
   cudaStream_t ast_ = nullptr;  // stream of the current setup / solve (stream-ordered allocations)
 };

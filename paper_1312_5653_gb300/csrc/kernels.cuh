@@ -11,6 +11,7 @@
 // Dirichlet preconditioner P^{-1} = sum_s B_D^s S^s B_D^s^T, B_D = B / multiplicity (Eq.
 // dirichletpreconditioner with W = (sum B B^T)^+).
 #pragma once
+#include "gmres.h"
 #include "layered.cuh"
 
 namespace schur {
@@ -564,55 +565,172 @@ __global__ void k_scatter(Geom g, MapsView m, const cx<T>* __restrict__ Y, const
   out[(size_t)r * g.nlam + lam] = v;
 }
 
-// ------------------------------------------------------------------------------- GMRES
-// Block partial dot products h_j = <V_j, w> (conjugate-linear in V_j) for j = 0..k of right-hand
-// side r = blockIdx.y; the block's segment of w is staged in shared memory, one warp per j.
-// Products in the working precision, accumulation in FP64.
-template <class T>
-__global__ void k_dots(const cx<T>* __restrict__ V, long long vstride, int nlam, int R, int k,
-                       const cx<T>* __restrict__ w, const int* __restrict__ active, int nblk, cx<double>* part) {
-  extern __shared__ unsigned char smraw[];
-  cx<T>* ws = reinterpret_cast<cx<T>*>(smraw);
-  const int r = blockIdx.y;
-  if (!active[r]) return;
-  const int seg = (nlam + nblk - 1) / nblk, lo = blockIdx.x * seg, hi = min(nlam, lo + seg);
-  const int n = max(0, hi - lo);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) ws[i] = w[(size_t)r * nlam + lo + i];
+// ------------------------------------------------------------------ fused Gram-Schmidt (CGS2)
+// Orthogonalisation of w against V_0..V_k for each right-hand side r: grid (nblk, R), block bx
+// owns the contiguous slice bx of the vectors.  Each kernel leaves FP64 partial sums per block;
+// the last block of r to finish (ticket counter) adds them in block order, so the result does not
+// depend on scheduling, and resets the counter for the next launch.
+//   k_orth_dots:        h = V^H w                           -> hc, H[:, k] += h
+//   k_orth_update_dots: w -= V hc; h = V^H w                -> hc, H[:, k] += h
+//   k_orth_update_norm: w -= V hc; h_{k+1,k} = |w|, Givens rotation of column k
+struct OrthArgs {
+  long long vstride;
+  int nlam, k, m, nblk;
+  const int* active;
+  cx<double>* part;  // [R][kMaxKdev][nblk]
+  double* nrm_part;  // [R][nblk]
+  int* cnt;          // [R] tickets, zero between launches
+  cx<double>* H;
+  cx<double>* hc;
+  // Givens state
+  double* cs_c;
+  cx<double>* cs_s;
+  cx<double>* gvec;
+  const double* beta0;
+  double tol;
+  int* active_w;
+  int* kk;
+  double* inv_nrm;
+  double* resid;
+  int* bad;
+};
+
+__device__ __forceinline__ bool orth_last_block(int* cnt, int nblk) {
+  __shared__ int is_last;
+  __threadfence();
   __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(cnt, 1) == nblk - 1);
+  __syncthreads();
+  return is_last != 0;
+}
+
+// partial dots of the block slice ws (in shared memory) with V_0..V_k, one warp per j
+template <class T>
+__device__ __forceinline__ void orth_block_dots(const cx<T>* __restrict__ V, const OrthArgs& a, int r, int lo, int n,
+                                                const cx<T>* ws) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int j = warp; j <= k; j += nw) {
-    const cx<T>* vj = V + j * vstride + (size_t)r * nlam + lo;
+  for (int j = warp; j <= a.k; j += nw) {
+    const cx<T>* vj = V + j * a.vstride + (size_t)r * a.nlam + lo;
     double re = 0, im = 0;
     for (int i = lane; i < n; i += 32) {
-      cx<T> a = vj[i], b = ws[i];
-      re += (double)(a.re * b.re + a.im * b.im);
-      im += (double)(a.re * b.im - a.im * b.re);
+      const cx<T> x = vj[i], y = ws[i];
+      re += (double)(x.re * y.re + x.im * y.im);
+      im += (double)(x.re * y.im - x.im * y.re);
     }
     for (int o = 16; o > 0; o >>= 1) {
       re += __shfl_xor_sync(0xffffffffu, re, o);
       im += __shfl_xor_sync(0xffffffffu, im, o);
     }
-    if (lane == 0) part[((size_t)r * kMaxKdev + j) * nblk + blockIdx.x] = mkc<double>(re, im);
+    if (lane == 0) a.part[((size_t)r * kMaxKdev + j) * a.nblk + blockIdx.x] = mkc<double>(re, im);
   }
 }
 
-// h_j = sum of the block partials (fixed order); H[r][j][k] += h_j; hc[r][j] = h_j.
-__global__ void k_dots_reduce(const cx<double>* __restrict__ part, int nblk, int R, int k, int m,
-                              const int* __restrict__ active, cx<double>* H, cx<double>* hc);
+// last block: h_j = sum over blocks in order; hc = h, H[:, k] += h
+__device__ __forceinline__ void orth_finish_dots(const OrthArgs& a, int r) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = warp; j <= a.k; j += nw) {
+    const cx<double>* p = a.part + ((size_t)r * kMaxKdev + j) * a.nblk;
+    double re = 0, im = 0;
+    for (int b = lane; b < a.nblk; b += 32) {
+      const double2 v = __ldcg(reinterpret_cast<const double2*>(p + b));
+      re += v.x;
+      im += v.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) {
+      a.hc[(size_t)r * kMaxKdev + j] = mkc<double>(re, im);
+      cx<double>& h = a.H[((size_t)r * a.m + a.k) * (a.m + 1) + j];
+      h = cadd(h, mkc<double>(re, im));
+    }
+  }
+  if (threadIdx.x == 0) a.cnt[r] = 0;
+}
+
+// slice [lo, lo + n) of block bx
+__device__ __forceinline__ void orth_slice(const OrthArgs& a, int* lo, int* n) {
+  const int seg = (a.nlam + a.nblk - 1) / a.nblk;
+  *lo = blockIdx.x * seg;
+  *n = max(0, min(a.nlam, *lo + seg) - *lo);
+}
+
+// ws = w - V hc on the slice (written back to w); hc staged in shared memory as T
+template <class T>
+__device__ __forceinline__ void orth_block_update(const cx<T>* __restrict__ V, const OrthArgs& a, int r, int lo, int n,
+                                                  cx<T>* w, cx<T>* ws, cx<T>* h) {
+  for (int j = threadIdx.x; j <= a.k; j += blockDim.x) h[j] = ccast<T>(a.hc[(size_t)r * kMaxKdev + j]);
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    cx<T> acc = w[(size_t)r * a.nlam + lo + i];
+    for (int j = 0; j <= a.k; ++j) cfms(acc, h[j], V[j * a.vstride + (size_t)r * a.nlam + lo + i]);
+    w[(size_t)r * a.nlam + lo + i] = acc;
+    ws[i] = acc;
+  }
+  __syncthreads();
+}
 
 template <class T>
-__global__ void k_update(cx<T>* V, long long vstride, int nlam, int R, int k, const cx<double>* __restrict__ hc,
-                         const int* __restrict__ active, cx<T>* w) {
+__global__ void __launch_bounds__(256) k_orth_dots(const cx<T>* __restrict__ V, const cx<T>* __restrict__ w, OrthArgs a) {
+  extern __shared__ unsigned char smraw[];
+  cx<T>* ws = reinterpret_cast<cx<T>*>(smraw);
+  const int r = blockIdx.y;
+  if (!a.active[r]) return;
+  int lo, n;
+  orth_slice(a, &lo, &n);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) ws[i] = w[(size_t)r * a.nlam + lo + i];
+  __syncthreads();
+  orth_block_dots(V, a, r, lo, n, ws);
+  if (orth_last_block(a.cnt + r, a.nblk)) orth_finish_dots(a, r);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_orth_update_dots(const cx<T>* __restrict__ V, cx<T>* w, OrthArgs a) {
+  extern __shared__ unsigned char smraw[];
+  cx<T>* h = reinterpret_cast<cx<T>*>(smraw);  // k + 1
+  cx<T>* ws = h + (a.k + 1);                   // slice
+  const int r = blockIdx.y;
+  if (!a.active[r]) return;
+  int lo, n;
+  orth_slice(a, &lo, &n);
+  orth_block_update(V, a, r, lo, n, w, ws, h);
+  orth_block_dots(V, a, r, lo, n, ws);
+  if (orth_last_block(a.cnt + r, a.nblk)) orth_finish_dots(a, r);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_orth_update_norm(const cx<T>* __restrict__ V, cx<T>* w, OrthArgs a) {
   extern __shared__ unsigned char smraw[];
   cx<T>* h = reinterpret_cast<cx<T>*>(smraw);
+  cx<T>* ws = h + (a.k + 1);
+  __shared__ double red[32];
   const int r = blockIdx.y;
-  if (!active[r]) return;
-  for (int j = threadIdx.x; j <= k; j += blockDim.x) h[j] = ccast<T>(hc[(size_t)r * kMaxKdev + j]);
+  if (!a.active[r]) return;
+  int lo, n;
+  orth_slice(a, &lo, &n);
+  orth_block_update(V, a, r, lo, n, w, ws, h);
+  double s = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)ws[i].re * (double)ws[i].re + (double)ws[i].im * (double)ws[i].im;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nlam; i += (long long)gridDim.x * blockDim.x) {
-    cx<T> acc = w[(size_t)r * nlam + i];
-    for (int j = 0; j <= k; ++j) cfms(acc, h[j], V[j * vstride + (size_t)r * nlam + i]);
-    w[(size_t)r * nlam + i] = acc;
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) a.nrm_part[(size_t)r * a.nblk + blockIdx.x] = s;
+  }
+  if (orth_last_block(a.cnt + r, a.nblk)) {
+    if (threadIdx.x < 32) {
+      double t = 0;
+      for (int b = threadIdx.x; b < a.nblk; b += 32) t += __ldcg(a.nrm_part + (size_t)r * a.nblk + b);
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (threadIdx.x == 0) {
+        givens_step(r, a.k, a.m, sqrt(t), a.H, a.cs_c, a.cs_s, a.gvec, a.beta0, a.tol, a.active_w, a.kk, a.inv_nrm,
+                    a.resid, a.bad);
+        a.cnt[r] = 0;
+      }
+    }
   }
 }
 
