@@ -93,8 +93,8 @@ typedef struct {
   long long bytes_operators; /* device bytes held by factors and local/coarse operators     */
 } schur_info_t;
 
-/* Defaults: nsub = 4 per axis, FP64, tol 1e-12, inner_tol by precision, max_iter 300,
- * max_refine 8, per-subdomain local operators. */
+/* Defaults: nsub = 4 per axis, FP64, tol 1e-12, inner_tol by precision (1e-12 FP64, 3e-5
+ * mixed), max_iter 300, max_refine 8, per-subdomain local operators. */
 void schur_default_opts(schur_opts* opts);
 
 /* Builds the solver for one mesh and beta: per-subdomain Q1 assembly of K + i gamma M, batched

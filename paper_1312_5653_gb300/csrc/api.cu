@@ -210,7 +210,7 @@ int ctx_outer(schur_ctx* c, const double* bre, const double* bim, int ldb, int R
   double rel[kMaxR];
   int steps = 0, iters_total = 0, iters_first = -1;
   int status = SCHUR_OK;
-  const double inner_tol = c->opts.inner_tol > 0 ? c->opts.inner_tol : (c->opts.precision == SCHUR_MIXED ? 1e-5 : 1e-12);
+  const double inner_tol = c->opts.inner_tol > 0 ? c->opts.inner_tol : (c->opts.precision == SCHUR_MIXED ? 3e-5 : 1e-12);
   while (true) {
     rc = ctx_residual(c, bre, bim, ldb, R, st, rel);
     if (rc) return rc;

@@ -254,6 +254,79 @@ __global__ void __launch_bounds__(256) k_gj_block(const cx<S>* __restrict__ Din,
   for (int e = tid; e < (int)bb; e += 256) dst[e] = A[e];
 }
 
+// Register-resident variant for b <= 64: thread (tx, ty) of the 32 x 8 grid keeps entries
+// (ty + 8 r, tx + 32 c) in registers; per pivot the owners publish row k and column k to a double
+// buffer in shared memory, so one barrier per pivot suffices.
+template <class S>
+__global__ void __launch_bounds__(256) k_gj_regs(const cx<S>* __restrict__ Din, cx<S>* Dout,
+                                                 const int* __restrict__ list, int b, int* err) {
+  constexpr int RPT = 8, CPT = 2;
+  __shared__ cx<S> rowk[2][64], colk[2][64];
+  const int which = list[blockIdx.x];
+  const size_t bb = (size_t)b * b;
+  const cx<S>* src = Din + (size_t)which * bb;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  cx<S> a[RPT][CPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r)
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int i = ty + 8 * r, j = tx + 32 * c;
+      a[r][c] = (i < b && j < b) ? src[(size_t)i * b + j] : mkc<S>(0, 0);
+    }
+  for (int k = 0; k < b; ++k) {
+    const int buf = k & 1;
+    if (ty == (k & 7)) {
+#pragma unroll
+      for (int r = 0; r < RPT; ++r)
+        if (r == (k >> 3)) {
+#pragma unroll
+          for (int c = 0; c < CPT; ++c) rowk[buf][tx + 32 * c] = a[r][c];
+        }
+    }
+    if (tx == (k & 31)) {
+#pragma unroll
+      for (int c = 0; c < CPT; ++c)
+        if (c == (k >> 5)) {
+#pragma unroll
+          for (int r = 0; r < RPT; ++r) colk[buf][ty + 8 * r] = a[r][c];
+        }
+    }
+    __syncthreads();
+    const cx<S> p = rowk[buf][k];
+    const cx<S> piv = cinv(p);
+    if (threadIdx.x == 0 && !finite_nonzero(p)) atomicExch(err, 1);
+    cx<S> rs[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) rs[c] = cmul(rowk[buf][tx + 32 * c], piv);
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int i = ty + 8 * r;
+      const cx<S> ci = colk[buf][i];
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) {
+        const int j = tx + 32 * c;
+        if (i == k) {
+          a[r][c] = (j == k) ? piv : rs[c];
+        } else if (j == k) {
+          const cx<S> v = cmul(ci, piv);
+          a[r][c] = mkc<S>(-v.re, -v.im);
+        } else {
+          cfms(a[r][c], ci, rs[c]);
+        }
+      }
+    }
+  }
+  cx<S>* dst = Dout + (size_t)which * bb;
+#pragma unroll
+  for (int r = 0; r < RPT; ++r)
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int i = ty + 8 * r, j = tx + 32 * c;
+      if (i < b && j < b) dst[(size_t)i * b + j] = a[r][c];
+    }
+}
+
 template <class S>
 static size_t gj_block_smem(int b) {
   return ((size_t)b * b + 2 * (size_t)b) * sizeof(cx<S>);
@@ -270,6 +343,10 @@ static size_t bcr_gj_smem(int b, int CL) {
 template <class S>
 static cudaError_t launch_gj_batch(const cx<S>* Din, cx<S>* Dout, const int* dlist, int nblk, int b, int* err,
                                    cudaStream_t st) {
+  if (sizeof(S) == 4 && b <= 64) {
+    k_gj_regs<S><<<nblk, 256, 0, st>>>(Din, Dout, dlist, b, err);
+    return cudaGetLastError();
+  }
   if (gj_block_smem<S>(b) <= 200 * 1024) {
     const size_t smem = gj_block_smem<S>(b);
     cudaError_t e = smem_attr((const void*)k_gj_block<S>, (int)smem);
