@@ -62,6 +62,16 @@ __host__ __device__ __forceinline__ cx<R> cinv(cx<R> a) {
 template <class R, class S>
 __host__ __device__ __forceinline__ cx<R> ccast(cx<S> a) { return mkc<R>((R)a.re, (R)a.im); }
 
+// ------------------------------------------------------------------ symmetric packed storage
+// Complex symmetric n x n matrices (the local F and S) keep their upper triangle row by row:
+// entry (i, j), i <= j, at sym_off(i, n) + j - i.  Each matrix takes sym_ld(n) entries, an even
+// count, so consecutive FP32 matrices start on 16-byte boundaries.
+__host__ __device__ __forceinline__ int sym_off(int i, int n) { return i * n - (i * (i - 1)) / 2; }
+__host__ __device__ __forceinline__ int sym_idx(int i, int j, int n) {
+  return i <= j ? sym_off(i, n) + (j - i) : sym_off(j, n) + (i - j);
+}
+__host__ __device__ __forceinline__ long long sym_ld(int n) { return (((long long)n * (n + 1) / 2) + 1) & ~1LL; }
+
 // --------------------------------------------------------------------------------- geometry
 // One uniform Q1 mesh on [0,1]^dim split into nsub[a] boxes of s[a] elements per axis.
 // Node numbering everywhere: lexicographic with axis 0 fastest.

@@ -237,11 +237,11 @@ class Engine : public EngineBase {
       ENG_LAUNCH();
     }
     // ---- local operators
-    ENG_CK(alloc(&F_, (size_t)ncls_ * g.nD * g.nD * cxT));
+    ENG_CK(alloc(&F_, (size_t)ncls_ * sym_ld(g.nD) * cxT));  // packed symmetric
     ENG_CK(alloc(&Frc_, (size_t)ncls_ * g.nD * g.nc * cxT));
-    ENG_CK(alloc(&Sd_, (size_t)ncls_ * g.nD * g.nD * cxT));
+    ENG_CK(alloc(&Sd_, (size_t)ncls_ * sym_ld(g.nD) * cxT));  // packed symmetric
     ENG_CK(alloc(&Kcc_, (size_t)ncls_ * g.nc * g.nc * sizeof(cx<double>)));
-    op_bytes_ += (long long)ncls_ * g.nD * (2 * g.nD + g.nc) * cxT;
+    op_bytes_ += (long long)ncls_ * (2 * sym_ld(g.nD) + (long long)g.nD * g.nc) * cxT;
     {
       const int C = 32;
       cx<T>* Xws = nullptr;
@@ -451,9 +451,21 @@ class Engine : public EngineBase {
     };
     int rc = 0;
     if (which <= 2 && (cls < 0 || cls >= ncls_)) return SCHUR_EINVAL;
-    if (which == 0) rc = fetch(F_ + (size_t)cls * g.nD * g.nD, (size_t)g.nD * g.nD);
-    else if (which == 1) rc = fetch(Frc_ + (size_t)cls * g.nD * g.nc, (size_t)g.nD * g.nc);
-    else if (which == 2) rc = fetch(Sd_ + (size_t)cls * g.nD * g.nD, (size_t)g.nD * g.nD);
+    auto unpack = [&]() {  // packed upper triangle -> full symmetric matrix
+      std::vector<cx<double>> full((size_t)g.nD * g.nD);
+      for (int i = 0; i < g.nD; ++i)
+        for (int j = 0; j < g.nD; ++j) full[(size_t)i * g.nD + j] = host[sym_idx(i, j, g.nD)];
+      host.swap(full);
+    };
+    if (which == 0) {
+      rc = fetch(F_ + (size_t)cls * sym_ld(g.nD), (size_t)sym_ld(g.nD));
+      if (!rc) unpack();
+    } else if (which == 1) {
+      rc = fetch(Frc_ + (size_t)cls * g.nD * g.nc, (size_t)g.nD * g.nc);
+    } else if (which == 2) {
+      rc = fetch(Sd_ + (size_t)cls * sym_ld(g.nD), (size_t)sym_ld(g.nD));
+      if (!rc) unpack();
+    }
     else if (which == 3 || which == 4) {
       if (g.ncor == 0) return SCHUR_EINVAL;
       if (which == 4) {
@@ -625,14 +637,17 @@ class Engine : public EngineBase {
                   cudaStream_t st, std::string* msg) {
     const Geom& g = g_;
     int thr = std::min(512, ((g.nD + 31) / 32) * 32);
-    size_t smem = (size_t)R * g.nD * sizeof(cx<T>);
+    const size_t xcnt = ((size_t)R * g.nD + 1) & ~(size_t)1;
+    const size_t opb = (size_t)sym_ld(g.nD) * sizeof(cx<T>);
+    const int stage = (xcnt * sizeof(cx<T>) + opb <= ((size_t)96 << 10)) ? 1 : 0;
+    size_t smem = xcnt * sizeof(cx<T>) + (stage ? opb : 0);
     cx<T>* tc = want_tc ? Tc_ : nullptr;
 #define LA_CASE(SC, MR)                                                                                 \
   do {                                                                                                  \
     ENG_CK(smem_attr((const void*)k_local_apply<T, SC, MR>,                                       \
                                 (int)std::max<size_t>(smem, 1)));                                       \
     prof_start(SC ? KC_APPLY_S : KC_APPLY_F, st);                                                      \
-    k_local_apply<T, SC, MR><<<g.nsd, thr, smem, st>>>(g, mv_, Op, Frc_, v, R, active, Y_, tc);         \
+    k_local_apply<T, SC, MR><<<g.nsd, thr, smem, st>>>(g, mv_, Op, Frc_, v, R, active, Y_, tc, stage);         \
     prof_stop(SC ? KC_APPLY_S : KC_APPLY_F, st);                                                       \
   } while (0)
     if (precond) {

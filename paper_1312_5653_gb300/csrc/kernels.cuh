@@ -79,7 +79,9 @@ __global__ void k_form_rr(StencilProv<T> P, Geom g, MapsView m, const cx<T>* __r
       int j = e / C, c = e - j * C, col = col0 + c;
       if (col >= ncol) continue;
       cx<T> v = X[(size_t)m.slot_node[j] * C + c];
-      if (col < nD) F[((size_t)q * nD + j) * nD + col] = v;
+      if (col < nD) {
+        if (j <= col) F[(size_t)q * sym_ld(nD) + sym_idx(j, col, nD)] = v;
+      }
       else Frc[((size_t)q * nD + j) * nc + (col - nD)] = v;
     }
     for (int e = tid; e < nc * C; e += nthr) {
@@ -156,18 +158,20 @@ __global__ void k_form_ii(StencilProv<T> P, Geom g, MapsView m, const cx<T>* __r
 template <class T>
 __global__ void k_mask_S(Geom g, MapsView m, int ncls, const cx<T>* __restrict__ Sbase, cx<T>* Sd) {
   const long long tot = (long long)ncls * g.nD * g.nD;
+  const long long ld = sym_ld(g.nD);
   int ext[3];
   local_ext(g, ext);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
     int q = (int)(e / ((long long)g.nD * g.nD));
     int r = (int)(e % ((long long)g.nD * g.nD));
     int j = r / g.nD, k = r % g.nD;
+    if (j > k) continue;  // upper triangle (packed)
     int lj[3], lk[3];
     idx2crd(m.slot_node[j], ext, g.dim, lj);
     idx2crd(m.slot_node[k], ext, g.dim, lk);
     int code = m.cls_code[q];
     bool act = !local_dirichlet(code, lj, g.s, g.dim) && !local_dirichlet(code, lk, g.s, g.dim);
-    Sd[e] = act ? Sbase[r] : czero<T>();
+    Sd[(size_t)q * ld + sym_idx(j, k, g.nD)] = act ? Sbase[r] : czero<T>();
   }
 }
 
@@ -479,14 +483,14 @@ __global__ void k_dual_rhs(Geom g, MapsView m, const cx<T>* __restrict__ VD, con
 
 // Local dense apply per subdomain with the gather of B^T lambda fused in front:
 //   x_j = scale_j * sum_k sign_k lam[idx_k]        (scale = 1/multiplicity for the preconditioner)
-//   Y   = Op[cls] x                                 (Op = F or S, nD x nD, symmetric)
+//   Y   = Op[cls] x                                 (Op = F or S, nD x nD, symmetric, packed)
 //   Tc  = Frc[cls]^T x                              (only when Tc != null)
 template <class T, bool SCALE, int MR>
 __global__ void k_local_apply(Geom g, MapsView m, const cx<T>* __restrict__ Op, const cx<T>* __restrict__ Frc,
                               const cx<T>* __restrict__ lam, int R, const int* __restrict__ active, cx<T>* Y,
-                              cx<T>* Tc) {
-  extern __shared__ unsigned char smraw[];
-  cx<T>* x = reinterpret_cast<cx<T>*>(smraw);
+                              cx<T>* Tc, int stage) {
+  extern __shared__ __align__(16) unsigned char smla[];
+  cx<T>* x = reinterpret_cast<cx<T>*>(smla);
   const int sd = blockIdx.x, nD = g.nD, tid = threadIdx.x, nthr = blockDim.x, md = g.maxdeg;
   const int q = m.sd_cls[sd];
   for (int e = tid; e < R * nD; e += nthr) {
@@ -503,14 +507,27 @@ __global__ void k_local_apply(Geom g, MapsView m, const cx<T>* __restrict__ Op, 
     }
     x[e] = v;
   }
+  // packed upper triangle of Op[cls]; staged in shared memory with 16-byte copies when it fits
+  const long long ld = sym_ld(nD);
+  const cx<T>* A = Op + (size_t)q * ld;
+  if (stage) {
+    cx<T>* As = x + (((long long)R * nD + 1) & ~1LL);
+    const int n16 = (int)(ld * (long long)sizeof(cx<T>) / 16);
+    const float4* src = reinterpret_cast<const float4*>(A);
+    float4* dst = reinterpret_cast<float4*>(As);
+    for (int i = tid; i < n16; i += nthr) dst[i] = src[i];
+    A = As;
+  }
   __syncthreads();
-  const cx<T>* A = Op + (size_t)q * nD * nD;
   for (int j = tid; j < nD; j += nthr) {
     cx<T> acc[MR];
     for (int r = 0; r < MR; ++r) acc[r] = czero<T>();
+    const int offj = sym_off(j, nD);
+    int ok = 0;  // sym_off(k, nD)
 #pragma unroll 4
     for (int k = 0; k < nD; ++k) {
-      cx<T> a = A[(size_t)k * nD + j];
+      const cx<T> a = A[k <= j ? ok + (j - k) : offj + (k - j)];
+      ok += nD - k;
 #pragma unroll
       for (int r = 0; r < MR; ++r)
         if (r < R) cfma(acc[r], a, x[r * nD + k]);

@@ -242,7 +242,9 @@ __global__ void __launch_bounds__(128) k_form_rr_cols(StencilProv<T> P, Geom g, 
           if (i < b) {
             const int j = slot_s[K * b + i];
             if (j >= 0) {
-              if (is_unit) F[((size_t)q * nD + j) * nD + c] = x[i];
+              if (is_unit) {
+                if (j <= c) F[(size_t)q * sym_ld(nD) + sym_idx(j, c, nD)] = x[i];
+              }
               else Frc[((size_t)q * nD + j) * nc + cc] = x[i];
             }
           }
@@ -701,7 +703,9 @@ __global__ void k_form_rr_warp(StencilProv<T> P, Geom g, MapsView m, const cx<T>
     int j = e / C, c = e - j * C, col = col0 + c;
     if (col >= ncol) continue;
     cx<T> v = X[(size_t)m.slot_node[j] + (size_t)c * g.nl];
-    if (col < nD) F[((size_t)q * nD + j) * nD + col] = v;
+    if (col < nD) {
+      if (j <= col) F[(size_t)q * sym_ld(nD) + sym_idx(j, col, nD)] = v;
+    }
     else Frc[((size_t)q * nD + j) * nc + (col - nD)] = v;
   }
   for (int e = lane; e < nc * C; e += 32) {
