@@ -395,10 +395,11 @@ static cudaError_t launch_gj_batch(const cx<S>* Din, cx<S>* Dout, const int* dli
   return last;
 }
 
+// X = [I 0]: n rows of ld >= n entries
 template <class T>
-__global__ void k_bcr_identity(cx<T>* X, int n) {
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * n; e += (size_t)gridDim.x * blockDim.x)
-    X[e] = mkc<T>((e / n) == (e % n) ? T(1) : T(0), T(0));
+__global__ void k_bcr_identity(cx<T>* X, int n, int ld) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * ld; e += (size_t)gridDim.x * blockDim.x)
+    X[e] = mkc<T>((e / ld) == (e % ld) ? T(1) : T(0), T(0));
 }
 
 // ------------------------------------------------------------------ host orchestration
@@ -465,7 +466,7 @@ struct BcrPlan {
 };
 
 template <class T>
-int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int* err, cudaStream_t st, std::string* msg,
+int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int ldk, int* err, cudaStream_t st, std::string* msg,
                long long* launches) {
   const int b = P.ly.b, L = P.ly.L;
   const size_t bb = (size_t)b * b, n = (size_t)b * L;
@@ -503,7 +504,7 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int* err, cudaStream_t 
   BCR_CK(mal(&Lp, L * bb * sizeof(cx<T>)), "alloc");
   BCR_CK(mal(&Lq, L * bb * sizeof(cx<T>)), "alloc");
   BCR_CK(mal(&Unew, L * bb * sizeof(cx<T>)), "alloc");
-  BCR_CK(mal(&Tmp, n * n * sizeof(cx<T>)), "alloc");
+  BCR_CK(mal(&Tmp, n * (size_t)ldk * sizeof(cx<T>)), "alloc");
   cx<T>* UPT = UP + (size_t)L * bb;
   cx<T>* UQT = UQ + (size_t)L * bb;
 
@@ -561,7 +562,7 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int* err, cudaStream_t 
   // ---- plan: explicit inverse, a cyclic-reduction solve with X = I (in place in Kinv).  Forward
   // products only touch the block columns where row block j can be nonzero: [lo_j, hi_j], which
   // starts as {j} and grows by the ranges of the eliminated neighbours.
-  const size_t bN = (size_t)b * n;
+  const size_t bN = (size_t)b * ldk;  // one block row of X (row stride ldk)
   const int N = (int)n;
   std::vector<int> lo(L), hi(L);
   for (int i = 0; i < L; ++i) lo[i] = hi[i] = i;
@@ -572,11 +573,11 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int* err, cudaStream_t 
       const int j = lj[lv][k], p = lp[lv][k], q = lq[lv][k];
       const int c0 = lo[j], w = (hi[j] - lo[j] + 1) * b;
       // Tmp_j = Dinv_j X_j ; X_p -= A_pj Tmp_j ; X_q -= A_qj Tmp_j  (on the columns of j)
-      ts.push_back({Dinv + j * bb, sub(Kinv, j, c0), const_cast<cx<T>*>(sub(Tmp, j, c0)), b, N, N, 0, T(1), 0, w});
+      ts.push_back({Dinv + j * bb, sub(Kinv, j, c0), const_cast<cx<T>*>(sub(Tmp, j, c0)), b, ldk, ldk, 0, T(1), 0, w});
       if (p >= 0)
-        ta.push_back({UP + j * bb, sub(Tmp, j, c0), const_cast<cx<T>*>(sub(Kinv, p, c0)), b, N, N, 0, T(-1), 1, w});
+        ta.push_back({UP + j * bb, sub(Tmp, j, c0), const_cast<cx<T>*>(sub(Kinv, p, c0)), b, ldk, ldk, 0, T(-1), 1, w});
       if (q >= 0)
-        tb.push_back({UQT + j * bb, sub(Tmp, j, c0), const_cast<cx<T>*>(sub(Kinv, q, c0)), b, N, N, 0, T(-1), 1, w});
+        tb.push_back({UQT + j * bb, sub(Tmp, j, c0), const_cast<cx<T>*>(sub(Kinv, q, c0)), b, ldk, ldk, 0, T(-1), 1, w});
     }
     plan.add_gemm(ts);
     plan.add_gemm(ta);
@@ -598,9 +599,9 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int* err, cudaStream_t 
     for (size_t k = 0; k < lj[lv].size(); ++k) {
       const int j = lj[lv][k], p = lp[lv][k], q = lq[lv][k];
       // X_j -= A_jp X_p ; X_j -= A_jq X_q ; X_j = Dinv_j X_j (through Tmp_j)
-      if (p >= 0) ta.push_back({UPT + j * bb, sub(Kinv, p, 0), const_cast<cx<T>*>(sub(Kinv, j, 0)), b, N, N, 0, T(-1), 1, N});
-      if (q >= 0) tb.push_back({UQ + j * bb, sub(Kinv, q, 0), const_cast<cx<T>*>(sub(Kinv, j, 0)), b, N, N, 0, T(-1), 1, N});
-      ts.push_back({Dinv + j * bb, sub(Kinv, j, 0), const_cast<cx<T>*>(sub(Tmp, j, 0)), b, N, N, 0, T(1), 0, N});
+      if (p >= 0) ta.push_back({UPT + j * bb, sub(Kinv, p, 0), const_cast<cx<T>*>(sub(Kinv, j, 0)), b, ldk, ldk, 0, T(-1), 1, N});
+      if (q >= 0) tb.push_back({UQ + j * bb, sub(Kinv, q, 0), const_cast<cx<T>*>(sub(Kinv, j, 0)), b, ldk, ldk, 0, T(-1), 1, N});
+      ts.push_back({Dinv + j * bb, sub(Kinv, j, 0), const_cast<cx<T>*>(sub(Tmp, j, 0)), b, ldk, ldk, 0, T(1), 0, N});
       cs.push_back({sub(Tmp, j, 0), const_cast<cx<T>*>(sub(Kinv, j, 0)), (long long)bN, 0});
     }
     plan.add_gemm(ta);
@@ -639,7 +640,7 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int* err, cudaStream_t 
       prof_stop(KC_COARSE_SETUP, st);
       prof_start(KC_COARSE_INV, st);
       in_inverse = true;
-      k_bcr_identity<T><<<(int)std::min<size_t>((n * n + 255) / 256, 8192), 256, 0, st>>>(Kinv, (int)n);
+      k_bcr_identity<T><<<(int)std::min<size_t>((n * ldk + 255) / 256, 8192), 256, 0, st>>>(Kinv, (int)n, ldk);
       BCR_CK(cudaGetLastError(), "identity");
       ++*launches;
     }
@@ -662,7 +663,7 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int* err, cudaStream_t 
 #undef BCR_CK
 }
 
-template int coarse_bcr<float>(const StoredProv<double>&, cx<float>*, int*, cudaStream_t, std::string*, long long*);
-template int coarse_bcr<double>(const StoredProv<double>&, cx<double>*, int*, cudaStream_t, std::string*, long long*);
+template int coarse_bcr<float>(const StoredProv<double>&, cx<float>*, int, int*, cudaStream_t, std::string*, long long*);
+template int coarse_bcr<double>(const StoredProv<double>&, cx<double>*, int, int*, cudaStream_t, std::string*, long long*);
 
 }  // namespace schur

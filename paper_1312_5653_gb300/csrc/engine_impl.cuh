@@ -341,10 +341,11 @@ class Engine : public EngineBase {
       cprov_.CA = CA_;
       cprov_.CB = CB_;
       // FP64 block cyclic reduction over the coarse layers, explicit inverse in precision T
-      ENG_CK(alloc(&Kinv_, (size_t)g.ncor * g.ncor * cxT));
-      op_bytes_ += (long long)g.ncor * g.ncor * cxT;
+      ldk_ = (g.ncor + 1) & ~1;  // even row stride: 16-byte aligned FP32 rows
+      ENG_CK(alloc(&Kinv_, (size_t)g.ncor * ldk_ * cxT));
+      op_bytes_ += (long long)g.ncor * ldk_ * cxT;
       (void)cbb;
-      int crc = coarse_bcr<T>(cprov_, Kinv_, err_ + 2, st, msg, &launches);
+      int crc = coarse_bcr<T>(cprov_, Kinv_, ldk_, err_ + 2, st, msg, &launches);
       if (crc) return crc;
     }
     ENG_CK(cudaStreamSynchronize(st));
@@ -469,7 +470,13 @@ class Engine : public EngineBase {
     else if (which == 3 || which == 4) {
       if (g.ncor == 0) return SCHUR_EINVAL;
       if (which == 4) {
-        rc = fetch(Kinv_, (size_t)g.ncor * g.ncor);
+        rc = fetch(Kinv_, (size_t)g.ncor * ldk_);
+        if (!rc) {
+          std::vector<cx<double>> full((size_t)g.ncor * g.ncor);
+          for (int i = 0; i < g.ncor; ++i)
+            for (int j = 0; j < g.ncor; ++j) full[(size_t)i * g.ncor + j] = host[(size_t)i * ldk_ + j];
+          host.swap(full);
+        }
       } else {
         const int nt = nbr_count(g.dim);
         std::vector<cx<double>> ca((size_t)g.cL * g.cb * nt), cb((size_t)g.cL * g.cb * nt);
@@ -623,10 +630,10 @@ class Engine : public EngineBase {
   int coarse_apply(const cx<T>* gv, int R, const int* active, cx<T>* w, cudaStream_t st, std::string* msg) {
     const int rows_per_block = 8, grid = (g_.ncor + rows_per_block - 1) / rows_per_block;
     prof_start(KC_COARSE_APPLY, st);
-    if (R == 1) k_coarse_apply<T, 1><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, gv, R, active, w);
-    else if (R <= 4) k_coarse_apply<T, 4><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, gv, R, active, w);
-    else if (R <= 8) k_coarse_apply<T, 8><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, gv, R, active, w);
-    else k_coarse_apply<T, 16><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, gv, R, active, w);
+    if (R == 1) k_coarse_apply<T, 1><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, ldk_, gv, R, active, w);
+    else if (R <= 4) k_coarse_apply<T, 4><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, ldk_, gv, R, active, w);
+    else if (R <= 8) k_coarse_apply<T, 8><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, ldk_, gv, R, active, w);
+    else k_coarse_apply<T, 16><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, ldk_, gv, R, active, w);
     prof_stop(KC_COARSE_APPLY, st);
     ENG_LAUNCH();
     return SCHUR_OK;
@@ -817,7 +824,7 @@ class Engine : public EngineBase {
   Stencil<T> st_;
   StencilProv<T> prr_, pii_;
   StoredProv<double> cprov_;
-  int ncls_ = 0, nsm_ = 152, nblk_ = 1, coarse_cluster_ = 0;
+  int ncls_ = 0, nsm_ = 152, nblk_ = 1, coarse_cluster_ = 0, ldk_ = 0;
   long long op_bytes_ = 0;
   std::vector<void*> allocs_, ws_;
   int* err_ = nullptr;

@@ -46,6 +46,25 @@ __device__ __forceinline__ long long gidx(const Geom& g, const int* G) {
 template <class T>
 __device__ __forceinline__ cx<T> czero() { return mkc<T>(T(0), T(0)); }
 
+// Asynchronous global -> shared copies (cp.async, L1-allocating), one complex entry per lane.
+template <class T>
+__device__ __forceinline__ void cp_async_cx(cx<T>* smem, const cx<T>* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (sizeof(cx<T>) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// 16-byte asynchronous copy (L2 only); both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
 // ================================================================================= setup
 // F, Frc, Kcc of each class: solve A_rr X = [E_Delta, A_rc] column chunk by chunk.
 template <class T>
@@ -421,22 +440,41 @@ __global__ void k_corner_gather(Geom g, const cx<T>* __restrict__ Tc, int R, con
   out[(size_t)r * g.ncor + cI] = v;
 }
 
-// w = Kinv gvec for R columns: one warp per coarse row.
+// w = Kinv gvec for R columns: one warp per coarse row; rows of ldk (even) entries read as pairs
+// of complex entries per 16-byte load (FP32) so more bytes are in flight per warp.
 template <class T, int MR>
-__global__ void k_coarse_apply(const cx<T>* __restrict__ Kinv, int ncor, const cx<T>* __restrict__ gv, int R,
+__global__ void k_coarse_apply(const cx<T>* __restrict__ Kinv, int ncor, int ldk, const cx<T>* __restrict__ gv, int R,
                                const int* __restrict__ active, cx<T>* w) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = blockIdx.x * (blockDim.x >> 5) + warp;
   if (row >= ncor) return;
   cx<T> acc[MR];
   for (int r = 0; r < MR; ++r) acc[r] = czero<T>();
-  const cx<T>* Krow = Kinv + (size_t)row * ncor;
+  const cx<T>* Krow = Kinv + (size_t)row * ldk;
+  if constexpr (sizeof(T) == 4) {
+    const float4* K4 = reinterpret_cast<const float4*>(Krow);
+    const int np = ldk / 2;
 #pragma unroll 4
-  for (int j = lane; j < ncor; j += 32) {
-    cx<T> a = Krow[j];
+    for (int p = lane; p < np; p += 32) {
+      const float4 v = K4[p];
+      const int j0 = 2 * p, j1 = j0 + 1;
+      const cx<T> a0 = mkc<T>(v.x, v.y);
+      const cx<T> a1 = j1 < ncor ? mkc<T>(v.z, v.w) : czero<T>();
 #pragma unroll
-    for (int r = 0; r < MR; ++r)
-      if (r < R) cfma(acc[r], a, gv[(size_t)r * ncor + j]);
+      for (int r = 0; r < MR; ++r)
+        if (r < R) {
+          cfma(acc[r], a0, gv[(size_t)r * ncor + j0]);
+          if (j1 < ncor) cfma(acc[r], a1, gv[(size_t)r * ncor + j1]);
+        }
+    }
+  } else {
+#pragma unroll 4
+    for (int j = lane; j < ncor; j += 32) {
+      const cx<T> a = Krow[j];
+#pragma unroll
+      for (int r = 0; r < MR; ++r)
+        if (r < R) cfma(acc[r], a, gv[(size_t)r * ncor + j]);
+    }
   }
 #pragma unroll
   for (int r = 0; r < MR; ++r) {
@@ -493,6 +531,18 @@ __global__ void k_local_apply(Geom g, MapsView m, const cx<T>* __restrict__ Op, 
   cx<T>* x = reinterpret_cast<cx<T>*>(smla);
   const int sd = blockIdx.x, nD = g.nD, tid = threadIdx.x, nthr = blockDim.x, md = g.maxdeg;
   const int q = m.sd_cls[sd];
+  // packed upper triangle of Op[cls]; staged in shared memory by asynchronous 16-byte copies that
+  // overlap the gather of x when it fits
+  const long long ld = sym_ld(nD);
+  const cx<T>* A = Op + (size_t)q * ld;
+  if (stage) {
+    unsigned char* As = reinterpret_cast<unsigned char*>(x + (((long long)R * nD + 1) & ~1LL));
+    const int n16 = (int)(ld * (long long)sizeof(cx<T>) / 16);
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(A);
+    for (int i = tid; i < n16; i += nthr) cp_async16(As + 16 * (size_t)i, src + 16 * (size_t)i);
+    cp_async_commit();
+    A = reinterpret_cast<const cx<T>*>(As);
+  }
   for (int e = tid; e < R * nD; e += nthr) {
     int r = e / nD, j = e - r * nD;
     cx<T> v = czero<T>();
@@ -507,17 +557,7 @@ __global__ void k_local_apply(Geom g, MapsView m, const cx<T>* __restrict__ Op, 
     }
     x[e] = v;
   }
-  // packed upper triangle of Op[cls]; staged in shared memory with 16-byte copies when it fits
-  const long long ld = sym_ld(nD);
-  const cx<T>* A = Op + (size_t)q * ld;
-  if (stage) {
-    cx<T>* As = x + (((long long)R * nD + 1) & ~1LL);
-    const int n16 = (int)(ld * (long long)sizeof(cx<T>) / 16);
-    const float4* src = reinterpret_cast<const float4*>(A);
-    float4* dst = reinterpret_cast<float4*>(As);
-    for (int i = tid; i < n16; i += nthr) dst[i] = src[i];
-    A = As;
-  }
+  if (stage) cp_async_wait<0>();
   __syncthreads();
   for (int j = tid; j < nD; j += nthr) {
     cx<T> acc[MR];

@@ -12,19 +12,6 @@ __device__ __forceinline__ cx<T> shfl_cx(cx<T> v, int src) {
   return mkc<T>(__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src));
 }
 
-// Asynchronous global -> shared copies (cp.async, L1-allocating), one complex entry per lane.
-template <class T>
-__device__ __forceinline__ void cp_async_cx(cx<T>* smem, const cx<T>* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  if (sizeof(cx<T>) == 8)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
 // Warp-wide asynchronous copy of one b x b layer block into shared memory.
 template <class T>
 __device__ __forceinline__ void warp_stage_block(cx<T>* dst, const cx<T>* __restrict__ src, int bb) {
@@ -431,27 +418,35 @@ __global__ void __launch_bounds__(128) k_factor_cols(StencilProv<T> P, const int
   };
   diag_block(0);
   for (int K = 0; K < L; ++K) {
-    // ---- explicit inverse of the pivot block (Gauss-Jordan, no pivoting)
+    // ---- explicit inverse of the pivot block (Gauss-Jordan, no pivoting).  After each pivot the
+    // rows rotate by one register, so the pivot row is always d[0] and the pivot loop stays rolled
+    // (small code); B rotations in total restore the row order.
+    for (int k = 0; k < b; ++k) {
+      const cx<T> p = shfl_cx(d[0], k);
+      const cx<T> piv = cinv(p);
+      if (lane == 0 && !finite_nonzero(p)) atomicExch(err, 1);
+      const cx<T> rk = cmul(d[0], piv);
+      d[0] = (lane == k) ? piv : rk;
 #pragma unroll
-    for (int k = 0; k < B; ++k) {
-      if (k < b) {
-        const cx<T> p = shfl_cx(d[k], k);
-        const cx<T> piv = cinv(p);
-        if (lane == 0 && !finite_nonzero(p)) atomicExch(err, 1);
-        const cx<T> rk = cmul(d[k], piv);
-#pragma unroll
-        for (int i = 0; i < B; ++i) {
-          const cx<T> ci = shfl_cx(d[i], k);
-          if (i == k) {
-            d[i] = (lane == k) ? piv : rk;
-          } else if (lane == k) {
-            const cx<T> v = cmul(ci, piv);
-            d[i] = mkc<T>(-v.re, -v.im);
-          } else {
-            cfms(d[i], ci, rk);
-          }
+      for (int i = 1; i < B; ++i) {
+        const cx<T> ci = shfl_cx(d[i], k);
+        if (lane == k) {
+          const cx<T> v = cmul(ci, piv);
+          d[i] = mkc<T>(-v.re, -v.im);
+        } else {
+          cfms(d[i], ci, rk);
         }
       }
+      const cx<T> t0 = d[0];
+#pragma unroll
+      for (int i = 0; i + 1 < B; ++i) d[i] = d[i + 1];
+      d[B - 1] = t0;
+    }
+    for (int k = b; k < B; ++k) {
+      const cx<T> t0 = d[0];
+#pragma unroll
+      for (int i = 0; i + 1 < B; ++i) d[i] = d[i + 1];
+      d[B - 1] = t0;
     }
     // ---- symmetric average (D + D^T) / 2 through the shared tile; store D_K^{-1}
     if (lane < B) {
