@@ -4,10 +4,9 @@
 // the sequential layer recursion, every level eliminates every other remaining layer j at once:
 //   Dinv_j = D_j^{-1},  Lp = A_pj Dinv_j,  Lq = A_qj Dinv_j,
 //   D_p -= Lp A_jp,  D_q -= Lq A_jq,  A_pq = -Lp A_jq          (p, q: remaining neighbours of j)
-// so the critical path is log2(L) levels of batched dense work.  The factor and the explicit
-// inverse (a cyclic-reduction solve with the identity as right-hand side) are computed in the
-// working precision of the solver: FP64, or FP32 for the inner solver of the mixed form, whose
-// outer FP64 refinement absorbs the rounding of the coarse problem like that of the local ones.
+// so the critical path is log2(L) levels of batched dense work.  The factor is always computed in
+// FP64; the explicit inverse (a cyclic-reduction solve with the identity as right-hand side) in
+// the working precision of the solver, from FP32 copies of the factor in the mixed form.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -129,10 +128,11 @@ struct CopyTask {
 
 // C[M x N] (+)= alpha * A[M x Kd] * B[Kd x N]  (B^T when transB), TM x TM output tiles per CTA,
 // 16 x 16 threads with (TM/16)^2 outputs each, K in steps of 16 staged in shared memory.  FP64 uses
-// 32 x 32 tiles: its per-SM rate is low, so more CTAs per b x b task keep more SMs busy.
+// 16 x 16 tiles: its per-SM rate is low (about 2 FMA per clock), so many CTAs per b x b task keep
+// all SMs busy.
 template <class S>
 struct GemmTile {
-  static constexpr int TM = sizeof(S) == 8 ? 32 : 64;
+  static constexpr int TM = sizeof(S) == 8 ? 16 : 64;
 };
 
 template <class S, int TM>
@@ -347,7 +347,7 @@ static cudaError_t launch_gj_batch(const cx<S>* Din, cx<S>* Dout, const int* dli
     k_gj_regs<S><<<nblk, 256, 0, st>>>(Din, Dout, dlist, b, err);
     return cudaGetLastError();
   }
-  if (gj_block_smem<S>(b) <= 200 * 1024) {
+  if (sizeof(S) == 4 && gj_block_smem<S>(b) <= 200 * 1024) {
     const size_t smem = gj_block_smem<S>(b);
     cudaError_t e = smem_attr((const void*)k_gj_block<S>, (int)smem);
     if (e != cudaSuccess) return e;
@@ -392,7 +392,20 @@ static cudaError_t launch_gj_batch(const cx<S>* Din, cx<S>* Dout, const int* dli
     cudaGetLastError();
     last = e;
   }
+  if (gj_block_smem<S>(b) <= 200 * 1024) {
+    const size_t smem = gj_block_smem<S>(b);
+    cudaError_t e = smem_attr((const void*)k_gj_block<S>, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gj_block<S><<<nblk, 256, smem, st>>>(Din, Dout, dlist, b, err);
+    return cudaGetLastError();
+  }
   return last;
+}
+
+template <class S>
+__global__ void k_bcr_convert(const cx<double>* __restrict__ in, cx<S>* out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = ccast<S>(in[i]);
 }
 
 // X = [I 0]: n rows of ld >= n entries
@@ -433,8 +446,7 @@ struct BcrOp {
   BcrOpKind kind;
   size_t off;  // first task (GEMM, COPY) or list entry (GJ)
   int count;
-  int maxN;      // GEMM: widest task; COPY: longest copy
-  bool timed_inverse;  // first op of the inverse phase (profiling boundary)
+  int maxN;  // GEMM: widest task; COPY: longest copy
 };
 
 template <class T>
@@ -447,7 +459,7 @@ struct BcrPlan {
     if (ts.empty()) return;
     int mx = 0;
     for (auto& t : ts) mx = std::max(mx, t.N);
-    ops.push_back({OP_GEMM, gemm.size(), (int)ts.size(), mx, false});
+    ops.push_back({OP_GEMM, gemm.size(), (int)ts.size(), mx});
     gemm.insert(gemm.end(), ts.begin(), ts.end());
     ts.clear();
   }
@@ -455,15 +467,52 @@ struct BcrPlan {
     if (ts.empty()) return;
     long long mx = 0;
     for (auto& t : ts) mx = std::max(mx, t.count);
-    ops.push_back({OP_COPY, copy.size(), (int)ts.size(), (int)std::min<long long>(mx, 1 << 30), false});
+    ops.push_back({OP_COPY, copy.size(), (int)ts.size(), (int)std::min<long long>(mx, 1 << 30)});
     copy.insert(copy.end(), ts.begin(), ts.end());
     ts.clear();
   }
   void add_gj(const std::vector<int>& J) {
-    ops.push_back({OP_GJ, list.size(), (int)J.size(), 0, false});
+    ops.push_back({OP_GJ, list.size(), (int)J.size(), 0});
     list.insert(list.end(), J.begin(), J.end());
   }
 };
+
+// Uploads the task arrays of a plan and launches its operations in order (GJ operations invert
+// blocks of Dsrc into Ddst).
+template <class S>
+static cudaError_t run_plan(const BcrPlan<S>& plan, GemmTask<S>* dG, CopyTask<S>* dC, int* dL, const cx<S>* Dsrc,
+                            cx<S>* Ddst, int b, int* err, cudaStream_t st, long long* launches) {
+  if (!plan.gemm.empty()) {
+    cudaError_t e = cudaMemcpyAsync(dG, plan.gemm.data(), plan.gemm.size() * sizeof(GemmTask<S>), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+  }
+  if (!plan.copy.empty()) {
+    cudaError_t e = cudaMemcpyAsync(dC, plan.copy.data(), plan.copy.size() * sizeof(CopyTask<S>), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+  }
+  if (!plan.list.empty()) {
+    cudaError_t e = cudaMemcpyAsync(dL, plan.list.data(), plan.list.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+  }
+  constexpr int TM = GemmTile<S>::TM;
+  for (const BcrOp& op : plan.ops) {
+    cudaError_t e;
+    if (op.kind == OP_GJ) {
+      e = launch_gj_batch<S>(Dsrc, Ddst, dL + op.off, op.count, b, err, st);
+    } else if (op.kind == OP_GEMM) {
+      dim3 grid((op.maxN + TM - 1) / TM, (b + TM - 1) / TM, (unsigned)op.count);
+      k_gemm_batch<S, TM><<<grid, 256, 0, st>>>(dG + op.off, b, b);
+      e = cudaGetLastError();
+    } else {
+      const int chunks = (int)std::min<long long>(((long long)op.maxN + 255) / 256, 256);
+      k_copy_blocks<S><<<dim3(chunks, op.count), 256, 0, st>>>(dC + op.off, b);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return e;
+    ++*launches;
+  }
+  return cudaSuccess;
+}
 
 template <class T>
 int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int ldk, int* err, cudaStream_t st, std::string* msg,
@@ -494,94 +543,109 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int ldk, int* err, cuda
       for (void* p : *m) cudaFreeAsync(p, s);
     }
   } guard{&mem, st};
-  cx<T>*D = nullptr, *Ucur = nullptr, *Dinv = nullptr, *UP = nullptr, *UQ = nullptr, *Lp = nullptr, *Lq = nullptr,
-        *Unew = nullptr, *Tmp = nullptr;
-  BCR_CK(mal(&D, L * bb * sizeof(cx<T>)), "alloc");
-  BCR_CK(mal(&Ucur, L * bb * sizeof(cx<T>)), "alloc");
-  BCR_CK(mal(&Dinv, L * bb * sizeof(cx<T>)), "alloc");
-  BCR_CK(mal(&UP, 2 * L * bb * sizeof(cx<T>)), "alloc");  // UP_j = A_pj, then the transposes
-  BCR_CK(mal(&UQ, 2 * L * bb * sizeof(cx<T>)), "alloc");  // UQ_j = A_jq, then the transposes
-  BCR_CK(mal(&Lp, L * bb * sizeof(cx<T>)), "alloc");
-  BCR_CK(mal(&Lq, L * bb * sizeof(cx<T>)), "alloc");
-  BCR_CK(mal(&Unew, L * bb * sizeof(cx<T>)), "alloc");
-  BCR_CK(mal(&Tmp, n * (size_t)ldk * sizeof(cx<T>)), "alloc");
-  cx<T>* UPT = UP + (size_t)L * bb;
-  cx<T>* UQT = UQ + (size_t)L * bb;
+  using D64 = cx<double>;
+  D64 *D = nullptr, *Ucur = nullptr, *Dinv = nullptr, *UP = nullptr, *UQ = nullptr, *Lp = nullptr, *Lq = nullptr,
+      *Unew = nullptr;
+  BCR_CK(mal(&D, L * bb * sizeof(D64)), "alloc");
+  BCR_CK(mal(&Ucur, L * bb * sizeof(D64)), "alloc");
+  BCR_CK(mal(&Dinv, L * bb * sizeof(D64)), "alloc");
+  BCR_CK(mal(&UP, 2 * L * bb * sizeof(D64)), "alloc");  // UP_j = A_pj, then the transposes
+  BCR_CK(mal(&UQ, 2 * L * bb * sizeof(D64)), "alloc");  // UQ_j = A_jq, then the transposes
+  BCR_CK(mal(&Lp, L * bb * sizeof(D64)), "alloc");
+  BCR_CK(mal(&Lq, L * bb * sizeof(D64)), "alloc");
+  BCR_CK(mal(&Unew, L * bb * sizeof(D64)), "alloc");
+  D64* UPT = UP + (size_t)L * bb;
+  D64* UQT = UQ + (size_t)L * bb;
 
-  // ---- plan: factorisation
-  BcrPlan<T> plan;
-  std::vector<GemmTask<T>> ts;
-  std::vector<CopyTask<T>> cs;
+  // ---- plan: FP64 factorisation
+  BcrPlan<double> fp;
+  std::vector<GemmTask<double>> ts;
+  std::vector<CopyTask<double>> cs;
   const long long lbb = (long long)bb;
   for (size_t lv = 0; lv < lj.size(); ++lv) {
     const std::vector<int>& J = lj[lv];
-    plan.add_gj(J);  // Dinv_j = D_j^{-1}
+    fp.add_gj(J);  // Dinv_j = D_j^{-1}
     for (size_t k = 0; k < J.size(); ++k) {
       const int j = J[k], p = lp[lv][k], q = lq[lv][k];
       if (p >= 0) cs.push_back({Ucur + p * bb, UP + j * bb, lbb, 0});  // UP_j = A_pj
       if (q >= 0) cs.push_back({Ucur + j * bb, UQ + j * bb, lbb, 0});  // UQ_j = A_jq
       if (q >= 0) cs.push_back({Ucur + j * bb, UQT + j * bb, lbb, 1});  // UQ_j^T
     }
-    plan.add_copy(cs);
+    fp.add_copy(cs);
     for (size_t k = 0; k < J.size(); ++k) {
       const int j = J[k], p = lp[lv][k], q = lq[lv][k];
       // Lp_j = A_pj Dinv_j ; Lq_j = Dinv_j A_jq (= (A_qj Dinv_j)^T, Dinv_j symmetric)
-      if (p >= 0) ts.push_back({Ucur + p * bb, Dinv + j * bb, Lp + j * bb, b, b, b, 0, T(1), 0, b});
-      if (q >= 0) ts.push_back({Dinv + j * bb, Ucur + j * bb, Lq + j * bb, b, b, b, 0, T(1), 0, b});
+      if (p >= 0) ts.push_back({Ucur + p * bb, Dinv + j * bb, Lp + j * bb, b, b, b, 0, 1.0, 0, b});
+      if (q >= 0) ts.push_back({Dinv + j * bb, Ucur + j * bb, Lq + j * bb, b, b, b, 0, 1.0, 0, b});
     }
-    plan.add_gemm(ts);
+    fp.add_gemm(ts);
     // D_p -= Lp_j A_jp = Lp_j UP_j^T ; A_pq (new coupling of p) = -Lp_j UQ_j.  A separate launch
     // for D_q -= A_qj Dinv_j A_jq = UQ_j^T Lq_j: no two tasks of one launch write the same block.
     for (size_t k = 0; k < J.size(); ++k) {
       const int j = J[k], p = lp[lv][k], q = lq[lv][k];
       if (p >= 0) {
-        ts.push_back({Lp + j * bb, UP + j * bb, D + p * bb, b, b, b, 1, T(-1), 1, b});
-        if (q >= 0) ts.push_back({Lp + j * bb, UQ + j * bb, Unew + p * bb, b, b, b, 0, T(-1), 0, b});
+        ts.push_back({Lp + j * bb, UP + j * bb, D + p * bb, b, b, b, 1, -1.0, 1, b});
+        if (q >= 0) ts.push_back({Lp + j * bb, UQ + j * bb, Unew + p * bb, b, b, b, 0, -1.0, 0, b});
       }
     }
-    plan.add_gemm(ts);
+    fp.add_gemm(ts);
     for (size_t k = 0; k < J.size(); ++k) {
       const int j = J[k], q = lq[lv][k];
-      if (q >= 0) ts.push_back({UQT + j * bb, Lq + j * bb, D + q * bb, b, b, b, 0, T(-1), 1, b});
+      if (q >= 0) ts.push_back({UQT + j * bb, Lq + j * bb, D + q * bb, b, b, b, 0, -1.0, 1, b});
     }
-    plan.add_gemm(ts);
+    fp.add_gemm(ts);
     // a remaining p whose right neighbour j was eliminated now couples to q (or to nothing)
     for (size_t k = 0; k < J.size(); ++k) {
       const int p = lp[lv][k], q = lq[lv][k];
       if (p >= 0) cs.push_back({q >= 0 ? Unew + p * bb : nullptr, Ucur + p * bb, lbb, 0});
     }
-    plan.add_copy(cs);
+    fp.add_copy(cs);
   }
   // transposes of UP for the back substitution
   for (size_t lv = 0; lv < lj.size(); ++lv)
     for (size_t k = 0; k < lj[lv].size(); ++k)
       if (lp[lv][k] >= 0) cs.push_back({UP + lj[lv][k] * bb, UPT + lj[lv][k] * bb, lbb, 1});
-  plan.add_copy(cs);
-  const size_t inv_begin = plan.ops.size();
+  fp.add_copy(cs);
+
+  // ---- factor operands of the solve in precision T
+  cx<T>*DinvT = nullptr, *UPt = nullptr, *UQt = nullptr, *Tmp = nullptr;
+  if (sizeof(T) == sizeof(double)) {
+    DinvT = reinterpret_cast<cx<T>*>(Dinv);
+    UPt = reinterpret_cast<cx<T>*>(UP);
+    UQt = reinterpret_cast<cx<T>*>(UQ);
+  } else {
+    BCR_CK(mal(&DinvT, L * bb * sizeof(cx<T>)), "alloc");
+    BCR_CK(mal(&UPt, 2 * L * bb * sizeof(cx<T>)), "alloc");
+    BCR_CK(mal(&UQt, 2 * L * bb * sizeof(cx<T>)), "alloc");
+  }
+  BCR_CK(mal(&Tmp, n * (size_t)ldk * sizeof(cx<T>)), "alloc");
+  cx<T>* UPTt = UPt + (size_t)L * bb;
+  cx<T>* UQTt = UQt + (size_t)L * bb;
 
   // ---- plan: explicit inverse, a cyclic-reduction solve with X = I (in place in Kinv).  Forward
   // products only touch the block columns where row block j can be nonzero: [lo_j, hi_j], which
   // starts as {j} and grows by the ranges of the eliminated neighbours.
+  BcrPlan<T> ip;
+  std::vector<GemmTask<T>> ti;
+  std::vector<CopyTask<T>> ci;
   const size_t bN = (size_t)b * ldk;  // one block row of X (row stride ldk)
   const int N = (int)n;
   std::vector<int> lo(L), hi(L);
   for (int i = 0; i < L; ++i) lo[i] = hi[i] = i;
-  auto sub = [&](const cx<T>* base, int blockrow, int c0) { return base + (size_t)blockrow * bN + (size_t)c0 * b; };
+  auto sub = [&](cx<T>* base, int blockrow, int c0) { return base + (size_t)blockrow * bN + (size_t)c0 * b; };
   for (size_t lv = 0; lv < lj.size(); ++lv) {
     std::vector<GemmTask<T>> ta, tb;
     for (size_t k = 0; k < lj[lv].size(); ++k) {
       const int j = lj[lv][k], p = lp[lv][k], q = lq[lv][k];
       const int c0 = lo[j], w = (hi[j] - lo[j] + 1) * b;
       // Tmp_j = Dinv_j X_j ; X_p -= A_pj Tmp_j ; X_q -= A_qj Tmp_j  (on the columns of j)
-      ts.push_back({Dinv + j * bb, sub(Kinv, j, c0), const_cast<cx<T>*>(sub(Tmp, j, c0)), b, ldk, ldk, 0, T(1), 0, w});
-      if (p >= 0)
-        ta.push_back({UP + j * bb, sub(Tmp, j, c0), const_cast<cx<T>*>(sub(Kinv, p, c0)), b, ldk, ldk, 0, T(-1), 1, w});
-      if (q >= 0)
-        tb.push_back({UQT + j * bb, sub(Tmp, j, c0), const_cast<cx<T>*>(sub(Kinv, q, c0)), b, ldk, ldk, 0, T(-1), 1, w});
+      ti.push_back({DinvT + j * bb, sub(Kinv, j, c0), sub(Tmp, j, c0), b, ldk, ldk, 0, T(1), 0, w});
+      if (p >= 0) ta.push_back({UPt + j * bb, sub(Tmp, j, c0), sub(Kinv, p, c0), b, ldk, ldk, 0, T(-1), 1, w});
+      if (q >= 0) tb.push_back({UQTt + j * bb, sub(Tmp, j, c0), sub(Kinv, q, c0), b, ldk, ldk, 0, T(-1), 1, w});
     }
-    plan.add_gemm(ts);
-    plan.add_gemm(ta);
-    plan.add_gemm(tb);
+    ip.add_gemm(ti);
+    ip.add_gemm(ta);
+    ip.add_gemm(tb);
     for (size_t k = 0; k < lj[lv].size(); ++k) {
       const int j = lj[lv][k], p = lp[lv][k], q = lq[lv][k];
       if (p >= 0) {
@@ -599,65 +663,53 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int ldk, int* err, cuda
     for (size_t k = 0; k < lj[lv].size(); ++k) {
       const int j = lj[lv][k], p = lp[lv][k], q = lq[lv][k];
       // X_j -= A_jp X_p ; X_j -= A_jq X_q ; X_j = Dinv_j X_j (through Tmp_j)
-      if (p >= 0) ta.push_back({UPT + j * bb, sub(Kinv, p, 0), const_cast<cx<T>*>(sub(Kinv, j, 0)), b, ldk, ldk, 0, T(-1), 1, N});
-      if (q >= 0) tb.push_back({UQ + j * bb, sub(Kinv, q, 0), const_cast<cx<T>*>(sub(Kinv, j, 0)), b, ldk, ldk, 0, T(-1), 1, N});
-      ts.push_back({Dinv + j * bb, sub(Kinv, j, 0), const_cast<cx<T>*>(sub(Tmp, j, 0)), b, ldk, ldk, 0, T(1), 0, N});
-      cs.push_back({sub(Tmp, j, 0), const_cast<cx<T>*>(sub(Kinv, j, 0)), (long long)bN, 0});
+      if (p >= 0) ta.push_back({UPTt + j * bb, sub(Kinv, p, 0), sub(Kinv, j, 0), b, ldk, ldk, 0, T(-1), 1, N});
+      if (q >= 0) tb.push_back({UQt + j * bb, sub(Kinv, q, 0), sub(Kinv, j, 0), b, ldk, ldk, 0, T(-1), 1, N});
+      ti.push_back({DinvT + j * bb, sub(Kinv, j, 0), sub(Tmp, j, 0), b, ldk, ldk, 0, T(1), 0, N});
+      ci.push_back({sub(Tmp, j, 0), sub(Kinv, j, 0), (long long)bN, 0});
     }
-    plan.add_gemm(ta);
-    plan.add_gemm(tb);
-    plan.add_gemm(ts);
-    plan.add_copy(cs);
+    ip.add_gemm(ta);
+    ip.add_gemm(tb);
+    ip.add_gemm(ti);
+    ip.add_copy(ci);
   }
-  if (inv_begin < plan.ops.size()) plan.ops[inv_begin].timed_inverse = true;
 
-  // ---- upload the task arrays once
-  GemmTask<T>* dG = nullptr;
-  CopyTask<T>* dC = nullptr;
+  // ---- device task arrays
+  GemmTask<double>* dG = nullptr;
+  CopyTask<double>* dC = nullptr;
   int* dL = nullptr;
-  BCR_CK(mal(&dG, plan.gemm.size() * sizeof(GemmTask<T>)), "alloc");
-  BCR_CK(mal(&dC, plan.copy.size() * sizeof(CopyTask<T>)), "alloc");
-  BCR_CK(mal(&dL, plan.list.size() * sizeof(int)), "alloc");
-  if (!plan.gemm.empty())
-    BCR_CK(cudaMemcpyAsync(dG, plan.gemm.data(), plan.gemm.size() * sizeof(GemmTask<T>), cudaMemcpyHostToDevice, st), "upload");
-  if (!plan.copy.empty())
-    BCR_CK(cudaMemcpyAsync(dC, plan.copy.data(), plan.copy.size() * sizeof(CopyTask<T>), cudaMemcpyHostToDevice, st), "upload");
-  if (!plan.list.empty())
-    BCR_CK(cudaMemcpyAsync(dL, plan.list.data(), plan.list.size() * sizeof(int), cudaMemcpyHostToDevice, st), "upload");
+  GemmTask<T>* dGi = nullptr;
+  CopyTask<T>* dCi = nullptr;
+  BCR_CK(mal(&dG, fp.gemm.size() * sizeof(GemmTask<double>)), "alloc");
+  BCR_CK(mal(&dC, fp.copy.size() * sizeof(CopyTask<double>)), "alloc");
+  BCR_CK(mal(&dL, fp.list.size() * sizeof(int)), "alloc");
+  BCR_CK(mal(&dGi, ip.gemm.size() * sizeof(GemmTask<T>)), "alloc");
+  BCR_CK(mal(&dCi, ip.copy.size() * sizeof(CopyTask<T>)), "alloc");
 
-  // ---- run
-  BCR_CK(cudaMemsetAsync(UP, 0, 2 * L * bb * sizeof(cx<T>), st), "memset");
-  BCR_CK(cudaMemsetAsync(UQ, 0, 2 * L * bb * sizeof(cx<T>), st), "memset");
+  // ---- run: factorisation
+  BCR_CK(cudaMemsetAsync(UP, 0, 2 * L * bb * sizeof(D64), st), "memset");
+  BCR_CK(cudaMemsetAsync(UQ, 0, 2 * L * bb * sizeof(D64), st), "memset");
   const int gs = (int)std::min<size_t>((L * bb + 255) / 256, 4096);
   prof_start(KC_COARSE_SETUP, st);
-  k_bcr_densify<T><<<gs, 256, 0, st>>>(P, D, Ucur);
+  k_bcr_densify<double><<<gs, 256, 0, st>>>(P, D, Ucur);
   BCR_CK(cudaGetLastError(), "densify");
   ++*launches;
-  constexpr int TM = GemmTile<T>::TM;
-  bool in_inverse = false;
-  for (const BcrOp& op : plan.ops) {
-    if (op.timed_inverse) {
-      prof_stop(KC_COARSE_SETUP, st);
-      prof_start(KC_COARSE_INV, st);
-      in_inverse = true;
-      k_bcr_identity<T><<<(int)std::min<size_t>((n * ldk + 255) / 256, 8192), 256, 0, st>>>(Kinv, (int)n, ldk);
-      BCR_CK(cudaGetLastError(), "identity");
-      ++*launches;
-    }
-    if (op.kind == OP_GJ) {
-      BCR_CK(launch_gj_batch<T>(D, Dinv, dL + op.off, op.count, b, err, st), "inversion");
-    } else if (op.kind == OP_GEMM) {
-      dim3 grid((op.maxN + TM - 1) / TM, (b + TM - 1) / TM, (unsigned)op.count);
-      k_gemm_batch<T, TM><<<grid, 256, 0, st>>>(dG + op.off, b, b);
-      BCR_CK(cudaGetLastError(), "gemm");
-    } else {
-      const int chunks = (int)std::min<long long>(((long long)op.maxN + 255) / 256, 256);
-      k_copy_blocks<T><<<dim3(chunks, op.count), 256, 0, st>>>(dC + op.off, b);
-      BCR_CK(cudaGetLastError(), "copy");
-    }
-    ++*launches;
+  BCR_CK(run_plan<double>(fp, dG, dC, dL, D, Dinv, b, err, st, launches), "factorisation");
+  prof_stop(KC_COARSE_SETUP, st);
+  // ---- run: explicit inverse
+  prof_start(KC_COARSE_INV, st);
+  if (sizeof(T) != sizeof(double)) {
+    k_bcr_convert<T><<<gs, 256, 0, st>>>(Dinv, DinvT, L * bb);
+    k_bcr_convert<T><<<gs, 256, 0, st>>>(UP, UPt, 2 * L * bb);
+    k_bcr_convert<T><<<gs, 256, 0, st>>>(UQ, UQt, 2 * L * bb);
+    BCR_CK(cudaGetLastError(), "convert");
+    *launches += 3;
   }
-  prof_stop(in_inverse ? KC_COARSE_INV : KC_COARSE_SETUP, st);
+  k_bcr_identity<T><<<(int)std::min<size_t>((n * ldk + 255) / 256, 8192), 256, 0, st>>>(Kinv, (int)n, ldk);
+  BCR_CK(cudaGetLastError(), "identity");
+  ++*launches;
+  BCR_CK(run_plan<T>(ip, dGi, dCi, nullptr, nullptr, nullptr, b, err, st, launches), "inverse");
+  prof_stop(KC_COARSE_INV, st);
   BCR_CK(cudaStreamSynchronize(st), "sync");
   return SCHUR_OK;
 #undef BCR_CK
