@@ -668,12 +668,13 @@ __device__ __forceinline__ void orth_block_dots(const cx<T>* __restrict__ V, con
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int j = warp; j <= a.k; j += nw) {
     const cx<T>* vj = V + j * a.vstride + (size_t)r * a.nlam + lo;
-    double re = 0, im = 0;
+    T pre = 0, pim = 0;  // per-lane partial sums (a few terms) in T, combined in FP64
     for (int i = lane; i < n; i += 32) {
       const cx<T> x = vj[i], y = ws[i];
-      re += (double)(x.re * y.re + x.im * y.im);
-      im += (double)(x.re * y.im - x.im * y.re);
+      pre += x.re * y.re + x.im * y.im;
+      pim += x.re * y.im - x.im * y.re;
     }
+    double re = pre, im = pim;
     for (int o = 16; o > 0; o >>= 1) {
       re += __shfl_xor_sync(0xffffffffu, re, o);
       im += __shfl_xor_sync(0xffffffffu, im, o);
@@ -767,8 +768,9 @@ __global__ void __launch_bounds__(256) k_orth_update_norm(const cx<T>* __restric
   int lo, n;
   orth_slice(a, &lo, &n);
   orth_block_update(V, a, r, lo, n, w, ws, h);
-  double s = 0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)ws[i].re * (double)ws[i].re + (double)ws[i].im * (double)ws[i].im;
+  T ps = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) ps += ws[i].re * ws[i].re + ws[i].im * ws[i].im;
+  double s = ps;
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
