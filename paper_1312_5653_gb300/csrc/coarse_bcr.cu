@@ -102,6 +102,132 @@ __global__ void __launch_bounds__(256) k_gj_batch_cluster(const cx<S>* __restric
   cluster.sync();
 }
 
+// Gauss-Jordan inversion by column panels, one thread-block cluster of CL CTAs per matrix (no
+// pivoting).  CTA c owns columns [c*cw, c*cw + ncol) in shared memory (row-major, stride cw), and
+// panel step k uses the columns of CTA k as the pivot block K.  The owner publishes the panel
+// A[:, K] and P = A[K, K]^{-1} in its shared memory; after one cluster barrier every CTA reads them
+// through distributed shared memory and updates its own columns:
+//   A[K, j] <- P A[K, j],   A[i, j] <- A[i, j] - A[i, K] A[K, j]_new   (i not in K)
+// while the owner sets A[i, K] <- -A[i, K] P (i not in K) and A[K, K] <- P.  One cluster barrier
+// per panel instead of one per pivot.
+template <class S>
+__device__ void gj_small_warp(cx<S>* A, int n, int ld, int* err) {
+  // in-place inverse of the n x n block A (row stride ld) by one warp, n <= 32
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k < n; ++k) {
+    const cx<S> p = A[k * ld + k];
+    const cx<S> piv = cinv(p);
+    if (lane == 0 && !finite_nonzero(p)) atomicExch(err, 1);
+    cx<S> rk = lane < n ? cmul(A[k * ld + lane], piv) : mkc<S>(0, 0);
+    __syncwarp();
+    for (int i = 0; i < n; ++i) {
+      const cx<S> ci = A[i * ld + k];
+      __syncwarp();
+      if (lane < n) {
+        cx<S>& a = A[i * ld + lane];
+        if (i == k) {
+          a = (lane == k) ? piv : rk;
+        } else if (lane == k) {
+          const cx<S> v = cmul(ci, piv);
+          a = mkc<S>(-v.re, -v.im);
+        } else {
+          cfms(a, ci, rk);
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+template <class S>
+static size_t gj_blocked_smem(int b, int CL) {
+  const size_t cw = (size_t)(b + CL - 1) / CL;
+  return (3 * (b * cw + cw * cw) + 2 * cw * cw) * sizeof(cx<S>);
+}
+
+template <class S>
+__global__ void __launch_bounds__(256) k_gj_blocked(const cx<S>* __restrict__ Din, cx<S>* Dout,
+                                                    const int* __restrict__ list, int b, int* err) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CL = (int)cluster.num_blocks(), me = (int)cluster.block_rank();
+  const int which = list[blockIdx.x / CL];
+  const int cw = (b + CL - 1) / CL, c0 = me * cw, ncol = max(0, min(b, c0 + cw) - c0);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int pnl = b * cw + cw * cw;  // panel (b x cw) followed by P (cw x cw)
+  extern __shared__ __align__(16) unsigned char smgjb[];
+  cx<S>* Aown = reinterpret_cast<cx<S>*>(smgjb);  // b x cw
+  cx<S>* pub = Aown + pnl;                        // published panel + P (owner step only)
+  cx<S>* pan = pub + pnl;                         // local copy of the current panel + P
+  cx<S>* tmp = pan + pnl;                         // cw x cw: P A[K, own]
+  const size_t bb = (size_t)b * b;
+  const cx<S>* src = Din + (size_t)which * bb;
+  for (int e = tid; e < b * cw; e += nthr) {
+    const int i = e / cw, jl = e - i * cw;
+    Aown[e] = jl < ncol ? src[(size_t)i * b + c0 + jl] : mkc<S>(0, 0);
+  }
+  __syncthreads();
+  for (int step = 0; step < CL; ++step) {
+    const int k0 = step * cw, kp = max(0, min(b, k0 + cw) - k0);
+    if (kp == 0) break;  // same for every CTA of the cluster
+    if (me == step) {
+      for (int e = tid; e < b * cw; e += nthr) pub[e] = Aown[e];
+      __syncthreads();
+      cx<S>* Pm = pub + b * cw;
+      for (int e = tid; e < cw * cw; e += nthr) {
+        const int r = e / cw, c = e - r * cw;
+        Pm[e] = (r < kp && c < kp) ? pub[(size_t)(k0 + r) * cw + c] : mkc<S>(0, 0);
+      }
+      __syncthreads();
+      if (tid < 32) gj_small_warp(Pm, kp, cw, err);
+      __syncthreads();
+    }
+    cluster.sync();
+    const cx<S>* rp = cluster.map_shared_rank(pub, step);
+    for (int e = tid; e < pnl; e += nthr) pan[e] = rp[e];
+    __syncthreads();
+    const cx<S>* Pm = pan + b * cw;
+    if (me != step) {
+      // tmp = P A[K, own]
+      for (int e = tid; e < kp * cw; e += nthr) {
+        const int r = e / cw, jl = e - r * cw;
+        cx<S> acc = mkc<S>(0, 0);
+        for (int m2 = 0; m2 < kp; ++m2) cfma(acc, Pm[r * cw + m2], Aown[(size_t)(k0 + m2) * cw + jl]);
+        tmp[e] = acc;
+      }
+      __syncthreads();
+      for (int e = tid; e < b * cw; e += nthr) {
+        const int i = e / cw, jl = e - i * cw;
+        if (i >= k0 && i < k0 + kp) {
+          Aown[e] = tmp[(i - k0) * cw + jl];
+        } else {
+          cx<S> a = Aown[e];
+          for (int m2 = 0; m2 < kp; ++m2) cfms(a, pan[(size_t)i * cw + m2], tmp[m2 * cw + jl]);
+          Aown[e] = a;
+        }
+      }
+    } else {
+      for (int e = tid; e < b * cw; e += nthr) {
+        const int i = e / cw, kl = e - i * cw;
+        if (kl >= kp) continue;
+        if (i >= k0 && i < k0 + kp) {
+          Aown[e] = Pm[(i - k0) * cw + kl];
+        } else {
+          cx<S> a = mkc<S>(0, 0);
+          for (int m2 = 0; m2 < kp; ++m2) cfms(a, pan[(size_t)i * cw + m2], Pm[m2 * cw + kl]);
+          Aown[e] = a;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  cx<S>* dst = Dout + (size_t)which * bb;
+  for (int e = tid; e < b * ncol; e += nthr) {
+    const int i = e / ncol, jl = e - i * ncol;
+    dst[(size_t)i * b + c0 + jl] = Aown[(size_t)i * cw + jl];
+  }
+  cluster.sync();  // keep this CTA's shared memory alive until every remote read is done
+}
+
 // One batched complex GEMM task: C (+)= alpha * A * op(B), A b x b, B and C b x N (N per task),
 // row-major with leading dimensions; transB: use B^T.
 template <class S>
@@ -254,79 +380,6 @@ __global__ void __launch_bounds__(256) k_gj_block(const cx<S>* __restrict__ Din,
   for (int e = tid; e < (int)bb; e += 256) dst[e] = A[e];
 }
 
-// Register-resident variant for b <= 64: thread (tx, ty) of the 32 x 8 grid keeps entries
-// (ty + 8 r, tx + 32 c) in registers; per pivot the owners publish row k and column k to a double
-// buffer in shared memory, so one barrier per pivot suffices.
-template <class S>
-__global__ void __launch_bounds__(256) k_gj_regs(const cx<S>* __restrict__ Din, cx<S>* Dout,
-                                                 const int* __restrict__ list, int b, int* err) {
-  constexpr int RPT = 8, CPT = 2;
-  __shared__ cx<S> rowk[2][64], colk[2][64];
-  const int which = list[blockIdx.x];
-  const size_t bb = (size_t)b * b;
-  const cx<S>* src = Din + (size_t)which * bb;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  cx<S> a[RPT][CPT];
-#pragma unroll
-  for (int r = 0; r < RPT; ++r)
-#pragma unroll
-    for (int c = 0; c < CPT; ++c) {
-      const int i = ty + 8 * r, j = tx + 32 * c;
-      a[r][c] = (i < b && j < b) ? src[(size_t)i * b + j] : mkc<S>(0, 0);
-    }
-  for (int k = 0; k < b; ++k) {
-    const int buf = k & 1;
-    if (ty == (k & 7)) {
-#pragma unroll
-      for (int r = 0; r < RPT; ++r)
-        if (r == (k >> 3)) {
-#pragma unroll
-          for (int c = 0; c < CPT; ++c) rowk[buf][tx + 32 * c] = a[r][c];
-        }
-    }
-    if (tx == (k & 31)) {
-#pragma unroll
-      for (int c = 0; c < CPT; ++c)
-        if (c == (k >> 5)) {
-#pragma unroll
-          for (int r = 0; r < RPT; ++r) colk[buf][ty + 8 * r] = a[r][c];
-        }
-    }
-    __syncthreads();
-    const cx<S> p = rowk[buf][k];
-    const cx<S> piv = cinv(p);
-    if (threadIdx.x == 0 && !finite_nonzero(p)) atomicExch(err, 1);
-    cx<S> rs[CPT];
-#pragma unroll
-    for (int c = 0; c < CPT; ++c) rs[c] = cmul(rowk[buf][tx + 32 * c], piv);
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-      const int i = ty + 8 * r;
-      const cx<S> ci = colk[buf][i];
-#pragma unroll
-      for (int c = 0; c < CPT; ++c) {
-        const int j = tx + 32 * c;
-        if (i == k) {
-          a[r][c] = (j == k) ? piv : rs[c];
-        } else if (j == k) {
-          const cx<S> v = cmul(ci, piv);
-          a[r][c] = mkc<S>(-v.re, -v.im);
-        } else {
-          cfms(a[r][c], ci, rs[c]);
-        }
-      }
-    }
-  }
-  cx<S>* dst = Dout + (size_t)which * bb;
-#pragma unroll
-  for (int r = 0; r < RPT; ++r)
-#pragma unroll
-    for (int c = 0; c < CPT; ++c) {
-      const int i = ty + 8 * r, j = tx + 32 * c;
-      if (i < b && j < b) dst[(size_t)i * b + j] = a[r][c];
-    }
-}
-
 template <class S>
 static size_t gj_block_smem(int b) {
   return ((size_t)b * b + 2 * (size_t)b) * sizeof(cx<S>);
@@ -338,24 +391,52 @@ static size_t bcr_gj_smem(int b, int CL) {
   return ((size_t)b * cw + 3 * (size_t)b + cw) * sizeof(cx<S>);
 }
 
-// Inversion of the listed blocks: one CTA per block when the block fits in shared memory, else
-// one thread-block cluster per block with the columns distributed over its CTAs.
+// Inversion of the listed blocks: a cluster per block with column panels (k_gj_blocked), else a
+// cluster with one barrier per pivot, else one CTA per block with the block in shared memory.
 template <class S>
 static cudaError_t launch_gj_batch(const cx<S>* Din, cx<S>* Dout, const int* dlist, int nblk, int b, int* err,
                                    cudaStream_t st) {
-  if (sizeof(S) == 4 && b <= 64) {
-    k_gj_regs<S><<<nblk, 256, 0, st>>>(Din, Dout, dlist, b, err);
-    return cudaGetLastError();
-  }
-  if (sizeof(S) == 4 && gj_block_smem<S>(b) <= 200 * 1024) {
-    const size_t smem = gj_block_smem<S>(b);
-    cudaError_t e = smem_attr((const void*)k_gj_block<S>, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_gj_block<S><<<nblk, 256, smem, st>>>(Din, Dout, dlist, b, err);
-    return cudaGetLastError();
+  cudaError_t last = cudaErrorInvalidConfiguration;
+  if (b >= 16) {
+    static const int bsizes[] = {8, 16, 4};
+    for (int CL : bsizes) {
+      if ((b + CL - 1) / CL > 32) continue;  // the pivot block is inverted by one warp
+      const size_t smem = gj_blocked_smem<S>(b, CL);
+      if (smem > 200 * 1024) continue;
+      cudaError_t e = smem_attr((const void*)k_gj_blocked<S>, (int)smem);
+      if (e == cudaSuccess && CL > 8)
+        e = cudaFuncSetAttribute(k_gj_blocked<S>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        last = e;
+        continue;
+      }
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(nblk * CL, 1, 1);
+      cfg.blockDim = dim3(256, 1, 1);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = CL;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int ncl = 0;
+      e = cudaOccupancyMaxActiveClusters(&ncl, k_gj_blocked<S>, &cfg);
+      if (e != cudaSuccess || ncl < 1) {
+        cudaGetLastError();
+        last = e != cudaSuccess ? e : cudaErrorInvalidConfiguration;
+        continue;
+      }
+      e = cudaLaunchKernelEx(&cfg, k_gj_blocked<S>, Din, Dout, dlist, b, err);
+      if (e == cudaSuccess) return cudaSuccess;
+      cudaGetLastError();
+      last = e;
+    }
   }
   static const int sizes[] = {16, 8, 4, 2, 1};
-  cudaError_t last = cudaErrorInvalidConfiguration;
   for (int CL : sizes) {
     if (CL > 1 && nblk * CL > 4 * 152 && CL > 4) continue;  // keep many clusters resident at once
     size_t smem = bcr_gj_smem<S>(b, CL);

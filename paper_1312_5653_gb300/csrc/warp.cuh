@@ -635,16 +635,7 @@ __global__ void k_local_solve_warp(StencilProv<T> P, Geom g, MapsView m, const c
   cx<T>* X = Xs + (size_t)sd * g.nl * R;
   extern __shared__ unsigned char smraw[];
   cx<T>* Ds = reinterpret_cast<cx<T>*>(smraw) + (size_t)(threadIdx.x >> 5) * 2 * b * b;
-  // right-hand side of every remainder node first, all lanes in parallel (independent loads), into
-  // X; each layer's entries are read back before the sweep overwrites them
-  const int nlr = L * b * R;
-#pragma unroll 4
-  for (int e = lane; e < nlr; e += 32) {
-    const int node = e / R, c = e - node * R, K = node / b, i = node - K * b;
-    X[e] = remainder_rhs(P, g, m, sd, S, f, ldf, lam, uc, K, i, c);
-  }
-  __syncwarp();
-  auto rhs = [&](int K, int i, int c) -> cx<T> { return X[(size_t)(K * b + i) * R + c]; };
+  auto rhs = [&](int K, int i, int c) -> cx<T> { return remainder_rhs(P, g, m, sd, S, f, ldf, lam, uc, K, i, c); };
   warp_layered_solve<T, C>(P, Dinv + (size_t)q * L * b * b, R, rhs, X, R, 1, Ds);
   if (!VD) return;
   __syncwarp();
