@@ -277,14 +277,23 @@ __global__ void __launch_bounds__(256) k_gemm_batch(const GemmTask<S>* __restric
 #pragma unroll
     for (int c = 0; c < Q; ++c) acc[a][c] = mkc<S>(0, 0);
   for (int k0 = 0; k0 < Kd; k0 += 16) {
+    // row-major operands read along their rows (k fastest) so consecutive threads touch
+    // consecutive addresses; non-transposed B along its rows too (columns fastest)
     for (int e = threadIdx.x; e < 16 * TM; e += 256) {
-      int kk = e / TM, r = e % TM;
-      int gr = row0 + r, gk = k0 + kk;
+      const int r = e >> 4, kk = e & 15;
+      const int gr = row0 + r, gk = k0 + kk;
       As[kk][r] = (gr < M && gk < Kd) ? t.A[(size_t)gr * t.lda + gk] : mkc<S>(0, 0);
-      int gc = col0 + r;
-      cx<S> bv = mkc<S>(0, 0);
-      if (gc < N && gk < Kd) bv = t.transB ? t.B[(size_t)gc * t.ldb + gk] : t.B[(size_t)gk * t.ldb + gc];
-      Bs[kk][r] = bv;
+      if (t.transB) {
+        const int gc = col0 + r;
+        Bs[kk][r] = (gc < N && gk < Kd) ? t.B[(size_t)gc * t.ldb + gk] : mkc<S>(0, 0);
+      }
+    }
+    if (!t.transB) {
+      for (int e = threadIdx.x; e < 16 * TM; e += 256) {
+        const int kk = e / TM, c = e % TM;
+        const int gk = k0 + kk, gc = col0 + c;
+        Bs[kk][c] = (gc < N && gk < Kd) ? t.B[(size_t)gk * t.ldb + gc] : mkc<S>(0, 0);
+      }
     }
     __syncthreads();
 #pragma unroll 4
