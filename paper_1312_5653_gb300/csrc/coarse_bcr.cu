@@ -324,6 +324,70 @@ __global__ void __launch_bounds__(256) k_gemm_batch(const GemmTask<S>* __restric
     }
 }
 
+// C (+)= alpha * A * op(B) for a banded operand (level 0 of the reduction, where the blocks still
+// have the stencil's band): A banded (|i - k| <= w) when bandA, else op(B) banded (|k - j| <= w).
+// One thread per output entry, grid (chunks, tasks).
+template <class S>
+__global__ void k_gemm_band(const GemmTask<S>* __restrict__ tasks, int M, int Kd, int w, int bandA) {
+  const GemmTask<S> t = tasks[blockIdx.y];
+  const int N = t.N;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M * N; e += gridDim.x * blockDim.x) {
+    const int i = e / N, j = e - i * N;
+    const int c = bandA ? i : j;
+    const int k0 = max(0, c - w), k1 = min(Kd - 1, c + w);
+    cx<S> acc = mkc<S>(0, 0);
+    for (int k = k0; k <= k1; ++k)
+      cfma(acc, t.A[(size_t)i * t.lda + k], t.transB ? t.B[(size_t)j * t.ldb + k] : t.B[(size_t)k * t.ldb + j]);
+    cx<S>& o = t.C[(size_t)i * t.ldc + j];
+    const cx<S> v = cscale(acc, t.alpha);
+    o = t.accumulate ? cadd(o, v) : v;
+  }
+}
+
+// Inverses of tridiagonal b x b blocks (listed), one thread per column of the inverse: the Thomas
+// recurrence without pivoting, its multipliers shared through shared memory.
+template <class S>
+__global__ void k_tri_inverse(const cx<S>* __restrict__ Din, cx<S>* Dout, const int* __restrict__ list, int b,
+                              int* err) {
+  extern __shared__ __align__(16) unsigned char smtri[];
+  cx<S>* cp = reinterpret_cast<cx<S>*>(smtri);  // b: modified super-diagonal c'_i
+  cx<S>* dp = cp + b;                           // b: 1 / (pivot_i)
+  const int which = list[blockIdx.x];
+  const cx<S>* D = Din + (size_t)which * b * b;
+  if (threadIdx.x == 0) {
+    cx<S> cprev = mkc<S>(0, 0);
+    for (int i = 0; i < b; ++i) {
+      cx<S> piv = D[(size_t)i * b + i];
+      if (i > 0) cfms(piv, D[(size_t)i * b + i - 1], cprev);
+      if (!finite_nonzero(piv)) atomicExch(err, 1);
+      const cx<S> ip = cinv(piv);
+      dp[i] = ip;
+      cprev = i + 1 < b ? cmul(D[(size_t)i * b + i + 1], ip) : mkc<S>(0, 0);
+      cp[i] = cprev;
+    }
+  }
+  __syncthreads();
+  cx<S>* X = Dout + (size_t)which * b * b;
+  for (int col = threadIdx.x; col < b; col += blockDim.x) {
+    // forward: y_i = (e_col,i - l_i y_{i-1}) / pivot_i with l_i = D[i][i-1]
+    cx<S> y = mkc<S>(0, 0);
+    for (int i = 0; i < b; ++i) {
+      cx<S> r = mkc<S>(i == col ? S(1) : S(0), S(0));
+      if (i > 0) cfms(r, D[(size_t)i * b + i - 1], y);
+      y = cmul(r, dp[i]);
+      X[(size_t)i * b + col] = y;
+    }
+    // backward: x_i = y_i - c'_i x_{i+1}
+    cx<S> x = X[(size_t)(b - 1) * b + col];
+    for (int i = b - 2; i >= 0; --i) {
+      cx<S> v = X[(size_t)i * b + col];
+      cfms(v, cp[i], x);
+      x = v;
+      X[(size_t)i * b + col] = x;
+    }
+  }
+}
+
 // Batched block copies, grid (chunks, tasks).  Transposed copies are b x b blocks (count = b*b).
 template <class S>
 __global__ void k_copy_blocks(const CopyTask<S>* __restrict__ tasks, int b) {
@@ -531,7 +595,7 @@ static void bcr_schedule(int L, std::vector<std::vector<int>>* lev_j, std::vecto
 
 // The whole reduction as a list of launches over task arrays that are built on the host and
 // uploaded once.
-enum BcrOpKind { OP_GJ, OP_GEMM, OP_COPY };
+enum BcrOpKind { OP_GJ, OP_GEMM, OP_COPY, OP_TRI, OP_BAND_A, OP_BAND_B };
 struct BcrOp {
   BcrOpKind kind;
   size_t off;  // first task (GEMM, COPY) or list entry (GJ)
@@ -561,9 +625,17 @@ struct BcrPlan {
     copy.insert(copy.end(), ts.begin(), ts.end());
     ts.clear();
   }
-  void add_gj(const std::vector<int>& J) {
-    ops.push_back({OP_GJ, list.size(), (int)J.size(), 0});
+  void add_gj(const std::vector<int>& J, BcrOpKind kind = OP_GJ) {
+    ops.push_back({kind, list.size(), (int)J.size(), 0});
     list.insert(list.end(), J.begin(), J.end());
+  }
+  void add_band(std::vector<GemmTask<T>>& ts, bool bandA) {
+    if (ts.empty()) return;
+    int mx = 0;
+    for (auto& t : ts) mx = std::max(mx, t.N);
+    ops.push_back({bandA ? OP_BAND_A : OP_BAND_B, gemm.size(), (int)ts.size(), mx});
+    gemm.insert(gemm.end(), ts.begin(), ts.end());
+    ts.clear();
   }
 };
 
@@ -571,7 +643,7 @@ struct BcrPlan {
 // blocks of Dsrc into Ddst).
 template <class S>
 static cudaError_t run_plan(const BcrPlan<S>& plan, GemmTask<S>* dG, CopyTask<S>* dC, int* dL, const cx<S>* Dsrc,
-                            cx<S>* Ddst, int b, int* err, cudaStream_t st, long long* launches) {
+                            cx<S>* Ddst, int b, int w, int* err, cudaStream_t st, long long* launches) {
   if (!plan.gemm.empty()) {
     cudaError_t e = cudaMemcpyAsync(dG, plan.gemm.data(), plan.gemm.size() * sizeof(GemmTask<S>), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
@@ -589,6 +661,13 @@ static cudaError_t run_plan(const BcrPlan<S>& plan, GemmTask<S>* dG, CopyTask<S>
     cudaError_t e;
     if (op.kind == OP_GJ) {
       e = launch_gj_batch<S>(Dsrc, Ddst, dL + op.off, op.count, b, err, st);
+    } else if (op.kind == OP_TRI) {
+      k_tri_inverse<S><<<op.count, 64, 2 * b * sizeof(cx<S>), st>>>(Dsrc, Ddst, dL + op.off, b, err);
+      e = cudaGetLastError();
+    } else if (op.kind == OP_BAND_A || op.kind == OP_BAND_B) {
+      const int chunks = std::max(1, std::min((b * op.maxN + 255) / 256, 64));
+      k_gemm_band<S><<<dim3(chunks, op.count), 256, 0, st>>>(dG + op.off, b, b, w, op.kind == OP_BAND_A ? 1 : 0);
+      e = cudaGetLastError();
     } else if (op.kind == OP_GEMM) {
       dim3 grid((op.maxN + TM - 1) / TM, (b + TM - 1) / TM, (unsigned)op.count);
       k_gemm_batch<S, TM><<<grid, 256, 0, st>>>(dG + op.off, b, b);
@@ -652,9 +731,15 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int ldk, int* err, cuda
   std::vector<GemmTask<double>> ts;
   std::vector<CopyTask<double>> cs;
   const long long lbb = (long long)bb;
+  // Level 0 still sees the stencil's band: the layer blocks couple in-layer neighbours only, so
+  // every product there has a banded operand (half-width 1 in 2D, a layer row + 1 in 3D), and in
+  // 2D the pivot blocks are tridiagonal and are inverted by the Thomas recurrence.
+  const int wband = P.ly.dim == 2 ? 1 : P.ly.ext[0] + 1;
+  const bool tri0 = P.ly.dim == 2;
   for (size_t lv = 0; lv < lj.size(); ++lv) {
     const std::vector<int>& J = lj[lv];
-    fp.add_gj(J);  // Dinv_j = D_j^{-1}
+    const bool band = lv == 0;
+    fp.add_gj(J, band && tri0 ? OP_TRI : OP_GJ);  // Dinv_j = D_j^{-1}
     for (size_t k = 0; k < J.size(); ++k) {
       const int j = J[k], p = lp[lv][k], q = lq[lv][k];
       if (p >= 0) cs.push_back({Ucur + p * bb, UP + j * bb, lbb, 0});  // UP_j = A_pj
@@ -662,13 +747,20 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int ldk, int* err, cuda
       if (q >= 0) cs.push_back({Ucur + j * bb, UQT + j * bb, lbb, 1});  // UQ_j^T
     }
     fp.add_copy(cs);
+    // Lp_j = A_pj Dinv_j ; Lq_j = Dinv_j A_jq (= (A_qj Dinv_j)^T, Dinv_j symmetric)
+    std::vector<GemmTask<double>> tq;
     for (size_t k = 0; k < J.size(); ++k) {
       const int j = J[k], p = lp[lv][k], q = lq[lv][k];
-      // Lp_j = A_pj Dinv_j ; Lq_j = Dinv_j A_jq (= (A_qj Dinv_j)^T, Dinv_j symmetric)
       if (p >= 0) ts.push_back({Ucur + p * bb, Dinv + j * bb, Lp + j * bb, b, b, b, 0, 1.0, 0, b});
-      if (q >= 0) ts.push_back({Dinv + j * bb, Ucur + j * bb, Lq + j * bb, b, b, b, 0, 1.0, 0, b});
+      if (q >= 0) tq.push_back({Dinv + j * bb, Ucur + j * bb, Lq + j * bb, b, b, b, 0, 1.0, 0, b});
     }
-    fp.add_gemm(ts);
+    if (band) {
+      fp.add_band(ts, true);
+      fp.add_band(tq, false);
+    } else {
+      ts.insert(ts.end(), tq.begin(), tq.end());
+      fp.add_gemm(ts);
+    }
     // D_p -= Lp_j A_jp = Lp_j UP_j^T ; A_pq (new coupling of p) = -Lp_j UQ_j.  A separate launch
     // for D_q -= A_qj Dinv_j A_jq = UQ_j^T Lq_j: no two tasks of one launch write the same block.
     for (size_t k = 0; k < J.size(); ++k) {
@@ -678,12 +770,14 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int ldk, int* err, cuda
         if (q >= 0) ts.push_back({Lp + j * bb, UQ + j * bb, Unew + p * bb, b, b, b, 0, -1.0, 0, b});
       }
     }
-    fp.add_gemm(ts);
+    if (band) fp.add_band(ts, false);
+    else fp.add_gemm(ts);
     for (size_t k = 0; k < J.size(); ++k) {
       const int j = J[k], q = lq[lv][k];
       if (q >= 0) ts.push_back({UQT + j * bb, Lq + j * bb, D + q * bb, b, b, b, 0, -1.0, 1, b});
     }
-    fp.add_gemm(ts);
+    if (band) fp.add_band(ts, true);
+    else fp.add_gemm(ts);
     // a remaining p whose right neighbour j was eliminated now couples to q (or to nothing)
     for (size_t k = 0; k < J.size(); ++k) {
       const int p = lp[lv][k], q = lq[lv][k];
@@ -784,7 +878,7 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int ldk, int* err, cuda
   k_bcr_densify<double><<<gs, 256, 0, st>>>(P, D, Ucur);
   BCR_CK(cudaGetLastError(), "densify");
   ++*launches;
-  BCR_CK(run_plan<double>(fp, dG, dC, dL, D, Dinv, b, err, st, launches), "factorisation");
+  BCR_CK(run_plan<double>(fp, dG, dC, dL, D, Dinv, b, wband, err, st, launches), "factorisation");
   prof_stop(KC_COARSE_SETUP, st);
   // ---- run: explicit inverse
   prof_start(KC_COARSE_INV, st);
@@ -798,7 +892,7 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int ldk, int* err, cuda
   k_bcr_identity<T><<<(int)std::min<size_t>((n * ldk + 255) / 256, 8192), 256, 0, st>>>(Kinv, (int)n, ldk);
   BCR_CK(cudaGetLastError(), "identity");
   ++*launches;
-  BCR_CK(run_plan<T>(ip, dGi, dCi, nullptr, nullptr, nullptr, b, err, st, launches), "inverse");
+  BCR_CK(run_plan<T>(ip, dGi, dCi, nullptr, nullptr, nullptr, b, 0, err, st, launches), "inverse");
   prof_stop(KC_COARSE_INV, st);
   BCR_CK(cudaStreamSynchronize(st), "sync");
   return SCHUR_OK;

@@ -56,8 +56,8 @@ template <class R>
 __host__ __device__ __forceinline__ cx<R> cscale(cx<R> a, R s) { return mkc<R>(a.re * s, a.im * s); }
 template <class R>
 __host__ __device__ __forceinline__ cx<R> cinv(cx<R> a) {
-  R d = a.re * a.re + a.im * a.im;
-  return mkc<R>(a.re / d, -a.im / d);
+  const R s = R(1) / (a.re * a.re + a.im * a.im);  // one division
+  return mkc<R>(a.re * s, -a.im * s);
 }
 template <class R, class S>
 __host__ __device__ __forceinline__ cx<R> ccast(cx<S> a) { return mkc<R>((R)a.re, (R)a.im); }
