@@ -13,7 +13,13 @@ local operators, coarse factorisation) + schur_solve (FETI-DP GMRES with FP64 re
 refinement); the plain FP64 form and the cached-factor solve rate are reported beside it.
 L2 is flushed (256 MB write) between timed steps.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Further rows in the same JSON line (rank 0, skipped with --no-extra): the 3D precision form
+(128^3, 16^3 subdomains, mixed vs FP64), the full-space KKT form (512^2, MINRES, 8 right-hand
+sides, two betas) and the serving stream (mixed 2D/3D sizes, 6 betas, 1-16 right-hand sides,
+Poisson arrivals at 0.8 x measured capacity; p50/p99 latency, mixed vs FP64).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-extra]
+                  [--serve-requests R]
 """
 import argparse
 import json
@@ -42,6 +48,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-extra", action="store_true", help="skip the 3D, full-space and serving rows")
+    p.add_argument("--serve-requests", type=int, default=200, help="requests in the serving stream")
     return p.parse_args()
 
 
@@ -191,6 +199,155 @@ def algorithmic(cat, info, prec_bytes):
         ntask = sum(1 + 2 * p + q + 2 * q for lev in bcr_tasks(cL) for p, q in lev)
         return "alu", ntask * cb_ ** 3 * cmac
     return None, None
+
+
+# ------------------------------------------------------------------ further measured rows
+def _events(torch, stream):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def row_3d(args, torch, S, inputs, oracle, dev, stream):
+    """Precision form: 3D, 128^3 Q1 elements, 16^3 subdomains of 8^3, beta = 1e-6, 8 sine modes;
+    setup + one solve, mixed (refined to 1e-10) and plain FP64, error against the oracle."""
+    N, P, beta = 128, 16, 1e-6
+    yb = inputs.random_modes_3d(N, count=8, seed=2)
+    bh = oracle.apply_M(3, N, yb)
+    b = torch.from_numpy(bh).to(dev)
+    n = bh.size
+    t0 = time.perf_counter()
+    xref = oracle.fd_schur_solve(3, N, beta, bh)
+    t_or = time.perf_counter() - t0
+    out = {"workload": "3d-q1-128^3-dirichlet-16^3sub-8^3el-8-sine-modes-beta1e-6", "n_dofs": n,
+           "oracle_s": t_or}
+    precs = [(S.SCHUR_MIXED, "mixed")] + ([] if args.no_fp64 else [(S.SCHUR_FP64, "fp64")])
+    for prec, key in precs:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sol = S.Solver(3, N, beta, nsub=P, precision=prec, tol=OUTER_TOL)
+        t_setup = time.perf_counter() - t0
+        e0, e1 = _events(torch, stream)
+        e0.record(stream)
+        x = sol.schur_solve(b)
+        e1.record(stream)
+        e1.synchronize()
+        ms_solve = e0.elapsed_time(e1)
+        st = sol.last_stats
+        err = float(np.linalg.norm(x.cpu().numpy() - xref) / np.linalg.norm(xref))
+        sol.close()
+        out[key] = {"ms_setup": 1e3 * t_setup, "ms_solve": ms_solve,
+                    "mdof_s": n / (t_setup + ms_solve / 1e3) / 1e6, "mdof_s_cached": n / (ms_solve / 1e3) / 1e6,
+                    "relerr_vs_oracle": err, "gmres_iters": st["iters_total"], "outer_steps": st["outer_steps"],
+                    "rel_residual": st["rel_residual"]}
+    return out
+
+
+def row_kkt(args, torch, S, inputs, oracle, dev, stream):
+    """Full-space form: 2D 512^2, 32 x 32 subdomains, MINRES with P_mgw on 8 right-hand sides
+    (M y_bar_k, 0, 0), y_bar_k = smoothed noise seeds 10..17, to 1e-10; per beta."""
+    N, P = 512, 32
+    n = (N - 1) ** 2
+    yb = inputs.smoothed_noise(2, N, seed=10, nrhs=8)
+    ry = oracle.apply_M(2, N, yb)
+    rhs = np.zeros((8, 3 * n))
+    rhs[:, :n] = ry
+    rd = torch.from_numpy(rhs).to(dev)
+    out = {"workload": "2d-q1-512x512-32x32sub-kkt-minres-8rhs", "n_dofs_per_block": n, "nrhs": 8}
+    for beta in (1e-4, 1e-8):
+        y, u, l = oracle.fd_kkt_solve(2, N, beta, ry=ry)
+        ref = np.concatenate([y, u, l], axis=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sol = S.Solver(2, N, beta, nsub=P, precision=S.SCHUR_MIXED, tol=OUTER_TOL)
+        t_setup = time.perf_counter() - t0
+        e0, e1 = _events(torch, stream)
+        e0.record(stream)
+        x, it = sol.schur_kkt_minres(rd, tol=1e-10, max_it=60)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        xh = x.cpu().numpy()
+        err = max(float(np.linalg.norm(xh[c] - ref[c]) / np.linalg.norm(ref[c])) for c in range(8))
+        sol.close()
+        out["beta_%g" % beta] = {"ms_setup": 1e3 * t_setup, "ms_minres": ms, "minres_iters": it,
+                                 "max_relerr_vs_oracle": err,
+                                 "mdof_s": 8 * 3 * n / (t_setup + ms / 1e3) / 1e6}
+    return out
+
+
+def serve_stream(args, S, inputs, oracle):
+    """Serving form: Poisson arrivals of mixed 2D/3D sizes, beta from 6 cached values, 1-16 seeded
+    right-hand sides per request.  Capacity is measured closed-loop (all requests at t = 0); the
+    open-loop stream then arrives at 0.8 x that rate, served by the mixed and by the plain FP64
+    form.  Latency = arrival -> result on the host."""
+    nreq = args.serve_requests
+    sizes = [(2, 64), (2, 128), (2, 256), (2, 512), (2, 1024), (3, 32), (3, 64), (3, 96)]
+    betas = [10.0 ** (-8 + 1.2 * k) for k in range(6)]
+    rng = np.random.default_rng(5)
+    reqs = []
+    for i in range(nreq):
+        r = np.random.default_rng(i)
+        dim, N = sizes[r.integers(len(sizes))]
+        reqs.append((dim, N, betas[r.integers(6)], int(r.integers(1, 17)), i))
+    pool = {}
+    for dim, N in sizes:  # 16 seeded targets per size, b = M y_bar
+        yb = inputs.smoothed_noise(dim, N, seed=100 + N, nrhs=16) if dim == 2 else \
+            inputs.random_modes_3d(N, count=8, seed=100 + N, nrhs=16)
+        pool[(dim, N)] = np.ascontiguousarray(oracle.apply_M(dim, N, yb))
+
+    def rhs_of(q):
+        dim, N, beta, R, i = q
+        return np.ascontiguousarray(np.roll(pool[(dim, N)], i, axis=0)[:R])
+
+    def run(prec, arrivals):
+        srv = S.Server(budget_bytes=64 << 30, workers=4, precision=prec, tol=1e-10)
+        try:
+            lat, done, pend, nsolve = [], 0, {}, 0
+            t0 = time.perf_counter()
+            k = 0
+            while k < nreq or pend:
+                now = time.perf_counter() - t0
+                while k < nreq and arrivals[k] <= now:
+                    q = reqs[k]
+                    pend[srv.submit(q[0], q[1], q[2], rhs_of(q))] = (arrivals[k], q)
+                    k += 1
+                moved = False
+                for t in list(pend):
+                    ok, x, st = srv.poll(t)
+                    if ok:
+                        arr, q = pend.pop(t)
+                        lat.append(time.perf_counter() - t0 - arr)
+                        nsolve += q[3]
+                        moved = True
+                if not moved:
+                    time.sleep(0.0002)
+            span = time.perf_counter() - t0
+        finally:
+            srv.close()
+        lat = np.array(lat) * 1e3
+        return {"requests": nreq, "rhs_solved": nsolve, "makespan_s": span, "solves_s": nsolve / span,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+
+    closed = run(S.SCHUR_MIXED, np.zeros(nreq))
+    rate = 0.8 * nreq / closed["makespan_s"]
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq))
+    out = {"workload": "serve-mixed-2d-64..1024^2-3d-32..96^3-6-betas-1..16-rhs-poisson", "requests": nreq,
+           "capacity_requests_s": nreq / closed["makespan_s"], "arrival_rate_requests_s": rate,
+           "mixed": run(S.SCHUR_MIXED, arrivals)}
+    if not args.no_fp64:
+        out["fp64"] = run(S.SCHUR_FP64, arrivals)
+    # spot check of served results against the oracle (first 2D requests up to 256^2)
+    srv = S.Server(budget_bytes=8 << 30, workers=2, precision=S.SCHUR_MIXED, tol=1e-10)
+    try:
+        errs = []
+        for q in [q for q in reqs if q[0] == 2 and q[1] <= 256][:4]:
+            b = rhs_of(q)
+            x, _ = srv.wait(srv.submit(q[0], q[1], q[2], b))
+            xr = np.stack([oracle.fd_schur_solve(2, q[1], q[2], b[c]) for c in range(b.shape[0])])
+            errs.append(float(np.linalg.norm(x - xr) / np.linalg.norm(xr)))
+        out["spot_max_relerr_vs_oracle"] = max(errs) if errs else None
+    finally:
+        srv.close()
+    return out
 
 
 def main():
@@ -378,6 +535,14 @@ def main():
             roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
                     "traffic": None, "launches": nl_, "avg_us": avg_s * 1e6}
 
+    extra = {}
+    if rank == 0 and not args.no_extra:
+        import oracle
+        oracle.build()
+        extra["precision_form_3d"] = row_3d(args, torch, S, inputs, oracle, dev, stream)
+        extra["full_space_kkt"] = row_kkt(args, torch, S, inputs, oracle, dev, stream)
+        extra["serving"] = serve_stream(args, S, inputs, oracle)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MDoF/s", "n_gpus": world, "steps": args.steps,
@@ -396,6 +561,7 @@ def main():
             "profile_ms_by_kernel": {k: v[1] for k, v in (prof_all or {}).items()},
             "clocks": clk.summary(),
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
