@@ -58,6 +58,25 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def rank_seed(rank):
+    """Seed of the right-hand side a rank solves: independent problems per rank (weak scaling)."""
+    return 1 + rank
+
+
+def max_over_ranks(torch, value, device, world):
+    """The job's time: the largest of the ranks' values (barrier-bracketed timed regions)."""
+    if world == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, n, steps, total_ms):
+    """Whole-job MDoF/s: every rank solves n dofs per step; time = max over ranks."""
+    return world * n * steps / (total_ms / 1e3) / 1e6
+
+
 class Clocks:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -378,7 +397,7 @@ def main():
     lib = S.load()
     n = S.schur_ndof(2, N_EL)
     # each rank solves its own seeded right-hand side (independent problems: weak scaling)
-    yb = inputs.smoothed_noise(2, N_EL, seed=1 + rank)
+    yb = inputs.smoothed_noise(2, N_EL, seed=rank_seed(rank))
     ybd = torch.from_numpy(yb).to(dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
@@ -425,11 +444,7 @@ def main():
         prof = S.schur_profile_end() if profile_mask else None
         if world > 1:
             torch.distributed.barrier()
-        total = float(np.sum(times))
-        if world > 1:
-            t = torch.tensor([total], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total = float(t.item())
+        total = max_over_ranks(torch, float(np.sum(times)), dev, world)
         return total, times, stats, launches, prof
 
     import ctypes
@@ -446,7 +461,7 @@ def main():
     with Clocks(local_rank) as clk:
         total, times, stats, launches, prof = timed(S.SCHUR_MIXED, args.steps, args.warmup, profile_mask=dom_mask)
     ms_step = total / args.steps
-    value = world * n * args.steps / (total / 1e3) / 1e6
+    value = job_rate(world, n, args.steps, total)
 
     # accuracy of the timed path vs the oracle on one step (rank 0)
     relerr = None
