@@ -347,6 +347,14 @@ class Engine : public EngineBase {
       (void)cbb;
       int crc = coarse_bcr<T>(cprov_, Kinv_, ldk_, err_ + 2, st, msg, &launches);
       if (crc) return crc;
+      // keep the upper 32 x 32 tiles of the symmetric inverse; the full matrix is released
+      prof_start(KC_COARSE_INV, st);
+      k_pack_ctiles<T><<<(int)std::min<long long>(ctile_count(nct_), 8 * nsm_), 256, 0, st>>>(Kinv_, g.ncor, ldk_,
+                                                                                            nct_, Kt_);
+      prof_stop(KC_COARSE_INV, st);
+      ENG_LAUNCH();
+      free_one(Kinv_);
+      Kinv_ = nullptr;
     }
     ENG_CK(cudaStreamSynchronize(st));
     int herr[4];
@@ -470,11 +478,16 @@ class Engine : public EngineBase {
     else if (which == 3 || which == 4) {
       if (g.ncor == 0) return SCHUR_EINVAL;
       if (which == 4) {
-        rc = fetch(Kinv_, (size_t)g.ncor * ldk_);
-        if (!rc) {
+        rc = fetch(Kt_, (size_t)ctile_count(nct_) * kCT * kCT);
+        if (!rc) {  // upper tiles -> full symmetric matrix (lower tiles are the transposes)
           std::vector<cx<double>> full((size_t)g.ncor * g.ncor);
           for (int i = 0; i < g.ncor; ++i)
-            for (int j = 0; j < g.ncor; ++j) full[(size_t)i * g.ncor + j] = host[(size_t)i * ldk_ + j];
+            for (int j = 0; j < g.ncor; ++j) {
+              const int I = i / kCT, J = j / kCT;
+              const size_t e = I <= J ? (size_t)ctile_idx(I, J, nct_) * kCT * kCT + (i % kCT) * kCT + j % kCT
+                                      : (size_t)ctile_idx(J, I, nct_) * kCT * kCT + (j % kCT) * kCT + i % kCT;
+              full[(size_t)i * g.ncor + j] = host[e];
+            }
           host.swap(full);
         }
       } else {
@@ -558,6 +571,11 @@ class Engine : public EngineBase {
     ENG_CK(wa(&gc_, nco * R * cxT));
     ENG_CK(wa(&wc_, nco * R * cxT));
     ENG_CK(wa(&uc_, nco * R * cxT));
+    if (g.ncor > 0) {
+      const size_t np = (size_t)ctile_count(nct_) * kCT * R;
+      ENG_CK(wa(&cpu_, np * cxT));
+      ENG_CK(wa(&cpv_, np * cxT));
+    }
     nblk_ = std::max(1, std::min((int)((nl + 255) / 256), 2 * nsm_));
     nblk_ = std::max(nblk_, (int)((nl + 2047) / 2048));
     ENG_CK(wa(&part_, (size_t)kMaxRdev * kMaxKdev * nblk_ * sizeof(cx<double>)));
@@ -628,13 +646,12 @@ class Engine : public EngineBase {
   }
 
   int coarse_apply(const cx<T>* gv, int R, const int* active, cx<T>* w, cudaStream_t st, std::string* msg) {
-    const int rows_per_block = 8, grid = (g_.ncor + rows_per_block - 1) / rows_per_block;
+    const long long ntile = ctile_count(nct_);
     prof_start(KC_COARSE_APPLY, st);
-    if (R == 1) k_coarse_apply<T, 1><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, ldk_, gv, R, active, w);
-    else if (R <= 4) k_coarse_apply<T, 4><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, ldk_, gv, R, active, w);
-    else if (R <= 8) k_coarse_apply<T, 8><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, ldk_, gv, R, active, w);
-    else k_coarse_apply<T, 16><<<grid, 256, 0, st>>>(Kinv_, g_.ncor, ldk_, gv, R, active, w);
+    k_coarse_tiles<T><<<(int)((ntile + 3) / 4), 128, 0, st>>>(Kt_, nct_, g_.ncor, gv, R, active, cpu_, cpv_);
+    k_coarse_reduce<T><<<(nct_ * R * 32 + 255) / 256, 256, 0, st>>>(cpu_, cpv_, nct_, g_.ncor, R, active, w);
     prof_stop(KC_COARSE_APPLY, st);
+    ENG_LAUNCH();
     ENG_LAUNCH();
     return SCHUR_OK;
   }
@@ -824,12 +841,13 @@ class Engine : public EngineBase {
   Stencil<T> st_;
   StencilProv<T> prr_, pii_;
   StoredProv<double> cprov_;
-  int ncls_ = 0, nsm_ = 152, nblk_ = 1, coarse_cluster_ = 0, ldk_ = 0;
+  int ncls_ = 0, nsm_ = 152, nblk_ = 1, coarse_cluster_ = 0, ldk_ = 0, nct_ = 0;
   long long op_bytes_ = 0;
   std::vector<void*> allocs_, ws_;
   int* err_ = nullptr;
   int* ones_ = nullptr;
-  cx<T>*Dinv_ = nullptr, *F_ = nullptr, *Frc_ = nullptr, *Sd_ = nullptr, *Kinv_ = nullptr;
+  cx<T>*Dinv_ = nullptr, *F_ = nullptr, *Frc_ = nullptr, *Sd_ = nullptr, *Kinv_ = nullptr, *Kt_ = nullptr;
+  cx<T>*cpu_ = nullptr, *cpv_ = nullptr;  // partial products of the packed coarse inverse
   cx<double>*Kcc_ = nullptr, *CA_ = nullptr, *CB_ = nullptr, *Dc_ = nullptr;
   int wsR_ = 0, wsM_ = 0;
   cx<T>*Xs_ = nullptr, *VD_ = nullptr, *Y_ = nullptr, *Tc_ = nullptr, *d_ = nullptr, *zv_ = nullptr, *lam_ = nullptr,

@@ -46,6 +46,11 @@ __device__ __forceinline__ long long gidx(const Geom& g, const int* G) {
 template <class T>
 __device__ __forceinline__ cx<T> czero() { return mkc<T>(T(0), T(0)); }
 
+template <class T>
+__device__ __forceinline__ cx<T> shfl_cx(cx<T> v, int src) {
+  return mkc<T>(__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src));
+}
+
 // Asynchronous global -> shared copies (cp.async, L1-allocating), one complex entry per lane.
 template <class T>
 __device__ __forceinline__ void cp_async_cx(cx<T>* smem, const cx<T>* gmem) {
@@ -440,52 +445,91 @@ __global__ void k_corner_gather(Geom g, const cx<T>* __restrict__ Tc, int R, con
   out[(size_t)r * g.ncor + cI] = v;
 }
 
-// w = Kinv gvec for R columns: one warp per coarse row; rows of ldk (even) entries read as pairs
-// of complex entries per 16-byte load (FP32) so more bytes are in flight per warp.
-template <class T, int MR>
-__global__ void k_coarse_apply(const cx<T>* __restrict__ Kinv, int ncor, int ldk, const cx<T>* __restrict__ gv, int R,
-                               const int* __restrict__ active, cx<T>* w) {
+// ------------------------------------------------------------------ coarse inverse, packed tiles
+// The coarse inverse is complex symmetric: only its upper 32 x 32 tiles (I <= J) are kept, tile
+// (I, J) at index ctile_idx(I, J) as a row-major 32 x 32 block, zero past n_c.  w = Kinv g is
+// formed in two launches: every tile produces its row product T g_J (for w_I) and, off the
+// diagonal, its transposed product T^T g_I (for w_J) into a partial buffer; then each row block
+// adds its partials in tile order (deterministic).
+constexpr int kCT = 32;
+__host__ __device__ __forceinline__ long long ctile_idx(int I, int J, int nt) {
+  return (long long)I * nt - (long long)I * (I - 1) / 2 + (J - I);
+}
+__host__ __device__ __forceinline__ long long ctile_count(int nt) { return (long long)nt * (nt + 1) / 2; }
+
+// tiles from the full inverse (n rows of ld entries); one block per tile
+template <class T>
+__global__ void k_pack_ctiles(const cx<T>* __restrict__ K, int n, int ld, int nt, cx<T>* tiles) {
+  for (long long t = blockIdx.x; t < ctile_count(nt); t += gridDim.x) {
+    // tile coordinates from the packed index
+    int I = 0;
+    long long rem = t;
+    while (rem >= nt - I) {
+      rem -= nt - I;
+      ++I;
+    }
+    const int J = I + (int)rem;
+    for (int e = threadIdx.x; e < kCT * kCT; e += blockDim.x) {
+      const int r = I * kCT + e / kCT, c = J * kCT + e % kCT;
+      tiles[t * kCT * kCT + e] = (r < n && c < n) ? K[(size_t)r * ld + c] : czero<T>();
+    }
+  }
+}
+
+// phase 1: one warp per tile (4 per block), the tile staged in shared memory (row stride 33)
+template <class T>
+__global__ void __launch_bounds__(128) k_coarse_tiles(const cx<T>* __restrict__ tiles, int nt, int ncor,
+                                                      const cx<T>* __restrict__ gv, int R, const int* __restrict__ active,
+                                                      cx<T>* part_u, cx<T>* part_v) {
+  __shared__ cx<T> Ts[4][kCT][kCT + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (row >= ncor) return;
-  cx<T> acc[MR];
-  for (int r = 0; r < MR; ++r) acc[r] = czero<T>();
-  const cx<T>* Krow = Kinv + (size_t)row * ldk;
-  if constexpr (sizeof(T) == 4) {
-    const float4* K4 = reinterpret_cast<const float4*>(Krow);
-    const int np = ldk / 2;
-#pragma unroll 4
-    for (int p = lane; p < np; p += 32) {
-      const float4 v = K4[p];
-      const int j0 = 2 * p, j1 = j0 + 1;
-      const cx<T> a0 = mkc<T>(v.x, v.y);
-      const cx<T> a1 = j1 < ncor ? mkc<T>(v.z, v.w) : czero<T>();
-#pragma unroll
-      for (int r = 0; r < MR; ++r)
-        if (r < R) {
-          cfma(acc[r], a0, gv[(size_t)r * ncor + j0]);
-          if (j1 < ncor) cfma(acc[r], a1, gv[(size_t)r * ncor + j1]);
-        }
-    }
-  } else {
-#pragma unroll 4
-    for (int j = lane; j < ncor; j += 32) {
-      const cx<T> a = Krow[j];
-#pragma unroll
-      for (int r = 0; r < MR; ++r)
-        if (r < R) cfma(acc[r], a, gv[(size_t)r * ncor + j]);
-    }
+  const long long t = (long long)blockIdx.x * 4 + warp;
+  const long long ntile = ctile_count(nt);
+  if (t >= ntile) return;
+  int I = 0;
+  long long rem = t;
+  while (rem >= nt - I) {
+    rem -= nt - I;
+    ++I;
   }
-#pragma unroll
-  for (int r = 0; r < MR; ++r) {
-    if (r >= R) break;
-    T re = acc[r].re, im = acc[r].im;
-    for (int o = 16; o > 0; o >>= 1) {
-      re += __shfl_xor_sync(0xffffffffu, re, o);
-      im += __shfl_xor_sync(0xffffffffu, im, o);
+  const int J = I + (int)rem;
+  const cx<T>* src = tiles + t * kCT * kCT;
+#pragma unroll 8
+  for (int r = 0; r < kCT; ++r) Ts[warp][r][lane] = src[r * kCT + lane];
+  __syncwarp();
+  for (int r = 0; r < R; ++r) {
+    if (!active[r]) continue;
+    const cx<T>* g = gv + (size_t)r * ncor;
+    const int gi = I * kCT + lane, gj = J * kCT + lane;
+    const cx<T> gJ = gj < ncor ? g[gj] : czero<T>();
+    const cx<T> gI = gi < ncor ? g[gi] : czero<T>();
+    cx<T> u = czero<T>(), v = czero<T>();
+#pragma unroll 8
+    for (int k = 0; k < kCT; ++k) {
+      cfma(u, Ts[warp][lane][k], shfl_cx(gJ, k));  // row lane of T times g_J
+      cfma(v, Ts[warp][k][lane], shfl_cx(gI, k));  // column lane of T times g_I
     }
-    if (lane == 0 && (!active || active[r])) w[(size_t)r * ncor + row] = mkc<T>(re, im);
+    part_u[((size_t)r * ntile + t) * kCT + lane] = u;
+    if (I != J) part_v[((size_t)r * ntile + t) * kCT + lane] = v;
   }
+}
+
+// phase 2: w_I = sum_{J >= I} part_u(I, J) + sum_{J < I} part_v(J, I); one warp per (I, rhs)
+template <class T>
+__global__ void k_coarse_reduce(const cx<T>* __restrict__ part_u, const cx<T>* __restrict__ part_v, int nt, int ncor,
+                                int R, const int* __restrict__ active, cx<T>* w) {
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int I = wid % nt, r = wid / nt;
+  if (r >= R || !active[r]) return;
+  const long long ntile = ctile_count(nt);
+  const cx<T>* pu = part_u + (size_t)r * ntile * kCT;
+  const cx<T>* pv = part_v + (size_t)r * ntile * kCT;
+  cx<T> acc = czero<T>();
+  for (int J = 0; J < I; ++J) acc = cadd(acc, pv[ctile_idx(J, I, nt) * kCT + lane]);
+  const long long t0 = ctile_idx(I, I, nt);
+  for (int J = I; J < nt; ++J) acc = cadd(acc, pu[(t0 + (J - I)) * kCT + lane]);
+  const int row = I * kCT + lane;
+  if (row < ncor) w[(size_t)r * ncor + row] = acc;
 }
 
 // Frc^s w_s on slot j of subdomain sd (w: coarse vector of one right-hand side).

@@ -7,10 +7,6 @@
 
 namespace schur {
 
-template <class T>
-__device__ __forceinline__ cx<T> shfl_cx(cx<T> v, int src) {
-  return mkc<T>(__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src));
-}
 
 // Warp-wide asynchronous copy of one b x b layer block into shared memory.
 template <class T>
