@@ -341,9 +341,11 @@ class Engine : public EngineBase {
       cprov_.CA = CA_;
       cprov_.CB = CB_;
       // FP64 block cyclic reduction over the coarse layers, explicit inverse in precision T
-      ldk_ = (g.ncor + 1) & ~1;  // even row stride: 16-byte aligned FP32 rows
+      ldk_ = (g.ncor + 1) & ~1;  // even row stride of the full inverse (temporary)
+      nct_ = (g.ncor + kCT - 1) / kCT;
       ENG_CK(alloc(&Kinv_, (size_t)g.ncor * ldk_ * cxT));
-      op_bytes_ += (long long)g.ncor * ldk_ * cxT;
+      ENG_CK(alloc(&Kt_, (size_t)ctile_count(nct_) * kCT * kCT * cxT));
+      op_bytes_ += (long long)ctile_count(nct_) * kCT * kCT * cxT;
       (void)cbb;
       int crc = coarse_bcr<T>(cprov_, Kinv_, ldk_, err_ + 2, st, msg, &launches);
       if (crc) return crc;

@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(128) k_coarse_tiles(const cx<T>* __restrict__ 
   for (int r = 0; r < kCT; ++r) Ts[warp][r][lane] = src[r * kCT + lane];
   __syncwarp();
   for (int r = 0; r < R; ++r) {
-    if (!active[r]) continue;
+    if (active && !active[r]) continue;  // active == null: every right-hand side
     const cx<T>* g = gv + (size_t)r * ncor;
     const int gi = I * kCT + lane, gj = J * kCT + lane;
     const cx<T> gJ = gj < ncor ? g[gj] : czero<T>();
@@ -520,7 +520,7 @@ __global__ void k_coarse_reduce(const cx<T>* __restrict__ part_u, const cx<T>* _
                                 int R, const int* __restrict__ active, cx<T>* w) {
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   const int I = wid % nt, r = wid / nt;
-  if (r >= R || !active[r]) return;
+  if (r >= R || (active && !active[r])) return;
   const long long ntile = ctile_count(nt);
   const cx<T>* pu = part_u + (size_t)r * ntile * kCT;
   const cx<T>* pv = part_v + (size_t)r * ntile * kCT;
