@@ -494,8 +494,22 @@ __global__ void __launch_bounds__(128) k_coarse_tiles(const cx<T>* __restrict__ 
   }
   const int J = I + (int)rem;
   const cx<T>* src = tiles + t * kCT * kCT;
+  if constexpr (sizeof(T) == 4) {
+    // the whole 8 KB tile in flight at once: 16 x 16-byte loads per lane, then to shared memory
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4 v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = s4[i * 32 + lane];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int e = 2 * (i * 32 + lane), r = e / kCT, c = e % kCT;
+      Ts[warp][r][c] = mkc<T>(v[i].x, v[i].y);
+      Ts[warp][r][c + 1] = mkc<T>(v[i].z, v[i].w);
+    }
+  } else {
 #pragma unroll 8
-  for (int r = 0; r < kCT; ++r) Ts[warp][r][lane] = src[r * kCT + lane];
+    for (int r = 0; r < kCT; ++r) Ts[warp][r][lane] = src[r * kCT + lane];
+  }
   __syncwarp();
   for (int r = 0; r < R; ++r) {
     if (active && !active[r]) continue;  // active == null: every right-hand side
@@ -514,22 +528,31 @@ __global__ void __launch_bounds__(128) k_coarse_tiles(const cx<T>* __restrict__ 
   }
 }
 
-// phase 2: w_I = sum_{J >= I} part_u(I, J) + sum_{J < I} part_v(J, I); one warp per (I, rhs)
+// phase 2: w_I = sum_{J >= I} part_u(I, J) + sum_{J < I} part_v(J, I); one block of 4 warps per
+// (I, rhs), warp q adding a contiguous quarter of the J range, the quarters combined in order
 template <class T>
-__global__ void k_coarse_reduce(const cx<T>* __restrict__ part_u, const cx<T>* __restrict__ part_v, int nt, int ncor,
-                                int R, const int* __restrict__ active, cx<T>* w) {
-  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const int I = wid % nt, r = wid / nt;
+__global__ void __launch_bounds__(128) k_coarse_reduce(const cx<T>* __restrict__ part_u, const cx<T>* __restrict__ part_v,
+                                                       int nt, int ncor, int R, const int* __restrict__ active, cx<T>* w) {
+  __shared__ cx<T> red[4][kCT];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int I = blockIdx.x % nt, r = blockIdx.x / nt;
   if (r >= R || (active && !active[r])) return;
   const long long ntile = ctile_count(nt);
   const cx<T>* pu = part_u + (size_t)r * ntile * kCT;
   const cx<T>* pv = part_v + (size_t)r * ntile * kCT;
-  cx<T> acc = czero<T>();
-  for (int J = 0; J < I; ++J) acc = cadd(acc, pv[ctile_idx(J, I, nt) * kCT + lane]);
   const long long t0 = ctile_idx(I, I, nt);
-  for (int J = I; J < nt; ++J) acc = cadd(acc, pu[(t0 + (J - I)) * kCT + lane]);
-  const int row = I * kCT + lane;
-  if (row < ncor) w[(size_t)r * ncor + row] = acc;
+  const int q0 = (nt * warp) / 4, q1 = (nt * (warp + 1)) / 4;
+  cx<T> acc = czero<T>();
+#pragma unroll 4
+  for (int J = q0; J < q1; ++J)
+    acc = cadd(acc, J < I ? pv[ctile_idx(J, I, nt) * kCT + lane] : pu[(t0 + (J - I)) * kCT + lane]);
+  red[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    const cx<T> tot = cadd(cadd(red[0][lane], red[1][lane]), cadd(red[2][lane], red[3][lane]));
+    const int row = I * kCT + lane;
+    if (row < ncor) w[(size_t)r * ncor + row] = tot;
+  }
 }
 
 // Frc^s w_s on slot j of subdomain sd (w: coarse vector of one right-hand side).
