@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-extra", action="store_true", help="skip the 3D, full-space and serving rows")
     p.add_argument("--serve-requests", type=int, default=200, help="requests in the serving stream")
+    p.add_argument("--ncu-case", action="store_true",
+                   help="one setup + one solve of the headline workload (beta = 1e-4), for profiler captures")
     return p.parse_args()
 
 
@@ -387,11 +389,27 @@ def serve_stream(args, S, inputs, oracle):
     return out
 
 
+def ncu_case():
+    """One mixed-precision setup + solve of the headline workload: the profiled unit of work."""
+    import torch
+    from paper_1312_5653_gb300 import inputs
+    from paper_1312_5653_gb300 import schur as S
+    yb = torch.from_numpy(inputs.smoothed_noise(2, N_EL, seed=1)).cuda()
+    sol = S.Solver(2, N_EL, 1e-4, nsub=N_SUB, precision=S.SCHUR_MIXED, tol=OUTER_TOL)
+    b = sol.schur_apply_mass(yb)
+    sol.schur_solve(b)
+    torch.cuda.synchronize()
+    print(json.dumps(sol.last_stats))
+    sol.close()
+
+
 def main():
     args = parse()
     rank, local_rank, world = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.ncu_case:
+        return ncu_case()
     import torch
     from paper_1312_5653_gb300 import inputs
     from paper_1312_5653_gb300 import schur as S
