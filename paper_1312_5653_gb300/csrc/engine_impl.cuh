@@ -665,18 +665,15 @@ class Engine : public EngineBase {
     int thr = std::min(512, ((g.nD + 31) / 32) * 32);
     const size_t xcnt = ((size_t)R * g.nD + 1) & ~(size_t)1;
     const size_t opb = (size_t)sym_ld(g.nD) * sizeof(cx<T>);
-    // double-buffered operator and gathered vector per persistent block
-    const int stage = (2 * (xcnt * sizeof(cx<T>) + opb) <= ((size_t)96 << 10)) ? 1 : 0;
-    size_t smem = 2 * xcnt * sizeof(cx<T>) + (stage ? 2 * opb : 0);
-    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(16, ((size_t)200 << 10) / std::max<size_t>(smem, 1)));
-    const int grid = std::max(1, std::min(g.nsd, per_sm * nsm_));
+    const int stage = (xcnt * sizeof(cx<T>) + opb <= ((size_t)96 << 10)) ? 1 : 0;
+    size_t smem = xcnt * sizeof(cx<T>) + (stage ? opb : 0);
     cx<T>* tc = want_tc ? Tc_ : nullptr;
 #define LA_CASE(SC, MR)                                                                                 \
   do {                                                                                                  \
     ENG_CK(smem_attr((const void*)k_local_apply<T, SC, MR>,                                       \
                                 (int)std::max<size_t>(smem, 1)));                                       \
     prof_start(SC ? KC_APPLY_S : KC_APPLY_F, st);                                                      \
-    k_local_apply<T, SC, MR><<<grid, thr, smem, st>>>(g, mv_, Op, Frc_, v, R, active, Y_, tc, stage);         \
+    k_local_apply<T, SC, MR><<<g.nsd, thr, smem, st>>>(g, mv_, Op, Frc_, v, R, active, Y_, tc, stage);         \
     prof_stop(SC ? KC_APPLY_S : KC_APPLY_F, st);                                                       \
   } while (0)
     if (precond) {

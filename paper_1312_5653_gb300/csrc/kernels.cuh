@@ -594,91 +594,78 @@ template <class T, bool SCALE, int MR>
 __global__ void k_local_apply(Geom g, MapsView m, const cx<T>* __restrict__ Op, const cx<T>* __restrict__ Frc,
                               const cx<T>* __restrict__ lam, int R, const int* __restrict__ active, cx<T>* Y,
                               cx<T>* Tc, int stage) {
-  // Persistent blocks walk the subdomains; with stage set, the packed operator of the next
-  // subdomain is copied into the other half of a shared-memory double buffer (cp.async, 16 B)
-  // while the current one is gathered and applied.
   extern __shared__ __align__(16) unsigned char smla[];
-  const int nD = g.nD, tid = threadIdx.x, nthr = blockDim.x, md = g.maxdeg, nsd = g.nsd;
+  cx<T>* x = reinterpret_cast<cx<T>*>(smla);
+  const int sd = blockIdx.x, nD = g.nD, tid = threadIdx.x, nthr = blockDim.x, md = g.maxdeg;
+  const int q = m.sd_cls[sd];
+  // packed upper triangle of Op[cls]; staged in shared memory by asynchronous 16-byte copies that
+  // overlap the gather of x when it fits
   const long long ld = sym_ld(nD);
-  const long long xcnt = ((long long)R * nD + 1) & ~1LL;
-  cx<T>* base = reinterpret_cast<cx<T>*>(smla);
-  cx<T>* xb[2] = {base, base + xcnt};
-  cx<T>* Ab[2] = {base + 2 * xcnt, base + 2 * xcnt + ld};
-  const int n16 = (int)(ld * (long long)sizeof(cx<T>) / 16);
-  auto issue = [&](int sdn, int buf) {
-    const unsigned char* src = reinterpret_cast<const unsigned char*>(Op + (size_t)m.sd_cls[sdn] * ld);
-    unsigned char* dst = reinterpret_cast<unsigned char*>(Ab[buf]);
-    for (int i = tid; i < n16; i += nthr) cp_async16(dst + 16 * (size_t)i, src + 16 * (size_t)i);
-  };
-  if (stage && (int)blockIdx.x < nsd) issue(blockIdx.x, 0);
-  cp_async_commit();
-  __shared__ cx<T> red[32];
-  int it = 0;
-  for (int sd = blockIdx.x; sd < nsd; sd += gridDim.x, ++it) {
-    const int buf = it & 1;
-    const int q = m.sd_cls[sd];
-    if (stage && sd + (int)gridDim.x < nsd) issue(sd + gridDim.x, buf ^ 1);
+  const cx<T>* A = Op + (size_t)q * ld;
+  if (stage) {
+    unsigned char* As = reinterpret_cast<unsigned char*>(x + (((long long)R * nD + 1) & ~1LL));
+    const int n16 = (int)(ld * (long long)sizeof(cx<T>) / 16);
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(A);
+    for (int i = tid; i < n16; i += nthr) cp_async16(As + 16 * (size_t)i, src + 16 * (size_t)i);
     cp_async_commit();
-    cx<T>* x = xb[buf];
-    for (int e = tid; e < R * nD; e += nthr) {
-      int r = e / nD, j = e - r * nD;
-      cx<T> v = czero<T>();
-      if (active[r]) {
-        const int* refs = m.sd_lam + ((size_t)sd * nD + j) * md;
-        for (int k = 0; k < md; ++k) {
-          int ref = refs[k];
-          if (ref > 0) v = cadd(v, lam[(size_t)r * g.nlam + ref - 1]);
-          else if (ref < 0) v = csub(v, lam[(size_t)r * g.nlam - ref - 1]);
-        }
-        if (SCALE) v = cscale(v, (T)m.sd_minv[(size_t)sd * nD + j]);
+    A = reinterpret_cast<const cx<T>*>(As);
+  }
+  for (int e = tid; e < R * nD; e += nthr) {
+    int r = e / nD, j = e - r * nD;
+    cx<T> v = czero<T>();
+    if (active[r]) {
+      const int* refs = m.sd_lam + ((size_t)sd * nD + j) * md;
+      for (int k = 0; k < md; ++k) {
+        int ref = refs[k];
+        if (ref > 0) v = cadd(v, lam[(size_t)r * g.nlam + ref - 1]);
+        else if (ref < 0) v = csub(v, lam[(size_t)r * g.nlam - ref - 1]);
       }
-      x[e] = v;
+      if (SCALE) v = cscale(v, (T)m.sd_minv[(size_t)sd * nD + j]);
     }
-    if (stage) cp_async_wait<1>();  // this subdomain's operator (the newest copy may still run)
-    __syncthreads();
-    const cx<T>* A = stage ? Ab[buf] : Op + (size_t)q * ld;
-    for (int j = tid; j < nD; j += nthr) {
-      cx<T> acc[MR];
-      for (int r = 0; r < MR; ++r) acc[r] = czero<T>();
-      const int offj = sym_off(j, nD);
-      int ok = 0;  // sym_off(k, nD)
+    x[e] = v;
+  }
+  if (stage) cp_async_wait<0>();
+  __syncthreads();
+  for (int j = tid; j < nD; j += nthr) {
+    cx<T> acc[MR];
+    for (int r = 0; r < MR; ++r) acc[r] = czero<T>();
+    const int offj = sym_off(j, nD);
+    int ok = 0;  // sym_off(k, nD)
 #pragma unroll 4
-      for (int k = 0; k < nD; ++k) {
-        const cx<T> a = A[k <= j ? ok + (j - k) : offj + (k - j)];
-        ok += nD - k;
-#pragma unroll
-        for (int r = 0; r < MR; ++r)
-          if (r < R) cfma(acc[r], a, x[r * nD + k]);
-      }
+    for (int k = 0; k < nD; ++k) {
+      const cx<T> a = A[k <= j ? ok + (j - k) : offj + (k - j)];
+      ok += nD - k;
 #pragma unroll
       for (int r = 0; r < MR; ++r)
-        if (r < R) Y[((size_t)sd * R + r) * nD + j] = acc[r];
+        if (r < R) cfma(acc[r], a, x[r * nD + k]);
     }
-    if (Tc) {
-      // Tc[r][c] = sum_j Frc[j][c] x[r][j]: per-thread partials over j, warp shuffles, then warps
-      const int lane = tid & 31, warp = tid >> 5, nw = (nthr + 31) >> 5;
-      const cx<T>* Fr = Frc + (size_t)q * nD * g.nc;
-      for (int rc = 0; rc < R * g.nc; ++rc) {
-        const int r = rc / g.nc, c = rc - r * g.nc;
-        cx<T> p = czero<T>();
-        for (int j = tid; j < nD; j += nthr) cfma(p, Fr[(size_t)j * g.nc + c], x[r * nD + j]);
-        for (int o = 16; o > 0; o >>= 1) {
-          p.re += __shfl_xor_sync(0xffffffffu, p.re, o);
-          p.im += __shfl_xor_sync(0xffffffffu, p.im, o);
-        }
-        __syncthreads();
-        if (lane == 0) red[warp] = p;
-        __syncthreads();
-        if (tid == 0) {
-          cx<T> s = czero<T>();
-          for (int w = 0; w < nw; ++w) s = cadd(s, red[w]);
-          Tc[((size_t)sd * R + r) * g.nc + c] = s;
-        }
+#pragma unroll
+    for (int r = 0; r < MR; ++r)
+      if (r < R) Y[((size_t)sd * R + r) * nD + j] = acc[r];
+  }
+  if (Tc) {
+    // Tc[r][c] = sum_j Frc[j][c] x[r][j]: per-thread partials over j, warp shuffles, then warps
+    __shared__ cx<T> red[32];
+    const int lane = tid & 31, warp = tid >> 5, nw = (nthr + 31) >> 5;
+    const cx<T>* Fr = Frc + (size_t)q * nD * g.nc;
+    for (int rc = 0; rc < R * g.nc; ++rc) {
+      const int r = rc / g.nc, c = rc - r * g.nc;
+      cx<T> p = czero<T>();
+      for (int j = tid; j < nD; j += nthr) cfma(p, Fr[(size_t)j * g.nc + c], x[r * nD + j]);
+      for (int o = 16; o > 0; o >>= 1) {
+        p.re += __shfl_xor_sync(0xffffffffu, p.re, o);
+        p.im += __shfl_xor_sync(0xffffffffu, p.im, o);
+      }
+      __syncthreads();
+      if (lane == 0) red[warp] = p;
+      __syncthreads();
+      if (tid == 0) {
+        cx<T> s = czero<T>();
+        for (int w = 0; w < nw; ++w) s = cadd(s, red[w]);
+        Tc[((size_t)sd * R + r) * g.nc + c] = s;
       }
     }
-    __syncthreads();  // buffers of this subdomain are refilled two iterations later
   }
-  cp_async_wait<0>();
 }
 
 // out_lambda = sum over sides sigma * scale * (Y + Frc wc):  B (Y + Frc wc) for the dual operator,
