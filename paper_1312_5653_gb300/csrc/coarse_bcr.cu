@@ -471,7 +471,7 @@ static cudaError_t launch_gj_batch(const cx<S>* Din, cx<S>* Dout, const int* dli
                                    cudaStream_t st) {
   cudaError_t last = cudaErrorInvalidConfiguration;
   if (b >= 16) {
-    static const int bsizes[] = {8, 16, 4};
+    static const int bsizes[] = {16, 8, 4};
     for (int CL : bsizes) {
       if ((b + CL - 1) / CL > 32) continue;  // the pivot block is inverted by one warp
       const size_t smem = gj_blocked_smem<S>(b, CL);
