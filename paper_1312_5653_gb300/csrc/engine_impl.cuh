@@ -651,7 +651,7 @@ class Engine : public EngineBase {
     const long long ntile = ctile_count(nct_);
     prof_start(KC_COARSE_APPLY, st);
     k_coarse_tiles<T><<<(int)((ntile + 3) / 4), 128, 0, st>>>(Kt_, nct_, g_.ncor, gv, R, active, cpu_, cpv_);
-    k_coarse_reduce<T><<<nct_ * R, 128, 0, st>>>(cpu_, cpv_, nct_, g_.ncor, R, active, w);
+    k_coarse_reduce<T><<<nct_ * R, 512, 0, st>>>(cpu_, cpv_, nct_, g_.ncor, R, active, w);
     prof_stop(KC_COARSE_APPLY, st);
     ENG_LAUNCH();
     ENG_LAUNCH();

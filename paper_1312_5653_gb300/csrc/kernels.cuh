@@ -50,6 +50,10 @@ template <class T>
 __device__ __forceinline__ cx<T> shfl_cx(cx<T> v, int src) {
   return mkc<T>(__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src));
 }
+template <class T>
+__device__ __forceinline__ cx<T> shfl_xor_cx(cx<T> v, int m) {
+  return mkc<T>(__shfl_xor_sync(0xffffffffu, v.re, m), __shfl_xor_sync(0xffffffffu, v.im, m));
+}
 
 // Asynchronous global -> shared copies (cp.async, L1-allocating), one complex entry per lane.
 template <class T>
@@ -476,12 +480,14 @@ __global__ void k_pack_ctiles(const cx<T>* __restrict__ K, int n, int ld, int nt
   }
 }
 
-// phase 1: one warp per tile (4 per block), the tile staged in shared memory (row stride 33)
+// phase 1: one warp per tile (4 per block).  FP32: the tile stays in registers, lane l holding
+// rows 2i + h (h = l / 16, i = 0..15) of columns 2(l % 16) and 2(l % 16) + 1 after sixteen
+// coalesced 16-byte loads; the transposed product T^T g_I is accumulated per lane and folded
+// across the two row halves, the row product T g_J is reduce-scattered over the 16 lanes of a half.
 template <class T>
 __global__ void __launch_bounds__(128) k_coarse_tiles(const cx<T>* __restrict__ tiles, int nt, int ncor,
                                                       const cx<T>* __restrict__ gv, int R, const int* __restrict__ active,
                                                       cx<T>* part_u, cx<T>* part_v) {
-  __shared__ cx<T> Ts[4][kCT][kCT + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long t = (long long)blockIdx.x * 4 + warp;
   const long long ntile = ctile_count(nt);
@@ -494,46 +500,77 @@ __global__ void __launch_bounds__(128) k_coarse_tiles(const cx<T>* __restrict__ 
   }
   const int J = I + (int)rem;
   const cx<T>* src = tiles + t * kCT * kCT;
+  const int h = lane >> 4, c0 = 2 * (lane & 15);
+  cx<T> a0[16], a1[16];  // rows 2i + h, columns c0 and c0 + 1
   if constexpr (sizeof(T) == 4) {
-    // the whole 8 KB tile in flight at once: 16 x 16-byte loads per lane, then to shared memory
     const float4* s4 = reinterpret_cast<const float4*>(src);
-    float4 v[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = s4[i * 32 + lane];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-      const int e = 2 * (i * 32 + lane), r = e / kCT, c = e % kCT;
-      Ts[warp][r][c] = mkc<T>(v[i].x, v[i].y);
-      Ts[warp][r][c + 1] = mkc<T>(v[i].z, v[i].w);
+      const float4 v = s4[i * 32 + lane];
+      a0[i] = mkc<T>(v.x, v.y);
+      a1[i] = mkc<T>(v.z, v.w);
     }
   } else {
-#pragma unroll 8
-    for (int r = 0; r < kCT; ++r) Ts[warp][r][lane] = src[r * kCT + lane];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      a0[i] = src[(2 * i + h) * kCT + c0];
+      a1[i] = src[(2 * i + h) * kCT + c0 + 1];
+    }
   }
-  __syncwarp();
   for (int r = 0; r < R; ++r) {
     if (active && !active[r]) continue;  // active == null: every right-hand side
     const cx<T>* g = gv + (size_t)r * ncor;
-    const int gi = I * kCT + lane, gj = J * kCT + lane;
-    const cx<T> gJ = gj < ncor ? g[gj] : czero<T>();
-    const cx<T> gI = gi < ncor ? g[gi] : czero<T>();
-    cx<T> u = czero<T>(), v = czero<T>();
-#pragma unroll 8
-    for (int k = 0; k < kCT; ++k) {
-      cfma(u, Ts[warp][lane][k], shfl_cx(gJ, k));  // row lane of T times g_J
-      cfma(v, Ts[warp][k][lane], shfl_cx(gI, k));  // column lane of T times g_I
+    // g_J at columns c0, c0 + 1; g_I at rows 2i + h (from the lane holding index 2i + h)
+    const int gj0 = J * kCT + c0;
+    const cx<T> gJ0 = gj0 < ncor ? g[gj0] : czero<T>();
+    const cx<T> gJ1 = gj0 + 1 < ncor ? g[gj0 + 1] : czero<T>();
+    const int gi = I * kCT + lane;
+    const cx<T> gIl = gi < ncor ? g[gi] : czero<T>();
+    // transposed product: v[c] = sum_rows T[row][c] g_I[row]
+    cx<T> v0 = czero<T>(), v1 = czero<T>();
+    cx<T> p[16];  // row partials of T g_J for rows 2i + h
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const cx<T> gI = shfl_cx(gIl, 2 * i + h);
+      cfma(v0, a0[i], gI);
+      cfma(v1, a1[i], gI);
+      p[i] = cmul(a0[i], gJ0);
+      cfma(p[i], a1[i], gJ1);
     }
+    v0 = cadd(v0, shfl_xor_cx(v0, 16));  // add the other row half
+    v1 = cadd(v1, shfl_xor_cx(v1, 16));
+    // reduce-scatter of p over the 16 lanes of this half: after the four steps lane with
+    // bit pattern b (lane & 15) holds the full sum for row index i = bitreverse-free order below
+#pragma unroll
+    for (int st = 3; st >= 0; --st) {
+      const int half = 1 << st;  // keep p[0..half) or p[half..2 half) of the current window
+      const bool up = (lane >> st) & 1;
+#pragma unroll
+      for (int i = 0; i < half; ++i) {
+        const cx<T> send = up ? p[i] : p[i + half];
+        const cx<T> keep = up ? p[i + half] : p[i];
+        p[i] = cadd(keep, shfl_xor_cx(send, half));
+      }
+    }
+    // lane (h, b = lane & 15) now holds row 2 * b + h; rows 0..31 are lanes 2b + h -> reorder
+    const cx<T> u = shfl_cx(p[0], ((lane & 1) << 4) | (lane >> 1));
     part_u[((size_t)r * ntile + t) * kCT + lane] = u;
-    if (I != J) part_v[((size_t)r * ntile + t) * kCT + lane] = v;
+    if (I != J) {
+      // lane holds v for columns c0, c0 + 1 (duplicated in both halves): lane l writes column l
+      const int srcl = (lane >> 1) & 15;
+      const cx<T> va = shfl_cx(v0, srcl), vb = shfl_cx(v1, srcl);
+      part_v[((size_t)r * ntile + t) * kCT + lane] = (lane & 1) ? vb : va;
+    }
   }
 }
 
-// phase 2: w_I = sum_{J >= I} part_u(I, J) + sum_{J < I} part_v(J, I); one block of 4 warps per
-// (I, rhs), warp q adding a contiguous quarter of the J range, the quarters combined in order
+// phase 2: w_I = sum_{J >= I} part_u(I, J) + sum_{J < I} part_v(J, I); one block of 16 warps per
+// (I, rhs), warp q adding a contiguous sixteenth of the J range, the sixteen partials combined in
+// order
 template <class T>
-__global__ void __launch_bounds__(128) k_coarse_reduce(const cx<T>* __restrict__ part_u, const cx<T>* __restrict__ part_v,
+__global__ void __launch_bounds__(512) k_coarse_reduce(const cx<T>* __restrict__ part_u, const cx<T>* __restrict__ part_v,
                                                        int nt, int ncor, int R, const int* __restrict__ active, cx<T>* w) {
-  __shared__ cx<T> red[4][kCT];
+  __shared__ cx<T> red[16][kCT];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int I = blockIdx.x % nt, r = blockIdx.x / nt;
   if (r >= R || (active && !active[r])) return;
@@ -541,15 +578,15 @@ __global__ void __launch_bounds__(128) k_coarse_reduce(const cx<T>* __restrict__
   const cx<T>* pu = part_u + (size_t)r * ntile * kCT;
   const cx<T>* pv = part_v + (size_t)r * ntile * kCT;
   const long long t0 = ctile_idx(I, I, nt);
-  const int q0 = (nt * warp) / 4, q1 = (nt * (warp + 1)) / 4;
+  const int q0 = (nt * warp) / 16, q1 = (nt * (warp + 1)) / 16;
   cx<T> acc = czero<T>();
-#pragma unroll 4
   for (int J = q0; J < q1; ++J)
     acc = cadd(acc, J < I ? pv[ctile_idx(J, I, nt) * kCT + lane] : pu[(t0 + (J - I)) * kCT + lane]);
   red[warp][lane] = acc;
   __syncthreads();
   if (warp == 0) {
-    const cx<T> tot = cadd(cadd(red[0][lane], red[1][lane]), cadd(red[2][lane], red[3][lane]));
+    cx<T> tot = red[0][lane];
+    for (int q = 1; q < 16; ++q) tot = cadd(tot, red[q][lane]);
     const int row = I * kCT + lane;
     if (row < ncor) w[(size_t)r * ncor + row] = tot;
   }
