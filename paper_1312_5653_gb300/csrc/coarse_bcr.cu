@@ -1,12 +1,15 @@
 // Block cyclic reduction (odd-even reduction over layers) of the coarse corner matrix.
 //
 // The coarse matrix of Sec. 5 is block tridiagonal over the layers of the corner grid.  Instead of
-// the sequential layer recursion, every level eliminates every other remaining layer j at once:
-//   Dinv_j = D_j^{-1},  Lp = A_pj Dinv_j,  Lq = A_qj Dinv_j,
-//   D_p -= Lp A_jp,  D_q -= Lq A_jq,  A_pq = -Lp A_jq          (p, q: remaining neighbours of j)
+// the sequential layer recursion, every level eliminates every other remaining layer j at once
+// (p, q: its remaining neighbours; A_pj = U_p, A_jq = U_j, symmetric blocks):
+//   Dinv_j = D_j^{-1},  Lp_j = A_pj Dinv_j,  Lq_j = Dinv_j A_jq,
+//   D_p -= Lp_j A_pj^T,  D_q -= A_jq^T Lq_j,  A_pq = -Lp_j A_jq
 // so the critical path is log2(L) levels of batched dense work.  The factor is always computed in
-// FP64; the explicit inverse (a cyclic-reduction solve with the identity as right-hand side) in
-// the working precision of the solver, from FP32 copies of the factor in the mixed form.
+// FP64.  The explicit inverse is a cyclic-reduction solve with the identity as right-hand side in
+// the working precision (FP32 copies of Dinv, Lp, Lq in the mixed form):
+//   forward  X_p -= Lp_j X_j,  X_q -= Lq_j^T X_j
+//   backward X_j  = Dinv_j X_j - Lp_j^T X_p - Lq_j X_q
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -228,16 +231,25 @@ __global__ void __launch_bounds__(256) k_gj_blocked(const cx<S>* __restrict__ Di
   cluster.sync();  // keep this CTA's shared memory alive until every remote read is done
 }
 
-// One batched complex GEMM task: C (+)= alpha * A * op(B), A b x b, B and C b x N (N per task),
-// row-major with leading dimensions; transB: use B^T.
+// One batched complex GEMM task: C (+)= sum_s alpha_s op(A_s) op(B_s) over up to three operand
+// pairs (A_s b x b, B_s b x N, N per task), row-major with leading dimensions.  band (level 0 of
+// the reduction, where the blocks still have the stencil's band): 1 = op(A_s) banded, 2 = op(B_s)
+// banded, half-width w of the launch.
 template <class S>
-struct GemmTask {
+struct GemmPair {
   const cx<S>* A;
   const cx<S>* B;
-  cx<S>* C;
-  int lda, ldb, ldc;
-  int transB;
+  int lda, ldb;
+  int transA, transB;
   S alpha;  // real scale (+1 / -1)
+  int band;
+};
+template <class S>
+struct GemmTask {
+  GemmPair<S> p[3];
+  int np;
+  cx<S>* C;
+  int ldc;
   int accumulate;
   int N;
 };
@@ -252,10 +264,9 @@ struct CopyTask {
   int transpose;
 };
 
-// C[M x N] (+)= alpha * A[M x Kd] * B[Kd x N]  (B^T when transB), TM x TM output tiles per CTA,
-// 16 x 16 threads with (TM/16)^2 outputs each, K in steps of 16 staged in shared memory.  FP64 uses
-// 16 x 16 tiles: its per-SM rate is low (about 2 FMA per clock), so many CTAs per b x b task keep
-// all SMs busy.
+// Dense tasks: TM x TM output tiles per CTA, 16 x 16 threads with (TM/16)^2 outputs each, K in
+// steps of 16 staged in shared memory with alpha folded into the A tile.  FP64 uses 16 x 16 tiles:
+// its per-SM rate is low (about 2 FMA per clock), so many CTAs per b x b task keep all SMs busy.
 template <class S>
 struct GemmTile {
   static constexpr int TM = sizeof(S) == 8 ? 16 : 64;
@@ -264,8 +275,8 @@ struct GemmTile {
 template <class S, int TM>
 __global__ void __launch_bounds__(256) k_gemm_batch(const GemmTask<S>* __restrict__ tasks, int M, int Kd) {
   constexpr int Q = TM / 16;
-  const GemmTask<S> t = tasks[blockIdx.z];
-  const int N = t.N;
+  const GemmTask<S>& tk = tasks[blockIdx.z];
+  const int N = tk.N;
   const int row0 = blockIdx.y * TM, col0 = blockIdx.x * TM;
   if (col0 >= N) return;  // tasks narrower than the grid
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -276,40 +287,50 @@ __global__ void __launch_bounds__(256) k_gemm_batch(const GemmTask<S>* __restric
   for (int a = 0; a < Q; ++a)
 #pragma unroll
     for (int c = 0; c < Q; ++c) acc[a][c] = mkc<S>(0, 0);
-  for (int k0 = 0; k0 < Kd; k0 += 16) {
-    // row-major operands read along their rows (k fastest) so consecutive threads touch
-    // consecutive addresses; non-transposed B along its rows too (columns fastest)
-    for (int e = threadIdx.x; e < 16 * TM; e += 256) {
-      const int r = e >> 4, kk = e & 15;
-      const int gr = row0 + r, gk = k0 + kk;
-      As[kk][r] = (gr < M && gk < Kd) ? t.A[(size_t)gr * t.lda + gk] : mkc<S>(0, 0);
+  const int np = tk.np;
+  for (int s = 0; s < np; ++s) {
+    const GemmPair<S> t = tk.p[s];
+    for (int k0 = 0; k0 < Kd; k0 += 16) {
+      // operands read along their contiguous dimension so consecutive threads touch consecutive
+      // addresses
+      if (!t.transA) {
+        for (int e = threadIdx.x; e < 16 * TM; e += 256) {
+          const int r = e >> 4, kk = e & 15, gr = row0 + r, gk = k0 + kk;
+          As[kk][r] = (gr < M && gk < Kd) ? cscale(t.A[(size_t)gr * t.lda + gk], t.alpha) : mkc<S>(0, 0);
+        }
+      } else {
+        for (int e = threadIdx.x; e < 16 * TM; e += 256) {
+          const int kk = e / TM, r = e % TM, gr = row0 + r, gk = k0 + kk;
+          As[kk][r] = (gr < M && gk < Kd) ? cscale(t.A[(size_t)gk * t.lda + gr], t.alpha) : mkc<S>(0, 0);
+        }
+      }
       if (t.transB) {
-        const int gc = col0 + r;
-        Bs[kk][r] = (gc < N && gk < Kd) ? t.B[(size_t)gc * t.ldb + gk] : mkc<S>(0, 0);
+        for (int e = threadIdx.x; e < 16 * TM; e += 256) {
+          const int c = e >> 4, kk = e & 15, gc = col0 + c, gk = k0 + kk;
+          Bs[kk][c] = (gc < N && gk < Kd) ? t.B[(size_t)gc * t.ldb + gk] : mkc<S>(0, 0);
+        }
+      } else {
+        for (int e = threadIdx.x; e < 16 * TM; e += 256) {
+          const int kk = e / TM, c = e % TM, gk = k0 + kk, gc = col0 + c;
+          Bs[kk][c] = (gc < N && gk < Kd) ? t.B[(size_t)gk * t.ldb + gc] : mkc<S>(0, 0);
+        }
       }
-    }
-    if (!t.transB) {
-      for (int e = threadIdx.x; e < 16 * TM; e += 256) {
-        const int kk = e / TM, c = e % TM;
-        const int gk = k0 + kk, gc = col0 + c;
-        Bs[kk][c] = (gc < N && gk < Kd) ? t.B[(size_t)gk * t.ldb + gc] : mkc<S>(0, 0);
-      }
-    }
-    __syncthreads();
+      __syncthreads();
 #pragma unroll 4
-    for (int kk = 0; kk < 16; ++kk) {
-      cx<S> a[Q], bq[Q];
+      for (int kk = 0; kk < 16; ++kk) {
+        cx<S> a[Q], bq[Q];
 #pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        a[q] = As[kk][ty + 16 * q];
-        bq[q] = Bs[kk][tx + 16 * q];
+        for (int q = 0; q < Q; ++q) {
+          a[q] = As[kk][ty + 16 * q];
+          bq[q] = Bs[kk][tx + 16 * q];
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+          for (int c = 0; c < Q; ++c) cfma(acc[q][c], a[q], bq[c]);
       }
-#pragma unroll
-      for (int q = 0; q < Q; ++q)
-#pragma unroll
-        for (int c = 0; c < Q; ++c) cfma(acc[q][c], a[q], bq[c]);
+      __syncthreads();
     }
-    __syncthreads();
   }
 #pragma unroll
   for (int q = 0; q < Q; ++q)
@@ -317,30 +338,41 @@ __global__ void __launch_bounds__(256) k_gemm_batch(const GemmTask<S>* __restric
     for (int c = 0; c < Q; ++c) {
       int gr = row0 + ty + 16 * q, gc = col0 + tx + 16 * c;
       if (gr < M && gc < N) {
-        cx<S>& o = t.C[(size_t)gr * t.ldc + gc];
-        cx<S> v = cscale(acc[q][c], t.alpha);
-        o = t.accumulate ? cadd(o, v) : v;
+        cx<S>& o = tk.C[(size_t)gr * tk.ldc + gc];
+        o = tk.accumulate ? cadd(o, acc[q][c]) : acc[q][c];
       }
     }
 }
 
-// C (+)= alpha * A * op(B) for a banded operand (level 0 of the reduction, where the blocks still
-// have the stencil's band): A banded (|i - k| <= w) when bandA, else op(B) banded (|k - j| <= w).
-// One thread per output entry, grid (chunks, tasks).
+// Tasks with banded operands: one thread per output entry, the K range of each pair restricted
+// to its band; grid (chunks, tasks).
 template <class S>
-__global__ void k_gemm_band(const GemmTask<S>* __restrict__ tasks, int M, int Kd, int w, int bandA) {
-  const GemmTask<S> t = tasks[blockIdx.y];
-  const int N = t.N;
+__global__ void k_gemm_band(const GemmTask<S>* __restrict__ tasks, int M, int Kd, int w) {
+  const GemmTask<S>& tk = tasks[blockIdx.y];
+  const int N = tk.N;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M * N; e += gridDim.x * blockDim.x) {
     const int i = e / N, j = e - i * N;
-    const int c = bandA ? i : j;
-    const int k0 = max(0, c - w), k1 = min(Kd - 1, c + w);
     cx<S> acc = mkc<S>(0, 0);
-    for (int k = k0; k <= k1; ++k)
-      cfma(acc, t.A[(size_t)i * t.lda + k], t.transB ? t.B[(size_t)j * t.ldb + k] : t.B[(size_t)k * t.ldb + j]);
-    cx<S>& o = t.C[(size_t)i * t.ldc + j];
-    const cx<S> v = cscale(acc, t.alpha);
-    o = t.accumulate ? cadd(o, v) : v;
+    for (int s = 0; s < tk.np; ++s) {
+      const GemmPair<S> t = tk.p[s];
+      int k0 = 0, k1 = Kd - 1;
+      if (t.band == 1) {
+        k0 = max(0, i - w);
+        k1 = min(Kd - 1, i + w);
+      } else if (t.band == 2) {
+        k0 = max(0, j - w);
+        k1 = min(Kd - 1, j + w);
+      }
+      cx<S> part = mkc<S>(0, 0);
+      for (int k = k0; k <= k1; ++k) {
+        const cx<S> a = t.transA ? t.A[(size_t)k * t.lda + i] : t.A[(size_t)i * t.lda + k];
+        const cx<S> bv = t.transB ? t.B[(size_t)j * t.ldb + k] : t.B[(size_t)k * t.ldb + j];
+        cfma(part, a, bv);
+      }
+      acc = cadd(acc, cscale(part, t.alpha));
+    }
+    cx<S>& o = tk.C[(size_t)i * tk.ldc + j];
+    o = tk.accumulate ? cadd(o, acc) : acc;
   }
 }
 
@@ -595,12 +627,12 @@ static void bcr_schedule(int L, std::vector<std::vector<int>>* lev_j, std::vecto
 
 // The whole reduction as a list of launches over task arrays that are built on the host and
 // uploaded once.
-enum BcrOpKind { OP_GJ, OP_GEMM, OP_COPY, OP_TRI, OP_BAND_A, OP_BAND_B };
+enum BcrOpKind { OP_GJ, OP_TRI, OP_GEMM, OP_BAND, OP_COPY };
 struct BcrOp {
   BcrOpKind kind;
-  size_t off;  // first task (GEMM, COPY) or list entry (GJ)
+  size_t off;  // first task (GEMM, BAND, COPY) or list entry (GJ, TRI)
   int count;
-  int maxN;  // GEMM: widest task; COPY: longest copy
+  int maxN;  // GEMM/BAND: widest task; COPY: longest copy
 };
 
 template <class T>
@@ -609,11 +641,11 @@ struct BcrPlan {
   std::vector<CopyTask<T>> copy;
   std::vector<int> list;
   std::vector<BcrOp> ops;
-  void add_gemm(std::vector<GemmTask<T>>& ts) {
+  void add_gemm(std::vector<GemmTask<T>>& ts, bool band) {
     if (ts.empty()) return;
     int mx = 0;
     for (auto& t : ts) mx = std::max(mx, t.N);
-    ops.push_back({OP_GEMM, gemm.size(), (int)ts.size(), mx});
+    ops.push_back({band ? OP_BAND : OP_GEMM, gemm.size(), (int)ts.size(), mx});
     gemm.insert(gemm.end(), ts.begin(), ts.end());
     ts.clear();
   }
@@ -625,22 +657,40 @@ struct BcrPlan {
     copy.insert(copy.end(), ts.begin(), ts.end());
     ts.clear();
   }
-  void add_gj(const std::vector<int>& J, BcrOpKind kind = OP_GJ) {
+  void add_inv(const std::vector<int>& J, BcrOpKind kind) {
     ops.push_back({kind, list.size(), (int)J.size(), 0});
     list.insert(list.end(), J.begin(), J.end());
   }
-  void add_band(std::vector<GemmTask<T>>& ts, bool bandA) {
-    if (ts.empty()) return;
-    int mx = 0;
-    for (auto& t : ts) mx = std::max(mx, t.N);
-    ops.push_back({bandA ? OP_BAND_A : OP_BAND_B, gemm.size(), (int)ts.size(), mx});
-    gemm.insert(gemm.end(), ts.begin(), ts.end());
-    ts.clear();
-  }
 };
 
-// Uploads the task arrays of a plan and launches its operations in order (GJ operations invert
-// blocks of Dsrc into Ddst).
+template <class S>
+static GemmPair<S> pair(const cx<S>* A, int lda, int transA, const cx<S>* B, int ldb, int transB, S alpha, int band) {
+  GemmPair<S> q;
+  q.A = A;
+  q.B = B;
+  q.lda = lda;
+  q.ldb = ldb;
+  q.transA = transA;
+  q.transB = transB;
+  q.alpha = alpha;
+  q.band = band;
+  return q;
+}
+
+template <class S>
+static GemmTask<S> task(cx<S>* C, int ldc, int accumulate, int N, std::initializer_list<GemmPair<S>> ps) {
+  GemmTask<S> t = {};
+  t.np = 0;
+  for (const GemmPair<S>& q : ps) t.p[t.np++] = q;
+  t.C = C;
+  t.ldc = ldc;
+  t.accumulate = accumulate;
+  t.N = N;
+  return t;
+}
+
+// Uploads the task arrays of a plan and launches its operations in order (inversions turn blocks
+// of Dsrc into Ddst).
 template <class S>
 static cudaError_t run_plan(const BcrPlan<S>& plan, GemmTask<S>* dG, CopyTask<S>* dC, int* dL, const cx<S>* Dsrc,
                             cx<S>* Ddst, int b, int w, int* err, cudaStream_t st, long long* launches) {
@@ -664,9 +714,9 @@ static cudaError_t run_plan(const BcrPlan<S>& plan, GemmTask<S>* dG, CopyTask<S>
     } else if (op.kind == OP_TRI) {
       k_tri_inverse<S><<<op.count, 64, 2 * b * sizeof(cx<S>), st>>>(Dsrc, Ddst, dL + op.off, b, err);
       e = cudaGetLastError();
-    } else if (op.kind == OP_BAND_A || op.kind == OP_BAND_B) {
+    } else if (op.kind == OP_BAND) {
       const int chunks = std::max(1, std::min((b * op.maxN + 255) / 256, 64));
-      k_gemm_band<S><<<dim3(chunks, op.count), 256, 0, st>>>(dG + op.off, b, b, w, op.kind == OP_BAND_A ? 1 : 0);
+      k_gemm_band<S><<<dim3(chunks, op.count), 256, 0, st>>>(dG + op.off, b, b, w);
       e = cudaGetLastError();
     } else if (op.kind == OP_GEMM) {
       dim3 grid((op.maxN + TM - 1) / TM, (b + TM - 1) / TM, (unsigned)op.count);
@@ -713,148 +763,149 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int ldk, int* err, cuda
     }
   } guard{&mem, st};
   using D64 = cx<double>;
-  D64 *D = nullptr, *Ucur = nullptr, *Dinv = nullptr, *UP = nullptr, *UQ = nullptr, *Lp = nullptr, *Lq = nullptr,
-      *Unew = nullptr;
+  D64 *D = nullptr, *Ucur = nullptr, *Dinv = nullptr, *Lp = nullptr, *Lq = nullptr, *Unew = nullptr;
   BCR_CK(mal(&D, L * bb * sizeof(D64)), "alloc");
   BCR_CK(mal(&Ucur, L * bb * sizeof(D64)), "alloc");
   BCR_CK(mal(&Dinv, L * bb * sizeof(D64)), "alloc");
-  BCR_CK(mal(&UP, 2 * L * bb * sizeof(D64)), "alloc");  // UP_j = A_pj, then the transposes
-  BCR_CK(mal(&UQ, 2 * L * bb * sizeof(D64)), "alloc");  // UQ_j = A_jq, then the transposes
   BCR_CK(mal(&Lp, L * bb * sizeof(D64)), "alloc");
   BCR_CK(mal(&Lq, L * bb * sizeof(D64)), "alloc");
   BCR_CK(mal(&Unew, L * bb * sizeof(D64)), "alloc");
-  D64* UPT = UP + (size_t)L * bb;
-  D64* UQT = UQ + (size_t)L * bb;
 
-  // ---- plan: FP64 factorisation
+  // ---- plan: FP64 factorisation.  Level 0 still sees the stencil's band (the layer blocks couple
+  // in-layer neighbours only): half-width 1 in 2D, a layer row + 1 in 3D, and in 2D the pivot
+  // blocks are tridiagonal and are inverted by the Thomas recurrence.
+  const int wband = P.ly.dim == 2 ? 1 : P.ly.ext[0] + 1;
+  const bool tri0 = P.ly.dim == 2;
   BcrPlan<double> fp;
   std::vector<GemmTask<double>> ts;
   std::vector<CopyTask<double>> cs;
   const long long lbb = (long long)bb;
-  // Level 0 still sees the stencil's band: the layer blocks couple in-layer neighbours only, so
-  // every product there has a banded operand (half-width 1 in 2D, a layer row + 1 in 3D), and in
-  // 2D the pivot blocks are tridiagonal and are inverted by the Thomas recurrence.
-  const int wband = P.ly.dim == 2 ? 1 : P.ly.ext[0] + 1;
-  const bool tri0 = P.ly.dim == 2;
+  auto blk = [&](D64* base, int K) { return base + (size_t)K * bb; };
   for (size_t lv = 0; lv < lj.size(); ++lv) {
     const std::vector<int>& J = lj[lv];
     const bool band = lv == 0;
-    fp.add_gj(J, band && tri0 ? OP_TRI : OP_GJ);  // Dinv_j = D_j^{-1}
+    const int bA = band ? 1 : 0, bB = band ? 2 : 0;
+    fp.add_inv(J, band && tri0 ? OP_TRI : OP_GJ);  // Dinv_j = D_j^{-1}
+    // Lp_j = U_p Dinv_j ; Lq_j = Dinv_j U_j
     for (size_t k = 0; k < J.size(); ++k) {
       const int j = J[k], p = lp[lv][k], q = lq[lv][k];
-      if (p >= 0) cs.push_back({Ucur + p * bb, UP + j * bb, lbb, 0});  // UP_j = A_pj
-      if (q >= 0) cs.push_back({Ucur + j * bb, UQ + j * bb, lbb, 0});  // UQ_j = A_jq
-      if (q >= 0) cs.push_back({Ucur + j * bb, UQT + j * bb, lbb, 1});  // UQ_j^T
+      if (p >= 0) ts.push_back(task<double>(blk(Lp, j), b, 0, b, {pair<double>(blk(Ucur, p), b, 0, blk(Dinv, j), b, 0, 1.0, bA)}));
+      if (q >= 0) ts.push_back(task<double>(blk(Lq, j), b, 0, b, {pair<double>(blk(Dinv, j), b, 0, blk(Ucur, j), b, 0, 1.0, bB)}));
     }
-    fp.add_copy(cs);
-    // Lp_j = A_pj Dinv_j ; Lq_j = Dinv_j A_jq (= (A_qj Dinv_j)^T, Dinv_j symmetric)
-    std::vector<GemmTask<double>> tq;
+    fp.add_gemm(ts, band);
+    // remaining block t: D_t -= Lp_j U_t^T (t = p of j) and U_j'^T Lq_j' (t = q of j'), one task
+    // per t; new coupling A_pq = -Lp_j U_j
+    std::vector<int> left_of(L, -1), right_of(L, -1);  // eliminated neighbour j of t on each side
+    for (size_t k = 0; k < J.size(); ++k) {
+      if (lp[lv][k] >= 0) right_of[lp[lv][k]] = J[k];  // t = p: j is its right neighbour
+      if (lq[lv][k] >= 0) left_of[lq[lv][k]] = J[k];   // t = q: j is its left neighbour
+    }
+    for (int t = 0; t < L; ++t) {
+      const int jr = right_of[t], jl = left_of[t];
+      if (jr < 0 && jl < 0) continue;
+      if (jr >= 0 && jl >= 0)
+        ts.push_back(task<double>(blk(D, t), b, 1, b,
+                                  {pair<double>(blk(Lp, jr), b, 0, blk(Ucur, t), b, 1, -1.0, bB),
+                                   pair<double>(blk(Ucur, jl), b, 1, blk(Lq, jl), b, 0, -1.0, bA)}));
+      else if (jr >= 0)
+        ts.push_back(task<double>(blk(D, t), b, 1, b, {pair<double>(blk(Lp, jr), b, 0, blk(Ucur, t), b, 1, -1.0, bB)}));
+      else
+        ts.push_back(task<double>(blk(D, t), b, 1, b, {pair<double>(blk(Ucur, jl), b, 1, blk(Lq, jl), b, 0, -1.0, bA)}));
+    }
     for (size_t k = 0; k < J.size(); ++k) {
       const int j = J[k], p = lp[lv][k], q = lq[lv][k];
-      if (p >= 0) ts.push_back({Ucur + p * bb, Dinv + j * bb, Lp + j * bb, b, b, b, 0, 1.0, 0, b});
-      if (q >= 0) tq.push_back({Dinv + j * bb, Ucur + j * bb, Lq + j * bb, b, b, b, 0, 1.0, 0, b});
+      if (p >= 0 && q >= 0)
+        ts.push_back(task<double>(blk(Unew, p), b, 0, b, {pair<double>(blk(Lp, j), b, 0, blk(Ucur, j), b, 0, -1.0, bB)}));
     }
-    if (band) {
-      fp.add_band(ts, true);
-      fp.add_band(tq, false);
-    } else {
-      ts.insert(ts.end(), tq.begin(), tq.end());
-      fp.add_gemm(ts);
-    }
-    // D_p -= Lp_j A_jp = Lp_j UP_j^T ; A_pq (new coupling of p) = -Lp_j UQ_j.  A separate launch
-    // for D_q -= A_qj Dinv_j A_jq = UQ_j^T Lq_j: no two tasks of one launch write the same block.
-    for (size_t k = 0; k < J.size(); ++k) {
-      const int j = J[k], p = lp[lv][k], q = lq[lv][k];
-      if (p >= 0) {
-        ts.push_back({Lp + j * bb, UP + j * bb, D + p * bb, b, b, b, 1, -1.0, 1, b});
-        if (q >= 0) ts.push_back({Lp + j * bb, UQ + j * bb, Unew + p * bb, b, b, b, 0, -1.0, 0, b});
-      }
-    }
-    if (band) fp.add_band(ts, false);
-    else fp.add_gemm(ts);
-    for (size_t k = 0; k < J.size(); ++k) {
-      const int j = J[k], q = lq[lv][k];
-      if (q >= 0) ts.push_back({UQT + j * bb, Lq + j * bb, D + q * bb, b, b, b, 0, -1.0, 1, b});
-    }
-    if (band) fp.add_band(ts, true);
-    else fp.add_gemm(ts);
-    // a remaining p whose right neighbour j was eliminated now couples to q (or to nothing)
+    fp.add_gemm(ts, band);
+    // the remaining p whose right neighbour j was eliminated now couples to q (or to nothing)
     for (size_t k = 0; k < J.size(); ++k) {
       const int p = lp[lv][k], q = lq[lv][k];
-      if (p >= 0) cs.push_back({q >= 0 ? Unew + p * bb : nullptr, Ucur + p * bb, lbb, 0});
+      if (p >= 0) cs.push_back({q >= 0 ? blk(Unew, p) : nullptr, blk(Ucur, p), lbb, 0});
     }
     fp.add_copy(cs);
   }
-  // transposes of UP for the back substitution
-  for (size_t lv = 0; lv < lj.size(); ++lv)
-    for (size_t k = 0; k < lj[lv].size(); ++k)
-      if (lp[lv][k] >= 0) cs.push_back({UP + lj[lv][k] * bb, UPT + lj[lv][k] * bb, lbb, 1});
-  fp.add_copy(cs);
 
   // ---- factor operands of the solve in precision T
-  cx<T>*DinvT = nullptr, *UPt = nullptr, *UQt = nullptr, *Tmp = nullptr;
+  cx<T>*DinvT = nullptr, *LpT = nullptr, *LqT = nullptr, *Tmp = nullptr;
   if (sizeof(T) == sizeof(double)) {
     DinvT = reinterpret_cast<cx<T>*>(Dinv);
-    UPt = reinterpret_cast<cx<T>*>(UP);
-    UQt = reinterpret_cast<cx<T>*>(UQ);
+    LpT = reinterpret_cast<cx<T>*>(Lp);
+    LqT = reinterpret_cast<cx<T>*>(Lq);
   } else {
     BCR_CK(mal(&DinvT, L * bb * sizeof(cx<T>)), "alloc");
-    BCR_CK(mal(&UPt, 2 * L * bb * sizeof(cx<T>)), "alloc");
-    BCR_CK(mal(&UQt, 2 * L * bb * sizeof(cx<T>)), "alloc");
+    BCR_CK(mal(&LpT, L * bb * sizeof(cx<T>)), "alloc");
+    BCR_CK(mal(&LqT, L * bb * sizeof(cx<T>)), "alloc");
   }
-  BCR_CK(mal(&Tmp, n * (size_t)ldk * sizeof(cx<T>)), "alloc");
-  cx<T>* UPTt = UPt + (size_t)L * bb;
-  cx<T>* UQTt = UQt + (size_t)L * bb;
+  // the backward sweep overwrites X_j in place when one CTA spans the b rows of a tile column;
+  // otherwise it writes to Tmp and copies back
+  constexpr int TMi = GemmTile<T>::TM;
+  const bool inplace = TMi >= b;
+  if (!inplace) BCR_CK(mal(&Tmp, n * (size_t)ldk * sizeof(cx<T>)), "alloc");
 
-  // ---- plan: explicit inverse, a cyclic-reduction solve with X = I (in place in Kinv).  Forward
-  // products only touch the block columns where row block j can be nonzero: [lo_j, hi_j], which
-  // starts as {j} and grows by the ranges of the eliminated neighbours.
+  // ---- plan: explicit inverse, X = I in place in Kinv.  Forward products only touch the block
+  // columns where row block j can be nonzero: [lo_j, hi_j], which starts as {j} and grows by the
+  // ranges of the eliminated neighbours.
   BcrPlan<T> ip;
   std::vector<GemmTask<T>> ti;
   std::vector<CopyTask<T>> ci;
   const size_t bN = (size_t)b * ldk;  // one block row of X (row stride ldk)
   const int N = (int)n;
+  auto tb = [&](cx<T>* base, int K) { return base + (size_t)K * bb; };
+  auto xb = [&](cx<T>* base, int K, int c0) { return base + (size_t)K * bN + (size_t)c0 * b; };
   std::vector<int> lo(L), hi(L);
   for (int i = 0; i < L; ++i) lo[i] = hi[i] = i;
-  auto sub = [&](cx<T>* base, int blockrow, int c0) { return base + (size_t)blockrow * bN + (size_t)c0 * b; };
   for (size_t lv = 0; lv < lj.size(); ++lv) {
-    std::vector<GemmTask<T>> ta, tb;
+    std::vector<int> left_of(L, -1), right_of(L, -1);
     for (size_t k = 0; k < lj[lv].size(); ++k) {
-      const int j = lj[lv][k], p = lp[lv][k], q = lq[lv][k];
-      const int c0 = lo[j], w = (hi[j] - lo[j] + 1) * b;
-      // Tmp_j = Dinv_j X_j ; X_p -= A_pj Tmp_j ; X_q -= A_qj Tmp_j  (on the columns of j)
-      ti.push_back({DinvT + j * bb, sub(Kinv, j, c0), sub(Tmp, j, c0), b, ldk, ldk, 0, T(1), 0, w});
-      if (p >= 0) ta.push_back({UPt + j * bb, sub(Tmp, j, c0), sub(Kinv, p, c0), b, ldk, ldk, 0, T(-1), 1, w});
-      if (q >= 0) tb.push_back({UQTt + j * bb, sub(Tmp, j, c0), sub(Kinv, q, c0), b, ldk, ldk, 0, T(-1), 1, w});
+      if (lp[lv][k] >= 0) right_of[lp[lv][k]] = lj[lv][k];
+      if (lq[lv][k] >= 0) left_of[lq[lv][k]] = lj[lv][k];
     }
-    ip.add_gemm(ti);
-    ip.add_gemm(ta);
-    ip.add_gemm(tb);
-    for (size_t k = 0; k < lj[lv].size(); ++k) {
-      const int j = lj[lv][k], p = lp[lv][k], q = lq[lv][k];
-      if (p >= 0) {
-        lo[p] = std::min(lo[p], lo[j]);
-        hi[p] = std::max(hi[p], hi[j]);
+    // X_t -= Lp_jr X_jr (t = p of jr) + Lq_jl^T X_jl (t = q of jl) on the union of their ranges
+    for (int t = 0; t < L; ++t) {
+      const int jr = right_of[t], jl = left_of[t];
+      if (jr < 0 && jl < 0) continue;
+      int c0 = 1 << 30, c1 = -1;
+      if (jr >= 0) {
+        c0 = std::min(c0, lo[jr]);
+        c1 = std::max(c1, hi[jr]);
       }
-      if (q >= 0) {
-        lo[q] = std::min(lo[q], lo[j]);
-        hi[q] = std::max(hi[q], hi[j]);
+      if (jl >= 0) {
+        c0 = std::min(c0, lo[jl]);
+        c1 = std::max(c1, hi[jl]);
+      }
+      const int w = (c1 - c0 + 1) * b;
+      if (jr >= 0 && jl >= 0)
+        ti.push_back(task<T>(xb(Kinv, t, c0), ldk, 1, w,
+                             {pair<T>(tb(LpT, jr), b, 0, xb(Kinv, jr, c0), ldk, 0, T(-1), 0),
+                              pair<T>(tb(LqT, jl), b, 1, xb(Kinv, jl, c0), ldk, 0, T(-1), 0)}));
+      else if (jr >= 0)
+        ti.push_back(task<T>(xb(Kinv, t, c0), ldk, 1, w, {pair<T>(tb(LpT, jr), b, 0, xb(Kinv, jr, c0), ldk, 0, T(-1), 0)}));
+      else
+        ti.push_back(task<T>(xb(Kinv, t, c0), ldk, 1, w, {pair<T>(tb(LqT, jl), b, 1, xb(Kinv, jl, c0), ldk, 0, T(-1), 0)}));
+    }
+    ip.add_gemm(ti, false);
+    for (int t = 0; t < L; ++t) {
+      for (int j : {right_of[t], left_of[t]}) {
+        if (j >= 0) {
+          lo[t] = std::min(lo[t], lo[j]);
+          hi[t] = std::max(hi[t], hi[j]);
+        }
       }
     }
   }
   for (int lv = (int)lj.size() - 1; lv >= 0; --lv) {
-    std::vector<GemmTask<T>> ta, tb;
+    // X_j = Dinv_j X_j - Lp_j^T X_p - Lq_j X_q
     for (size_t k = 0; k < lj[lv].size(); ++k) {
       const int j = lj[lv][k], p = lp[lv][k], q = lq[lv][k];
-      // X_j -= A_jp X_p ; X_j -= A_jq X_q ; X_j = Dinv_j X_j (through Tmp_j)
-      if (p >= 0) ta.push_back({UPTt + j * bb, sub(Kinv, p, 0), sub(Kinv, j, 0), b, ldk, ldk, 0, T(-1), 1, N});
-      if (q >= 0) tb.push_back({UQt + j * bb, sub(Kinv, q, 0), sub(Kinv, j, 0), b, ldk, ldk, 0, T(-1), 1, N});
-      ti.push_back({DinvT + j * bb, sub(Kinv, j, 0), sub(Tmp, j, 0), b, ldk, ldk, 0, T(1), 0, N});
-      ci.push_back({sub(Tmp, j, 0), sub(Kinv, j, 0), (long long)bN, 0});
+      cx<T>* out = inplace ? xb(Kinv, j, 0) : xb(Tmp, j, 0);
+      GemmTask<T> t = task<T>(out, ldk, 0, N, {pair<T>(tb(DinvT, j), b, 0, xb(Kinv, j, 0), ldk, 0, T(1), 0)});
+      if (p >= 0) t.p[t.np++] = pair<T>(tb(LpT, j), b, 1, xb(Kinv, p, 0), ldk, 0, T(-1), 0);
+      if (q >= 0) t.p[t.np++] = pair<T>(tb(LqT, j), b, 0, xb(Kinv, q, 0), ldk, 0, T(-1), 0);
+      ti.push_back(t);
+      if (!inplace) ci.push_back({xb(Tmp, j, 0), xb(Kinv, j, 0), (long long)bN, 0});
     }
-    ip.add_gemm(ta);
-    ip.add_gemm(tb);
-    ip.add_gemm(ti);
+    ip.add_gemm(ti, false);
     ip.add_copy(ci);
   }
 
@@ -871,8 +922,6 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int ldk, int* err, cuda
   BCR_CK(mal(&dCi, ip.copy.size() * sizeof(CopyTask<T>)), "alloc");
 
   // ---- run: factorisation
-  BCR_CK(cudaMemsetAsync(UP, 0, 2 * L * bb * sizeof(D64), st), "memset");
-  BCR_CK(cudaMemsetAsync(UQ, 0, 2 * L * bb * sizeof(D64), st), "memset");
   const int gs = (int)std::min<size_t>((L * bb + 255) / 256, 4096);
   prof_start(KC_COARSE_SETUP, st);
   k_bcr_densify<double><<<gs, 256, 0, st>>>(P, D, Ucur);
@@ -884,8 +933,8 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int ldk, int* err, cuda
   prof_start(KC_COARSE_INV, st);
   if (sizeof(T) != sizeof(double)) {
     k_bcr_convert<T><<<gs, 256, 0, st>>>(Dinv, DinvT, L * bb);
-    k_bcr_convert<T><<<gs, 256, 0, st>>>(UP, UPt, 2 * L * bb);
-    k_bcr_convert<T><<<gs, 256, 0, st>>>(UQ, UQt, 2 * L * bb);
+    k_bcr_convert<T><<<gs, 256, 0, st>>>(Lp, LpT, L * bb);
+    k_bcr_convert<T><<<gs, 256, 0, st>>>(Lq, LqT, L * bb);
     BCR_CK(cudaGetLastError(), "convert");
     *launches += 3;
   }

@@ -539,21 +539,19 @@ __global__ void __launch_bounds__(128) k_coarse_tiles(const cx<T>* __restrict__ 
     }
     v0 = cadd(v0, shfl_xor_cx(v0, 16));  // add the other row half
     v1 = cadd(v1, shfl_xor_cx(v1, 16));
-    // reduce-scatter of p over the 16 lanes of this half: after the four steps lane with
-    // bit pattern b (lane & 15) holds the full sum for row index i = bitreverse-free order below
+    // reduce-scatter of p over the 16 lanes of this half (lane bit 3, 2, 1, 0 in turn picks the
+    // upper or lower half of the remaining window): lane b = lane & 15 ends with the row-2b+h sum
+    const bool u3 = (lane >> 3) & 1, u2 = (lane >> 2) & 1, u1 = (lane >> 1) & 1, u0 = lane & 1;
+    cx<T> p8[8], p4[4], p2[2];
 #pragma unroll
-    for (int st = 3; st >= 0; --st) {
-      const int half = 1 << st;  // keep p[0..half) or p[half..2 half) of the current window
-      const bool up = (lane >> st) & 1;
+    for (int i = 0; i < 8; ++i) p8[i] = cadd(u3 ? p[i + 8] : p[i], shfl_xor_cx(u3 ? p[i] : p[i + 8], 8));
 #pragma unroll
-      for (int i = 0; i < half; ++i) {
-        const cx<T> send = up ? p[i] : p[i + half];
-        const cx<T> keep = up ? p[i + half] : p[i];
-        p[i] = cadd(keep, shfl_xor_cx(send, half));
-      }
-    }
+    for (int i = 0; i < 4; ++i) p4[i] = cadd(u2 ? p8[i + 4] : p8[i], shfl_xor_cx(u2 ? p8[i] : p8[i + 4], 4));
+#pragma unroll
+    for (int i = 0; i < 2; ++i) p2[i] = cadd(u1 ? p4[i + 2] : p4[i], shfl_xor_cx(u1 ? p4[i] : p4[i + 2], 2));
+    const cx<T> p1 = cadd(u0 ? p2[1] : p2[0], shfl_xor_cx(u0 ? p2[0] : p2[1], 1));
     // lane (h, b = lane & 15) now holds row 2 * b + h; rows 0..31 are lanes 2b + h -> reorder
-    const cx<T> u = shfl_cx(p[0], ((lane & 1) << 4) | (lane >> 1));
+    const cx<T> u = shfl_cx(p1, ((lane & 1) << 4) | (lane >> 1));
     part_u[((size_t)r * ntile + t) * kCT + lane] = u;
     if (I != J) {
       // lane holds v for columns c0, c0 + 1 (duplicated in both halves): lane l writes column l
