@@ -108,6 +108,9 @@ class Engine : public EngineBase {
     for (void* p : allocs_) cudaFreeAsync(p, nullptr);
     cudaStreamSynchronize(nullptr);
     if (h_active_) cudaFreeHost(h_active_);
+    if (side_) cudaStreamDestroy(side_);
+    if (fork_) cudaEventDestroy(fork_);
+    if (join_) cudaEventDestroy(join_);
   }
 
   long long op_bytes() const override { return op_bytes_; }
@@ -145,6 +148,84 @@ class Engine : public EngineBase {
         prof_stop(KC_FACTOR, st);
         ENG_LAUNCH();
       }
+    }
+    // ---- local operator storage
+    ENG_CK(alloc(&F_, (size_t)ncls_ * sym_ld(g.nD) * cxT));  // packed symmetric
+    ENG_CK(alloc(&Frc_, (size_t)ncls_ * g.nD * g.nc * cxT));
+    ENG_CK(alloc(&Sd_, (size_t)ncls_ * sym_ld(g.nD) * cxT));  // packed symmetric
+    ENG_CK(alloc(&Kcc_, (size_t)ncls_ * g.nc * g.nc * sizeof(cx<double>)));
+    op_bytes_ += (long long)ncls_ * (2 * sym_ld(g.nD) + (long long)g.nD * g.nc) * cxT;
+    // ---- interior branch on a second stream: the interior problem is independent of the
+    // remainder problems, so its factor and the Dirichlet S run beside the remainder factors and F
+    const int C = 32;
+    const int nchunk2 = (g.nD + C - 1) / C;
+    cx<T>* Xi = nullptr;
+    cx<T>* Sbase = nullptr;
+    ENG_CK(alloc(&Xi, (size_t)nchunk2 * g.ni * C * cxT));
+    ENG_CK(alloc(&Sbase, (size_t)g.nD * g.nD * cxT));
+    // interior factor (identical for all subdomains)
+    const int ibb = g.ib * g.ib;
+    cx<T>* Dii = nullptr;
+    ENG_CK(alloc(&Dii, (size_t)g.iL * ibb * cxT));
+    if (!side_) {
+      ENG_CK(cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking));
+      ENG_CK(cudaEventCreateWithFlags(&fork_, cudaEventDisableTiming));
+      ENG_CK(cudaEventCreateWithFlags(&join_, cudaEventDisableTiming));
+    }
+    // every buffer the side stream touches is allocated (stream-ordered on st) before the fork
+    const bool cols_if = sizeof(T) == 4 && g.dim == 2 && g.ib <= 32;
+    const size_t need_if = (2 * (size_t)ibb + 2 * g.ib) * cxT;
+    const int use_smem_if = need_if <= 200 * 1024;
+    cx<T>* gws_if = nullptr;
+    if (!cols_if && !use_smem_if) ENG_CK(alloc(&gws_if, 2 * (size_t)ibb * cxT));
+    ENG_CK(cudaEventRecord(fork_, st));
+    ENG_CK(cudaStreamWaitEvent(side_, fork_, 0));
+    bool ifactored = false;
+    if constexpr (sizeof(T) == 4) {
+      if (cols_if) {
+        const int Bp = g.ib == 9 ? 9 : g.ib == 17 ? 17 : ((g.ib + 7) / 8) * 8;
+        prof_start(KC_FACTOR, side_);
+        cudaError_t fe = cudaErrorInvalidValue;
+#define FK_CASE(BV) \
+  case BV: fe = launch_factor_cols<T, BV>(pii_, dm_->cls_code, 1, Dii, err_ + 1, side_); break
+        switch (Bp) {
+          FK_CASE(8);
+          FK_CASE(9);
+          FK_CASE(16);
+          FK_CASE(17);
+          FK_CASE(24);
+          FK_CASE(32);
+          default: break;
+        }
+#undef FK_CASE
+        ENG_CK(fe);
+        prof_stop(KC_FACTOR, side_);
+        ENG_LAUNCH();
+        ifactored = true;
+      }
+    }
+    if (!ifactored) {
+      size_t smem = use_smem_if ? need_if : 2 * g.ib * cxT;
+      ENG_CK(smem_attr((const void*)k_factor<T, StencilProv<T>>, (int)smem));
+      prof_start(KC_FACTOR, side_);
+      k_factor<T, StencilProv<T>><<<1, ibb >= 1024 ? 512 : 256, smem, side_>>>(pii_, dm_->cls_code, Dii, gws_if, use_smem_if,
+                                                                               err_ + 1);
+      prof_stop(KC_FACTOR, side_);
+      ENG_LAUNCH();
+    }
+    {
+      size_t smem2 = 2 * (size_t)g.ib * C * cxT;
+      ENG_CK(smem_attr((const void*)k_form_ii<T>, (int)smem2));
+      prof_start(KC_FORM, side_);
+      k_form_ii<T><<<nchunk2, 256, smem2, side_>>>(pii_, g, mv_, Dii, C, Xi, Sbase);
+      prof_stop(KC_FORM, side_);
+      ENG_LAUNCH();
+      long long tot = (long long)ncls_ * g.nD * g.nD;
+      int gs = (int)std::min<long long>((tot + 255) / 256, 16LL * nsm_);
+      prof_start(KC_FORM, side_);
+      k_mask_S<T><<<gs, 256, 0, side_>>>(g, mv_, ncls_, Sbase, Sd_);
+      prof_stop(KC_FORM, side_);
+      ENG_LAUNCH();
     }
     // ---- remainder factors, one per class
     ENG_CK(alloc(&Dinv_, (size_t)ncls_ * g.lL * bb * cxT));
@@ -196,54 +277,8 @@ class Engine : public EngineBase {
       prof_stop(KC_FACTOR, st);
       ENG_LAUNCH();
     }
-    // ---- interior factor (identical for all subdomains)
-    const int ibb = g.ib * g.ib;
-    cx<T>* Dii = nullptr;
-    ENG_CK(alloc(&Dii, (size_t)g.iL * ibb * cxT));
-    bool ifactored = false;
-    if constexpr (sizeof(T) == 4) {
-      if (g.dim == 2 && g.ib <= 32) {
-        const int Bp = g.ib == 9 ? 9 : g.ib == 17 ? 17 : ((g.ib + 7) / 8) * 8;
-        prof_start(KC_FACTOR, st);
-        cudaError_t fe = cudaErrorInvalidValue;
-#define FK_CASE(BV) \
-  case BV: fe = launch_factor_cols<T, BV>(pii_, dm_->cls_code, 1, Dii, err_ + 1, st); break
-        switch (Bp) {
-          FK_CASE(8);
-          FK_CASE(9);
-          FK_CASE(16);
-          FK_CASE(17);
-          FK_CASE(24);
-          FK_CASE(32);
-          default: break;
-        }
-#undef FK_CASE
-        ENG_CK(fe);
-        prof_stop(KC_FACTOR, st);
-        ENG_LAUNCH();
-        ifactored = true;
-      }
-    }
-    if (!ifactored) {
-      size_t need = (2 * (size_t)ibb + 2 * g.ib) * cxT;
-      int use_smem = need <= 200 * 1024;
-      size_t smem = use_smem ? need : 2 * g.ib * cxT;
-      cx<T>* gws = nullptr;
-      if (!use_smem) ENG_CK(alloc(&gws, 2 * (size_t)ibb * cxT));
-      ENG_CK(smem_attr((const void*)k_factor<T, StencilProv<T>>, (int)smem));
-      prof_start(KC_FACTOR, st);
-      k_factor<T, StencilProv<T>><<<1, ibb >= 1024 ? 512 : 256, smem, st>>>(pii_, dm_->cls_code, Dii, gws, use_smem, err_ + 1);
-      prof_stop(KC_FACTOR, st);
-      ENG_LAUNCH();
-    }
     // ---- local operators
-    ENG_CK(alloc(&F_, (size_t)ncls_ * sym_ld(g.nD) * cxT));  // packed symmetric
-    ENG_CK(alloc(&Frc_, (size_t)ncls_ * g.nD * g.nc * cxT));
-    ENG_CK(alloc(&Sd_, (size_t)ncls_ * sym_ld(g.nD) * cxT));  // packed symmetric
-    ENG_CK(alloc(&Kcc_, (size_t)ncls_ * g.nc * g.nc * sizeof(cx<double>)));
-    op_bytes_ += (long long)ncls_ * (2 * sym_ld(g.nD) + (long long)g.nD * g.nc) * cxT;
     {
-      const int C = 32;
       cx<T>* Xws = nullptr;
       bool formed = false;
       if constexpr (sizeof(T) == 4) {
@@ -298,23 +333,9 @@ class Engine : public EngineBase {
         prof_stop(KC_FORM, st);
         ENG_LAUNCH();
       }
-      const int nchunk2 = (g.nD + C - 1) / C;
-      cx<T>* Xi = nullptr;
-      cx<T>* Sbase = nullptr;
-      ENG_CK(alloc(&Xi, (size_t)nchunk2 * g.ni * C * cxT));
-      ENG_CK(alloc(&Sbase, (size_t)g.nD * g.nD * cxT));
-      size_t smem2 = 2 * (size_t)g.ib * C * cxT;
-      ENG_CK(smem_attr((const void*)k_form_ii<T>, (int)smem2));
-      prof_start(KC_FORM, st);
-      k_form_ii<T><<<nchunk2, 256, smem2, st>>>(pii_, g, mv_, Dii, C, Xi, Sbase);
-      prof_stop(KC_FORM, st);
-      ENG_LAUNCH();
-      long long tot = (long long)ncls_ * g.nD * g.nD;
-      int gs = (int)std::min<long long>((tot + 255) / 256, 16LL * nsm_);
-      prof_start(KC_FORM, st);
-      k_mask_S<T><<<gs, 256, 0, st>>>(g, mv_, ncls_, Sbase, Sd_);
-      prof_stop(KC_FORM, st);
-      ENG_LAUNCH();
+      // join the interior branch (S) before the buffers are released
+      ENG_CK(cudaEventRecord(join_, side_));
+      ENG_CK(cudaStreamWaitEvent(st, join_, 0));
       ENG_CK(cudaStreamSynchronize(st));
       if (Xws) free_one(Xws);
       free_one(Xi);
@@ -705,7 +726,10 @@ class Engine : public EngineBase {
   }
 
   // out = F_DP v = F_rr v + Frc~ Kcc~^{-1} Frc~^T v
-  int dual_apply(const cx<T>* v, int R, const int* active, cx<T>* out, cudaStream_t st, std::string* msg) {
+  // out = F_DP v; with oa set, the closing scatter also takes the first Gram-Schmidt dots of out
+  // against the Krylov basis (k_scatter_orth_dots)
+  int dual_apply(const cx<T>* v, int R, const int* active, cx<T>* out, cudaStream_t st, std::string* msg,
+                 const OrthArgs* oa = nullptr) {
     const bool coarse = g_.ncor > 0;
     int rc = local_apply(false, F_, v, R, active, coarse, st, msg);
     if (rc) return rc;
@@ -717,6 +741,15 @@ class Engine : public EngineBase {
       ENG_LAUNCH();
       rc = coarse_apply(gc_, R, active, wc_, st, msg);
       if (rc) return rc;
+    }
+    if (oa) {
+      const int seg = (g_.nlam + oa->nblk - 1) / oa->nblk;
+      prof_start(KC_GMRES_DOTS, st);
+      k_scatter_orth_dots<T><<<dim3(oa->nblk, R), 256, (size_t)seg * sizeof(cx<T>), st>>>(
+          g_, mv_, Y_, Frc_, coarse ? wc_ : nullptr, V_, out, R, *oa);
+      prof_stop(KC_GMRES_DOTS, st);
+      ENG_LAUNCH();
+      return SCHUR_OK;
     }
     long long tot = (long long)R * g_.nlam;
     prof_start(KC_SCATTER, st);
@@ -750,7 +783,7 @@ class Engine : public EngineBase {
     ENG_LAUNCH();
     const int seg = (nlam + nblk - 1) / nblk;
     const size_t dot_smem = (size_t)seg * cxT, upd_smem = (size_t)(seg + m + 1) * cxT;
-    ENG_CK(smem_attr((const void*)k_orth_dots<T>, (int)dot_smem));
+    ENG_CK(smem_attr((const void*)k_scatter_orth_dots<T>, (int)dot_smem));
     ENG_CK(smem_attr((const void*)k_orth_update_dots<T>, (int)upd_smem));
     ENG_CK(smem_attr((const void*)k_orth_update_norm<T>, (int)upd_smem));
     OrthArgs oa;
@@ -781,14 +814,10 @@ class Engine : public EngineBase {
       cx<T>* vk1 = V_ + (k + 1) * vstride;
       int rc = precond(vk, R, active_, zv_, st, msg);
       if (rc) return rc;
-      rc = dual_apply(zv_, R, active_, vk1, st, msg);
-      if (rc) return rc;
       oa.k = k;
+      rc = dual_apply(zv_, R, active_, vk1, st, msg, &oa);  // with the first Gram-Schmidt dots
+      if (rc) return rc;
       const dim3 og(nblk, R);
-      prof_start(KC_GMRES_DOTS, st);
-      k_orth_dots<T><<<og, 256, dot_smem, st>>>(V_, vk1, oa);
-      prof_stop(KC_GMRES_DOTS, st);
-      ENG_LAUNCH();
       prof_start(KC_GMRES_UPDATE, st);
       k_orth_update_dots<T><<<og, 256, upd_smem, st>>>(V_, vk1, oa);
       prof_stop(KC_GMRES_UPDATE, st);
@@ -859,6 +888,8 @@ class Engine : public EngineBase {
   int *active_ = nullptr, *kk_ = nullptr, *bad_ = nullptr, *cnt_ = nullptr;
   int* h_active_ = nullptr;
   cudaStream_t ast_ = nullptr;  // stream of the current setup / solve (stream-ordered allocations)
+  cudaStream_t side_ = nullptr;  // second setup stream (interior branch)
+  cudaEvent_t fork_ = nullptr, join_ = nullptr;
 };
 
 }  // namespace schur

@@ -729,7 +729,7 @@ __global__ void k_scatter(Geom g, MapsView m, const cx<T>* __restrict__ Y, const
 // owns the contiguous slice bx of the vectors.  Each kernel leaves FP64 partial sums per block;
 // the last block of r to finish (ticket counter) adds them in block order, so the result does not
 // depend on scheduling, and resets the counter for the next launch.
-//   k_orth_dots:        h = V^H w                           -> hc, H[:, k] += h
+//   k_scatter_orth_dots: w = B (Y + Frc wc); h = V^H w       -> hc, H[:, k] += h
 //   k_orth_update_dots: w -= V hc; h = V^H w                -> hc, H[:, k] += h
 //   k_orth_update_norm: w -= V hc; h_{k+1,k} = |w|, Givens rotation of column k
 struct OrthArgs {
@@ -831,15 +831,32 @@ __device__ __forceinline__ void orth_block_update(const cx<T>* __restrict__ V, c
   __syncthreads();
 }
 
+// The dual operator's final scatter fused with the first Gram-Schmidt pass: the block computes
+// its slice of w = B (Y + Frc wc) (the new Arnoldi vector, written out) straight into shared memory
+// and takes its partial dots with V_0..V_k.
 template <class T>
-__global__ void __launch_bounds__(256) k_orth_dots(const cx<T>* __restrict__ V, const cx<T>* __restrict__ w, OrthArgs a) {
+__global__ void __launch_bounds__(256) k_scatter_orth_dots(Geom g, MapsView m, const cx<T>* __restrict__ Y,
+                                                           const cx<T>* __restrict__ Frc, const cx<T>* __restrict__ wc,
+                                                           const cx<T>* __restrict__ V, cx<T>* w, int R, OrthArgs a) {
   extern __shared__ unsigned char smraw[];
   cx<T>* ws = reinterpret_cast<cx<T>*>(smraw);
   const int r = blockIdx.y;
   if (!a.active[r]) return;
   int lo, n;
   orth_slice(a, &lo, &n);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) ws[i] = w[(size_t)r * a.nlam + lo + i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int lam = lo + i;
+    cx<T> v = czero<T>();
+    for (int side = 0; side < 2; ++side) {
+      const int code = m.lam_side[2 * lam + side];
+      const int sd = code / g.nD, j = code - sd * g.nD;
+      cx<T> t = Y[((size_t)sd * R + r) * g.nD + j];
+      if (wc) t = cadd(t, frc_corr(g, m, Frc, wc + (size_t)r * g.ncor, sd, j));
+      v = side == 0 ? cadd(v, t) : csub(v, t);
+    }
+    w[(size_t)r * a.nlam + lam] = v;
+    ws[i] = v;
+  }
   __syncthreads();
   orth_block_dots(V, a, r, lo, n, ws);
   if (orth_last_block(a.cnt + r, a.nblk)) orth_finish_dots(a, r);
