@@ -642,11 +642,17 @@ class Engine : public EngineBase {
       else LS_ATTR(16);
 #undef LS_ATTR
       prof_start(cat, st);
-      if (R == 1) k_local_solve_warp<T, 1><<<grid, 32 * wpb, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc);
-      else if (R == 2) k_local_solve_warp<T, 2><<<grid, 32 * wpb, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc);
-      else if (R <= 4) k_local_solve_warp<T, 4><<<grid, 32 * wpb, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc);
-      else if (R <= 8) k_local_solve_warp<T, 8><<<grid, 32 * wpb, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc);
-      else k_local_solve_warp<T, 16><<<grid, 32 * wpb, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc);
+      {  // all remainder right-hand sides first, one thread per (subdomain, node, column)
+        const long long tot = (long long)g.nsd * g.nl * R;
+        k_remainder_rhs<T><<<(int)std::min<long long>((tot + 255) / 256, 16LL * nsm_), 256, 0, st>>>(prr_, g, mv_, fc, ldf,
+                                                                                                   lam, uc, R, Xs_);
+        ENG_LAUNCH();
+      }
+      if (R == 1) k_local_solve_warp<T, 1><<<grid, 32 * wpb, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc, 1);
+      else if (R == 2) k_local_solve_warp<T, 2><<<grid, 32 * wpb, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc, 1);
+      else if (R <= 4) k_local_solve_warp<T, 4><<<grid, 32 * wpb, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc, 1);
+      else if (R <= 8) k_local_solve_warp<T, 8><<<grid, 32 * wpb, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc, 1);
+      else k_local_solve_warp<T, 16><<<grid, 32 * wpb, smem, st>>>(prr_, g, mv_, Dinv_, fc, ldf, lam, uc, R, Xs_, vd, tc, 1);
       prof_stop(cat, st);
       ENG_LAUNCH();
       return SCHUR_OK;

@@ -614,12 +614,31 @@ __device__ __forceinline__ cx<T> remainder_rhs(const StencilProv<T>& P, const Ge
   return v;
 }
 
+// Remainder right-hand sides of every subdomain node and column, one thread each, into the
+// per-subdomain solution buffers (layout [sd][node][R]) ahead of the layered solves.
+template <class T>
+__global__ void k_remainder_rhs(StencilProv<T> P, Geom g, MapsView m, const cx<double>* __restrict__ f, int ldf,
+                                const cx<T>* __restrict__ lam, const cx<T>* __restrict__ uc, int R, cx<T>* Xs) {
+  const int nl = P.ly.L * P.ly.b;
+  const long long tot = (long long)g.nsd * nl * R;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int sd = (int)(e / ((long long)nl * R));
+    const int rem = (int)(e - (long long)sd * nl * R);
+    const int node = rem / R, c = rem - node * R, K = node / P.ly.b, i = node - K * P.ly.b;
+    StencilProv<T> Pq = P;
+    Pq.select(m.sd_cls[sd], m.cls_code);
+    int S[3];
+    idx2crd(sd, g.nsub, g.dim, S);
+    Xs[(size_t)sd * g.nl * R + rem] = remainder_rhs(Pq, g, m, sd, S, f, ldf, lam, uc, K, i, c);
+  }
+}
+
 // Per-solve local solves, one warp per subdomain.  VD/Tc extraction when VD != null (right-hand
 // side split); otherwise the solution stays in Xs (primal recovery).
 template <class T, int C>
 __global__ void k_local_solve_warp(StencilProv<T> P, Geom g, MapsView m, const cx<T>* __restrict__ Dinv,
                                    const cx<double>* __restrict__ f, int ldf, const cx<T>* __restrict__ lam,
-                                   const cx<T>* __restrict__ uc, int R, cx<T>* Xs, cx<T>* VD, cx<T>* Tc) {
+                                   const cx<T>* __restrict__ uc, int R, cx<T>* Xs, cx<T>* VD, cx<T>* Tc, int rhs_pre) {
   const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
   const int sd = blockIdx.x * wpb + (threadIdx.x >> 5);
   if (sd >= g.nsd) return;
@@ -631,8 +650,13 @@ __global__ void k_local_solve_warp(StencilProv<T> P, Geom g, MapsView m, const c
   cx<T>* X = Xs + (size_t)sd * g.nl * R;
   extern __shared__ unsigned char smraw[];
   cx<T>* Ds = reinterpret_cast<cx<T>*>(smraw) + (size_t)(threadIdx.x >> 5) * 2 * b * b;
-  auto rhs = [&](int K, int i, int c) -> cx<T> { return remainder_rhs(P, g, m, sd, S, f, ldf, lam, uc, K, i, c); };
-  warp_layered_solve<T, C>(P, Dinv + (size_t)q * L * b * b, R, rhs, X, R, 1, Ds);
+  if (rhs_pre) {  // right-hand sides already in X (k_remainder_rhs); read back layer by layer
+    auto rhs = [&](int K, int i, int c) -> cx<T> { return X[(size_t)(K * b + i) * R + c]; };
+    warp_layered_solve<T, C>(P, Dinv + (size_t)q * L * b * b, R, rhs, X, R, 1, Ds);
+  } else {
+    auto rhs = [&](int K, int i, int c) -> cx<T> { return remainder_rhs(P, g, m, sd, S, f, ldf, lam, uc, K, i, c); };
+    warp_layered_solve<T, C>(P, Dinv + (size_t)q * L * b * b, R, rhs, X, R, 1, Ds);
+  }
   if (!VD) return;
   __syncwarp();
   for (int e = lane; e < R * nD; e += 32) {
