@@ -184,7 +184,7 @@ class Engine : public EngineBase {
     if constexpr (sizeof(T) == 4) {
       if (cols_if) {
         const int Bp = g.ib == 9 ? 9 : g.ib == 17 ? 17 : ((g.ib + 7) / 8) * 8;
-        prof_start(KC_FACTOR, side_);
+        prof_start(KC_INTERIOR, side_);
         cudaError_t fe = cudaErrorInvalidValue;
 #define FK_CASE(BV) \
   case BV: fe = launch_factor_cols<T, BV>(pii_, dm_->cls_code, 1, Dii, err_ + 1, side_); break
@@ -199,7 +199,7 @@ class Engine : public EngineBase {
         }
 #undef FK_CASE
         ENG_CK(fe);
-        prof_stop(KC_FACTOR, side_);
+        prof_stop(KC_INTERIOR, side_);
         ENG_LAUNCH();
         ifactored = true;
       }
@@ -207,24 +207,24 @@ class Engine : public EngineBase {
     if (!ifactored) {
       size_t smem = use_smem_if ? need_if : 2 * g.ib * cxT;
       ENG_CK(smem_attr((const void*)k_factor<T, StencilProv<T>>, (int)smem));
-      prof_start(KC_FACTOR, side_);
+      prof_start(KC_INTERIOR, side_);
       k_factor<T, StencilProv<T>><<<1, ibb >= 1024 ? 512 : 256, smem, side_>>>(pii_, dm_->cls_code, Dii, gws_if, use_smem_if,
                                                                                err_ + 1);
-      prof_stop(KC_FACTOR, side_);
+      prof_stop(KC_INTERIOR, side_);
       ENG_LAUNCH();
     }
     {
       size_t smem2 = 2 * (size_t)g.ib * C * cxT;
       ENG_CK(smem_attr((const void*)k_form_ii<T>, (int)smem2));
-      prof_start(KC_FORM, side_);
+      prof_start(KC_INTERIOR, side_);
       k_form_ii<T><<<nchunk2, 256, smem2, side_>>>(pii_, g, mv_, Dii, C, Xi, Sbase);
-      prof_stop(KC_FORM, side_);
+      prof_stop(KC_INTERIOR, side_);
       ENG_LAUNCH();
       long long tot = (long long)ncls_ * g.nD * g.nD;
       int gs = (int)std::min<long long>((tot + 255) / 256, 16LL * nsm_);
-      prof_start(KC_FORM, side_);
+      prof_start(KC_INTERIOR, side_);
       k_mask_S<T><<<gs, 256, 0, side_>>>(g, mv_, ncls_, Sbase, Sd_);
-      prof_stop(KC_FORM, side_);
+      prof_stop(KC_INTERIOR, side_);
       ENG_LAUNCH();
     }
     // ---- remainder factors, one per class

@@ -20,8 +20,9 @@ enum KCat {
   KC_RECOVER = 12,    // primal recovery solves
   KC_ASSEMBLE = 13,   // z assembly
   KC_RESIDUAL = 14,   // FP64 refinement residual and shortcut
-  KC_COARSE_INV = 15,  // coarse inverse columns (and precision conversion)
-  KC_N = 16
+  KC_COARSE_INV = 15, // coarse inverse columns (and precision conversion)
+  KC_INTERIOR = 16,   // interior factor and Dirichlet S (second setup stream)
+  KC_N = 17
 };
 
 // start/stop brackets around one launch; no-ops unless the category is enabled

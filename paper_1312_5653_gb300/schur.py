@@ -138,15 +138,16 @@ def _check(code, where, allow=()):
     return code
 
 
-def schur_profile_begin(mask=0xFFFF):
+def schur_profile_begin(mask=0x1FFFF):
     _check(load().schur_profile_begin(mask), "schur_profile_begin")
 
 
 def schur_profile_end():
     """{category name: (launches, total ms)} since schur_profile_begin (synchronises)."""
-    arr = (schur_kernel_time * 16)()
+    cap = 32  # more than the library's category count
+    arr = (schur_kernel_time * cap)()
     cnt = ctypes.c_int(0)
-    _check(load().schur_profile_end(arr, 16, ctypes.byref(cnt)), "schur_profile_end")
+    _check(load().schur_profile_end(arr, cap, ctypes.byref(cnt)), "schur_profile_end")
     return {load().schur_kernel_category_name(arr[k].category).decode(): (arr[k].launches, arr[k].total_ms)
             for k in range(cnt.value)}
 
