@@ -232,10 +232,7 @@ int ctx_outer(schur_ctx* c, const double* bre, const double* bim, int ldb, int R
     }
     InnerResult ir;
     std::string msg;
-    // the inner solve only has to close the remaining gap to tol (with a margin of 10): the last
-    // refinement steps run with a looser GMRES stop than the first
-    const double step_tol = std::max(inner_tol, std::min(0.1, 0.1 * c->opts.tol / std::max(worst, 1e-300)));
-    rc = c->eng->inner_solve(c->res, (int)g.n, c->z, (int)g.n, R, step_tol, c->opts.max_iter, st, &ir, &msg);
+    rc = c->eng->inner_solve(c->res, (int)g.n, c->z, (int)g.n, R, inner_tol, c->opts.max_iter, st, &ir, &msg);
     c->launches += c->eng->launches;
     c->total_launches += c->eng->launches;
     if (rc) return set_error(rc, msg);
