@@ -771,6 +771,7 @@ __device__ __forceinline__ void orth_block_dots(const cx<T>* __restrict__ V, con
   for (int j = warp; j <= a.k; j += nw) {
     const cx<T>* vj = V + j * a.vstride + (size_t)r * a.nlam + lo;
     T pre = 0, pim = 0;  // per-lane partial sums (a few terms) in T, combined in FP64
+#pragma unroll 4
     for (int i = lane; i < n; i += 32) {
       const cx<T> x = vj[i], y = ws[i];
       pre += x.re * y.re + x.im * y.im;
@@ -791,6 +792,7 @@ __device__ __forceinline__ void orth_finish_dots(const OrthArgs& a, int r) {
   for (int j = warp; j <= a.k; j += nw) {
     const cx<double>* p = a.part + ((size_t)r * kMaxKdev + j) * a.nblk;
     double re = 0, im = 0;
+#pragma unroll 4
     for (int b = lane; b < a.nblk; b += 32) {
       const double2 v = __ldcg(reinterpret_cast<const double2*>(p + b));
       re += v.x;
@@ -824,6 +826,7 @@ __device__ __forceinline__ void orth_block_update(const cx<T>* __restrict__ V, c
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     cx<T> acc = w[(size_t)r * a.nlam + lo + i];
+#pragma unroll 4
     for (int j = 0; j <= a.k; ++j) cfms(acc, h[j], V[j * a.vstride + (size_t)r * a.nlam + lo + i]);
     w[(size_t)r * a.nlam + lo + i] = acc;
     ws[i] = acc;
@@ -901,6 +904,7 @@ __global__ void __launch_bounds__(256) k_orth_update_norm(const cx<T>* __restric
   if (orth_last_block(a.cnt + r, a.nblk)) {
     if (threadIdx.x < 32) {
       double t = 0;
+#pragma unroll 4
       for (int b = threadIdx.x; b < a.nblk; b += 32) t += __ldcg(a.nrm_part + (size_t)r * a.nblk + b);
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
       if (threadIdx.x == 0) {
