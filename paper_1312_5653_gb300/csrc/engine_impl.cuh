@@ -13,6 +13,7 @@
 #include "gmres.h"
 #include "kernels.cuh"
 #include "warp.cuh"
+#include "form_tc.cuh"
 #include "prof.h"
 #include "coarse.h"
 
@@ -283,7 +284,19 @@ class Engine : public EngineBase {
       bool formed = false;
       if constexpr (sizeof(T) == 4) {
         const int ncol = g.nD + g.nc, ldE = ((ncol + 31) / 32) * 32;
-        if (g.dim == 2 && g.lb <= 32 && ldE <= 128) {
+        if (g.dim == 3 && tc_nb(g.lb) <= kTcTmemCols) {
+          // 3D FP32: layer products on the tensor cores, 128 columns per CTA, two CTAs per SM
+          const int ntile = (ncol + kTcCols - 1) / kTcCols;
+          const size_t smem = form_tc_smem(g.lb, nbr_count(g.dim));
+          const int grid = std::max(1, std::min(ncls_ * ntile, 2 * nsm_));
+          ENG_CK(alloc(&Xws, (size_t)grid * g.nl * kTcCols * cxT));
+          ENG_CK(smem_attr((const void*)k_form_rr_tc<T>, (int)smem));
+          prof_start(KC_FORM, st);
+          k_form_rr_tc<T><<<grid, kTcCols, smem, st>>>(prr_, g, mv_, Dinv_, ncls_, Xws, F_, Frc_, Kcc_, err_ + 3);
+          prof_stop(KC_FORM, st);
+          ENG_LAUNCH();
+          formed = true;
+        } else if (g.dim == 2 && g.lb <= 32 && ldE <= 128) {
           const int Bp = g.lb == 9 ? 9 : g.lb == 17 ? 17 : ((g.lb + 7) / 8) * 8;
           const size_t per_cta = (size_t)g.lL * Bp * ldE * cxT;
           int grid = std::min(ncls_, 8 * nsm_);
@@ -385,6 +398,10 @@ class Engine : public EngineBase {
     if (herr[0] || herr[1] || herr[2]) {
       if (msg) *msg = "zero or non-finite pivot in a subdomain or coarse factorisation";
       return SCHUR_EBREAKDOWN;
+    }
+    if (herr[3]) {
+      if (msg) *msg = "tensor-core local operator formation: completion wait timed out";
+      return SCHUR_ETIMEOUT;
     }
     return SCHUR_OK;
   }

@@ -30,9 +30,12 @@ def gpu(a):
 
 
 # 2D layer sizes b = s + 1 of 5, 9, 14, 17 and 32 cover the exact (9, 17) and padded (8, 16, 32)
-# register-tile widths of the column-per-thread formation kernel.
+# register-tile widths of the column-per-thread formation kernel.  3D subdomains of 2^3, 4^3 and
+# 8^3 elements (layers of 9, 25 and 81 nodes; 8^3 is the size of the 128^3 workload) run the
+# tensor-core formation: one, three and four column tiles, ragged last tiles and chunks.
 @pytest.mark.parametrize("dim,N,P,beta", [(2, 8, 2, 1e-4), (2, 12, 3, 1e-2), (3, 6, 3, 1e-6), (2, 16, 2, 1e-6),
-                                          (2, 26, 2, 1e-3), (2, 32, 2, 1e-4), (2, 62, 2, 1e-2)])
+                                          (2, 26, 2, 1e-3), (2, 32, 2, 1e-4), (2, 62, 2, 1e-2), (3, 12, 3, 1e-4),
+                                          (3, 16, 2, 1e-6)])
 @pytest.mark.parametrize("prec", PRECS)
 def test_local_operators_match_dense_definitions(dim, N, P, beta, prec):
     sol = S.Solver(dim, N, beta, nsub=P, precision=prec)
