@@ -231,6 +231,15 @@ class Engine : public EngineBase {
     // ---- remainder factors, one per class
     ENG_CK(alloc(&Dinv_, (size_t)ncls_ * g.lL * bb * cxT));
     op_bytes_ += (long long)ncls_ * g.lL * bb * cxT;
+    // 3D FP32: the local operators are formed on the tensor cores from the layer couplings G, H
+    // of the factorisation (temporaries, released after the formation)
+    const bool tc_form = sizeof(T) == 4 && g.dim == 3 && g.lL <= 32 && tc_nb(g.lb) <= kTcTmemCols &&
+                         form_tc_smem(g.lb) <= (size_t)227 * 1024;
+    cx<T>*Gc = nullptr, *Hc = nullptr;
+    if (tc_form) {
+      ENG_CK(alloc(&Gc, (size_t)ncls_ * g.lL * bb * cxT));
+      ENG_CK(alloc(&Hc, (size_t)ncls_ * g.lL * bb * cxT));
+    }
     bool factored = false;
     if constexpr (sizeof(T) == 4) {
       if (g.dim == 2 && g.lb <= 32) {
@@ -256,7 +265,7 @@ class Engine : public EngineBase {
       }
     }
     if (factored) {
-    } else if (g.lb <= 32) {
+    } else if (g.lb <= 32 && !tc_form) {
       const size_t per_warp = (2 * (size_t)bb + 2 * g.lb) * cxT;
       const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, ((size_t)160 << 10) / per_warp));
       size_t smem = (size_t)wpb * per_warp;
@@ -274,7 +283,7 @@ class Engine : public EngineBase {
       ENG_CK(smem_attr((const void*)k_factor<T, StencilProv<T>>, (int)smem));
       int thr = bb >= 1024 ? 512 : 256;
       prof_start(KC_FACTOR, st);
-      k_factor<T, StencilProv<T>><<<ncls_, thr, smem, st>>>(prr_, dm_->cls_code, Dinv_, gws, use_smem, err_);
+      k_factor<T, StencilProv<T>><<<ncls_, thr, smem, st>>>(prr_, dm_->cls_code, Dinv_, gws, use_smem, err_, Gc, Hc);
       prof_stop(KC_FACTOR, st);
       ENG_LAUNCH();
     }
@@ -284,15 +293,16 @@ class Engine : public EngineBase {
       bool formed = false;
       if constexpr (sizeof(T) == 4) {
         const int ncol = g.nD + g.nc, ldE = ((ncol + 31) / 32) * 32;
-        if (g.dim == 3 && tc_nb(g.lb) <= kTcTmemCols) {
-          // 3D FP32: layer products on the tensor cores, 128 columns per CTA, two CTAs per SM
+        if (tc_form) {
+          // layer products on the tensor cores, 128 columns per CTA, one CTA per SM
           const int ntile = (ncol + kTcCols - 1) / kTcCols;
-          const size_t smem = form_tc_smem(g.lb, nbr_count(g.dim));
-          const int grid = std::max(1, std::min(ncls_ * ntile, 2 * nsm_));
+          const size_t smem = form_tc_smem(g.lb);
+          const int grid = std::max(1, std::min(ncls_ * ntile, nsm_));
           ENG_CK(alloc(&Xws, (size_t)grid * g.nl * kTcCols * cxT));
           ENG_CK(smem_attr((const void*)k_form_rr_tc<T>, (int)smem));
           prof_start(KC_FORM, st);
-          k_form_rr_tc<T><<<grid, kTcCols, smem, st>>>(prr_, g, mv_, Dinv_, ncls_, Xws, F_, Frc_, Kcc_, err_ + 3);
+          k_form_rr_tc<T><<<grid, kTcThreads, smem, st>>>(prr_, g, mv_, Dinv_, Gc, Hc, ncls_, Xws, F_, Frc_, Kcc_,
+                                                          err_ + 3);
           prof_stop(KC_FORM, st);
           ENG_LAUNCH();
           formed = true;
@@ -351,6 +361,8 @@ class Engine : public EngineBase {
       ENG_CK(cudaStreamWaitEvent(st, join_, 0));
       ENG_CK(cudaStreamSynchronize(st));
       if (Xws) free_one(Xws);
+      if (Gc) free_one(Gc);
+      if (Hc) free_one(Hc);
       free_one(Xi);
       free_one(Sbase);
       free_one(Dii);

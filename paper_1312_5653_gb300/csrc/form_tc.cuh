@@ -1,63 +1,127 @@
 // Local dual operators F^s, F_rc^s and K~_cc^s (Sec. 5) by multi-column layered solves with the
 // remainder factor, the dense layer products on the tensor cores (tcgen05, 3xTF32).
 //
-// One CTA of 128 threads owns a tile of 128 right-hand-side columns of one class (thread t =
-// column t = accumulator lane t).  The forward and backward sweeps of the block LDL^T solve
-//   forward   V_K = D_K^{-1} (R_K - A_{K,K-1} V_{K-1})
-//   backward  X_K = V_K - D_K^{-1} (A_{K,K+1} X_{K+1})
-// alternate a sparse coupling step, done per column on the CUDA cores from the column's own
-// previous layer, with the dense product by D_K^{-1}, done as one real GEMM per layer:
-//   out[t][2i+c'] = sum_j  W[t][2j+c] * B[2i+c'][2j+c],  B = [[Re D, -Im D], [Im D, Re D]] interleaved,
-// M = 128 columns, N = 2b rounded up to 16, K = 2b in chunks of 8 nodes (16 values, one 64-byte
-// swizzled row).  Each operand is split x = hi + lo into TF32 parts and the product is accumulated
-// in FP32 as hi*hi + hi*lo + lo*hi, which keeps FP32 accuracy.  Chunks are double-buffered in
-// shared memory: the threads build chunk c+1 while the tensor core multiplies chunk c.
-// The column solutions live in a per-CTA global scratch X[node][128] (coalesced per node).
+// With the layer couplings of the factorisation, G_K = D_K^{-1} A_{K,K+1} and
+// H_K = D_K^{-1} A_{K,K-1}, the block LDL^T solve of A_rr X = R is one dense product per layer:
+//   forward   V_0 = D_0^{-1} R_0,   V_K = D_K^{-1} R_K - H_K V_{K-1}
+//   backward  X_{L-1} = V_{L-1},    X_K = V_K - G_K X_{K+1}.
+// One CTA owns a tile of 128 right-hand-side columns of one class: 512 producer threads (column t =
+// accumulator lane t; the four threads t + 128 u share its work) and one issuer warp that only
+// launches the MMAs, so that issuing (which waits for the tensor pipe) never holds up the operand
+// builds.  Per layer the tensor core forms
+//   out[t][2i+c'] = sum_j  Y[t][2j+c] * B[2i+c'][2j+c],  B = -[[Re M, -Im M], [Im M, Re M]] interleaved,
+// M = H_K or G_K, Y = the previous layer of the column (V_{K-1} or X_{K+1}): M = 128 columns,
+// N = 2b rounded up to 16, K = 2b.  Every operand value is split x = hi + lo into TF32 parts and
+// the product accumulates hi*hi + hi*lo + lo*hi in FP32, which keeps FP32 accuracy.  Y stays in
+// shared memory for the whole layer (the operand of the next layer is written by the drain of the
+// accumulator); B is built chunk by chunk (8 nodes = one 64-byte swizzled row per chunk) into two
+// stages, so the threads build chunk c+1 while the tensor core multiplies chunk c.  The layers
+// V_K go to a per-CTA global scratch X[node][128] for the backward sweep and the output.
 #pragma once
 #include "kernels.cuh"
 #include "tc.cuh"
 
 namespace schur {
 
-constexpr int kTcCols = 128;         // columns per tile (MMA M)
-constexpr int kTcTmemCols = 256;     // tensor-memory columns per CTA (accumulator N <= 256)
+constexpr int kTcCols = 128;                // columns per tile (MMA M)
+constexpr int kTcProducers = 512;           // four producer threads per column
+constexpr int kTcThreads = kTcProducers + 32;  // + the MMA issuer warp
+constexpr int kTcTmemCols = 256;            // tensor-memory columns per CTA (accumulator N <= 256)
+constexpr int kTcRhs = 8;                   // nonzeros of one right-hand-side column at most
 constexpr long long kTcWaitLimit = 1LL << 26;
 
 __host__ __device__ inline int tc_nb(int b) { return ((2 * b + 15) / 16) * 16; }
-__host__ __device__ inline int tc_stage_bytes(int b) { return ((2 * 8192 + 2 * 64 * tc_nb(b)) + 1023) & ~1023; }
-// Dynamic shared memory of k_form_rr_tc: 2 operand stages, the layer coupling table, alignment slack.
-__host__ inline size_t form_tc_smem(int b, int nt) {
-  return 1024 + 2 * (size_t)tc_stage_bytes(b) + (size_t)b * nt * (sizeof(cx<float>) + sizeof(int));
+__host__ __device__ inline int tc_bstage_bytes(int b) { return (2 * 64 * tc_nb(b) + 1023) & ~1023; }
+// Dynamic shared memory of k_form_rr_tc: the layer operand (hi/lo, 16 KB per chunk of 8 nodes),
+// two B stages, the slot numbers of one layer, alignment slack.
+__host__ inline size_t form_tc_smem(int b) {
+  return 1024 + (size_t)((b + 7) / 8) * 16384 + 2 * (size_t)tc_bstage_bytes(b) + (size_t)b * sizeof(int);
 }
 
-// Writes the 16 values v (8 complex entries) of one operand row, split into TF32 hi/lo parts.
-__device__ __forceinline__ void tc_put_row(unsigned char* hi, unsigned char* lo, int r, const float* v) {
+// Named barriers: 1, 2 = "B chunk of stage s written" (producers arrive, the issuer waits);
+// 3 = producers only.
+__device__ __forceinline__ void tc_bar_arrive(int id, int n) { asm volatile("bar.arrive %0, %1;\n" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void tc_bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void tc_producers_sync() { tc_bar_sync(3, kTcProducers); }
+
+// Writes 4 values (2 complex entries) as one 16-byte chunk of an operand row, split into TF32 hi/lo.
+__device__ __forceinline__ void tc_put4(unsigned char* hi, unsigned char* lo, uint32_t o, const float* v) {
+  float a[4], c[4];
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    float h[4], l[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) tc::tf32_split(v[4 * p + e], h[e], l[e]);
-    const uint32_t o = tc::sw64_off(r, 4 * p);
-    *reinterpret_cast<float4*>(hi + o) = make_float4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<float4*>(lo + o) = make_float4(l[0], l[1], l[2], l[3]);
+  for (int e = 0; e < 4; ++e) tc::tf32_split(v[e], a[e], c[e]);
+  *reinterpret_cast<float4*>(hi + o) = make_float4(a[0], a[1], a[2], a[3]);
+  *reinterpret_cast<float4*>(lo + o) = make_float4(c[0], c[1], c[2], c[3]);
+}
+
+// Nonzeros of one right-hand-side column (kept in registers: indexed with constants only).
+struct TcRhs {
+  int n[kTcRhs];
+  cx<float> v[kTcRhs];
+  unsigned layers;  // bit K: a nonzero lies in layer K
+};
+
+// Entries j0, j0 + 1 (j0 = 8c + 2p) of row i of a b x b layer matrix M, zero past b.
+__device__ __forceinline__ void tc_load_m(const cx<float>* __restrict__ M, int b, int c, int i, int p, bool has,
+                                          cx<float>* d) {
+  const int j0 = 8 * c + 2 * p;
+  d[0] = has && j0 < b ? M[i * b + j0] : czero<float>();
+  d[1] = has && j0 + 1 < b ? M[i * b + j0 + 1] : czero<float>();
+}
+
+__device__ __forceinline__ void tc_prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p));
+}
+
+// Producer side of one chunk: waits until the stage of chunk gc is free (its MMAs of two chunks
+// ago completed), builds the B chunk (16-byte chunk bp of rows 2 bi, 2 bi + 1 of
+// B = -[[Re M, -Im M], [Im M, Re M]]) from `use`, loads the entries of the next chunk into `nxt`
+// (from Mn, chunk cn) and signals the issuer.  A timed-out wait sets *bad (later waits are skipped).
+__device__ __forceinline__ void tc_produce(int b, int NB, int BS, unsigned char* Bst, uint64_t* bar, unsigned& gc,
+                                           int bi, int bp, bool has_b, const cx<float>* use, cx<float>* nxt,
+                                           const cx<float>* __restrict__ Mn, int cn, volatile int* bad) {
+  const int s = gc & 1;
+  unsigned char* Bh = Bst + s * BS;
+  unsigned char* Bl = Bh + 64 * NB;
+  nxt[0] = czero<float>();
+  nxt[1] = czero<float>();
+  if (Mn) tc_load_m(Mn, b, cn, bi, bp, has_b, nxt);
+  if (gc >= 2 && !*bad && !tc::mbar_wait(&bar[s], ((gc - 2) >> 1) & 1, kTcWaitLimit)) *bad = 1;
+  if (has_b) {
+    const float r0[4] = {-use[0].re, use[0].im, -use[1].re, use[1].im};
+    const float r1[4] = {-use[0].im, -use[0].re, -use[1].im, -use[1].re};
+    tc_put4(Bh, Bl, tc::sw64_off(2 * bi, 4 * bp), r0);
+    tc_put4(Bh, Bl, tc::sw64_off(2 * bi + 1, 4 * bp), r1);
   }
+  tc::fence_proxy_async();
+  tc::fence_before();
+  // after a failure the issuer stops issuing and the producers stop waiting for commits; they then
+  // meet the issuer at every chunk instead of running ahead of it
+  if (*bad) tc_bar_sync(1 + s, kTcThreads);
+  else tc_bar_arrive(1 + s, kTcThreads);
+  ++gc;
 }
 
 template <class T>
-__global__ void __launch_bounds__(kTcCols) k_form_rr_tc(StencilProv<T> P, Geom g, MapsView m,
-                                                        const cx<T>* __restrict__ Dinv, int ncls, cx<T>* Xws,
-                                                        cx<T>* F, cx<T>* Frc, cx<double>* Kcc, int* err) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_form_rr_tc(StencilProv<T> P, Geom g, MapsView m,
+                                                              const cx<T>* __restrict__ Dinv,
+                                                              const cx<T>* __restrict__ Gc,
+                                                              const cx<T>* __restrict__ Hc, int ncls, cx<T>* Xws,
+                                                              cx<T>* F, cx<T>* Frc, cx<double>* Kcc, int* err) {
   static_assert(sizeof(T) == 4, "TF32 tensor-core path: FP32 working precision only");
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-  const int b = P.ly.b, L = P.ly.L, nt = nbr_count(P.ly.dim), dim = g.dim;
-  const int NB = tc_nb(b), SB = tc_stage_bytes(b), nch = (b + 7) / 8;
+  const int b = P.ly.b, L = P.ly.L, dim = g.dim;
+  const int NB = tc_nb(b), nch = (b + 7) / 8;
   const int nD = g.nD, nc = g.nc, ncol = nD + nc, ntile = (ncol + kTcCols - 1) / kTcCols;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  cx<float>* cf = reinterpret_cast<cx<float>*>(sm + 2 * SB);
-  int* nb = reinterpret_cast<int*>(cf + b * nt);
+  const int tid = threadIdx.x, warp = tid >> 5, ct = tid & (kTcCols - 1), qq = tid >> 7;
+  const size_t bb = (size_t)b * b;
+  unsigned char* Ybuf = sm;                       // chunk c: hi at c*16K, lo at c*16K + 8K
+  unsigned char* Bst = sm + (size_t)nch * 16384;  // two B stages (hi, lo)
+  const int BS = tc_bstage_bytes(b);
+  int* ns = reinterpret_cast<int*>(Bst + 2 * BS);  // slot numbers of the drained layer
   __shared__ uint64_t bar[2];
   __shared__ uint32_t tbase;
+  __shared__ volatile int bad;
 
   if (warp == 0) {
     tc::tmem_alloc(&tbase, kTcTmemCols);
@@ -67,202 +131,252 @@ __global__ void __launch_bounds__(kTcCols) k_form_rr_tc(StencilProv<T> P, Geom g
     tc::mbar_init(&bar[0], 1);
     tc::mbar_init(&bar[1], 1);
     tc::mbar_fence_init();
+    bad = 0;
   }
-  // operand rows past 2b are never written again: zero them once in both stages
-  for (int s = 0; s < 2; ++s)
-    for (int e = tid; e < (NB - 2 * b) * 16; e += kTcCols) {
+  // B rows past 2b are never written again: zero them once in both stages
+  for (int st = 0; st < 2; ++st)
+    for (int e = tid; e < (NB - 2 * b) * 16; e += kTcThreads) {
       const int r = 2 * b + e / 16, f = e % 16;
-      *reinterpret_cast<float*>(sm + s * SB + 16384 + tc::sw64_off(r, f)) = 0.f;
-      *reinterpret_cast<float*>(sm + s * SB + 16384 + 64 * NB + tc::sw64_off(r, f)) = 0.f;
+      *reinterpret_cast<float*>(Bst + st * BS + tc::sw64_off(r, f)) = 0.f;
+      *reinterpret_cast<float*>(Bst + st * BS + 64 * NB + tc::sw64_off(r, f)) = 0.f;
     }
   tc::fence_proxy_async();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tbase;
-  const uint32_t tlane = tmem + ((uint32_t)(warp * 32) << 16);
-  const uint32_t idesc = tc::idesc_tf32(kTcCols, NB);
-  cx<float>* X = Xws + (size_t)blockIdx.x * g.nl * kTcCols;
-  int ext[3];
-  local_ext(g, ext);
-  unsigned gc = 0;  // chunks issued so far (stage = gc & 1, per-stage phase = gc >> 1)
-  bool ok = true;
+  const int nwork = ncls * ntile, nphase = 2 * L - 2;
+  const int nmine = (nwork - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;  // items of this CTA
 
-  // One layer product: out = D_K^{-1} * (column values produced by `val(i)` for node i).
-  auto layer_gemm = [&](const cx<float>* D, auto val) -> bool {
-    for (int c = 0; c < nch; ++c) {
-      const int s = gc & 1;
-      const bool timed_out = gc >= 2 && !tc::mbar_wait(&bar[s], ((gc - 2) >> 1) & 1, kTcWaitLimit);
-      unsigned char* Ah = sm + s * SB;
-      unsigned char* Al = Ah + 8192;
-      unsigned char* Bh = Ah + 16384;
-      unsigned char* Bl = Bh + 64 * NB;
-      float v[16];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int i = 8 * c + k;
-        cx<float> w = i < b ? val(i) : czero<float>();
-        v[2 * k] = w.re;
-        v[2 * k + 1] = w.im;
-      }
-      tc_put_row(Ah, Al, tid, v);
-      for (int e = tid; e < 4 * b; e += kTcCols) {
-        const int i = e >> 2, p = e & 3, j0 = 8 * c + 2 * p;
-        const cx<float> d0 = j0 < b ? D[i * b + j0] : czero<float>();
-        const cx<float> d1 = j0 + 1 < b ? D[i * b + j0 + 1] : czero<float>();
-        float r0[4] = {d0.re, -d0.im, d1.re, -d1.im}, r1[4] = {d0.im, d0.re, d1.im, d1.re};
-        float h[4], l[4];
-        uint32_t o = tc::sw64_off(2 * i, 4 * p);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) tc::tf32_split(r0[q], h[q], l[q]);
-        *reinterpret_cast<float4*>(Bh + o) = make_float4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<float4*>(Bl + o) = make_float4(l[0], l[1], l[2], l[3]);
-        o = tc::sw64_off(2 * i + 1, 4 * p);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) tc::tf32_split(r1[q], h[q], l[q]);
-        *reinterpret_cast<float4*>(Bh + o) = make_float4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<float4*>(Bl + o) = make_float4(l[0], l[1], l[2], l[3]);
-      }
-      tc::fence_proxy_async();
-      if (__syncthreads_or(timed_out)) return false;
-      if (tid == 0) {
+  if (warp == kTcProducers / 32) {
+    // ---------------- issuer warp: for every chunk of every GEMM phase, in the producers' order
+    const uint32_t idesc = tc::idesc_tf32(kTcCols, NB);
+    const int lane = tid & 31;
+    unsigned gi = 0;
+    for (long long u = 0; u < (long long)nmine * nphase * nch; ++u) {
+      const int c = (int)(u % nch), s = gi & 1;
+      tc_bar_sync(1 + s, kTcThreads);
+      if (lane == 0 && !bad) {
         tc::fence_after();
-        const int ksteps = (2 * (b - 8 * c) + 7) / 8 < 2 ? (2 * (b - 8 * c) + 7) / 8 : 2;
+        const int left = 2 * (b - 8 * c), ksteps = left >= 16 ? 2 : (left + 7) / 8;
+        const uint32_t ya = tc::smem_u32(Ybuf + (size_t)c * 16384);
+        const uint32_t bh0 = tc::smem_u32(Bst + s * BS), bl0 = bh0 + 64 * NB;
         for (int st = 0; st < ksteps; ++st) {
-          const uint64_t ah = tc::desc_sw64(tc::smem_u32(Ah) + 32 * st);
-          const uint64_t al = tc::desc_sw64(tc::smem_u32(Al) + 32 * st);
-          const uint64_t bh = tc::desc_sw64(tc::smem_u32(Bh) + 32 * st);
-          const uint64_t bl = tc::desc_sw64(tc::smem_u32(Bl) + 32 * st);
+          const uint64_t ah = tc::desc_sw64(ya + 32 * st);
+          const uint64_t al = tc::desc_sw64(ya + 8192 + 32 * st);
+          const uint64_t bh = tc::desc_sw64(bh0 + 32 * st);
+          const uint64_t bl = tc::desc_sw64(bl0 + 32 * st);
           tc::mma_tf32(tmem, ah, bh, idesc, (c > 0 || st > 0) ? 1 : 0);
           tc::mma_tf32(tmem, ah, bl, idesc, 1);
           tc::mma_tf32(tmem, al, bh, idesc, 1);
         }
         tc::commit(&bar[s]);
       }
-      ++gc;
+      __syncwarp();
+      ++gi;
     }
-    const bool timed_out = !tc::mbar_wait(&bar[(gc - 1) & 1], ((gc - 1) >> 1) & 1, kTcWaitLimit);
-    if (__syncthreads_or(timed_out)) return false;
-    tc::fence_after();
-    return true;
-  };
-  // Reads the accumulator row of this column: node values out(i), i < b, passed to `use(i, v)`.
-  auto drain = [&](auto use) {
-    for (int n0 = 0; n0 < 2 * b; n0 += 16) {
-      float v[16];
-      tc::tmem_ld16(tlane + n0, v);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int i = n0 / 2 + k;
-        if (i < b) use(i, mkc<float>(v[2 * k], v[2 * k + 1]));
-      }
-    }
-    tc::fence_before();
-    __syncthreads();
-  };
+  } else {
+    // ---------------- producers
+    const uint32_t tlane = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    cx<float>* X = Xws + (size_t)blockIdx.x * g.nl * kTcCols + ct;  // this column's scratch, stride 128
+    int ext[3];
+    local_ext(g, ext);
+    unsigned gc = 0;  // chunks produced so far (stage = gc & 1, per-stage phase = gc >> 1)
+    // B operand item of this thread: rows 2 bi, 2 bi + 1, 16-byte chunk bp (entries j0, j0 + 1 of row bi)
+    const int bi = tid >> 2, bp = tid & 3;
+    const bool has_b = tid < 4 * b;
+    cx<float> mcur[2] = {czero<float>(), czero<float>()}, maux[2] = {czero<float>(), czero<float>()};
+    // layer matrix of GEMM phase ph (forward K = ph + 1 uses H_K, backward K = 2L - 3 - ph uses G_K)
+    auto phase_m = [&](const cx<float>* Gq, const cx<float>* Hq, int ph) -> const cx<float>* {
+      return ph < L - 1 ? Hq + (size_t)(ph + 1) * bb : Gq + (size_t)(2 * L - 3 - ph) * bb;
+    };
 
-  for (int w = blockIdx.x; w < ncls * ntile && ok; w += gridDim.x) {
-    const int q = w / ntile, col = (w % ntile) * kTcCols + tid;
-    P.select(q, m.cls_code);
-    const int code = P.code;
-    // this column's right-hand side: a unit vector at an interface node, or a column of A_rc
-    int my_node = -1, corner = -1;
-    int lc[3] = {0, 0, 0};
-    if (col < nD) {
-      int l[3];
-      my_node = m.slot_node[col];
-      idx2crd(my_node, ext, dim, l);
-      if (P.removed_l(l)) my_node = -1;
-    } else if (col < ncol) {
-      idx2crd(m.corner_node[col - nD], ext, dim, lc);
-      if (!local_dirichlet(code, lc, g.s, dim)) corner = col - nD;
-    }
-    const cx<float>* Dq = Dinv + (size_t)q * L * b * b;
-    // ---- forward sweep
-    for (int K = 0; K < L && ok; ++K) {
-      if (K > 0) {
-        for (int e = tid; e < b * nt; e += kTcCols) {
-          const int i = e / nt, t = e - i * nt, j = nbr_of(P.ly, i, t);
-          cf[e] = P.Al(K - 1, i, t);
-          nb[e] = j < 0 ? 0 : j;
-        }
-        __syncthreads();
+    // Drain of layer K: x = base(i) + accumulator (none for the first forward layer), written to
+    // the operand buffer (TF32 hi/lo) and to the scratch.  base = D_K^{-1} R_K (forward) or V_K
+    // (backward, read back from the scratch).  Thread u of a column handles chunks u, u + 4, ...
+    // Final layers (every backward layer and the last forward one) also store this column's
+    // entries of F (packed upper triangle; interface columns) or F_rc (corner columns).
+    auto drain = [&](int K, bool fwd, bool acc, const cx<float>* __restrict__ Dk, const TcRhs& R, int col,
+                     cx<float>* Fq, cx<float>* Frcq) {
+      cx<float>* Xk = X + (size_t)K * b * kTcCols;
+      const bool fin = !fwd || K == L - 1;
+      if (fin) {
+        for (int i = tid; i < b; i += kTcProducers) ns[i] = m.node_slot[K * b + i];
       }
-      const cx<float>* Xp = X + (size_t)(K > 0 ? K - 1 : 0) * b * kTcCols + tid;
-      auto val = [&](int i) -> cx<float> {
-        cx<float> r = czero<float>();
-        const int node = K * b + i;
-        if (node == my_node) r.re = 1.f;
-        if (corner >= 0) {
-          int l[3];
-          P.crd(K, i, l);
-          if (!P.removed_l(l)) r = q1_entry(P.st, g.s, l, lc);
-        }
-        if (K > 0)
-          for (int t = 0; t < nt; ++t) cfms(r, cf[i * nt + t], Xp[(size_t)nb[i * nt + t] * kTcCols]);
-        return r;
-      };
-      if (!layer_gemm(Dq + (size_t)K * b * b, val)) {
-        ok = false;
-        break;
-      }
-      cx<float>* Xk = X + (size_t)K * b * kTcCols + tid;
-      drain([&](int i, cx<float> v) { Xk[(size_t)i * kTcCols] = v; });
-    }
-    // ---- backward sweep
-    for (int K = L - 2; K >= 0 && ok; --K) {
-      for (int e = tid; e < b * nt; e += kTcCols) {
-        const int i = e / nt, t = e - i * nt, k = nbr_of(P.ly, i, t);
-        cf[e] = k < 0 ? czero<float>() : P.Al(K, k, nt - 1 - t);
-        nb[e] = k < 0 ? 0 : k;
-      }
-      __syncthreads();
-      const cx<float>* Xn = X + (size_t)(K + 1) * b * kTcCols + tid;
-      auto val = [&](int i) -> cx<float> {
-        cx<float> r = czero<float>();
-        for (int t = 0; t < nt; ++t) cfma(r, cf[i * nt + t], Xn[(size_t)nb[i * nt + t] * kTcCols]);
-        return r;
-      };
-      if (!layer_gemm(Dq + (size_t)K * b * b, val)) {
-        ok = false;
-        break;
-      }
-      cx<float>* Xk = X + (size_t)K * b * kTcCols + tid;
-      drain([&](int i, cx<float> v) { Xk[(size_t)i * kTcCols] = csub(Xk[(size_t)i * kTcCols], v); });
-    }
-    if (!ok) break;
-    // ---- F (packed upper triangle), F_rc and K~_cc of this column
-    const cx<float>* Xc = X + tid;
-    if (col < nD) {
-      cx<float>* Fq = F + (size_t)q * sym_ld(nD);
-      for (int j = 0; j <= col; ++j) Fq[sym_idx(j, col, nD)] = Xc[(size_t)m.slot_node[j] * kTcCols];
-    } else if (col < ncol) {
-      const int c2 = col - nD;
-      for (int j = 0; j < nD; ++j) Frc[((size_t)q * nD + j) * nc + c2] = Xc[(size_t)m.slot_node[j] * kTcCols];
-      for (int c1 = 0; c1 < nc; ++c1) {
-        int l1[3], l2[3];
-        idx2crd(m.corner_node[c1], ext, dim, l1);
-        idx2crd(m.corner_node[c2], ext, dim, l2);
-        cx<float> v = czero<float>();
-        if (!local_dirichlet(code, l1, g.s, dim) && !local_dirichlet(code, l2, g.s, dim)) {
-          if (c1 == c2) v = q1_entry(P.st, g.s, l1, l1);
-          const int noff = dim == 2 ? 9 : 27;
-          for (int o = 0; o < noff; ++o) {
-            int lp[3] = {l1[0] + o % 3 - 1, l1[1] + (o / 3) % 3 - 1, dim == 3 ? l1[2] + o / 9 - 1 : 0};
-            bool in = true;
-            for (int a = 0; a < dim; ++a) in = in && lp[a] >= 0 && lp[a] <= g.s[a];
-            if (!in || (lp[0] == l1[0] && lp[1] == l1[1] && lp[2] == l1[2])) continue;
-            if (P.removed_l(lp)) continue;
-            cfms(v, q1_entry(P.st, g.s, l1, lp), Xc[(size_t)crd2idx(lp, ext, dim) * kTcCols]);
+      tc_producers_sync();
+      for (int gq = qq; gq < nch; gq += 4) {
+        cx<float> x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = czero<float>();
+        if (!fwd) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            if (8 * gq + k < b) x[k] = Xk[(size_t)(8 * gq + k) * kTcCols];
+        } else if (R.layers >> K & 1) {
+          // D_K^{-1} R_K: sum over this column's nonzeros in layer K of value * row n of D_K^{-1}
+#pragma unroll
+          for (int e = 0; e < kTcRhs; ++e) {
+            const int n = R.n[e] - K * b;
+            if (n >= 0 && n < b) {
+              const cx<float>* Dr = Dk + (size_t)n * b;
+#pragma unroll
+              for (int k = 0; k < 8; ++k)
+                if (8 * gq + k < b) cfma(x[k], R.v[e], Dr[8 * gq + k]);
+            }
           }
         }
-        Kcc[((size_t)q * nc + c1) * nc + c2] = ccast<double>(v);
+        if (acc) {
+          float v[16];
+          tc::tmem_ld16(tlane + 16 * gq, v);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) x[k] = mkc<float>(x[k].re + v[2 * k], x[k].im + v[2 * k + 1]);
+        }
+        unsigned char* hi = Ybuf + (size_t)gq * 16384;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const float va[4] = {x[2 * p].re, x[2 * p].im, x[2 * p + 1].re, x[2 * p + 1].im};
+          tc_put4(hi, hi + 8192, tc::sw64_off(ct, 4 * p), va);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int i = 8 * gq + k;
+          if (i < b) {
+            Xk[(size_t)i * kTcCols] = x[k];
+            if (fin) {
+              const int j = ns[i];
+              if (j >= 0) {
+                if (col < nD) {
+                  if (j <= col) Fq[sym_idx(j, col, nD)] = x[k];
+                } else if (col < ncol) {
+                  Frcq[(size_t)j * nc + (col - nD)] = x[k];
+                }
+              }
+            }
+          }
+        }
       }
+      tc::fence_before();
+      tc_producers_sync();  // the slot table is reused by the next drain
+    };
+
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+      const int q = w / ntile, col = (w % ntile) * kTcCols + ct;
+      P.select(q, m.cls_code);
+      const int code = P.code;
+      // nonzeros of this column's right-hand side: a unit vector at an interface node, or the
+      // column of A_rc of a corner (its neighbours in the remainder set)
+      TcRhs R;
+      R.layers = 0;
+#pragma unroll
+      for (int e = 0; e < kTcRhs; ++e) {
+        R.n[e] = -1000000;
+        R.v[e] = czero<float>();
+      }
+      if (col < nD) {
+        int l[3];
+        idx2crd(m.slot_node[col], ext, dim, l);
+        if (!P.removed_l(l)) {
+          R.n[0] = m.slot_node[col];
+          R.v[0] = mkc<float>(1.f, 0.f);
+          R.layers = 1u << (R.n[0] / b);
+        }
+      } else if (col < ncol) {
+        int lc[3];
+        idx2crd(m.corner_node[col - nD], ext, dim, lc);
+        if (!local_dirichlet(code, lc, g.s, dim)) {
+          int k = 0;
+          for (int o = 0; o < (dim == 2 ? 9 : 27); ++o) {
+            int lp[3] = {lc[0] + o % 3 - 1, lc[1] + (o / 3) % 3 - 1, dim == 3 ? lc[2] + o / 9 - 1 : 0};
+            bool in = true;
+            for (int a = 0; a < dim; ++a) in = in && lp[a] >= 0 && lp[a] <= g.s[a];
+            if (!in || P.removed_l(lp)) continue;
+            const int node = crd2idx(lp, ext, dim);
+            const cx<float> a = q1_entry(P.st, g.s, lp, lc);
+#pragma unroll
+            for (int e = 0; e < kTcRhs; ++e)
+              if (e == k) {
+                R.n[e] = node;
+                R.v[e] = a;
+              }
+            R.layers |= 1u << (node / b);
+            ++k;
+          }
+        }
+      }
+      const size_t qoff = (size_t)q * L * bb;
+      const cx<float>* Dq = Dinv + qoff;
+      const cx<float>* Gq = Gc + qoff;
+      const cx<float>* Hq = Hc + qoff;
+      if (w == (int)blockIdx.x && nphase > 0) tc_load_m(phase_m(Gq, Hq, 0), b, 0, bi, bp, has_b, mcur);
+      const int wn = w + (int)gridDim.x;
+      const cx<float>* Mnext =
+          wn < nwork && nphase > 0
+              ? phase_m(Gc + (size_t)(wn / ntile) * L * bb, Hc + (size_t)(wn / ntile) * L * bb, 0)
+              : nullptr;
+      cx<float>* Fq = F + (size_t)q * sym_ld(nD);
+      cx<float>* Frcq = Frc + (size_t)q * nD * nc;
+      // first forward layer: V_0 = D_0^{-1} R_0
+      drain(0, true, false, Dq, R, col, Fq, Frcq);
+      // GEMM phases: forward K = 1..L-1, then backward K = L-2..0
+      for (int ph = 0; ph < nphase; ++ph) {
+        const bool fwd = ph < L - 1;
+        const int K = fwd ? ph + 1 : 2 * L - 3 - ph;
+        const cx<float>* M = phase_m(Gq, Hq, ph);
+        const cx<float>* Mn = ph + 1 < nphase ? phase_m(Gq, Hq, ph + 1) : Mnext;
+        // the next layer matrix (52 KB at b = 81) and, backward, the V_K this drain reads back are
+        // pulled into L2 while the layer is multiplied
+        if (Mn && tid * 16 < (int)bb) tc_prefetch_l2(Mn + (size_t)tid * 16);
+        if (!fwd) {
+          const char* xb = reinterpret_cast<const char*>(X - ct + (size_t)K * b * kTcCols);
+          for (int ln = tid; ln < b * kTcCols * 8 / 128; ln += kTcProducers) tc_prefetch_l2(xb + (size_t)ln * 128);
+        }
+        // chunks in pairs: the entries of chunk c + 1 are loaded into the other register set while
+        // chunk c is built, so no load result is waited for in the chunk that issues it
+        for (int c = 0; c < nch; c += 2) {
+          tc_produce(b, NB, BS, Bst, bar, gc, bi, bp, has_b, mcur, maux, c + 1 < nch ? M : Mn,
+                     c + 1 < nch ? c + 1 : 0, &bad);
+          if (c + 1 >= nch) break;
+          tc_produce(b, NB, BS, Bst, bar, gc, bi, bp, has_b, maux, mcur, c + 2 < nch ? M : Mn,
+                     c + 2 < nch ? c + 2 : 0, &bad);
+        }
+        if (nch & 1) {  // odd chunk count: the next chunk's entries are in maux
+          mcur[0] = maux[0];
+          mcur[1] = maux[1];
+        }
+        // every MMA of this layer has completed once its last chunk's commit has arrived
+        if (!bad && !tc::mbar_wait(&bar[(gc - 1) & 1], ((gc - 1) >> 1) & 1, kTcWaitLimit)) bad = 1;
+        tc::fence_after();
+        drain(K, fwd, true, Dq + (size_t)K * bb, R, col, Fq, Frcq);
+      }
+      // ---- K~_cc of corner columns (F and F_rc were stored by the drains); the four threads of a
+      // column split the rows.  Every value read was written by this column's threads before the
+      // last barrier.
+      if (col >= nD && col < ncol) {
+        const int c2 = col - nD;
+        for (int c1 = qq; c1 < nc; c1 += 4) {
+          int l1[3], l2[3];
+          idx2crd(m.corner_node[c1], ext, dim, l1);
+          idx2crd(m.corner_node[c2], ext, dim, l2);
+          cx<float> v = czero<float>();
+          if (!local_dirichlet(code, l1, g.s, dim) && !local_dirichlet(code, l2, g.s, dim)) {
+            if (c1 == c2) v = q1_entry(P.st, g.s, l1, l1);
+            const int noff = dim == 2 ? 9 : 27;
+            for (int o = 0; o < noff; ++o) {
+              int lp[3] = {l1[0] + o % 3 - 1, l1[1] + (o / 3) % 3 - 1, dim == 3 ? l1[2] + o / 9 - 1 : 0};
+              bool in = true;
+              for (int a = 0; a < dim; ++a) in = in && lp[a] >= 0 && lp[a] <= g.s[a];
+              if (!in || (lp[0] == l1[0] && lp[1] == l1[1] && lp[2] == l1[2])) continue;
+              if (P.removed_l(lp)) continue;
+              cfms(v, q1_entry(P.st, g.s, l1, lp), X[(size_t)crd2idx(lp, ext, dim) * kTcCols]);
+            }
+          }
+          Kcc[((size_t)q * nc + c1) * nc + c2] = ccast<double>(v);
+        }
+      }
+      tc_producers_sync();  // the next item rewrites the operand buffer
     }
+    if (bad && tid == 0) atomicExch(err, 1);
   }
-  if (!ok && tid == 0) atomicExch(err, 1);
-  // every MMA this CTA issued has completed once the last commit has arrived
-  if (tid == 0 && gc > 0) tc::mbar_wait(&bar[(gc - 1) & 1], ((gc - 1) >> 1) & 1, kTcWaitLimit);
   tc::fence_before();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, kTcTmemCols);

@@ -180,8 +180,13 @@ __device__ void gj_invert(cx<T>* A, int b, cx<T>* rc, int* err) {
 // Block LDL^T of one layered problem per block (blockIdx.x = problem).  Writes the L explicit
 // inverses D_K^{-1} (b x b, symmetric) to Dinv + q*L*b*b.  Workspace: 2 b^2 + 2 b entries in
 // shared memory when use_smem, else the (2 b^2 per block) global buffer gws (+2b in shared).
+// Optionally (non-null G, H, same layout as Dinv) also the dense layer couplings of the solve,
+//   G_K = D_K^{-1} A_{K,K+1}  (K < L-1),   H_K = D_K^{-1} A_{K,K-1}  (K > 0),
+// with which forward and backward sweeps become one dense product per layer:
+//   V_K = D_K^{-1} b_K - H_K V_{K-1},   X_K = V_K - G_K X_{K+1}.
 template <class T, class Prov>
-__global__ void k_factor(Prov P, const int* codes, cx<T>* Dinv, cx<T>* gws, int use_smem, int* err) {
+__global__ void k_factor(Prov P, const int* codes, cx<T>* Dinv, cx<T>* gws, int use_smem, int* err,
+                         cx<T>* G = nullptr, cx<T>* H = nullptr) {
   const int q = blockIdx.x;
   P.select(q, codes);
   const int b = P.ly.b, L = P.ly.L, bb = b * b, nt = nbr_count(P.ly.dim);
@@ -220,8 +225,22 @@ __global__ void k_factor(Prov P, const int* codes, cx<T>* Dinv, cx<T>* gws, int 
       out[(size_t)K * bb + e] = W[e];
     }
     __syncthreads();
+    if (H && K > 0) {
+      // H_K[k][j] = sum_t Dt[k][m] A(K, m ; K-1, j), m = nbr(j, t) (the reverse slot of m reaches j)
+      cx<T>* Hk = H + ((size_t)q * L + K) * bb;
+      for (int e = tid; e < bb; e += nthr) {
+        int k = e / b, j = e - k * b;
+        cx<T> acc = mkc<T>(0, 0);
+        for (int t = 0; t < nt; ++t) {
+          int m = nbr_of(P.ly, j, t);
+          if (m >= 0) cfma(acc, Dt[k * b + m], P.Al(K - 1, m, nt - 1 - t));
+        }
+        Hk[e] = acc;
+      }
+    }
     if (K + 1 == L) break;
     // W = D_K^{-1} A_{K,K+1}:  W[k][j] = sum_t Dt[k][nbr(j,t)] A(K+1, j ; K, nbr(j,t))
+    cx<T>* Gk = G ? G + ((size_t)q * L + K) * bb : nullptr;
     for (int e = tid; e < bb; e += nthr) {
       int k = e / b, j = e - k * b;
       cx<T> acc = mkc<T>(0, 0);
@@ -230,6 +249,7 @@ __global__ void k_factor(Prov P, const int* codes, cx<T>* Dinv, cx<T>* gws, int 
         if (m >= 0) cfma(acc, Dt[k * b + m], P.Al(K, j, t));
       }
       W[e] = acc;
+      if (Gk) Gk[e] = acc;
     }
     __syncthreads();
     // D_{K+1} = A_{K+1,K+1} - A_{K+1,K} W

@@ -114,6 +114,8 @@ struct schur_server {
     if (m.dim == 3) nlam *= 2;
     const long long cxb = o.precision == SCHUR_MIXED ? 8 : 16;
     long long ops = nsd * (L * b * b + 2 * nD * nD + 8 * nD) * cxb + nco * nco * cxb;
+    // 3D mixed setup also holds the two layer-coupling arrays of the tensor-core formation
+    if (m.dim == 3 && o.precision == SCHUR_MIXED) ops += 2 * nsd * L * b * b * cxb;
     const long long R = std::min(nrhs, 16);
     long long ws = nsd * nl * R * cxb + nlam * R * (o.max_iter + 5) * cxb + n * R * 32 + nsd * nD * R * 3 * cxb;
     return ops + ws + (64LL << 20);
