@@ -149,32 +149,36 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_form_rr_tc(StencilProv<T> P, 
   const int nmine = (nwork - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;  // items of this CTA
 
   if (warp == kTcProducers / 32) {
-    // ---------------- issuer warp: for every chunk of every GEMM phase, in the producers' order
+    // ---------------- issuer warp: every chunk of every GEMM phase, in the producers' order
     const uint32_t idesc = tc::idesc_tf32(kTcCols, NB);
     const int lane = tid & 31;
+    // descriptors of operand chunk 0 and of the two B stages (start-address field in 16-byte
+    // units: chunk c of Y starts 1024 units further, the lo parts 512 and 4 NB units, the
+    // second K step 2 units)
+    const uint64_t ya0 = tc::desc_sw64(tc::smem_u32(Ybuf));
+    const uint64_t bst[2] = {tc::desc_sw64(tc::smem_u32(Bst)), tc::desc_sw64(tc::smem_u32(Bst + BS))};
+    const uint64_t lo_off = 8192 >> 4, bl_off = (uint64_t)(64 * NB) >> 4, k_off = 32 >> 4;
     unsigned gi = 0;
-    for (long long u = 0; u < (long long)nmine * nphase * nch; ++u) {
-      const int c = (int)(u % nch), s = gi & 1;
-      tc_bar_sync(1 + s, kTcThreads);
-      if (lane == 0 && !bad) {
-        tc::fence_after();
-        const int left = 2 * (b - 8 * c), ksteps = left >= 16 ? 2 : (left + 7) / 8;
-        const uint32_t ya = tc::smem_u32(Ybuf + (size_t)c * 16384);
-        const uint32_t bh0 = tc::smem_u32(Bst + s * BS), bl0 = bh0 + 64 * NB;
-        for (int st = 0; st < ksteps; ++st) {
-          const uint64_t ah = tc::desc_sw64(ya + 32 * st);
-          const uint64_t al = tc::desc_sw64(ya + 8192 + 32 * st);
-          const uint64_t bh = tc::desc_sw64(bh0 + 32 * st);
-          const uint64_t bl = tc::desc_sw64(bl0 + 32 * st);
-          tc::mma_tf32(tmem, ah, bh, idesc, (c > 0 || st > 0) ? 1 : 0);
-          tc::mma_tf32(tmem, ah, bl, idesc, 1);
-          tc::mma_tf32(tmem, al, bh, idesc, 1);
+    for (int it = 0; it < nmine; ++it)
+      for (int ph = 0; ph < nphase; ++ph)
+        for (int c = 0; c < nch; ++c, ++gi) {
+          const int s = gi & 1;
+          tc_bar_sync(1 + s, kTcThreads);  // B chunk c written
+          if (lane == 0 && !bad) {
+            // the first chunk of a layer overwrites the accumulator the drain has just read
+            if (c == 0) tc::fence_after();
+            const int left = 2 * (b - 8 * c), ksteps = left >= 16 ? 2 : (left + 7) / 8;
+            const uint64_t ah = ya0 + (uint64_t)c * (16384 >> 4), bh = bst[s];
+            for (int st = 0; st < ksteps; ++st) {
+              const uint64_t o = (uint64_t)st * k_off;
+              tc::mma_tf32(tmem, ah + o, bh + o, idesc, (c > 0 || st > 0) ? 1 : 0);
+              tc::mma_tf32(tmem, ah + o, bh + bl_off + o, idesc, 1);
+              tc::mma_tf32(tmem, ah + lo_off + o, bh + o, idesc, 1);
+            }
+            tc::commit(&bar[s]);
+          }
+          __syncwarp();
         }
-        tc::commit(&bar[s]);
-      }
-      __syncwarp();
-      ++gi;
-    }
   } else {
     // ---------------- producers
     const uint32_t tlane = tmem + ((uint32_t)((warp & 3) * 32) << 16);
