@@ -51,8 +51,10 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-extra", action="store_true", help="skip the 3D, full-space and serving rows")
     p.add_argument("--serve-requests", type=int, default=200, help="requests in the serving stream")
-    p.add_argument("--ncu-case", action="store_true",
-                   help="one setup + one solve of the headline workload (beta = 1e-4), for profiler captures")
+    p.add_argument("--ncu-case", nargs="?", const="2d", choices=["2d", "3d"],
+                   help="one setup + one solve for profiler captures: 2d = the headline workload (beta = 1e-4); "
+                        "3d = 64^3 Q1 elements in 8^3 subdomains of 8^3 (beta = 1e-6), the layer size of the "
+                        "128^3 workload on 512 subdomains")
     return p.parse_args()
 
 
@@ -389,13 +391,18 @@ def serve_stream(args, S, inputs, oracle):
     return out
 
 
-def ncu_case():
-    """One mixed-precision setup + solve of the headline workload: the profiled unit of work."""
+def ncu_case(which):
+    """One mixed-precision setup + solve: the profiled unit of work (2d: the headline workload;
+    3d: a 64^3 cube with the 8^3 subdomains of the 128^3 workload)."""
     import torch
     from paper_1312_5653_gb300 import inputs
     from paper_1312_5653_gb300 import schur as S
-    yb = torch.from_numpy(inputs.smoothed_noise(2, N_EL, seed=1)).cuda()
-    sol = S.Solver(2, N_EL, 1e-4, nsub=N_SUB, precision=S.SCHUR_MIXED, tol=OUTER_TOL)
+    if which == "3d":
+        yb = torch.from_numpy(inputs.random_modes_3d(64, count=8, seed=2)).cuda()
+        sol = S.Solver(3, 64, 1e-6, nsub=8, precision=S.SCHUR_MIXED, tol=OUTER_TOL)
+    else:
+        yb = torch.from_numpy(inputs.smoothed_noise(2, N_EL, seed=1)).cuda()
+        sol = S.Solver(2, N_EL, 1e-4, nsub=N_SUB, precision=S.SCHUR_MIXED, tol=OUTER_TOL)
     b = sol.schur_apply_mass(yb)
     sol.schur_solve(b)
     torch.cuda.synchronize()
@@ -409,7 +416,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if args.ncu_case:
-        return ncu_case()
+        return ncu_case(args.ncu_case)
     import torch
     from paper_1312_5653_gb300 import inputs
     from paper_1312_5653_gb300 import schur as S
