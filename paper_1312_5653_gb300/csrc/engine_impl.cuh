@@ -718,6 +718,25 @@ class Engine : public EngineBase {
   int local_apply(bool precond, const cx<T>* Op, const cx<T>* v, int R, const int* active, bool want_tc,
                   cudaStream_t st, std::string* msg) {
     const Geom& g = g_;
+    if (R == 1 && g.nD > 128) {
+      // one right-hand side, large blocks: rows streamed with coalesced loads
+      const int thr = 512;
+      const size_t smem = (((size_t)g.nD + 1) & ~(size_t)1) * sizeof(cx<T>) + (size_t)(thr / 32) * g.nD * sizeof(cx<T>);
+      cx<T>* tc = want_tc ? Tc_ : nullptr;
+      if (precond) {
+        ENG_CK(smem_attr((const void*)k_local_apply_rows<T, true>, (int)smem));
+        prof_start(KC_APPLY_S, st);
+        k_local_apply_rows<T, true><<<g.nsd, thr, smem, st>>>(g, mv_, Op, Frc_, v, active, Y_, tc);
+        prof_stop(KC_APPLY_S, st);
+      } else {
+        ENG_CK(smem_attr((const void*)k_local_apply_rows<T, false>, (int)smem));
+        prof_start(KC_APPLY_F, st);
+        k_local_apply_rows<T, false><<<g.nsd, thr, smem, st>>>(g, mv_, Op, Frc_, v, active, Y_, tc);
+        prof_stop(KC_APPLY_F, st);
+      }
+      ENG_LAUNCH();
+      return SCHUR_OK;
+    }
     int thr = std::min(512, ((g.nD + 31) / 32) * 32);
     const size_t xcnt = ((size_t)R * g.nD + 1) & ~(size_t)1;
     const size_t opb = (size_t)sym_ld(g.nD) * sizeof(cx<T>);

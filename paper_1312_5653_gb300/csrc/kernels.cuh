@@ -703,6 +703,79 @@ __global__ void k_local_apply(Geom g, MapsView m, const cx<T>* __restrict__ Op, 
   }
 }
 
+// Single right-hand side, large blocks (3D: nD = 378, 573 KB per packed FP32 operator): the packed
+// upper triangle is streamed row by row with coalesced loads.  Warp w takes rows w, w + W, ...; for
+// row i its lanes read consecutive entries A[i][k], k >= i, and use each twice: the dot product
+// sum_k A[i][k] x_k (-> y_i) and the symmetric update y_k += A[i][k] x_i (k > i) into a per-warp
+// partial vector in shared memory.  The partial vectors are summed at the end.
+template <class T, bool SCALE>
+__global__ void __launch_bounds__(512) k_local_apply_rows(Geom g, MapsView m, const cx<T>* __restrict__ Op,
+                                                          const cx<T>* __restrict__ Frc,
+                                                          const cx<T>* __restrict__ lam,
+                                                          const int* __restrict__ active, cx<T>* Y, cx<T>* Tc) {
+  extern __shared__ __align__(16) unsigned char smla[];
+  const int sd = blockIdx.x, nD = g.nD, tid = threadIdx.x, nthr = blockDim.x, md = g.maxdeg;
+  const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+  cx<T>* x = reinterpret_cast<cx<T>*>(smla);
+  cx<T>* yp = x + ((nD + 1) & ~1);  // [nw][nD] partial results
+  const int q = m.sd_cls[sd];
+  const cx<T>* A = Op + (size_t)q * sym_ld(nD);
+  const bool on = active[0] != 0;
+  for (int j = tid; j < nD; j += nthr) {
+    cx<T> v = czero<T>();
+    if (on) {
+      const int* refs = m.sd_lam + ((size_t)sd * nD + j) * md;
+      for (int k = 0; k < md; ++k) {
+        int ref = refs[k];
+        if (ref > 0) v = cadd(v, lam[ref - 1]);
+        else if (ref < 0) v = csub(v, lam[-ref - 1]);
+      }
+      if (SCALE) v = cscale(v, (T)m.sd_minv[(size_t)sd * nD + j]);
+    }
+    x[j] = v;
+  }
+  for (int e = tid; e < nw * nD; e += nthr) yp[e] = czero<T>();
+  __syncthreads();
+  cx<T>* y = yp + (size_t)warp * nD;
+  for (int i = warp; i < nD; i += nw) {
+    const cx<T>* Ai = A + sym_off(i, nD) - i;  // Ai[k] = A[i][k], k >= i
+    const cx<T> xi = x[i];
+    cx<T> dot = czero<T>();
+#pragma unroll 4
+    for (int k = i + lane; k < nD; k += 32) {
+      const cx<T> a = Ai[k];
+      cfma(dot, a, x[k]);
+      if (k > i) cfma(y[k], a, xi);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      dot.re += __shfl_xor_sync(0xffffffffu, dot.re, o);
+      dot.im += __shfl_xor_sync(0xffffffffu, dot.im, o);
+    }
+    __syncwarp();
+    if (lane == 0) y[i] = cadd(y[i], dot);
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int j = tid; j < nD; j += nthr) {
+    cx<T> s = czero<T>();
+    for (int w = 0; w < nw; ++w) s = cadd(s, yp[(size_t)w * nD + j]);
+    Y[(size_t)sd * nD + j] = s;
+  }
+  if (Tc) {
+    // Tc[c] = sum_j Frc[j][c] x[j]: one warp per corner column
+    const cx<T>* Fr = Frc + (size_t)q * nD * g.nc;
+    for (int c = warp; c < g.nc; c += nw) {
+      cx<T> p = czero<T>();
+      for (int j = lane; j < nD; j += 32) cfma(p, Fr[(size_t)j * g.nc + c], x[j]);
+      for (int o = 16; o > 0; o >>= 1) {
+        p.re += __shfl_xor_sync(0xffffffffu, p.re, o);
+        p.im += __shfl_xor_sync(0xffffffffu, p.im, o);
+      }
+      if (lane == 0) Tc[(size_t)sd * g.nc + c] = p;
+    }
+  }
+}
+
 // out_lambda = sum over sides sigma * scale * (Y + Frc wc):  B (Y + Frc wc) for the dual operator,
 // B_D Y for the preconditioner (SCALE, wc = null).
 template <class T, bool SCALE>
