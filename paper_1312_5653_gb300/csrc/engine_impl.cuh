@@ -277,13 +277,18 @@ class Engine : public EngineBase {
     } else {
       size_t need = (2 * (size_t)bb + 2 * g.lb) * cxT;
       int use_smem = need <= 200 * 1024;
-      size_t smem = use_smem ? need : 2 * g.lb * cxT;
+      // the coupling table of the current layer fits beside the two blocks: FP32 up to two blocks
+      // per SM (113 KB each), FP64 one (up to 227 KB)
+      const size_t tabb = (size_t)g.lb * nbr_count(g.dim) * cxT;
+      const int use_tab = use_smem && need + tabb <= (sizeof(T) == 4 ? (size_t)113 << 10 : (size_t)227 << 10);
+      size_t smem = use_smem ? need + (use_tab ? tabb : 0) : 2 * g.lb * cxT;
       cx<T>* gws = nullptr;
       if (!use_smem) ENG_CK(alloc(&gws, (size_t)ncls_ * 2 * bb * cxT));
       ENG_CK(smem_attr((const void*)k_factor<T, StencilProv<T>>, (int)smem));
       int thr = bb >= 1024 ? 512 : 256;
       prof_start(KC_FACTOR, st);
-      k_factor<T, StencilProv<T>><<<ncls_, thr, smem, st>>>(prr_, dm_->cls_code, Dinv_, gws, use_smem, err_, Gc, Hc);
+      k_factor<T, StencilProv<T>><<<ncls_, thr, smem, st>>>(prr_, dm_->cls_code, Dinv_, gws, use_smem, err_, Gc, Hc,
+                                                            use_tab);
       prof_stop(KC_FACTOR, st);
       ENG_LAUNCH();
     }

@@ -149,28 +149,48 @@ __device__ __forceinline__ bool finite_nonzero(cx<T> p) {
 }
 
 // In-place Gauss-Jordan inversion without pivoting of the b x b matrix A (whole block).
-// rc: 2b scratch entries.  Sets *err on a zero or non-finite pivot.
+// rc: 2b scratch entries.  Sets *err on a zero or non-finite pivot.  With at least b threads,
+// thread (j, g) = (tid mod b, tid div b) updates column j of the rows g, g + Gn, ... (Gn =
+// floor(threads / b)), so no index is divided inside the pivot loop.
 template <class T>
 __device__ void gj_invert(cx<T>* A, int b, cx<T>* rc, int* err) {
-  const int nt = blockDim.x, tid = threadIdx.x, bb = b * b;
+  const int nthr = blockDim.x, tid = threadIdx.x, bb = b * b;
+  const int Gn = nthr / b, j = tid % b, g = tid / b;
   for (int k = 0; k < b; ++k) {
     cx<T> p = A[k * b + k];
     cx<T> piv = cinv(p);
     if (tid == 0 && !finite_nonzero(p)) atomicExch(err, 1);
-    for (int j = tid; j < b; j += nt) {
-      rc[j] = cmul(A[k * b + j], piv);
-      rc[b + j] = A[j * b + k];
+    for (int jj = tid; jj < b; jj += nthr) {
+      rc[jj] = cmul(A[k * b + jj], piv);
+      rc[b + jj] = A[jj * b + k];
     }
     __syncthreads();
-    for (int e = tid; e < bb; e += nt) {
-      int i = e / b, j = e - i * b;
-      if (i == k) {
-        A[e] = (j == k) ? piv : rc[j];
-      } else if (j == k) {
-        cx<T> v = cmul(rc[b + i], piv);
-        A[e] = mkc<T>(-v.re, -v.im);
-      } else {
-        cfms(A[e], rc[b + i], rc[j]);
+    if (Gn >= 1) {
+      if (g < Gn) {
+        const cx<T> rj = rc[j];
+        for (int i = g; i < b; i += Gn) {
+          cx<T>& a = A[i * b + j];
+          if (i == k) {
+            a = (j == k) ? piv : rj;
+          } else if (j == k) {
+            cx<T> v = cmul(rc[b + i], piv);
+            a = mkc<T>(-v.re, -v.im);
+          } else {
+            cfms(a, rc[b + i], rj);
+          }
+        }
+      }
+    } else {
+      for (int e = tid; e < bb; e += nthr) {
+        int i = e / b, jj = e - i * b;
+        if (i == k) {
+          A[e] = (jj == k) ? piv : rc[jj];
+        } else if (jj == k) {
+          cx<T> v = cmul(rc[b + i], piv);
+          A[e] = mkc<T>(-v.re, -v.im);
+        } else {
+          cfms(A[e], rc[b + i], rc[jj]);
+        }
       }
     }
     __syncthreads();
@@ -179,14 +199,17 @@ __device__ void gj_invert(cx<T>* A, int b, cx<T>* rc, int* err) {
 
 // Block LDL^T of one layered problem per block (blockIdx.x = problem).  Writes the L explicit
 // inverses D_K^{-1} (b x b, symmetric) to Dinv + q*L*b*b.  Workspace: 2 b^2 + 2 b entries in
-// shared memory when use_smem, else the (2 b^2 per block) global buffer gws (+2b in shared).
+// shared memory when use_smem (+ b * nbr_count entries for the couplings of the current layer
+// when use_tab), else the (2 b^2 per block) global buffer gws (+2b in shared).
 // Optionally (non-null G, H, same layout as Dinv) also the dense layer couplings of the solve,
 //   G_K = D_K^{-1} A_{K,K+1}  (K < L-1),   H_K = D_K^{-1} A_{K,K-1}  (K > 0),
 // with which forward and backward sweeps become one dense product per layer:
 //   V_K = D_K^{-1} b_K - H_K V_{K-1},   X_K = V_K - G_K X_{K+1}.
+// Matrix loops use the thread -> (column, row group) map of gj_invert when there are at least b
+// threads.
 template <class T, class Prov>
 __global__ void k_factor(Prov P, const int* codes, cx<T>* Dinv, cx<T>* gws, int use_smem, int* err,
-                         cx<T>* G = nullptr, cx<T>* H = nullptr) {
+                         cx<T>* G = nullptr, cx<T>* H = nullptr, int use_tab = 0) {
   const int q = blockIdx.x;
   P.select(q, codes);
   const int b = P.ly.b, L = P.ly.L, bb = b * b, nt = nbr_count(P.ly.dim);
@@ -203,6 +226,20 @@ __global__ void k_factor(Prov P, const int* codes, cx<T>* Dinv, cx<T>* gws, int 
     W = Dt + bb;
     rc = sm;
   }
+  // couplings A(K+1, i ; K, nbr(i, t)) of the current layer K: a shared table or the provider
+  cx<T>* tab = use_tab ? rc + 2 * b : nullptr;
+  auto al = [&](int K, int i, int t) -> cx<T> { return tab ? tab[i * nt + t] : P.Al(K, i, t); };
+  const int Gn = nthr / b, jc = tid % b, gc = tid / b;
+  const bool map2d = Gn >= 1;
+  // visits the entries (i, j) of a b x b matrix owned by this thread
+  auto for_entries = [&](auto f) {
+    if (map2d) {
+      if (gc < Gn)
+        for (int i = gc; i < b; i += Gn) f(i, jc);
+    } else {
+      for (int e = tid; e < bb; e += nthr) f(e / b, e % b);
+    }
+  };
   cx<T>* out = Dinv + (size_t)q * L * bb;
   for (int e = tid; e < bb; e += nthr) Dt[e] = mkc<T>(0, 0);
   __syncthreads();
@@ -214,55 +251,55 @@ __global__ void k_factor(Prov P, const int* codes, cx<T>* Dinv, cx<T>* gws, int 
   __syncthreads();
   for (int K = 0; K < L; ++K) {
     gj_invert(Dt, b, rc, err);
-    for (int e = tid; e < bb; e += nthr) {
-      int i = e / b, j = e - i * b;
-      cx<T> v = cadd(Dt[i * b + j], Dt[j * b + i]);
-      W[e] = cscale(v, T(0.5));
-    }
+    for_entries([&](int i, int j) { W[i * b + j] = cscale(cadd(Dt[i * b + j], Dt[j * b + i]), T(0.5)); });
     __syncthreads();
-    for (int e = tid; e < bb; e += nthr) {
-      Dt[e] = W[e];
-      out[(size_t)K * bb + e] = W[e];
-    }
+    for_entries([&](int i, int j) {
+      const cx<T> v = W[i * b + j];
+      Dt[i * b + j] = v;
+      out[(size_t)K * bb + i * b + j] = v;
+    });
     __syncthreads();
     if (H && K > 0) {
-      // H_K[k][j] = sum_t Dt[k][m] A(K, m ; K-1, j), m = nbr(j, t) (the reverse slot of m reaches j)
+      // H_K[k][j] = sum_t Dt[k][m] A(K, m ; K-1, j), m = nbr(j, t) (the reverse slot of m reaches j);
+      // the table still holds layer K-1
       cx<T>* Hk = H + ((size_t)q * L + K) * bb;
-      for (int e = tid; e < bb; e += nthr) {
-        int k = e / b, j = e - k * b;
+      for_entries([&](int k, int j) {
         cx<T> acc = mkc<T>(0, 0);
         for (int t = 0; t < nt; ++t) {
           int m = nbr_of(P.ly, j, t);
-          if (m >= 0) cfma(acc, Dt[k * b + m], P.Al(K - 1, m, nt - 1 - t));
+          if (m >= 0) cfma(acc, Dt[k * b + m], al(K - 1, m, nt - 1 - t));
         }
-        Hk[e] = acc;
-      }
+        Hk[(size_t)k * b + j] = acc;
+      });
     }
     if (K + 1 == L) break;
+    if (tab) {
+      __syncthreads();  // H has read the previous layer's table
+      for (int e = tid; e < b * nt; e += nthr) tab[e] = P.Al(K, e / nt, e % nt);
+      __syncthreads();
+    }
     // W = D_K^{-1} A_{K,K+1}:  W[k][j] = sum_t Dt[k][nbr(j,t)] A(K+1, j ; K, nbr(j,t))
     cx<T>* Gk = G ? G + ((size_t)q * L + K) * bb : nullptr;
-    for (int e = tid; e < bb; e += nthr) {
-      int k = e / b, j = e - k * b;
+    for_entries([&](int k, int j) {
       cx<T> acc = mkc<T>(0, 0);
       for (int t = 0; t < nt; ++t) {
         int m = nbr_of(P.ly, j, t);
-        if (m >= 0) cfma(acc, Dt[k * b + m], P.Al(K, j, t));
+        if (m >= 0) cfma(acc, Dt[k * b + m], al(K, j, t));
       }
-      W[e] = acc;
-      if (Gk) Gk[e] = acc;
-    }
+      W[k * b + j] = acc;
+      if (Gk) Gk[(size_t)k * b + j] = acc;
+    });
     __syncthreads();
     // D_{K+1} = A_{K+1,K+1} - A_{K+1,K} W
-    for (int e = tid; e < bb; e += nthr) {
-      int i = e / b, j = e - i * b;
+    for_entries([&](int i, int j) {
       int tj = nbr_slot(P.ly, i, j);
       cx<T> acc = tj >= 0 ? P.Ad(K + 1, i, tj) : mkc<T>(0, 0);
       for (int t = 0; t < nt; ++t) {
         int k = nbr_of(P.ly, i, t);
-        if (k >= 0) cfms(acc, P.Al(K, i, t), W[k * b + j]);
+        if (k >= 0) cfms(acc, al(K, i, t), W[k * b + j]);
       }
-      Dt[e] = acc;
-    }
+      Dt[i * b + j] = acc;
+    });
     __syncthreads();
   }
 }
