@@ -69,7 +69,10 @@ typedef struct {
   int max_iter;      /* GMRES iterations per inner solve (Krylov basis size, no restart)  */
   int max_refine;    /* outer refinement steps (each one inner FETI-DP solve)             */
   int local_mode;    /* SCHUR_LOCAL_PER_SUBDOMAIN or SCHUR_LOCAL_SHARED                   */
-  int reserved[5];   /* must be zero                                                      */
+  int tc_split;      /* mixed 3D local operators on the tensor cores (TF32 inputs, FP32
+                        accumulation): 0 or 3 = three products hi*hi + hi*lo + lo*hi of the
+                        split x = hi + lo (FP32 accuracy), 1 = one product (TF32 rounding)     */
+  int reserved[4];   /* must be zero                                                      */
 } schur_opts;
 
 typedef struct {
@@ -94,7 +97,8 @@ typedef struct {
 } schur_info_t;
 
 /* Defaults: nsub = 4 per axis, FP64, tol 1e-12, inner_tol by precision (1e-12 FP64, 3e-5
- * mixed), max_iter 300, max_refine 8, per-subdomain local operators. */
+ * mixed), max_iter 300, max_refine 8, per-subdomain local operators, tc_split 0 (three TF32
+ * products). */
 void schur_default_opts(schur_opts* opts);
 
 /* Builds the solver for one mesh and beta: per-subdomain Q1 assembly of K + i gamma M, batched

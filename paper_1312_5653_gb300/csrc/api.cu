@@ -318,7 +318,9 @@ int schur_setup(const schur_mesh* mesh, double beta, const schur_opts* opts, voi
     return set_error(SCHUR_EINVAL, "unknown local_mode");
   if (!(opts->tol > 0) || opts->max_iter < 1 || opts->max_iter >= kMaxKdev || opts->max_refine < 0)
     return set_error(SCHUR_EINVAL, "tol must be > 0, 1 <= max_iter < 512, max_refine >= 0");
-  for (int i = 0; i < 5; ++i)
+  if (opts->tc_split != 0 && opts->tc_split != 1 && opts->tc_split != 3)
+    return set_error(SCHUR_EINVAL, "tc_split must be 0, 1 or 3");
+  for (int i = 0; i < 4; ++i)
     if (opts->reserved[i]) return set_error(SCHUR_EINVAL, "reserved option fields must be zero");
   double t0 = now_ms();
   schur_ctx* c = new (std::nothrow) schur_ctx();
@@ -339,6 +341,7 @@ int schur_setup(const schur_mesh* mesh, double beta, const schur_opts* opts, voi
     schur_destroy(c);
     return set_error(SCHUR_ENOMEM, "engine allocation failed");
   }
+  c->eng->tc_terms = opts->tc_split == 1 ? 1 : 3;
   rc = c->eng->setup(reinterpret_cast<cudaStream_t>(stream), &msg);
   if (rc) {
     schur_destroy(c);

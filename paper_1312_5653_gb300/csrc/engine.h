@@ -44,6 +44,8 @@ class EngineBase {
                              std::string* msg) = 0;
   // Kernel launches issued by the most recent inner_solve.
   long long launches = 0;
+  // Tensor-core products per layer chunk of the 3D FP32 formation: 3 (TF32 split, FP32 accuracy) or 1.
+  int tc_terms = 3;
 };
 
 constexpr int kMaxR = 16;

@@ -307,7 +307,7 @@ class Engine : public EngineBase {
           ENG_CK(smem_attr((const void*)k_form_rr_tc<T>, (int)smem));
           prof_start(KC_FORM, st);
           k_form_rr_tc<T><<<grid, kTcThreads, smem, st>>>(prr_, g, mv_, Dinv_, Gc, Hc, ncls_, Xws, F_, Frc_, Kcc_,
-                                                          err_ + 3);
+                                                          err_ + 3, tc_terms);
           prof_stop(KC_FORM, st);
           ENG_LAUNCH();
           formed = true;

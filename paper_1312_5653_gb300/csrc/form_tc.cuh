@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_form_rr_tc(StencilProv<T> P, 
                                                               const cx<T>* __restrict__ Dinv,
                                                               const cx<T>* __restrict__ Gc,
                                                               const cx<T>* __restrict__ Hc, int ncls, cx<T>* Xws,
-                                                              cx<T>* F, cx<T>* Frc, cx<double>* Kcc, int* err) {
+                                                              cx<T>* F, cx<T>* Frc, cx<double>* Kcc, int* err,
+                                                              int nterms) {
   static_assert(sizeof(T) == 4, "TF32 tensor-core path: FP32 working precision only");
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
@@ -172,8 +173,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_form_rr_tc(StencilProv<T> P, 
             for (int st = 0; st < ksteps; ++st) {
               const uint64_t o = (uint64_t)st * k_off;
               tc::mma_tf32(tmem, ah + o, bh + o, idesc, (c > 0 || st > 0) ? 1 : 0);
-              tc::mma_tf32(tmem, ah + o, bh + bl_off + o, idesc, 1);
-              tc::mma_tf32(tmem, ah + lo_off + o, bh + o, idesc, 1);
+              if (nterms == 3) {
+                tc::mma_tf32(tmem, ah + o, bh + bl_off + o, idesc, 1);
+                tc::mma_tf32(tmem, ah + lo_off + o, bh + o, idesc, 1);
+              }
             }
             tc::commit(&bar[s]);
           }

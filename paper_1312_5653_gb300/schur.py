@@ -31,7 +31,7 @@ class schur_mesh(ctypes.Structure):
 class schur_opts(ctypes.Structure):
     _fields_ = [("nsub", ctypes.c_int * 3), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
                 ("inner_tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int),
-                ("local_mode", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("local_mode", ctypes.c_int), ("tc_split", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class schur_stats(ctypes.Structure):

@@ -157,6 +157,30 @@ def test_invalid_arguments_are_rejected():
         S.Solver(2, 32, -1.0, nsub=4)
     with pytest.raises(S.SchurError):
         S.Solver(2, 32, 1e-4, nsub=32)  # one element per subdomain: below the 2-element minimum
+    with pytest.raises(S.SchurError) as e:
+        S.Solver(3, 16, 1e-4, nsub=2, precision=S.SCHUR_MIXED, tc_split=2)  # 0, 1 or 3 only
+    assert e.value.code == S.SCHUR_EINVAL
+
+
+@pytest.mark.parametrize("split", [1, 3])
+def test_3d_tensor_core_split(split):
+    """3D, 16^3 Q1 elements in 2^3 subdomains of 8^3: the local operators formed from one TF32
+    product (tc_split = 1, TF32 rounding of the layer operands) or from the three-term split
+    (FP32 accuracy); the FP64 refinement reaches the mixed-precision target either way."""
+    dim, N, P, beta = 3, 16, 2, 1e-6
+    yb = inputs.random_modes_3d(N, count=8, seed=2)
+    b = oracle.apply_M(dim, N, yb)
+    xref = oracle.fd_schur_solve(dim, N, beta, b)
+    sol = S.Solver(dim, N, beta, nsub=P, precision=S.SCHUR_MIXED, tc_split=split)
+    F, _, _ = local_operators(dim, N, P, beta, 0)
+    got = sol.schur_debug_operator(0, 0)
+    err = np.abs(got - F).max() / np.abs(F).max()
+    # three products keep FP32 accuracy; one TF32 product has 10-bit operands
+    assert err <= (2e-5 if split == 3 else 2e-2), err
+    x = sol.schur_solve(gpu(b)).cpu().numpy()
+    print("split", split, "F err", err, sol.last_stats)
+    assert rel(x, xref) <= TOL[S.SCHUR_MIXED], sol.last_stats
+    sol.close()
 
 
 @pytest.mark.parametrize("beta", [1e-2, 1e-4, 1e-6, 1e-8])
