@@ -16,6 +16,29 @@ cudaError_t smem_attr(const void* func, int bytes);
 constexpr int kMaxRdev = 16;   // right-hand sides per FETI-DP solve
 constexpr int kMaxKdev = 512;  // Krylov basis size bound (max_iter < kMaxKdev)
 
+// Programmatic dependent launch: a kernel launched by launch_pdl may start while its predecessor
+// in the stream is still running; it calls pdl_wait() before anything else (which returns once the
+// predecessor has completed and its memory is visible; a no-op for an ordinary launch) and
+// pdl_trigger() to let its own successor start launching.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 template <class R>
 struct alignas(2 * sizeof(R)) cx {
   R re, im;

@@ -711,8 +711,9 @@ class Engine : public EngineBase {
   int coarse_apply(const cx<T>* gv, int R, const int* active, cx<T>* w, cudaStream_t st, std::string* msg) {
     const long long ntile = ctile_count(nct_);
     prof_start(KC_COARSE_APPLY, st);
-    k_coarse_tiles<T><<<(int)((ntile + 3) / 4), 128, 0, st>>>(Kt_, nct_, g_.ncor, gv, R, active, cpu_, cpv_);
-    k_coarse_reduce<T><<<nct_ * R, 512, 0, st>>>(cpu_, cpv_, nct_, g_.ncor, R, active, w);
+    ENG_CK(launch_pdl(k_coarse_tiles<T>, dim3((unsigned)((ntile + 3) / 4)), dim3(128), 0, st, Kt_, nct_, g_.ncor, gv, R,
+                      active, cpu_, cpv_));
+    ENG_CK(launch_pdl(k_coarse_reduce<T>, dim3(nct_ * R), dim3(512), 0, st, cpu_, cpv_, nct_, g_.ncor, R, active, w));
     prof_stop(KC_COARSE_APPLY, st);
     ENG_LAUNCH();
     ENG_LAUNCH();
@@ -731,12 +732,14 @@ class Engine : public EngineBase {
       if (precond) {
         ENG_CK(smem_attr((const void*)k_local_apply_rows<T, true>, (int)smem));
         prof_start(KC_APPLY_S, st);
-        k_local_apply_rows<T, true><<<g.nsd, thr, smem, st>>>(g, mv_, Op, Frc_, v, active, Y_, tc);
+        ENG_CK(launch_pdl(k_local_apply_rows<T, true>, dim3(g.nsd), dim3(thr), smem, st, g, mv_, Op, Frc_, v, active, Y_,
+                          tc));
         prof_stop(KC_APPLY_S, st);
       } else {
         ENG_CK(smem_attr((const void*)k_local_apply_rows<T, false>, (int)smem));
         prof_start(KC_APPLY_F, st);
-        k_local_apply_rows<T, false><<<g.nsd, thr, smem, st>>>(g, mv_, Op, Frc_, v, active, Y_, tc);
+        ENG_CK(launch_pdl(k_local_apply_rows<T, false>, dim3(g.nsd), dim3(thr), smem, st, g, mv_, Op, Frc_, v, active,
+                          Y_, tc));
         prof_stop(KC_APPLY_F, st);
       }
       ENG_LAUNCH();
@@ -753,7 +756,8 @@ class Engine : public EngineBase {
     ENG_CK(smem_attr((const void*)k_local_apply<T, SC, MR>,                                       \
                                 (int)std::max<size_t>(smem, 1)));                                       \
     prof_start(SC ? KC_APPLY_S : KC_APPLY_F, st);                                                      \
-    k_local_apply<T, SC, MR><<<g.nsd, thr, smem, st>>>(g, mv_, Op, Frc_, v, R, active, Y_, tc, stage);         \
+    ENG_CK(launch_pdl(k_local_apply<T, SC, MR>, dim3(g.nsd), dim3(thr), smem, st, g, mv_, Op, Frc_, v, R, active, Y_, \
+                      tc, stage));                                                                                     \
     prof_stop(SC ? KC_APPLY_S : KC_APPLY_F, st);                                                       \
   } while (0)
     if (precond) {
@@ -778,7 +782,8 @@ class Engine : public EngineBase {
     if (rc) return rc;
     long long tot = (long long)R * g_.nlam;
     prof_start(KC_SCATTER, st);
-    k_scatter<T, true><<<(int)((tot + 255) / 256), 256, 0, st>>>(g_, mv_, Y_, nullptr, nullptr, R, active, out);
+    ENG_CK(launch_pdl(k_scatter<T, true>, dim3((unsigned)((tot + 255) / 256)), dim3(256), 0, st, g_, mv_, Y_,
+                      (const cx<T>*)nullptr, (const cx<T>*)nullptr, R, active, out));
     prof_stop(KC_SCATTER, st);
     ENG_LAUNCH();
     return SCHUR_OK;
@@ -795,7 +800,8 @@ class Engine : public EngineBase {
     if (coarse) {
       int tot = R * g_.ncor;
       prof_start(KC_CORNER, st);
-      k_corner_gather<T><<<(tot + 255) / 256, 256, 0, st>>>(g_, Tc_, R, nullptr, 0, nullptr, T(1), gc_);
+      ENG_CK(launch_pdl(k_corner_gather<T>, dim3((tot + 255) / 256), dim3(256), 0, st, g_, Tc_, R,
+                        (const cx<double>*)nullptr, 0, (const cx<T>*)nullptr, T(1), gc_));
       prof_stop(KC_CORNER, st);
       ENG_LAUNCH();
       rc = coarse_apply(gc_, R, active, wc_, st, msg);
@@ -804,16 +810,16 @@ class Engine : public EngineBase {
     if (oa) {
       const int seg = (g_.nlam + oa->nblk - 1) / oa->nblk;
       prof_start(KC_GMRES_DOTS, st);
-      k_scatter_orth_dots<T><<<dim3(oa->nblk, R), 256, (size_t)seg * sizeof(cx<T>), st>>>(
-          g_, mv_, Y_, Frc_, coarse ? wc_ : nullptr, V_, out, R, *oa);
+      ENG_CK(launch_pdl(k_scatter_orth_dots<T>, dim3(oa->nblk, R), dim3(256), (size_t)seg * sizeof(cx<T>), st, g_, mv_,
+                        Y_, Frc_, coarse ? wc_ : nullptr, V_, out, R, *oa));
       prof_stop(KC_GMRES_DOTS, st);
       ENG_LAUNCH();
       return SCHUR_OK;
     }
     long long tot = (long long)R * g_.nlam;
     prof_start(KC_SCATTER, st);
-    k_scatter<T, false><<<(int)((tot + 255) / 256), 256, 0, st>>>(g_, mv_, Y_, Frc_, coarse ? wc_ : nullptr, R, active,
-                                                                  out);
+    ENG_CK(launch_pdl(k_scatter<T, false>, dim3((unsigned)((tot + 255) / 256)), dim3(256), 0, st, g_, mv_, Y_, Frc_,
+                      coarse ? wc_ : nullptr, R, active, out));
     prof_stop(KC_SCATTER, st);
     ENG_LAUNCH();
     return SCHUR_OK;
@@ -878,15 +884,16 @@ class Engine : public EngineBase {
       if (rc) return rc;
       const dim3 og(nblk, R);
       prof_start(KC_GMRES_UPDATE, st);
-      k_orth_update_dots<T><<<og, 256, upd_smem, st>>>(V_, vk1, oa);
+      ENG_CK(launch_pdl(k_orth_update_dots<T>, og, dim3(256), upd_smem, st, V_, vk1, oa));
       prof_stop(KC_GMRES_UPDATE, st);
       ENG_LAUNCH();
       prof_start(KC_GMRES_OTHER, st);
-      k_orth_update_norm<T><<<og, 256, upd_smem, st>>>(V_, vk1, oa);
+      ENG_CK(launch_pdl(k_orth_update_norm<T>, og, dim3(256), upd_smem, st, V_, vk1, oa));
       prof_stop(KC_GMRES_OTHER, st);
       ENG_LAUNCH();
       prof_start(KC_GMRES_OTHER, st);
-      k_scale_vec<T><<<dim3(gs, R), 256, 0, st>>>(vk1, nlam, R, active_, inv_nrm_);
+      ENG_CK(launch_pdl(k_scale_vec<T>, dim3(gs, R), dim3(256), 0, st, vk1, nlam, R, (const int*)active_,
+                        (const double*)inv_nrm_));
       prof_stop(KC_GMRES_OTHER, st);
       ENG_LAUNCH();
       if ((k + 1) % check_every == 0 || k + 1 == m) {

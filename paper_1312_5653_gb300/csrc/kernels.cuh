@@ -425,6 +425,8 @@ __global__ void k_local_rhs(StencilProv<T> P, Geom g, MapsView m, const cx<T>* _
 template <class T>
 __global__ void k_corner_gather(Geom g, const cx<T>* __restrict__ Tc, int R, const cx<double>* __restrict__ f, int ldf,
                                 const cx<T>* __restrict__ add, T sign, cx<T>* out) {
+  pdl_wait();
+  pdl_trigger();
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= R * g.ncor) return;
   int r = e / g.ncor, cI = e - r * g.ncor, dim = g.dim;
@@ -488,6 +490,8 @@ template <class T>
 __global__ void __launch_bounds__(128) k_coarse_tiles(const cx<T>* __restrict__ tiles, int nt, int ncor,
                                                       const cx<T>* __restrict__ gv, int R, const int* __restrict__ active,
                                                       cx<T>* part_u, cx<T>* part_v) {
+  pdl_wait();
+  pdl_trigger();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long t = (long long)blockIdx.x * 4 + warp;
   const long long ntile = ctile_count(nt);
@@ -568,6 +572,8 @@ __global__ void __launch_bounds__(128) k_coarse_tiles(const cx<T>* __restrict__ 
 template <class T>
 __global__ void __launch_bounds__(512) k_coarse_reduce(const cx<T>* __restrict__ part_u, const cx<T>* __restrict__ part_v,
                                                        int nt, int ncor, int R, const int* __restrict__ active, cx<T>* w) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ cx<T> red[16][kCT];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int I = blockIdx.x % nt, r = blockIdx.x / nt;
@@ -629,6 +635,8 @@ template <class T, bool SCALE, int MR>
 __global__ void k_local_apply(Geom g, MapsView m, const cx<T>* __restrict__ Op, const cx<T>* __restrict__ Frc,
                               const cx<T>* __restrict__ lam, int R, const int* __restrict__ active, cx<T>* Y,
                               cx<T>* Tc, int stage) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smla[];
   cx<T>* x = reinterpret_cast<cx<T>*>(smla);
   const int sd = blockIdx.x, nD = g.nD, tid = threadIdx.x, nthr = blockDim.x, md = g.maxdeg;
@@ -713,6 +721,8 @@ __global__ void __launch_bounds__(512) k_local_apply_rows(Geom g, MapsView m, co
                                                           const cx<T>* __restrict__ Frc,
                                                           const cx<T>* __restrict__ lam,
                                                           const int* __restrict__ active, cx<T>* Y, cx<T>* Tc) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smla[];
   const int sd = blockIdx.x, nD = g.nD, tid = threadIdx.x, nthr = blockDim.x, md = g.maxdeg;
   const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
@@ -781,6 +791,8 @@ __global__ void __launch_bounds__(512) k_local_apply_rows(Geom g, MapsView m, co
 template <class T, bool SCALE>
 __global__ void k_scatter(Geom g, MapsView m, const cx<T>* __restrict__ Y, const cx<T>* __restrict__ Frc,
                           const cx<T>* __restrict__ wc, int R, const int* __restrict__ active, cx<T>* out) {
+  pdl_wait();
+  pdl_trigger();
   long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= (long long)R * g.nlam) return;
   int r = (int)(e / g.nlam), lam = (int)(e % g.nlam);
@@ -914,6 +926,8 @@ template <class T>
 __global__ void __launch_bounds__(256) k_scatter_orth_dots(Geom g, MapsView m, const cx<T>* __restrict__ Y,
                                                            const cx<T>* __restrict__ Frc, const cx<T>* __restrict__ wc,
                                                            const cx<T>* __restrict__ V, cx<T>* w, int R, OrthArgs a) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ unsigned char smraw[];
   cx<T>* ws = reinterpret_cast<cx<T>*>(smraw);
   const int r = blockIdx.y;
@@ -940,6 +954,8 @@ __global__ void __launch_bounds__(256) k_scatter_orth_dots(Geom g, MapsView m, c
 
 template <class T>
 __global__ void __launch_bounds__(256) k_orth_update_dots(const cx<T>* __restrict__ V, cx<T>* w, OrthArgs a) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ unsigned char smraw[];
   cx<T>* h = reinterpret_cast<cx<T>*>(smraw);  // k + 1
   cx<T>* ws = h + (a.k + 1);                   // slice
@@ -954,6 +970,8 @@ __global__ void __launch_bounds__(256) k_orth_update_dots(const cx<T>* __restric
 
 template <class T>
 __global__ void __launch_bounds__(256) k_orth_update_norm(const cx<T>* __restrict__ V, cx<T>* w, OrthArgs a) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ unsigned char smraw[];
   cx<T>* h = reinterpret_cast<cx<T>*>(smraw);
   cx<T>* ws = h + (a.k + 1);
@@ -1013,6 +1031,8 @@ __global__ void k_norm2(const cx<T>* __restrict__ w, int nlam, int R, const int*
 
 template <class T>
 __global__ void k_scale_vec(cx<T>* w, int nlam, int R, const int* __restrict__ active, const double* __restrict__ sc) {
+  pdl_wait();
+  pdl_trigger();
   const int r = blockIdx.y;
   if (!active[r]) return;
   T s = (T)sc[r];
