@@ -38,11 +38,10 @@ __host__ inline size_t form_tc_smem(int b) {
   return 1024 + (size_t)((b + 7) / 8) * 16384 + 2 * (size_t)tc_bstage_bytes(b) + (size_t)b * sizeof(int);
 }
 
-// Named barriers: 1, 2 = "B chunk of stage s written" (producers arrive, the issuer waits);
-// 3 = producers only.
-__device__ __forceinline__ void tc_bar_arrive(int id, int n) { asm volatile("bar.arrive %0, %1;\n" ::"r"(id), "r"(n) : "memory"); }
-__device__ __forceinline__ void tc_bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory"); }
-__device__ __forceinline__ void tc_producers_sync() { tc_bar_sync(3, kTcProducers); }
+// Named barrier 1: the producers only (the issuer warp never waits on it).
+__device__ __forceinline__ void tc_producers_sync() {
+  asm volatile("bar.sync 1, %0;\n" ::"n"(kTcProducers) : "memory");
+}
 
 // Writes 4 values (2 complex entries) as one 16-byte chunk of an operand row, split into TF32 hi/lo.
 __device__ __forceinline__ void tc_put4(unsigned char* hi, unsigned char* lo, uint32_t o, const float* v) {
@@ -75,10 +74,13 @@ __device__ __forceinline__ void tc_prefetch_l2(const void* p) {
 // Producer side of one chunk: waits until the stage of chunk gc is free (its MMAs of two chunks
 // ago completed), builds the B chunk (16-byte chunk bp of rows 2 bi, 2 bi + 1 of
 // B = -[[Re M, -Im M], [Im M, Re M]]) from `use`, loads the entries of the next chunk into `nxt`
-// (from Mn, chunk cn) and signals the issuer.  A timed-out wait sets *bad (later waits are skipped).
-__device__ __forceinline__ void tc_produce(int b, int NB, int BS, unsigned char* Bst, uint64_t* bar, unsigned& gc,
-                                           int bi, int bp, bool has_b, const cx<float>* use, cx<float>* nxt,
-                                           const cx<float>* __restrict__ Mn, int cn, volatile int* bad) {
+// (from Mn, chunk cn) and signals the issuer: one arrival per warp on bfull[stage] (16 per chunk)
+// once the warp's writes are visible to the tensor core.  A timed-out wait sets *bad (later waits
+// are skipped).
+__device__ __forceinline__ void tc_produce(int b, int NB, int BS, unsigned char* Bst, uint64_t* bar, uint64_t* bfull,
+                                           unsigned& gc, int bi, int bp, bool has_b, const cx<float>* use,
+                                           cx<float>* nxt, const cx<float>* __restrict__ Mn, int cn,
+                                           volatile int* bad) {
   const int s = gc & 1;
   unsigned char* Bh = Bst + s * BS;
   unsigned char* Bl = Bh + 64 * NB;
@@ -93,11 +95,8 @@ __device__ __forceinline__ void tc_produce(int b, int NB, int BS, unsigned char*
     tc_put4(Bh, Bl, tc::sw64_off(2 * bi + 1, 4 * bp), r1);
   }
   tc::fence_proxy_async();
-  tc::fence_before();
-  // after a failure the issuer stops issuing and the producers stop waiting for commits; they then
-  // meet the issuer at every chunk instead of running ahead of it
-  if (*bad) tc_bar_sync(1 + s, kTcThreads);
-  else tc_bar_arrive(1 + s, kTcThreads);
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) tc::mbar_arrive(&bfull[s]);
   ++gc;
 }
 
@@ -120,7 +119,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_form_rr_tc(StencilProv<T> P, 
   unsigned char* Bst = sm + (size_t)nch * 16384;  // two B stages (hi, lo)
   const int BS = tc_bstage_bytes(b);
   int* ns = reinterpret_cast<int*>(Bst + 2 * BS);  // slot numbers of the drained layer
-  __shared__ uint64_t bar[2];
+  __shared__ uint64_t bar[2];    // stage s: the MMAs of its last chunk completed (tcgen05.commit)
+  __shared__ uint64_t bfull[2];  // stage s: its B chunk written (one arrival per producer warp)
   __shared__ uint32_t tbase;
   __shared__ volatile int bad;
 
@@ -131,6 +131,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_form_rr_tc(StencilProv<T> P, 
   if (tid == 0) {
     tc::mbar_init(&bar[0], 1);
     tc::mbar_init(&bar[1], 1);
+    tc::mbar_init(&bfull[0], kTcProducers / 32);
+    tc::mbar_init(&bfull[1], kTcProducers / 32);
     tc::mbar_fence_init();
     bad = 0;
   }
@@ -164,7 +166,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_form_rr_tc(StencilProv<T> P, 
       for (int ph = 0; ph < nphase; ++ph)
         for (int c = 0; c < nch; ++c, ++gi) {
           const int s = gi & 1;
-          tc_bar_sync(1 + s, kTcThreads);  // B chunk c written
+          if (lane == 0 && !bad && !tc::mbar_wait(&bfull[s], (gi >> 1) & 1, kTcWaitLimit)) bad = 1;
+          __syncwarp();
           if (lane == 0 && !bad) {
             // the first chunk of a layer overwrites the accumulator the drain has just read
             if (c == 0) tc::fence_after();
@@ -340,10 +343,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_form_rr_tc(StencilProv<T> P, 
         // chunks in pairs: the entries of chunk c + 1 are loaded into the other register set while
         // chunk c is built, so no load result is waited for in the chunk that issues it
         for (int c = 0; c < nch; c += 2) {
-          tc_produce(b, NB, BS, Bst, bar, gc, bi, bp, has_b, mcur, maux, c + 1 < nch ? M : Mn,
+          tc_produce(b, NB, BS, Bst, bar, bfull, gc, bi, bp, has_b, mcur, maux, c + 1 < nch ? M : Mn,
                      c + 1 < nch ? c + 1 : 0, &bad);
           if (c + 1 >= nch) break;
-          tc_produce(b, NB, BS, Bst, bar, gc, bi, bp, has_b, maux, mcur, c + 2 < nch ? M : Mn,
+          tc_produce(b, NB, BS, Bst, bar, bfull, gc, bi, bp, has_b, maux, mcur, c + 2 < nch ? M : Mn,
                      c + 2 < nch ? c + 2 : 0, &bad);
         }
         if (nch & 1) {  // odd chunk count: the next chunk's entries are in maux
