@@ -276,7 +276,37 @@ def row_3d(args, torch, S, inputs, oracle, dev, stream):
                     "mdof_s": n / (t_setup + ms_solve / 1e3) / 1e6, "mdof_s_cached": n / (ms_solve / 1e3) / 1e6,
                     "relerr_vs_oracle": err, "gmres_iters": st["iters_total"], "outer_steps": st["outer_steps"],
                     "rel_residual": st["rel_residual"]}
+    out["form_roofline"] = tc_form_roofline(S, N, P, beta)
     return out
+
+
+def tc_form_roofline(S, N, P, beta):
+    """Tensor-pipe roofline of the 3D tensor-core formation (mixed setup, three-product split):
+    executed TF32 MMA flops and useful complex FP32-equivalent flops over the event-timed 'form'
+    category, against the TF32 peak (measured bf16 peak x nominal TF32/bf16 = 1.1/2.25)."""
+    s = N // P
+    nsd, b, L = P ** 3, (s + 1) ** 2, s + 1
+    ncol = 6 * (s - 1) ** 2 + 12 * (s - 1) + 8
+    ntile, nb, ksteps = (ncol + 127) // 128, (2 * b + 15) // 16 * 16, (2 * b + 7) // 8
+    executed = nsd * ntile * (2 * L - 2) * ksteps * 3 * (2 * 128 * nb * 8)
+    useful = nsd * ncol * (2 * L - 2) * b * b * 8
+    S.schur_profile_begin(0x1FFFF)
+    sol = S.Solver(3, N, beta, nsub=P, precision=S.SCHUR_MIXED, tol=OUTER_TOL)
+    prof = S.schur_profile_end()
+    sol.close()
+    ms = prof.get("form", (0, float("nan")))[1]
+    try:
+        bf16 = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops")
+    except Exception:
+        bf16 = None
+    peak = bf16 * 1.1 / 2.25 if bf16 else 1900.0 * 1.1 / 2.25
+    ach = executed / (ms * 1e-3) / 1e12
+    return {"kernel": "k_form_rr_tc", "bound": "tensor", "precision": "tf32 (3-product split)", "ms": ms,
+            "executed_tflop": executed / 1e12, "useful_fp32_tflop": useful / 1e12, "achieved": ach,
+            "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "useful_tflops": useful / (ms * 1e-3) / 1e12,
+            "peak_source": ("measured bf16 %.1f x 1.1/2.25" % bf16) if bf16 else "fallback bf16 1.9 PF x 1.1/2.25",
+            "factor_ms": prof.get("factor", (0, float("nan")))[1]}
 
 
 def row_kkt(args, torch, S, inputs, oracle, dev, stream):
