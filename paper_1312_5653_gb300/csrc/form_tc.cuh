@@ -15,8 +15,10 @@
 // the product accumulates hi*hi + hi*lo + lo*hi in FP32, which keeps FP32 accuracy.  Y stays in
 // shared memory for the whole layer (the operand of the next layer is written by the drain of the
 // accumulator); B is built chunk by chunk (8 nodes = one 64-byte swizzled row per chunk) into two
-// stages, so the threads build chunk c+1 while the tensor core multiplies chunk c.  The layers
-// V_K go to a per-CTA global scratch X[node][128] for the backward sweep and the output.
+// stages, so the threads build chunk c+1 while the tensor core multiplies chunk c: a stage is
+// marked written through an mbarrier (one arrival per producer warp) and free again through the
+// tcgen05.commit of its MMAs.  The layers V_K go to a per-CTA global scratch X[node][128] for the
+// backward sweep and the corner rows; F and F_rc are stored from the drains of the final layers.
 #pragma once
 #include "kernels.cuh"
 #include "tc.cuh"
