@@ -452,6 +452,8 @@ class Engine : public EngineBase {
       if (rc) return rc;
     }
     int iters = 0, conv = 1;
+    // breakdown flags: cleared here too, since a problem without multipliers runs no Krylov loop
+    ENG_CK(cudaMemsetAsync(bad_, 0, kMaxRdev * sizeof(int), st));
     if (g.nlam > 0) {
       long long tot = (long long)R * g.nlam;
       prof_start(KC_SCATTER, st);

@@ -131,8 +131,11 @@ def test_multi_rhs_chunks_and_zero(prec):
     sol.close()
 
 
+# 3D cases of the tensor-core formation: a single 8^3 subdomain (every face Dirichlet), two 8^3
+# subdomains, and boxes of 6 x 4 x 8 elements (layers of 35 nodes, nine layers).
 @pytest.mark.parametrize("nel,nsub", [((12, 8), (3, 2)), ((8, 8), (2, 1)), ((6, 6), (1, 1)), ((6, 8, 4), (3, 2, 2)),
-                                      ((20, 20), (10, 10)), ((24, 16), (2, 2))])
+                                      ((20, 20), (10, 10)), ((24, 16), (2, 2)), ((8, 8, 8), (1, 1, 1)),
+                                      ((16, 8, 8), (2, 1, 1)), ((12, 8, 16), (2, 2, 2))])
 @pytest.mark.parametrize("prec", PRECS)
 def test_ragged_and_degenerate_partitions(nel, nsub, prec):
     """Anisotropic grids, no primal corners (nsub = 1 on an axis), a single subdomain (no
