@@ -723,8 +723,9 @@ class Engine : public EngineBase {
   }
 
   // Y = Op x with x = (scaled) B^T v gathered per subdomain; Tc = Frc^T x when want_tc.
+  // vscale (optional, per right-hand side) multiplies the gathered vector.
   int local_apply(bool precond, const cx<T>* Op, const cx<T>* v, int R, const int* active, bool want_tc,
-                  cudaStream_t st, std::string* msg) {
+                  cudaStream_t st, std::string* msg, const double* vscale = nullptr) {
     const Geom& g = g_;
     if (R == 1 && g.nD > 128) {
       // one right-hand side, large blocks: rows streamed with coalesced loads
@@ -735,13 +736,13 @@ class Engine : public EngineBase {
         ENG_CK(smem_attr((const void*)k_local_apply_rows<T, true>, (int)smem));
         prof_start(KC_APPLY_S, st);
         ENG_CK(launch_pdl(k_local_apply_rows<T, true>, dim3(g.nsd), dim3(thr), smem, st, g, mv_, Op, Frc_, v, active, Y_,
-                          tc));
+                          tc, vscale));
         prof_stop(KC_APPLY_S, st);
       } else {
         ENG_CK(smem_attr((const void*)k_local_apply_rows<T, false>, (int)smem));
         prof_start(KC_APPLY_F, st);
         ENG_CK(launch_pdl(k_local_apply_rows<T, false>, dim3(g.nsd), dim3(thr), smem, st, g, mv_, Op, Frc_, v, active,
-                          Y_, tc));
+                          Y_, tc, vscale));
         prof_stop(KC_APPLY_F, st);
       }
       ENG_LAUNCH();
@@ -759,7 +760,7 @@ class Engine : public EngineBase {
                                 (int)std::max<size_t>(smem, 1)));                                       \
     prof_start(SC ? KC_APPLY_S : KC_APPLY_F, st);                                                      \
     ENG_CK(launch_pdl(k_local_apply<T, SC, MR>, dim3(g.nsd), dim3(thr), smem, st, g, mv_, Op, Frc_, v, R, active, Y_, \
-                      tc, stage));                                                                                     \
+                      tc, stage, vscale));                                                                             \
     prof_stop(SC ? KC_APPLY_S : KC_APPLY_F, st);                                                       \
   } while (0)
     if (precond) {
@@ -778,9 +779,10 @@ class Engine : public EngineBase {
     return SCHUR_OK;
   }
 
-  // out = P^{-1} v  (Dirichlet preconditioner)
-  int precond(const cx<T>* v, int R, const int* active, cx<T>* out, cudaStream_t st, std::string* msg) {
-    int rc = local_apply(true, Sd_, v, R, active, false, st, msg);
+  // out = P^{-1} (diag(vscale) v)  (Dirichlet preconditioner; vscale optional)
+  int precond(const cx<T>* v, int R, const int* active, cx<T>* out, cudaStream_t st, std::string* msg,
+              const double* vscale = nullptr) {
+    int rc = local_apply(true, Sd_, v, R, active, false, st, msg, vscale);
     if (rc) return rc;
     long long tot = (long long)R * g_.nlam;
     prof_start(KC_SCATTER, st);
@@ -874,14 +876,18 @@ class Engine : public EngineBase {
     oa.inv_nrm = inv_nrm_;
     oa.resid = resid_;
     oa.bad = bad_;
+    oa.lazy = 0;
     const int check_every = 4;
     int k = 0;
     for (; k < m; ++k) {
       cx<T>* vk = V_ + k * vstride;
       cx<T>* vk1 = V_ + (k + 1) * vstride;
-      int rc = precond(vk, R, active_, zv_, st, msg);
+      // v_k (k > 0) is normalised lazily: the preconditioner scales what it gathers, and the first
+      // Gram-Schmidt pass scales v_k in place before reading it
+      int rc = precond(vk, R, active_, zv_, st, msg, k > 0 ? inv_nrm_ : nullptr);
       if (rc) return rc;
       oa.k = k;
+      oa.lazy = k > 0 ? 1 : 0;
       rc = dual_apply(zv_, R, active_, vk1, st, msg, &oa);  // with the first Gram-Schmidt dots
       if (rc) return rc;
       const dim3 og(nblk, R);
@@ -891,11 +897,6 @@ class Engine : public EngineBase {
       ENG_LAUNCH();
       prof_start(KC_GMRES_OTHER, st);
       ENG_CK(launch_pdl(k_orth_update_norm<T>, og, dim3(256), upd_smem, st, V_, vk1, oa));
-      prof_stop(KC_GMRES_OTHER, st);
-      ENG_LAUNCH();
-      prof_start(KC_GMRES_OTHER, st);
-      ENG_CK(launch_pdl(k_scale_vec<T>, dim3(gs, R), dim3(256), 0, st, vk1, nlam, R, (const int*)active_,
-                        (const double*)inv_nrm_));
       prof_stop(KC_GMRES_OTHER, st);
       ENG_LAUNCH();
       if ((k + 1) % check_every == 0 || k + 1 == m) {

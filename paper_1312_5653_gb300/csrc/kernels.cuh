@@ -634,7 +634,7 @@ __global__ void k_dual_rhs(Geom g, MapsView m, const cx<T>* __restrict__ VD, con
 template <class T, bool SCALE, int MR>
 __global__ void k_local_apply(Geom g, MapsView m, const cx<T>* __restrict__ Op, const cx<T>* __restrict__ Frc,
                               const cx<T>* __restrict__ lam, int R, const int* __restrict__ active, cx<T>* Y,
-                              cx<T>* Tc, int stage) {
+                              cx<T>* Tc, int stage, const double* __restrict__ vscale) {
   pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smla[];
@@ -664,6 +664,7 @@ __global__ void k_local_apply(Geom g, MapsView m, const cx<T>* __restrict__ Op, 
         else if (ref < 0) v = csub(v, lam[(size_t)r * g.nlam - ref - 1]);
       }
       if (SCALE) v = cscale(v, (T)m.sd_minv[(size_t)sd * nD + j]);
+      if (vscale) v = cscale(v, (T)vscale[r]);
     }
     x[e] = v;
   }
@@ -720,7 +721,8 @@ template <class T, bool SCALE>
 __global__ void __launch_bounds__(512) k_local_apply_rows(Geom g, MapsView m, const cx<T>* __restrict__ Op,
                                                           const cx<T>* __restrict__ Frc,
                                                           const cx<T>* __restrict__ lam,
-                                                          const int* __restrict__ active, cx<T>* Y, cx<T>* Tc) {
+                                                          const int* __restrict__ active, cx<T>* Y, cx<T>* Tc,
+                                                          const double* __restrict__ vscale) {
   pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smla[];
@@ -741,6 +743,7 @@ __global__ void __launch_bounds__(512) k_local_apply_rows(Geom g, MapsView m, co
         else if (ref < 0) v = csub(v, lam[-ref - 1]);
       }
       if (SCALE) v = cscale(v, (T)m.sd_minv[(size_t)sd * nD + j]);
+      if (vscale) v = cscale(v, (T)vscale[0]);
     }
     x[j] = v;
   }
@@ -837,6 +840,8 @@ struct OrthArgs {
   double* inv_nrm;
   double* resid;
   int* bad;
+  // lazy normalisation: V_k still holds w_k unscaled; the first pass scales its slice by inv_nrm
+  int lazy;
 };
 
 __device__ __forceinline__ bool orth_last_block(int* cnt, int nblk) {
@@ -925,7 +930,7 @@ __device__ __forceinline__ void orth_block_update(const cx<T>* __restrict__ V, c
 template <class T>
 __global__ void __launch_bounds__(256) k_scatter_orth_dots(Geom g, MapsView m, const cx<T>* __restrict__ Y,
                                                            const cx<T>* __restrict__ Frc, const cx<T>* __restrict__ wc,
-                                                           const cx<T>* __restrict__ V, cx<T>* w, int R, OrthArgs a) {
+                                                           cx<T>* V, cx<T>* w, int R, OrthArgs a) {
   pdl_wait();
   pdl_trigger();
   extern __shared__ unsigned char smraw[];
@@ -946,6 +951,11 @@ __global__ void __launch_bounds__(256) k_scatter_orth_dots(Geom g, MapsView m, c
     }
     w[(size_t)r * a.nlam + lam] = v;
     ws[i] = v;
+  }
+  if (a.lazy) {  // V_k = w_k / ||w_k||: this block's slice, before the dots read it
+    cx<T>* vk = V + a.k * a.vstride + (size_t)r * a.nlam + lo;
+    const T sc = (T)a.inv_nrm[r];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) vk[i] = cscale(vk[i], sc);
   }
   __syncthreads();
   orth_block_dots(V, a, r, lo, n, ws);
