@@ -299,17 +299,34 @@ class Engine : public EngineBase {
       if constexpr (sizeof(T) == 4) {
         const int ncol = g.nD + g.nc, ldE = ((ncol + 31) / 32) * 32;
         if (tc_form) {
-          // layer products on the tensor cores, 128 columns per CTA, one CTA per SM
-          const int ntile = (ncol + kTcCols - 1) / kTcCols;
+          // layer products on the tensor cores, 128 columns per CTA, one CTA per SM; a last tile of at
+          // most 16 columns (3D 8^3 subdomains: 386 = 3 x 128 + 2) goes to the CUDA-core kernel, so the
+          // tensor pipe does not spend a whole tile on it
+          const int rem = ncol % kTcCols;
+          const int ncol_tc = (rem > 0 && rem <= 16 && ncol > kTcCols) ? ncol - rem : ncol;
+          const int ntile = (ncol_tc + kTcCols - 1) / kTcCols;
           const size_t smem = form_tc_smem(g.lb);
           const int grid = std::max(1, std::min(ncls_ * ntile, nsm_));
           ENG_CK(alloc(&Xws, (size_t)grid * g.nl * kTcCols * cxT));
           ENG_CK(smem_attr((const void*)k_form_rr_tc<T>, (int)smem));
           prof_start(KC_FORM, st);
           k_form_rr_tc<T><<<grid, kTcThreads, smem, st>>>(prr_, g, mv_, Dinv_, Gc, Hc, ncls_, Xws, F_, Frc_, Kcc_,
-                                                          err_ + 3, tc_terms);
+                                                          err_ + 3, tc_terms, ncol_tc);
           prof_stop(KC_FORM, st);
           ENG_LAUNCH();
+          if (ncol_tc < ncol) {
+            const int Cr = ncol - ncol_tc;
+            const int grid2 = std::min(ncls_, 8 * nsm_);
+            cx<T>* Xr = nullptr;
+            ENG_CK(alloc(&Xr, (size_t)grid2 * g.nl * Cr * cxT));
+            const size_t smem2 = 2 * (size_t)g.lb * Cr * cxT;
+            ENG_CK(smem_attr((const void*)k_form_rr<T>, (int)smem2));
+            prof_start(KC_FORM, st);
+            k_form_rr<T><<<grid2, 256, smem2, st>>>(prr_, g, mv_, Dinv_, ncls_, Cr, Xr, F_, Frc_, Kcc_, ncol_tc);
+            prof_stop(KC_FORM, st);
+            ENG_LAUNCH();
+            free_one(Xr);
+          }
           formed = true;
         } else if (g.dim == 2 && g.lb <= 32 && ldE <= 128) {
           const int Bp = g.lb == 9 ? 9 : g.lb == 17 ? 17 : ((g.lb + 7) / 8) * 8;
@@ -357,7 +374,7 @@ class Engine : public EngineBase {
         size_t smem = 2 * (size_t)g.lb * C * cxT;
         ENG_CK(smem_attr((const void*)k_form_rr<T>, (int)smem));
         prof_start(KC_FORM, st);
-        k_form_rr<T><<<grid, 256, smem, st>>>(prr_, g, mv_, Dinv_, ncls_, C, Xws, F_, Frc_, Kcc_);
+        k_form_rr<T><<<grid, 256, smem, st>>>(prr_, g, mv_, Dinv_, ncls_, C, Xws, F_, Frc_, Kcc_, 0);
         prof_stop(KC_FORM, st);
         ENG_LAUNCH();
       }

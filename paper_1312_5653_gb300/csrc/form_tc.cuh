@@ -108,13 +108,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_form_rr_tc(StencilProv<T> P, 
                                                               const cx<T>* __restrict__ Gc,
                                                               const cx<T>* __restrict__ Hc, int ncls, cx<T>* Xws,
                                                               cx<T>* F, cx<T>* Frc, cx<double>* Kcc, int* err,
-                                                              int nterms) {
+                                                              int nterms, int ncol_tc) {
   static_assert(sizeof(T) == 4, "TF32 tensor-core path: FP32 working precision only");
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   const int b = P.ly.b, L = P.ly.L, dim = g.dim;
   const int NB = tc_nb(b), nch = (b + 7) / 8;
-  const int nD = g.nD, nc = g.nc, ncol = nD + nc, ntile = (ncol + kTcCols - 1) / kTcCols;
+  // the first ncol_tc of the nD + nc right-hand-side columns (the rest go to the CUDA-core kernel)
+  const int nD = g.nD, nc = g.nc, ncol = nD + nc, ntile = (ncol_tc + kTcCols - 1) / kTcCols;
   const int tid = threadIdx.x, warp = tid >> 5, ct = tid & (kTcCols - 1), qq = tid >> 7;
   const size_t bb = (size_t)b * b;
   unsigned char* Ybuf = sm;                       // chunk c: hi at c*16K, lo at c*16K + 8K

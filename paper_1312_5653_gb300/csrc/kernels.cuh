@@ -76,18 +76,19 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 
 // ================================================================================= setup
 // F, Frc, Kcc of each class: solve A_rr X = [E_Delta, A_rc] column chunk by chunk.
+// Columns [col_begin, nD + nc) only (the leftover columns of the tensor-core formation's tiles).
 template <class T>
 __global__ void k_form_rr(StencilProv<T> P, Geom g, MapsView m, const cx<T>* __restrict__ Dinv, int ncls, int C,
-                          cx<T>* Xws, cx<T>* F, cx<T>* Frc, cx<double>* Kcc) {
+                          cx<T>* Xws, cx<T>* F, cx<T>* Frc, cx<double>* Kcc, int col_begin) {
   extern __shared__ unsigned char smraw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smraw);
-  const int nD = g.nD, nc = g.nc, ncol = nD + nc, nchunk = (ncol + C - 1) / C;
+  const int nD = g.nD, nc = g.nc, ncol = nD + nc, nchunk = (ncol - col_begin + C - 1) / C;
   const int b = P.ly.b, L = P.ly.L, dim = g.dim, tid = threadIdx.x, nthr = blockDim.x;
   cx<T>* X = Xws + (size_t)blockIdx.x * g.nl * C;
   int ext[3];
   local_ext(g, ext);
   for (int w = blockIdx.x; w < ncls * nchunk; w += gridDim.x) {
-    const int q = w / nchunk, col0 = (w % nchunk) * C;
+    const int q = w / nchunk, col0 = col_begin + (w % nchunk) * C;
     P.select(q, m.cls_code);
     const int code = P.code;
     auto rhs = [&](int K, int i, int c) -> cx<T> {
