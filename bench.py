@@ -287,7 +287,10 @@ def tc_form_roofline(S, N, P, beta):
     s = N // P
     nsd, b, L = P ** 3, (s + 1) ** 2, s + 1
     ncol = 6 * (s - 1) ** 2 + 12 * (s - 1) + 8
-    ntile, nb, ksteps = (ncol + 127) // 128, (2 * b + 15) // 16 * 16, (2 * b + 7) // 8
+    # a last tile of at most 16 columns runs on the CUDA cores (inside the same 'form' category)
+    rem = ncol % 128
+    ncol_tc = ncol - rem if 0 < rem <= 16 and ncol > 128 else ncol
+    ntile, nb, ksteps = (ncol_tc + 127) // 128, (2 * b + 15) // 16 * 16, (2 * b + 7) // 8
     executed = nsd * ntile * (2 * L - 2) * ksteps * 3 * (2 * 128 * nb * 8)
     useful = nsd * ncol * (2 * L - 2) * b * b * 8
     S.schur_profile_begin(0x1FFFF)
