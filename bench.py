@@ -280,19 +280,30 @@ def row_3d(args, torch, S, inputs, oracle, dev, stream):
     return out
 
 
-def tc_form_roofline(S, N, P, beta):
-    """Tensor-pipe roofline of the 3D tensor-core formation (mixed setup, three-product split):
-    executed TF32 MMA flops and useful complex FP32-equivalent flops over the event-timed 'form'
-    category, against the TF32 peak (measured bf16 peak x nominal TF32/bf16 = 1.1/2.25)."""
+def tc_form_counts(N, P):
+    """Work of the 3D tensor-core formation on an N^3 cube in P^3 cubic subdomains: right-hand-side
+    columns per subdomain (interface slots + 8 corners), column tiles run on the tensor pipe (a last
+    tile of at most 16 columns runs on the CUDA cores), accumulator width, K steps of 8 per layer
+    product, executed TF32 MMA flops (three products per step, M = 128) and useful complex
+    FP32-equivalent flops (8 per complex multiply-add) of the 2L - 2 layer products."""
     s = N // P
     nsd, b, L = P ** 3, (s + 1) ** 2, s + 1
     ncol = 6 * (s - 1) ** 2 + 12 * (s - 1) + 8
-    # a last tile of at most 16 columns runs on the CUDA cores (inside the same 'form' category)
     rem = ncol % 128
     ncol_tc = ncol - rem if 0 < rem <= 16 and ncol > 128 else ncol
     ntile, nb, ksteps = (ncol_tc + 127) // 128, (2 * b + 15) // 16 * 16, (2 * b + 7) // 8
     executed = nsd * ntile * (2 * L - 2) * ksteps * 3 * (2 * 128 * nb * 8)
     useful = nsd * ncol * (2 * L - 2) * b * b * 8
+    return {"ncol": ncol, "ncol_tc": ncol_tc, "ntile": ntile, "nb": nb, "ksteps": ksteps, "executed": executed,
+            "useful": useful}
+
+
+def tc_form_roofline(S, N, P, beta):
+    """Tensor-pipe roofline of the 3D tensor-core formation (mixed setup, three-product split):
+    executed TF32 MMA flops and useful complex FP32-equivalent flops over the event-timed 'form'
+    category, against the TF32 peak (measured bf16 peak x nominal TF32/bf16 = 1.1/2.25)."""
+    cnt = tc_form_counts(N, P)
+    executed, useful = cnt["executed"], cnt["useful"]
     S.schur_profile_begin(0x1FFFF)
     sol = S.Solver(3, N, beta, nsub=P, precision=S.SCHUR_MIXED, tol=OUTER_TOL)
     prof = S.schur_profile_end()

@@ -1,0 +1,37 @@
+"""Host-side work models of bench.py (no GPU): the tensor-core formation counts agree with the
+library's partition (interface slots per subdomain) and with a chunk-by-chunk enumeration of the
+kernel's layer products (8 complex K values per operand chunk, two 8-wide K steps per full chunk)."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+from paper_1312_5653_gb300 import schur as S  # noqa: E402
+
+
+@pytest.mark.parametrize("N,P", [(128, 16), (64, 8), (32, 8), (24, 4)])
+def test_tc_form_columns_match_partition(N, P):
+    cnt = bench.tc_form_counts(N, P)
+    info = S.schur_partition(3, N, P)
+    assert cnt["ncol"] == info["n_delta"] + 8
+    assert info["n_local"] == (N // P + 1) ** 3
+
+
+@pytest.mark.parametrize("N,P", [(128, 16), (64, 8), (32, 8)])
+def test_tc_form_executed_flops_by_enumeration(N, P):
+    cnt = bench.tc_form_counts(N, P)
+    s = N // P
+    b, L = (s + 1) ** 2, s + 1
+    steps = 0
+    for c in range((b + 7) // 8):  # operand chunks of one layer product
+        left = 2 * (b - 8 * c)
+        steps += 2 if left >= 16 else (left + 7) // 8
+    assert steps == cnt["ksteps"]
+    per_mma = 2 * 128 * cnt["nb"] * 8
+    assert cnt["executed"] == P ** 3 * cnt["ntile"] * (2 * L - 2) * steps * 3 * per_mma
+    # 128^3 workload: 386 columns = 3 tensor-core tiles + 2 columns on the CUDA cores
+    if (N, P) == (128, 16):
+        assert (cnt["ncol"], cnt["ncol_tc"], cnt["ntile"], cnt["nb"]) == (386, 384, 3, 176)
