@@ -174,7 +174,7 @@ def flush_l2(buf):
 
 
 # FP32 FMA peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz; FP64 at
-# the nominal GB300 figure (its FP64 units are not counted in the tables this build has)
+# the nominal GB300 figure (no FP64 unit count per SM is published for it)
 ALU_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 ALU_FP64_TFLOPS = 1.25
 
