@@ -201,14 +201,18 @@ def algorithmic(cat, info, prec_bytes):
     cb_, cL = int(round(nco ** 0.5)), int(round(nco ** 0.5))  # coarse layer size, layers
     cb = 2 * prec_bytes  # complex entry
     cmac = 8  # real flops of one complex multiply-add
+    packed = ((nD * (nD + 1) // 2) + 1) // 2 * 2  # stored upper triangle of one symmetric block
     if cat == "apply_F":
-        byts = nsd * (nD * nD + nD * nc) * cb + nlam * cb + nsd * (nD + nc) * cb
+        # packed F and F_rc of every subdomain, the multipliers, the outputs Y and T_c
+        byts = nsd * (packed + nD * nc) * cb + nlam * cb + nsd * (nD + nc) * cb
         return "hbm", byts
     if cat == "apply_S":
-        byts = nsd * nD * nD * cb + nlam * cb + nsd * nD * cb
+        byts = nsd * packed * cb + nlam * cb + nsd * nD * cb
         return "hbm", byts
     if cat == "coarse_apply":
-        return "hbm", nco * nco * cb + 2 * nco * cb
+        # upper 32 x 32 tiles of the symmetric coarse inverse, input and output vectors
+        nct = (nco + 31) // 32
+        return "hbm", nct * (nct + 1) // 2 * 1024 * cb + 2 * nco * cb
     if cat == "scatter":
         return "hbm", nlam * cb + 2 * nlam * cb
     if cat == "form":

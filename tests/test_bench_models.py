@@ -35,3 +35,18 @@ def test_tc_form_executed_flops_by_enumeration(N, P):
     # 128^3 workload: 386 columns = 3 tensor-core tiles + 2 columns on the CUDA cores
     if (N, P) == (128, 16):
         assert (cnt["ncol"], cnt["ncol_tc"], cnt["ntile"], cnt["nb"]) == (386, 384, 3, 176)
+
+
+def test_apply_models_count_packed_storage():
+    """The HBM models of the local and coarse applies count the stored (packed) operators: the upper
+    triangle of each symmetric nD x nD block and the upper 32 x 32 tiles of the coarse inverse."""
+    info = S.schur_partition(2, 1024, 64)
+    nsd, nD, nlam, nco = info["n_sub"], info["n_delta"], info["n_lambda"], info["n_coarse"]
+    assert (nsd, nD, nco) == (4096, 60, 63 * 63)
+    cb = 8
+    _, f = bench.algorithmic("apply_F", info, 4)
+    assert f == nsd * (1830 + 60 * 4) * cb + nlam * cb + nsd * 64 * cb
+    _, sb = bench.algorithmic("apply_S", info, 4)
+    assert sb == nsd * 1830 * cb + nlam * cb + nsd * 60 * cb
+    _, c = bench.algorithmic("coarse_apply", info, 4)
+    assert c == (125 * 126 // 2) * 1024 * cb + 2 * nco * cb
