@@ -137,9 +137,13 @@ int schur_apply_mass(schur_ctx* ctx, const double* x_dev, double* y_dev, int nrh
 int schur_apply_stiffness(schur_ctx* ctx, const double* x_dev, double* y_dev, int nrhs, int ld,
                           void* stream);
 
-/* y = S x = K M^{-1} K x + M x / beta in FP64; M^{-1} by Jacobi-preconditioned conjugate
- * gradients to a relative residual of 1e-14 (a diagnostic, not on the solve path).
- * Synchronises. */
+/* y = S x = K M^{-1} K x + M x / beta in FP64 (Sec. 3.1, Eq. schurcomplementsystem); K and M are
+ * matrix-free Q1 stencils, M^{-1} is a fixed-degree Chebyshev iteration with Jacobi scaling on the
+ * Q1 mass spectrum bounds lambda(D^{-1} M) in (2^-d, (3/2)^d), the degree chosen for a relative
+ * error of 1e-15 (a fixed linear operator).  Not on the solve path (used by the refinement tests and
+ * by callers that need S itself).  x_dev, y_dev: n x nrhs, leading dimension ld >= n; only the
+ * first n entries of each column are read or written.  Synchronises.  Errors: EINVAL, ENOMEM
+ * (first call with more columns than before grows the context's workspace), ECUDA. */
 int schur_apply_S(schur_ctx* ctx, const double* x_dev, double* y_dev, int nrhs, int ld, void* stream);
 
 /* y = S x as schur_apply_S, but with no context and no device allocation at all (the paper has no
@@ -153,7 +157,8 @@ int schur_apply_S(schur_ctx* ctx, const double* x_dev, double* y_dev, int nrhs, 
  * The first call on a device looks up the array's device address with that device current; make
  * that first call before any stream capture.  All calls on all streams share the one array and
  * every call overwrites it completely before reading it: calls whose work overlaps on the GPU race
- * and must be ordered by the caller.  Asynchronous on `stream`.  Errors: EINVAL, ECUDA. */
+ * and must be ordered by the caller.  x_dev and y_dev must not overlap (EINVAL).  Asynchronous on
+ * `stream`.  Errors: EINVAL (with a message in schur_last_error), ECUDA. */
 int schur_apply_S_static(const schur_mesh* mesh, double beta, const double* x_dev, double* y_dev, int nrhs, int ld,
                          void* stream);
 

@@ -94,8 +94,13 @@ struct schur_server {
     return op;
   }
 
-  // device bytes a context for mesh m will hold (factors, operators, coarse inverse, workspace),
-  // from closed-form partition counts (no map building), or -1 for an unusable mesh
+  // right-hand-side columns of the largest batch a request can be solved in: batches hold up to
+  // max_batch_rhs columns, or one request alone if it is larger
+  int batch_cols(int nrhs) const { return std::max(nrhs, o.max_batch_rhs); }
+
+  // device bytes a context for mesh m will hold (factors, operators, coarse inverse, workspace for
+  // the largest batch it can serve: the solver works on at most 16 columns at a time), from
+  // closed-form partition counts (no map building), or -1 for an unusable mesh
   long long estimate(const schur_mesh& m, int nrhs) const {
     if (m.dim != 2 && m.dim != 3) return -1;
     long long nsd = 1, nl = 1, ni = 1, n = 1, nco = 1, nlam = 0, L = 1;
@@ -116,7 +121,7 @@ struct schur_server {
     long long ops = nsd * (L * b * b + 2 * nD * nD + 8 * nD) * cxb + nco * nco * cxb;
     // 3D mixed setup also holds the two layer-coupling arrays of the tensor-core formation
     if (m.dim == 3 && o.precision == SCHUR_MIXED) ops += 2 * nsd * L * b * b * cxb;
-    const long long R = std::min(nrhs, 16);
+    const long long R = std::min(batch_cols(nrhs), 16);
     long long ws = nsd * nl * R * cxb + nlam * R * (o.max_iter + 5) * cxb + n * R * 32 + nsd * nD * R * 3 * cxb;
     return ops + ws + (64LL << 20);
   }
@@ -141,18 +146,28 @@ struct schur_server {
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     double *hb = nullptr, *hx = nullptr, *db = nullptr, *dx = nullptr;
     size_t cap = 0;
+    // device bytes of this worker's b/x buffers counted in bytes_used (reserved before growing)
+    long long io_reserved = 0;
     std::unique_lock<std::mutex> lk(mu);
     while (true) {
-      // pick the oldest queued request whose key is not busy and whose memory can be admitted
+      // pick the oldest queued request whose key is not busy and whose memory (context and this
+      // worker's device buffers for its largest batch) can be admitted
       std::shared_ptr<Request> head;
       Entry* ent = nullptr;
       bool need_setup = false;
       long long need = 0;
       while (!stop) {
         for (auto& r : queue) {
+          const long long io = std::max(0LL, 2LL * r->n * batch_cols(r->nrhs) * (long long)sizeof(double) - io_reserved);
           auto it = cache.find(r->key);
           if (it != cache.end()) {
             if (it->second.busy) continue;
+            it->second.busy = 1;  // kept out of eviction while room is made for the buffers
+            const bool ok = make_room(io);
+            it->second.busy = 0;
+            if (!ok) continue;
+            bytes_used += io;
+            io_reserved += io;
             head = r;
             ent = &it->second;
             break;
@@ -163,7 +178,9 @@ struct schur_server {
             head = r;
             break;
           }
-          if (make_room(e)) {
+          if (make_room(e + io)) {
+            bytes_used += io;
+            io_reserved += io;
             head = r;
             need_setup = true;
             need = e;
@@ -264,6 +281,7 @@ struct schur_server {
       }
       finish(batch, rc, &sst);
     }
+    bytes_used -= io_reserved;
     lk.unlock();
     if (hb) cudaFreeHost(hb);
     if (hx) cudaFreeHost(hx);
@@ -335,6 +353,7 @@ int schur_submit(schur_server* s, const schur_mesh* mesh, double beta, const dou
     std::lock_guard<std::mutex> lk(s->mu);
     long long need = s->estimate(*mesh, nrhs);
     if (need < 0) return SCHUR_EINVAL;
+    need += 2LL * n * s->batch_cols(nrhs) * (long long)sizeof(double);  // a worker's b/x buffers
     if (need > (long long)s->o.device_mem_budget) return SCHUR_EBUSY;  // can never be admitted
     r->ticket = s->next_ticket++;
     s->reqs[r->ticket] = r;

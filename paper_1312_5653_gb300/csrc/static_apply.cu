@@ -9,8 +9,10 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <string>
 
 #include "../../include/schur.h"
+#include "api_internal.h"
 #include "outer.h"
 
 namespace schur {
@@ -60,27 +62,44 @@ using namespace schur;
 
 extern "C" int schur_apply_S_static(const schur_mesh* mesh, double beta, const double* x_dev, double* y_dev, int nrhs,
                                     int ld, void* stream) {
-  if (!mesh || (mesh->dim != 2 && mesh->dim != 3) || !(beta > 0) || !std::isfinite(beta) || nrhs < 0)
-    return SCHUR_EINVAL;
+  if (!mesh || (mesh->dim != 2 && mesh->dim != 3)) return set_error(SCHUR_EINVAL, "mesh: dim must be 2 or 3");
+  if (!(beta > 0) || !std::isfinite(beta)) return set_error(SCHUR_EINVAL, "beta must be positive and finite");
+  if (nrhs < 0) return set_error(SCHUR_EINVAL, "nrhs < 0");
   Geom g = Geom();
   g.dim = mesh->dim;
   long long n = 1;
   for (int a = 0; a < 3; ++a) {
     g.nel[a] = a < g.dim ? mesh->nel[a] : 1;
     if (a < g.dim) {
-      if (g.nel[a] < 2) return SCHUR_EINVAL;
+      if (g.nel[a] < 2) return set_error(SCHUR_EINVAL, "mesh: nel must be >= 2 on every axis");
+      // each factor and the running product stay <= 2^20, so the product never overflows
+      const long long na = (long long)g.nel[a] - 1;
+      if (na > kStaticMaxN || n * na > kStaticMaxN)
+        return set_error(SCHUR_EINVAL, "schur_apply_S_static: more than 2^20 interior nodes (its fixed work array)");
       g.h[a] = 1.0 / g.nel[a];
-      n *= g.nel[a] - 1;
+      n *= na;
     } else {
       g.h[a] = 1.0;
     }
   }
   g.n = n;
-  if (n > kStaticMaxN) return SCHUR_EINVAL;  // the fixed scratch holds one vector set of 2^20 nodes
   if (nrhs == 0) return SCHUR_OK;
-  if (!x_dev || !y_dev || (long long)ld < n) return SCHUR_EINVAL;
+  if (!x_dev || !y_dev) return set_error(SCHUR_EINVAL, "null x or y");
+  if ((long long)ld < n) return set_error(SCHUR_EINVAL, "ld < n");
+  {
+    // y = K w is written before M x / beta is added to it, so x and y must not share memory
+    const char* xb = reinterpret_cast<const char*>(x_dev);
+    const char* yb = reinterpret_cast<const char*>(y_dev);
+    const size_t span = ((size_t)(nrhs - 1) * ld + (size_t)n) * sizeof(double);
+    if (xb < yb + span && yb < xb + span) return set_error(SCHUR_EINVAL, "x and y overlap");
+  }
   double* scr = nullptr;
-  if (scratch_for_current_device(&scr) != cudaSuccess) return SCHUR_ECUDA;
+  {
+    cudaError_t e = scratch_for_current_device(&scr);
+    if (e != cudaSuccess)
+      return set_error(SCHUR_ECUDA, std::string("schur_apply_S_static: address of the work array: ") +
+                                        cudaGetErrorString(e));
+  }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   double* t = scr;
   double* w = scr + kStaticMaxN;
@@ -101,11 +120,10 @@ extern "C" int schur_apply_S_static(const schur_mesh* mesh, double beta, const d
     double* yc = y_dev + (size_t)c * ld;
     // t = K x ; r = t (every entry written before it is read, so no clearing is needed)
     k_apply_real<<<dim3(gs, 1), 256, 0, st>>>(g, cf, 1, xc, (int)n, t, (int)n, 1, 1.0, 0.0);
-    if (cudaMemcpyAsync(r, t, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-      return SCHUR_ECUDA;
+    cudaError_t e = cudaMemcpyAsync(r, t, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st);
     double rho = 1.0 / sigma;
-    k_static_cheb<<<gs, 256, 0, st>>>(n, w, r, d, Ad, 0.0, 1.0 / theta, dinv, 1);
-    for (int k = 1; k <= deg; ++k) {
+    if (e == cudaSuccess) k_static_cheb<<<gs, 256, 0, st>>>(n, w, r, d, Ad, 0.0, 1.0 / theta, dinv, 1);
+    for (int k = 1; k <= deg && e == cudaSuccess; ++k) {
       k_apply_real<<<dim3(gs, 1), 256, 0, st>>>(g, cf, 0, d, (int)n, Ad, (int)n, 1, 1.0, 0.0);
       double rho_new = 1.0 / (2.0 * sigma - rho);
       double c1 = rho_new * rho, c2 = 2.0 * rho_new / delta;
@@ -114,9 +132,14 @@ extern "C" int schur_apply_S_static(const schur_mesh* mesh, double beta, const d
       rho = rho_new;
     }
     // y = K w + M x / beta
-    k_apply_real<<<dim3(gs, 1), 256, 0, st>>>(g, cf, 1, w, (int)n, yc, ld, 1, 1.0, 0.0);
-    k_apply_real<<<dim3(gs, 1), 256, 0, st>>>(g, cf, 0, xc, ld, yc, ld, 1, 1.0 / beta, 1.0);
-    if (cudaGetLastError() != cudaSuccess) return SCHUR_ECUDA;
+    if (e == cudaSuccess) {
+      k_apply_real<<<dim3(gs, 1), 256, 0, st>>>(g, cf, 1, w, (int)n, yc, ld, 1, 1.0, 0.0);
+      k_apply_real<<<dim3(gs, 1), 256, 0, st>>>(g, cf, 0, xc, ld, yc, ld, 1, 1.0 / beta, 1.0);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess)
+      return set_error(SCHUR_ECUDA, std::string("schur_apply_S_static: column ") + std::to_string(c) + ": " +
+                                        cudaGetErrorString(e));
   }
   return SCHUR_OK;
 }
