@@ -13,14 +13,19 @@ local operators, coarse factorisation) + schur_solve (FETI-DP GMRES with FP64 re
 refinement); the plain FP64 form and the cached-factor solve rate are reported beside it.
 L2 is flushed (256 MB write) between timed steps.
 
+The roofline reported is that of the single kernel with the largest share of the step, timed by
+CUDA events inside the timed region, against arithmetic peaks measured on the same GPU at the start
+(schur_peak_probe) and the measured HBM copy bandwidth; its DRAM traffic per launch comes from the
+committed ncu summary while the kernel's sources are unchanged.
+
 Further rows in the same JSON line (rank 0, skipped with --no-extra): the 3D precision form
 (128^3, 16^3 subdomains, mixed vs FP64), the full-space KKT form (512^2, MINRES, 8 right-hand
-sides, two betas) and the serving stream (mixed 2D/3D sizes, 6 betas, 1-16 right-hand sides,
-Poisson arrivals at 0.8 x measured capacity; p50/p99 latency, mixed vs FP64 on the first 50
-requests of the same stream).
+sides, two betas) and the serving stream (2000 requests of mixed 2D/3D sizes, 6 betas, 1-16
+right-hand sides, Poisson arrivals at 0.8 x measured capacity; p50/p99 latency and batching
+counters, mixed vs FP64 on the first 60 requests of the same stream).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-extra]
-                  [--serve-requests R]
+                  [--serve-requests R] [--peaks] [--ncu-case 2d|3d]
 """
 import argparse
 import json
@@ -50,7 +55,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-extra", action="store_true", help="skip the 3D, full-space and serving rows")
-    p.add_argument("--serve-requests", type=int, default=200, help="requests in the serving stream")
+    p.add_argument("--serve-requests", type=int, default=2000, help="requests in the serving stream")
+    p.add_argument("--peaks", action="store_true", help="only measure the arithmetic peaks and print them")
     p.add_argument("--ncu-case", nargs="?", const="2d", choices=["2d", "3d"],
                    help="one setup + one solve for profiler captures: 2d = the headline workload (beta = 1e-4); "
                         "3d = 64^3 Q1 elements in 8^3 subdomains of 8^3 (beta = 1e-6), the layer size of the "
@@ -141,13 +147,28 @@ def cpu_oracle_solve(b, beta):
     return x, time.perf_counter() - t0
 
 
+def cpu_model():
+    """The host CPU model name (lscpu), or the machine type."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
 def run_reference(args, rank, world):
-    """The oracle (FP64 fast diagonalisation, single-threaded C) on the host cores."""
+    """The oracle (FP64 fast diagonalisation in C, sine-transform lines on every host core)."""
     if rank != 0:
         return
     import oracle
     from paper_1312_5653_gb300 import inputs
     oracle.build()
+    ncores = os.cpu_count() or 1
+    oracle.set_threads(ncores)
     yb = inputs.smoothed_noise(2, N_EL, seed=1)
     b = oracle.apply_M(2, N_EL, yb)
     n = b.size
@@ -162,9 +183,10 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_dofs": n, "beta": list(BETAS), "nrhs_per_step": 1},
-            "cpu_baseline": {"value": val, "unit": "MDoF/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": val, "unit": "MDoF/s", "cores": ncores, "kind": "oracle",
+                             "cpu_model": cpu_model(),
                              "sample": "one full-size right-hand side per step, fast-diagonalisation oracle "
-                                       "(dense sine transforms), single thread"},
+                                       "(dense sine transforms, lines shared over %d OpenMP threads)" % ncores},
             "e2e": {"value": val, "unit": "MDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -173,10 +195,20 @@ def flush_l2(buf):
     buf.add_(1.0)
 
 
-# FP32 FMA peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz; FP64 at
-# the nominal GB300 figure (no FP64 unit count per SM is published for it)
-ALU_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-ALU_FP64_TFLOPS = 1.25
+# iterations of each arithmetic peak probe (a few milliseconds each on a GB300)
+PEAK_ITERS = {0: 100, 1: 2000, 2: 100, 3: 50000}
+
+
+def measure_peaks(S, peaks_file):
+    """Arithmetic peaks measured on this GPU (schur_peak_probe: FP64 FMA, FP32 FMA, FP64 tensor
+    MMA, TF32 tcgen05 MMA; best of three) and the HBM copy bandwidth of MEASURED_PEAKS.json."""
+    out = {}
+    for kind, name in S.PEAK_KINDS.items():
+        out[name] = max(S.schur_peak_probe(kind, PEAK_ITERS[kind]) for _ in range(3))
+    out["unit"] = "TFLOP/s"
+    out["hbm_gbs"] = peaks_file.get("hbm_gbs")
+    out["source"] = "schur_peak_probe on this GPU (best of 3); hbm_gbs from MEASURED_PEAKS.json"
+    return out
 
 
 def bcr_tasks(L):
@@ -237,12 +269,90 @@ def algorithmic(cat, info, prec_bytes):
     return None, None
 
 
+CATEGORIES = ["factor", "form", "coarse_setup", "local_rhs", "apply_F", "apply_S", "scatter", "coarse_apply",
+              "corner", "gmres_dots", "gmres_update", "gmres_other", "recover", "assemble_z", "residual",
+              "coarse_inverse", "interior"]
+# profiling categories that hold exactly one kernel on the 2D mixed workload (16^2-element
+# subdomains: layer size 17, 60 interface slots, one right-hand side)
+KERNEL_OF = {"form": "k_form_rr_cols<float, 17>", "apply_F": "k_local_apply<float, 0, 1>",
+             "apply_S": "k_local_apply<float, 1, 1>", "assemble_z": "k_assemble_z<float>"}
+# source files whose contents determine each kernel (a recorded DRAM traffic figure is used only
+# while their hash is the one recorded with it)
+KERNEL_SOURCES = {"k_form_rr_cols<float, 17>": ["warp.cuh", "common.cuh"],
+                  "k_local_apply<float, 0, 1>": ["kernels.cuh", "common.cuh"],
+                  "k_local_apply<float, 1, 1>": ["kernels.cuh", "common.cuh"],
+                  "k_assemble_z<float>": ["kernels.cuh", "common.cuh"]}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic_2d_1024_mixed.md")
+
+
+def kernel_source_hash(kernel):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES.get(kernel, []):
+        with open(os.path.join(ROOT, "paper_1312_5653_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, path=TRAFFIC_FILE):
+    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu summary, or None when
+    there is none or the kernel's sources changed since it was captured.  Rows of the summary:
+    | `kernel` | launches | dram bytes per launch | source hash |"""
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    for ln in lines:
+        f = [t.strip() for t in ln.strip().strip("|").split("|")]
+        if len(f) >= 4 and f[0] == "`%s`" % kernel:
+            try:
+                byts = float(f[2].replace(",", ""))
+            except ValueError:
+                return None
+            return byts if f[3].strip("`") == kernel_source_hash(kernel) else None
+    return None
+
+
+def category_roofline(cat, info, launches, total_ms, steps, peaks):
+    """Roofline of one profiling category: algorithmic bytes (HBM-bound) or flops (ALU-bound) per
+    launch over the event-timed average launch, against the measured peak of its bound."""
+    prec_bytes = 4
+    bound, algo = algorithmic(cat, info, prec_bytes)
+    if bound is None or launches == 0:
+        return None
+    per_step = launches / steps
+    if bound == "hbm":
+        avg_s = total_ms / launches / 1e3
+        ach = algo / avg_s / 1e9
+        peak = peaks.get("hbm_gbs") or 6800.0
+        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                "launches": launches, "avg_us": avg_s * 1e6, "algorithmic_bytes_per_launch": algo,
+                "peak_source": "measured copy (MEASURED_PEAKS.json)" if peaks.get("hbm_gbs") else "fallback"}
+    # ALU categories: the model counts one step's work, spread over its launches
+    avg_s = total_ms / launches / 1e3
+    per_launch = algo / per_step
+    is64 = cat in ("coarse_setup",)
+    pk = peaks.get("fp64_fma" if is64 else "fp32_fma")
+    ach = per_launch / avg_s / 1e12
+    out = {"bound": "alu", "precision": "fp64" if is64 else "fp32", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+           "frac": ach / pk if pk else None, "traffic": None, "launches": launches, "avg_us": avg_s * 1e6,
+           "algorithmic_flops_per_launch": per_launch,
+           "peak_source": "measured %s FMA (schur_peak_probe)" % ("FP64" if is64 else "FP32")}
+    if cat == "form":
+        # the bytes it must move: read D^-1 of every subdomain, write packed F, F_rc and K_cc
+        nsd, nD, b = info["n_sub"], info["n_delta"], int(round(info["n_local"] ** 0.5))
+        packed = ((nD * (nD + 1) // 2) + 1) // 2 * 2
+        out["algorithmic_bytes_per_launch"] = (nsd * (b * b * b + packed + nD * 4) * 2 * prec_bytes +
+                                               nsd * 16 * 16) / per_step
+    return out
+
+
 # ------------------------------------------------------------------ further measured rows
 def _events(torch, stream):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def row_3d(args, torch, S, inputs, oracle, dev, stream):
+def row_3d(args, torch, S, inputs, oracle, dev, stream, peaks):
     """Precision form: 3D, 128^3 Q1 elements, 16^3 subdomains of 8^3, beta = 1e-6, 8 sine modes;
     setup + one solve, mixed (refined to 1e-10) and plain FP64, error against the oracle."""
     N, P, beta = 128, 16, 1e-6
@@ -280,7 +390,7 @@ def row_3d(args, torch, S, inputs, oracle, dev, stream):
                     "mdof_s": n / (t_setup + ms_solve / 1e3) / 1e6, "mdof_s_cached": n / (ms_solve / 1e3) / 1e6,
                     "relerr_vs_oracle": err, "gmres_iters": st["iters_total"], "outer_steps": st["outer_steps"],
                     "rel_residual": st["rel_residual"]}
-    out["form_roofline"] = tc_form_roofline(S, N, P, beta)
+    out["form_roofline"] = tc_form_roofline(S, N, P, beta, peaks)
     return out
 
 
@@ -302,10 +412,10 @@ def tc_form_counts(N, P):
             "useful": useful}
 
 
-def tc_form_roofline(S, N, P, beta):
+def tc_form_roofline(S, N, P, beta, peaks):
     """Tensor-pipe roofline of the 3D tensor-core formation (mixed setup, three-product split):
     executed TF32 MMA flops and useful complex FP32-equivalent flops over the event-timed 'form'
-    category, against the TF32 peak (measured bf16 peak x nominal TF32/bf16 = 1.1/2.25)."""
+    category, against the TF32 tcgen05 peak measured by schur_peak_probe."""
     cnt = tc_form_counts(N, P)
     executed, useful = cnt["executed"], cnt["useful"]
     S.schur_profile_begin(0x1FFFF)
@@ -313,23 +423,23 @@ def tc_form_roofline(S, N, P, beta):
     prof = S.schur_profile_end()
     sol.close()
     ms = prof.get("form", (0, float("nan")))[1]
-    try:
-        bf16 = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops")
-    except Exception:
-        bf16 = None
-    peak = bf16 * 1.1 / 2.25 if bf16 else 1900.0 * 1.1 / 2.25
+    peak = peaks["tf32_tcgen05"]
     ach = executed / (ms * 1e-3) / 1e12
     return {"kernel": "k_form_rr_tc", "bound": "tensor", "precision": "tf32 (3-product split)", "ms": ms,
             "executed_tflop": executed / 1e12, "useful_fp32_tflop": useful / 1e12, "achieved": ach,
             "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
             "useful_tflops": useful / (ms * 1e-3) / 1e12,
-            "peak_source": ("measured bf16 %.1f x 1.1/2.25" % bf16) if bf16 else "fallback bf16 1.9 PF x 1.1/2.25",
+            "peak_source": "measured tcgen05 kind::tf32 128x256x8 (schur_peak_probe)",
+            "useful_frac_of_fp32_fma": useful / (ms * 1e-3) / 1e12 / peaks["fp32_fma"],
             "factor_ms": prof.get("factor", (0, float("nan")))[1]}
 
 
 def row_kkt(args, torch, S, inputs, oracle, dev, stream):
     """Full-space form: 2D 512^2, 32 x 32 subdomains, MINRES with P_mgw on 8 right-hand sides
-    (M y_bar_k, 0, 0), y_bar_k = smoothed noise seeds 10..17, to 1e-10; per beta."""
+    (M y_bar_k, 0, 0), y_bar_k = smoothed noise seeds 10..17, to 1e-10; per beta, with the exact
+    Schur block (S by the complex factorisation of Sec. 4) and with the Pearson-Wathen S_p of
+    Sec. 3.2 (two real FETI-DP solves per application): MINRES iterations, S-block applications
+    (one per iteration plus the initial one) and time, the analogue of the paper's Table 7."""
     N, P = 512, 32
     n = (N - 1) ** 2
     yb = inputs.smoothed_noise(2, N, seed=10, nrhs=8)
@@ -339,37 +449,95 @@ def row_kkt(args, torch, S, inputs, oracle, dev, stream):
     rd = torch.from_numpy(rhs).to(dev)
     out = {"workload": "2d-q1-512x512-32x32sub-kkt-minres-8rhs", "n_dofs_per_block": n, "nrhs": 8}
     # first use of the multi-right-hand-side kernels and workspaces outside the timed runs
-    sol = S.Solver(2, N, 1e-4, nsub=P, precision=S.SCHUR_MIXED, tol=OUTER_TOL)
-    sol.schur_kkt_minres(rd, tol=1e-10, max_it=60)
-    sol.close()
+    for factor in (S.SCHUR_FACTOR_EXACT, S.SCHUR_FACTOR_PW):
+        sol = S.Solver(2, N, 1e-4, nsub=P, precision=S.SCHUR_MIXED, tol=OUTER_TOL, factor=factor)
+        sol.schur_kkt_minres(rd, tol=1e-10, max_it=80)
+        sol.close()
     torch.cuda.synchronize()
     for beta in (1e-4, 1e-8):
         y, u, l = oracle.fd_kkt_solve(2, N, beta, ry=ry)
         ref = np.concatenate([y, u, l], axis=1)
+        row = {}
+        for factor, key in ((S.SCHUR_FACTOR_EXACT, "S_c"), (S.SCHUR_FACTOR_PW, "S_p")):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sol = S.Solver(2, N, beta, nsub=P, precision=S.SCHUR_MIXED, tol=OUTER_TOL, factor=factor)
+            t_setup = time.perf_counter() - t0
+            e0, e1 = _events(torch, stream)
+            e0.record(stream)
+            x, it = sol.schur_kkt_minres(rd, tol=1e-10, max_it=80)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            xh = x.cpu().numpy()
+            err = max(float(np.linalg.norm(xh[c] - ref[c]) / np.linalg.norm(ref[c])) for c in range(8))
+            sol.close()
+            row[key] = {"ms_setup": 1e3 * t_setup, "ms_minres": ms, "minres_iters": it, "s_block_applies": it + 1,
+                        "ms_per_s_block_apply": ms / (it + 1), "max_relerr_vs_oracle": err,
+                        "mdof_s": 8 * 3 * n / (t_setup + ms / 1e3) / 1e6}
+        out["beta_%g" % beta] = row
+    return out
+
+
+# phi values of the paper's Table 1 (the thermal problem's regularisation sweep) run here
+THERMAL_PHIS = (2e-2, 2e-4, 2e-6, 2e-8, 2e-10, 2e-12)
+# the paper's Table 1, FETI-DPH iterations without augmentation on K + M/(i sqrt(phi)) ("+"), for context
+TABLE1_PLUS = {2e-2: 32, 2e-4: 38, 2e-6: 34, 2e-8: 38, 2e-10: 44, 2e-12: 62}
+
+
+def row_thermal(args, torch, S, inputs, oracle, dev, stream):
+    """The paper's thermal problem (Sec. 6.1): target (2x-1)^2 (2y-1)^2 on [0,1/2]^2, Dirichlet data
+    y_c = ybar, h = 2^-11 (2048^2 Q1 elements, 4,190,209 interior dofs), 128 x 128 subdomains of 16^2,
+    phi swept over Table 1's range.  Per phi: the FP64 form with one FETI-DP solve to 1e-10 (the
+    paper's threshold; iterations comparable with Table 1), the mixed form (setup + range-space
+    solve, timed), the relative constraint violation (Eq. relativeconstraintviolation), the relative
+    L2 (M-norm) distance of y to ybar and the L2 norm of u (the quantities of the paper's Fig. 2),
+    and at phi = 2e-8 the error of (y, u) against the oracle (sine basis)."""
+    N, P = 2048, 128
+    n = (N - 1) ** 2
+    yf = inputs.thermal_target(N)
+    yfd = torch.from_numpy(yf).to(dev)
+    ybi = oracle.interior_of(2, N, yf)
+    out = {"workload": "2d-q1-2048^2-dirichlet-thermal-target-128x128sub-16x16el", "n_dofs": n, "per_phi": {}}
+    S.Solver(2, N, THERMAL_PHIS[0], nsub=P, precision=S.SCHUR_MIXED, tol=OUTER_TOL).close()  # warm-up
+    for phi in THERMAL_PHIS:
+        r = {"table1_iters_plus_no_aug": TABLE1_PLUS.get(phi)}
+        # one FETI-DP solve (the outer stop at 1e-3 ends the refinement after its first step)
+        sol = S.Solver(2, N, phi, nsub=P, precision=S.SCHUR_FP64, tol=1e-3, inner_tol=1e-10, max_refine=1)
+        sol.schur_control_solve(yfd, want_violation=False)
+        r["fp64_gmres_iters"] = sol.last_stats["iters_first"]
+        sol.close()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sol = S.Solver(2, N, beta, nsub=P, precision=S.SCHUR_MIXED, tol=OUTER_TOL)
-        t_setup = time.perf_counter() - t0
-        e0, e1 = _events(torch, stream)
-        e0.record(stream)
-        x, it = sol.schur_kkt_minres(rd, tol=1e-10, max_it=60)
-        e1.record(stream)
-        e1.synchronize()
-        ms = e0.elapsed_time(e1)
-        xh = x.cpu().numpy()
-        err = max(float(np.linalg.norm(xh[c] - ref[c]) / np.linalg.norm(ref[c])) for c in range(8))
+        sol = S.Solver(2, N, phi, nsub=P, precision=S.SCHUR_MIXED, tol=OUTER_TOL)
+        y, u, lam, viol = sol.schur_control_solve(yfd)
+        torch.cuda.synchronize()
+        r["mixed_ms_setup_plus_solve"] = 1e3 * (time.perf_counter() - t0)
+        r["mixed_gmres_iters"] = sol.last_stats["iters_total"]
+        r["mixed_outer_steps"] = sol.last_stats["outer_steps"]
+        r["constraint_violation"] = float(viol[0])
         sol.close()
-        out["beta_%g" % beta] = {"ms_setup": 1e3 * t_setup, "ms_minres": ms, "minres_iters": it,
-                                 "max_relerr_vs_oracle": err,
-                                 "mdof_s": 8 * 3 * n / (t_setup + ms / 1e3) / 1e6}
+        yh, uh = y.cpu().numpy(), u.cpu().numpy()
+        d = yh - ybi
+        r["rel_l2_y_minus_ybar"] = float(np.sqrt(d @ oracle.apply_M(2, N, d) / (ybi @ oracle.apply_M(2, N, ybi))))
+        r["l2_norm_u"] = float(np.sqrt(uh @ oracle.apply_M(2, N, uh)))
+        if phi == 2e-8:
+            oracle.set_threads(os.cpu_count() or 1)
+            yr, ur, _ = oracle.control_solve(2, N, phi, yf, fd=True)
+            r["relerr_y_vs_oracle"] = float(np.linalg.norm(yh - yr) / np.linalg.norm(yr))
+            r["relerr_u_vs_oracle"] = float(np.linalg.norm(uh - ur) / np.linalg.norm(ur))
+        out["per_phi"]["%g" % phi] = r
     return out
 
 
 def serve_stream(args, S, inputs, oracle):
     """Serving form: Poisson arrivals of mixed 2D/3D sizes, beta from 6 cached values, 1-16 seeded
-    right-hand sides per request.  Capacity is measured closed-loop (all requests at t = 0); the
-    open-loop stream then arrives at 0.8 x that rate, served by the mixed and by the plain FP64
-    form.  Latency = arrival -> result on the host."""
+    right-hand sides per request.  Capacity is measured closed-loop (the first 400 requests all
+    submitted at t = 0); the open-loop stream of all requests then arrives at 0.8 x that rate,
+    served by the mixed form.  The plain FP64 form serves the first 60 requests of the same stream
+    (same arrival times) and, closed-loop, gives its own capacity.  Latency = arrival -> result on
+    the host.  Batching is reported from the server's counters: right-hand sides per multi-RHS solve,
+    requests that shared a solve, most batches on the device at once, factor-cache misses."""
     nreq = args.serve_requests
     sizes = [(2, 64), (2, 128), (2, 256), (2, 512), (2, 1024), (3, 32), (3, 64), (3, 96)]
     betas = [10.0 ** (-8 + 1.2 * k) for k in range(6)]
@@ -389,16 +557,16 @@ def serve_stream(args, S, inputs, oracle):
         dim, N, beta, R, i = q
         return np.ascontiguousarray(np.roll(pool[(dim, N)], i, axis=0)[:R])
 
-    def run(prec, arrivals, nreq=nreq):
+    def run(prec, arrivals, count):
         # Krylov space of at most 100 vectors per right-hand side (the FP64 form needs < 80 here)
         srv = S.Server(budget_bytes=64 << 30, workers=4, precision=prec, tol=1e-10, max_iter=100)
         try:
-            lat, done, pend, nsolve, rejected = [], 0, {}, 0, 0
+            lat, pend, nsolve, rejected = [], {}, 0, 0
             t0 = time.perf_counter()
             k = 0
-            while k < nreq or pend:
+            while k < count or pend:
                 now = time.perf_counter() - t0
-                while k < nreq and arrivals[k] <= now:
+                while k < count and arrivals[k] <= now:
                     q = reqs[k]
                     try:
                         pend[srv.submit(q[0], q[1], q[2], rhs_of(q))] = (arrivals[k], q)
@@ -418,33 +586,47 @@ def serve_stream(args, S, inputs, oracle):
                 if not moved:
                     time.sleep(0.0002)
             span = time.perf_counter() - t0
+            si = srv.info()
         finally:
             srv.close()
         lat = np.array(lat) * 1e3
-        return {"requests": nreq, "rejected": rejected, "rhs_solved": nsolve, "makespan_s": span,
-                "solves_s": nsolve / span,
-                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+        nb = max(1, si["batches"])
+        return {"requests": count, "rejected": rejected, "rhs_solved": nsolve, "makespan_s": span,
+                "solves_s": nsolve / span, "requests_s": count / span,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "batching": {"solve_calls": si["batches"], "rhs_per_solve_call": si["batch_columns"] / nb,
+                             "requests_per_solve_call": count / nb,
+                             "shared_request_fraction": si["shared_requests"] / max(1, count),
+                             "max_concurrent_batches": si["max_concurrent"], "factor_setups": si["setups"]}}
 
-    closed = run(S.SCHUR_MIXED, np.zeros(nreq))
-    rate = 0.8 * nreq / closed["makespan_s"]
+    ncap = min(nreq, 400)
+    closed = run(S.SCHUR_MIXED, np.zeros(ncap), ncap)
+    rate = 0.8 * ncap / closed["makespan_s"]
     arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq))
     out = {"workload": "serve-mixed-2d-64..1024^2-3d-32..96^3-6-betas-1..16-rhs-poisson", "requests": nreq,
-           "capacity_requests_s": nreq / closed["makespan_s"], "arrival_rate_requests_s": rate,
-           "mixed": run(S.SCHUR_MIXED, arrivals)}
+           "capacity_requests_s": ncap / closed["makespan_s"], "capacity_from_requests": ncap,
+           "capacity_closed_loop": closed, "arrival_rate_requests_s": rate,
+           "mixed": run(S.SCHUR_MIXED, arrivals, nreq)}
     if not args.no_fp64:
-        # the plain FP64 form on the first requests of the same stream (same arrival times): its
-        # capacity is far below the arrival rate, so the whole stream would only grow its queue
-        out["fp64"] = run(S.SCHUR_FP64, arrivals, nreq=min(nreq, 50))
-    # spot check of served results against the oracle (first 2D requests up to 256^2)
-    srv = S.Server(budget_bytes=8 << 30, workers=2, precision=S.SCHUR_MIXED, tol=1e-10)
+        nf = min(nreq, 60)
+        out["fp64"] = {"sample": "first %d requests of the same stream" % nf,
+                       "closed_loop": run(S.SCHUR_FP64, np.zeros(nf), nf),
+                       "same_arrivals": run(S.SCHUR_FP64, arrivals, nf)}
+    # spot check of served results against the oracle: the first requests of each kind (2D up to
+    # 256^2, 2D 1024^2, 3D up to 64^3; first two columns of each)
+    oracle.set_threads(os.cpu_count() or 1)
+    srv = S.Server(budget_bytes=16 << 30, workers=2, precision=S.SCHUR_MIXED, tol=1e-10)
     try:
         errs = []
-        for q in [q for q in reqs if q[0] == 2 and q[1] <= 256][:4]:
-            b = rhs_of(q)
+        picks = [q for q in reqs if q[0] == 2 and q[1] <= 256][:3] + [q for q in reqs if q[1] == 1024][:1] + \
+                [q for q in reqs if q[0] == 3 and q[1] <= 64][:2]
+        for q in picks:
+            b = rhs_of(q)[:2]
             x, _ = srv.wait(srv.submit(q[0], q[1], q[2], b))
-            xr = np.stack([oracle.fd_schur_solve(2, q[1], q[2], b[c]) for c in range(b.shape[0])])
+            xr = oracle.fd_schur_solve(q[0], q[1], q[2], b)
             errs.append(float(np.linalg.norm(x - xr) / np.linalg.norm(xr)))
-        out["spot_max_relerr_vs_oracle"] = max(errs) if errs else None
+        out["spot_check"] = {"requests": ["%dD %d, beta %.1e" % (q[0], q[1], q[2]) for q in picks],
+                             "max_relerr_vs_oracle": max(errs) if errs else None}
     finally:
         srv.close()
     return out
@@ -476,6 +658,15 @@ def main():
         return run_reference(args, rank, world)
     if args.ncu_case:
         return ncu_case(args.ncu_case)
+    if args.peaks:
+        from paper_1312_5653_gb300 import schur as S
+        pf = {}
+        try:
+            pf = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        print(json.dumps(measure_peaks(S, pf)), flush=True)
+        return
     import torch
     from paper_1312_5653_gb300 import inputs
     from paper_1312_5653_gb300 import schur as S
@@ -541,13 +732,12 @@ def main():
 
     import ctypes
 
-    # untimed profiling pass over one step per beta: find the dominant kernel category
+    # untimed profiling pass, one step per beta, every category: the per-category breakdown and the
+    # single kernel with the largest share (only that kernel's events are recorded while timing)
     _, _, _, _, prof_all = timed(S.SCHUR_MIXED, 4, 0, profile_mask=0x1FFFF)
-    dom = max(prof_all.items(), key=lambda kv: kv[1][1])[0] if prof_all else None
-    names = ["factor", "form", "coarse_setup", "local_rhs", "apply_F", "apply_S", "scatter", "coarse_apply",
-             "corner", "gmres_dots", "gmres_update", "gmres_other", "recover", "assemble_z", "residual",
-             "coarse_inverse", "interior"]
-    dom_mask = (1 << names.index(dom)) if dom in names else 0
+    single = [c for c in (prof_all or {}) if c in KERNEL_OF]
+    dom = max(single, key=lambda c: prof_all[c][1]) if single else None
+    dom_mask = (1 << CATEGORIES.index(dom)) if dom else 0
 
     # headline: mixed precision, timed region
     with Clocks(local_rank) as clk:
@@ -555,21 +745,33 @@ def main():
     ms_step = total / args.steps
     value = job_rate(world, n, args.steps, total)
 
-    # accuracy of the timed path vs the oracle on one step (rank 0)
+    # accuracy of the timed path vs the oracle on one step, and the oracle timed on the host cores
+    # (rank 0): all cores on one right-hand side per beta, one core on one right-hand side
     relerr = None
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
         bh = b.cpu().numpy()
-        xref, tcpu = cpu_oracle_solve(bh, BETAS[(args.steps - 1) % 4])
-        sol = make(BETAS[(args.steps - 1) % 4], S.SCHUR_MIXED)
+        ncores = os.cpu_count() or 1
+        oracle.set_threads(ncores)
+        t_all = []
+        for beta in BETAS:
+            xref, t = cpu_oracle_solve(bh, beta)
+            t_all.append(t)
+        sol = make(BETAS[-1], S.SCHUR_MIXED)
         xg = sol.schur_solve(b).cpu().numpy()
         sol.close()
         relerr = float(np.linalg.norm(xg - xref) / np.linalg.norm(xref))
-        cpu = {"value": n / tcpu / 1e6, "unit": "MDoF/s", "cores": 1, "kind": "oracle",
-               "sample": "one full-size right-hand side (1,046,529 dofs), fast-diagonalisation oracle, "
-                         "single thread, %.1f s" % tcpu}
+        oracle.set_threads(1)
+        _, t_one = cpu_oracle_solve(bh, BETAS[0])
+        cpu = {"value": n * len(t_all) / float(np.sum(t_all)) / 1e6, "unit": "MDoF/s", "cores": ncores,
+               "kind": "oracle", "cpu_model": cpu_model(),
+               "sample": "one full-size right-hand side (1,046,529 dofs) per beta (4 solves), fast-diagonalisation "
+                         "oracle with its sine-transform lines on %d OpenMP threads, %.1f s in all" %
+                         (ncores, float(np.sum(t_all))),
+               "single_thread": {"value": n / t_one / 1e6, "unit": "MDoF/s", "cores": 1,
+                                 "sample": "one full-size right-hand side, one thread, %.1f s" % t_one}}
 
     # cached-factor solve rate (factorisation reused across right-hand sides, as the server does)
     cached = {}
@@ -622,46 +824,41 @@ def main():
     e2e = {"value": world * n * len(e2e_t) / float(np.sum(e2e_t)) / 1e6, "unit": "MDoF/s",
            "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
 
-    # roofline of the dominant kernel category (event-timed inside the timed region)
-    roof = None
-    peaks = {}
+    # rooflines from the event-timed categories of the timed region, against measured peaks; the
+    # reported one is the single kernel with the largest share of the step
+    peaks_file = {}
     try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peaks_file = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    if prof and dom in prof:
+    peaks = measure_peaks(S, peaks_file)
+    sol = make(BETAS[0], S.SCHUR_MIXED)
+    info = sol.info()
+    sol.close()
+    by_cat = {}
+    for cat, (nl_, tot_ms) in (prof_all or {}).items():
+        r = category_roofline(cat, info, nl_, tot_ms, 4, peaks)
+        if r:
+            by_cat[cat] = r
+    roof = None
+    if dom and prof and dom in prof:
         nl_, tot_ms = prof[dom]
-        sol = make(BETAS[0], S.SCHUR_MIXED)
-        info = sol.info()
-        sol.close()
-        bound, algo = algorithmic(dom, info, 4)
-        # HBM models count one launch; ALU models count one step (setup once per step)
-        avg_s = tot_ms / nl_ / 1e3 if bound == "hbm" else tot_ms / args.steps / 1e3
-        if bound == "hbm":
-            peak = peaks.get("hbm_gbs", 6800.0)
-            ach = algo / avg_s / 1e9
-            roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                    "traffic": None, "launches": nl_, "avg_us": avg_s * 1e6, "algorithmic_bytes": algo,
-                    "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
-        elif bound == "alu":
-            ach = algo / avg_s / 1e12
-            is64 = dom == "coarse_setup"
-            peak = ALU_FP64_TFLOPS if is64 else ALU_FP32_TFLOPS
-            src = ("nominal GB300 FP64 (1.25 TFLOP/s, not measured)" if is64 else
-                   "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz")
-            roof = {"kernel": dom, "bound": "alu", "precision": "fp64" if is64 else "fp32", "achieved": ach,
-                    "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "launches": nl_,
-                    "us_per_step": avg_s * 1e6, "algorithmic_flops": algo, "peak_source": src}
-        else:
-            roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
-                    "traffic": None, "launches": nl_, "avg_us": avg_s * 1e6}
+        roof = category_roofline(dom, info, nl_, tot_ms, args.steps, peaks)
+        roof["kernel"] = KERNEL_OF[dom]
+        roof["category"] = dom
+        roof["share_of_step"] = tot_ms / total
+        roof["timed"] = "CUDA events on the solve stream around each launch of this kernel, inside the timed region"
+        roof["traffic"] = recorded_traffic(KERNEL_OF[dom])
+        if roof["traffic"] is not None:
+            roof["traffic_over_algorithmic"] = roof["traffic"] / roof["algorithmic_bytes_per_launch"]
 
     extra = {}
     if rank == 0 and not args.no_extra:
         import oracle
         oracle.build()
-        extra["precision_form_3d"] = row_3d(args, torch, S, inputs, oracle, dev, stream)
+        extra["precision_form_3d"] = row_3d(args, torch, S, inputs, oracle, dev, stream, peaks)
         extra["full_space_kkt"] = row_kkt(args, torch, S, inputs, oracle, dev, stream)
+        extra["thermal_range_space"] = row_thermal(args, torch, S, inputs, oracle, dev, stream)
         extra["serving"] = serve_stream(args, S, inputs, oracle)
 
     if rank == 0:
@@ -678,8 +875,9 @@ def main():
             "gmres_iters": [s["iters_total"] for s in stats], "outer_steps": [s["outer_steps"] for s in stats],
             "ms_setup": [s["ms_setup"] for s in stats],
             "cached_factor_solve": cached, "fp64": fp64,
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "profile_ms_by_kernel": {k: v[1] for k, v in (prof_all or {}).items()},
+            "roofline": roof, "roofline_by_category": by_cat, "peaks": peaks,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "profile_ms_per_step_by_category": {k: v[1] / 4 for k, v in (prof_all or {}).items()},
             "clocks": clk.summary(),
         }
         line.update(extra)

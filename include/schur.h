@@ -54,6 +54,10 @@ extern "C" {
 #define SCHUR_LOCAL_PER_SUBDOMAIN 0 /* one factor and one set of local operators per subdomain  */
 #define SCHUR_LOCAL_SHARED 1        /* subdomains with identical local matrices share them      */
 
+#define SCHUR_FACTOR_EXACT 0 /* S_c = (K + i gamma M) M^{-1} (K - i gamma M) = S exactly (Sec. 4)     */
+#define SCHUR_FACTOR_PW 1    /* S_p = (K + gamma M) M^{-1} (K + gamma M) = S + 2 gamma K, the
+                                Pearson-Wathen approximation (Sec. 3.2, Eq. pearsonapproximation)     */
+
 typedef struct schur_ctx schur_ctx;
 
 typedef struct {
@@ -72,7 +76,11 @@ typedef struct {
   int tc_split;      /* mixed 3D local operators on the tensor cores (TF32 inputs, FP32
                         accumulation): 0 or 3 = three products hi*hi + hi*lo + lo*hi of the
                         split x = hi + lo (FP32 accuracy), 1 = one product (TF32 rounding)     */
-  int reserved[4];   /* must be zero                                                      */
+  int factor;        /* which Schur complement schur_solve inverts: SCHUR_FACTOR_EXACT (S, by one
+                        complex FETI-DP solve with K + i gamma M and x = -Im(z)/gamma) or
+                        SCHUR_FACTOR_PW (S_p, by two real FETI-DP solves with K + gamma M and
+                        one M product: x = (K + gamma M)^{-1} M (K + gamma M)^{-1} b)          */
+  int reserved[3];   /* must be zero                                                      */
 } schur_opts;
 
 typedef struct {
@@ -125,7 +133,8 @@ int schur_solve(schur_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, in
 int schur_solve_host(schur_ctx* ctx, const double* b_host, double* x_host, int nrhs, int ld,
                      void* stream, schur_stats* st);
 
-/* z = (K + i gamma M)^{-1} (b_re + i b_im) (one factor of Sec. 4, the factor the shortcut uses).
+/* z = A^{-1} (b_re + i b_im) with the context's factor A: K + i gamma M (one factor of Sec. 4, the
+ * factor the shortcut uses) or, with SCHUR_FACTOR_PW, the real K + gamma M of S_p (Sec. 3.2).
  * b_im_dev may be NULL (real right-hand side).  z_dev: interleaved complex FP64 (re, im), n x nrhs
  * with leading dimension ld complex entries.  Synchronises.  Same refinement and stop rule as
  * schur_solve. */
@@ -162,13 +171,29 @@ int schur_apply_S(schur_ctx* ctx, const double* x_dev, double* y_dev, int nrhs, 
 int schur_apply_S_static(const schur_mesh* mesh, double beta, const double* x_dev, double* y_dev, int nrhs, int ld,
                          void* stream);
 
+/* The range-space method of Sec. 3.1 with Dirichlet data y = y_c on the boundary (the thermal
+ * problem of Sec. 6.1, Eqs. heatconduction and ex1boundarycondition: y_c = ybar there).
+ * ybar_full_dev: the target state on all prod(nel[a] + 1) grid nodes, boundary included
+ * (lexicographic, axis 0 fastest, leading dimension ldf); its boundary values are taken as y_c.
+ * Computes, on the n interior nodes (leading dimension ld >= n):
+ *   lambda = S^{-1} (K ybar + K_c y_c)            (Eq. schurcomplementsystem, by schur_solve)
+ *   y = ybar - M^{-1} K lambda,  u = lambda / beta (Eq. updateyandu; M^{-1} as in schur_apply_S)
+ * and, when viol_host != NULL, viol_host[c] = ||K y + K_c y_c - M u||_2 / ||K y||_2 for every
+ * column (the relative constraint violation, Eq. relativeconstraintviolation).  lambda_dev may be
+ * NULL.  Needs a context with factor SCHUR_FACTOR_EXACT.  Synchronises.  Returns ENOTCONV (outputs
+ * written) if the S solve misses its tolerance; EINVAL, ENOMEM, ECUDA as schur_solve. */
+int schur_control_solve(schur_ctx* ctx, const double* ybar_full_dev, int ldf, double* y_dev, double* u_dev,
+                        double* lambda_dev, int nrhs, int ld, double* viol_host, void* stream, schur_stats* st);
+
 /* Full-space KKT system of Sec. 2 with homogeneous Dirichlet data:
  *   [M 0 K; 0 beta M -M; K -M 0] (y, u, l).
  * Vectors hold the three blocks stacked: entries [0,n) = y, [n,2n) = u, [2n,3n) = lambda; ld >= 3n.
  * schur_kkt_apply: r = KKT v (asynchronous).
  * schur_kkt_precond_apply: z = P_mgw^{-1} r with P_mgw = diag(M, beta M, S) (Sec. 3.2,
  *   Eq. murphypreconditioner): M^{-1} by Chebyshev iteration with Jacobi scaling on the Q1 mass
- *   spectrum bounds (fixed degree, a fixed linear operator), S^{-1} by schur_solve.  Synchronises.
+ *   spectrum bounds (fixed degree, a fixed linear operator), S^{-1} by schur_solve.  With the
+ *   factor SCHUR_FACTOR_PW the third block is S_p^{-1} (the Pearson-Wathen approximation of
+ *   Eq. pearsonapproximation in place of S).  Synchronises.
  * schur_kkt_minres: MINRES on the KKT system preconditioned by P_mgw, FP64 Krylov, stop at
  *   ||r_k||/||r_0|| <= tol (preconditioned norm); iters receives the iteration count (max over
  *   right-hand sides).  Synchronises.  ENOTCONV if max_it is reached. */
@@ -208,6 +233,16 @@ int schur_profile_end(schur_kernel_time* out, int cap, int* count);
 const char* schur_kernel_category_name(int category);
 long long schur_launch_count(const schur_ctx* ctx);
 
+/* Arithmetic peak probe (measurement aid, no paper counterpart): runs one in-register or
+ * in-shared-memory loop of `iters` iterations on every SM of the current device, once to warm up
+ * and once timed with CUDA events on `stream`, and writes the achieved TFLOP/s to *tflops.
+ * kind 0: FP64 FMA (CUDA cores); 1: FP32 FMA (CUDA cores); 2: FP64 tensor MMA (mma.sync
+ * m8n8k4); 3: TF32 tensor MMA (tcgen05.mma kind::tf32, 128 x 256 x 8, accumulator in tensor
+ * memory).  These are the denominators of the ALU and tensor-pipe rooflines reported for this
+ * library's kernels.  Allocates a small output buffer; synchronises.  Errors: EINVAL,
+ * ETIMEOUT (tensor-core completion wait gave up), ECUDA. */
+int schur_peak_probe(int kind, int iters, double* tflops, void* stream);
+
 /* ---------------------------------------------------------------------------------------------
  * Serving.  A server owns worker threads (one CUDA stream each, on the device current at
  * creation) and a device-resident cache of contexts keyed by (mesh, beta) with the server's
@@ -238,6 +273,12 @@ typedef struct {
 typedef struct {
   int cached_contexts, queued;
   long long completed, bytes_reserved;
+  long long batches;         /* multi-RHS solves run (one per batch)                              */
+  long long batch_columns;   /* right-hand sides summed over those solves                         */
+  long long shared_requests; /* requests solved in one batch together with at least one other     */
+  long long setups;          /* contexts built (factor-cache misses)                              */
+  int max_concurrent;        /* most batches running on the device at the same time               */
+  int reserved[3];
 } schur_server_info_t;
 void schur_server_default_opts(schur_server_opts* opts);
 int schur_server_create(const schur_server_opts* opts, schur_server** out);

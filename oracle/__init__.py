@@ -4,8 +4,9 @@ TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the 
 ``--impl reference`` legs of ``bench.py`` may import this package.  The product library
 (``paper_1312_5653_gb300``) never imports, links or runs it, and the two share no code.
 
-The arithmetic lives in ``oracle.c`` (plain single-threaded C).  This module only marshals numpy
-arrays through ctypes.  Every function works on real FP64 vectors over the n interior nodes of a
+The arithmetic lives in ``oracle.c`` (plain C; only the independent lines of the O2 sine transforms
+are shared out over OpenMP threads, see ``set_threads``).  This module only marshals numpy arrays
+through ctypes.  Every function works on real FP64 vectors over the n interior nodes of a
 uniform Q1 grid on the unit box (lexicographic order, axis 0 fastest), column-major for several
 right-hand sides.  ``beta`` is the paper's regularisation phi and gamma = 1/sqrt(beta).
 
@@ -31,7 +32,7 @@ def build(force=False):
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
         tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -58,6 +59,10 @@ def _load():
         lib.or_fd_complex_solve.argtypes = [I, P, D, I, I, P, P, P, P]
         lib.or_fd_kkt_solve.argtypes = [I, P, D, I, P, P, P, P, P, P]
         lib.or_fd_eigs.argtypes = [I, P, P, P]
+        lib.or_full_stiffness.argtypes = [I, P, I, P, P]
+        lib.or_fd_pw_solve.argtypes = [I, P, D, I, P, P]
+        lib.or_set_threads.argtypes = [I]
+        lib.or_set_threads.restype = I
         _lib = lib
     return _lib
 
@@ -85,6 +90,12 @@ def _vec(x, n):
 def _check(rc, what):
     if rc != 0:
         raise RuntimeError("oracle %s failed with code %d" % (what, rc))
+
+
+def set_threads(nthreads):
+    """Threads of the O2 sine transforms (OpenMP); returns the count in effect.  The results are
+    the same for every count (each transform line is computed by one thread, in the same order)."""
+    return int(_load().or_set_threads(int(nthreads)))
 
 
 def ndof(dim, nel):
@@ -181,6 +192,16 @@ def fd_schur_solve(dim, nel, beta, b):
     return x[0] if sq else x
 
 
+def fd_pw_solve(dim, nel, beta, b):
+    """O2: x = S_p^{-1} b for the Pearson-Wathen S_p = (K + M/sqrt(beta)) M^-1 (K + M/sqrt(beta))
+    (Sec. 3.2) by fast diagonalisation."""
+    n = ndof(dim, nel)
+    bb, sq = _vec(b, n)
+    x = np.zeros_like(bb)
+    _check(_load().or_fd_pw_solve(dim, _p(_nel(dim, nel)), float(beta), bb.shape[0], _p(bb), _p(x)), "fd_pw_solve")
+    return x[0] if sq else x
+
+
 def fd_schur_apply(dim, nel, beta, x):
     n = ndof(dim, nel)
     xx, sq = _vec(x, n)
@@ -224,3 +245,58 @@ def fd_eigs(dim, nel):
     m = np.zeros(n)
     _check(_load().or_fd_eigs(dim, _p(_nel(dim, nel)), _p(k), _p(m)), "fd_eigs")
     return k, m
+
+
+def nfull(dim, nel):
+    """Grid nodes of the whole mesh, boundary included: prod(nel[a] + 1)."""
+    ne = _nel(dim, nel)
+    return int(np.prod(ne[:dim].astype(np.int64) + 1))
+
+
+def interior_of(dim, nel, yfull):
+    """The interior-node values (length n, oracle order) of full-grid vectors (..., nfull)."""
+    ne = _nel(dim, nel)[:dim]
+    yf = np.asarray(yfull, dtype=np.float64)
+    shp = tuple(int(e) + 1 for e in ne[::-1])  # C order: last axis fastest = grid axis 0
+    a = yf.reshape(yf.shape[:-1] + shp)
+    sl = (Ellipsis,) + tuple(slice(1, -1) for _ in range(dim))
+    return a[sl].reshape(yf.shape[:-1] + (-1,))
+
+
+def full_stiffness(dim, nel, yfull):
+    """K y_int + K_c y_c on the interior nodes for full-grid vectors (Sec. 2, element loop)."""
+    n, nf = ndof(dim, nel), nfull(dim, nel)
+    yy, sq = _vec(yfull, nf)
+    out = np.zeros((yy.shape[0], n))
+    _check(_load().or_full_stiffness(dim, _p(_nel(dim, nel)), yy.shape[0], _p(yy), _p(out)), "full_stiffness")
+    return out[0] if sq else out
+
+
+def boundary_coupling(dim, nel, yfull):
+    """K_c y_c alone: the full-grid vector with its interior values set to zero."""
+    yb = np.array(yfull, dtype=np.float64, copy=True)
+    n, nf = ndof(dim, nel), nfull(dim, nel)
+    flat = yb.reshape(-1, nf)
+    mask = np.ones(nf, dtype=bool)
+    mask[interior_index(dim, nel)] = False
+    flat[:, ~mask] = 0.0
+    return full_stiffness(dim, nel, yb)
+
+
+def interior_index(dim, nel):
+    """Positions of the interior nodes (oracle order) within the full-grid vector."""
+    ne = _nel(dim, nel)[:dim]
+    idx = np.arange(nfull(dim, nel)).reshape(tuple(int(e) + 1 for e in ne[::-1]))
+    sl = tuple(slice(1, -1) for _ in range(dim))
+    return idx[sl].reshape(-1)
+
+
+def control_solve(dim, nel, beta, yfull, fd=False):
+    """The range-space problem of Sec. 3.1 with Dirichlet data y_c = the boundary values of yfull
+    (the thermal problem of Sec. 6.1): the KKT system of Sec. 2 with right-hand side
+    (M ybar, 0, -K_c y_c), solved by O1 (banded KKT factorisation) or, with fd=True, by O2
+    (sine basis).  Returns (y, u, lambda) on the interior nodes."""
+    yb = interior_of(dim, nel, yfull)
+    ry = apply_M(dim, nel, yb)
+    rl = -boundary_coupling(dim, nel, yfull)
+    return (fd_kkt_solve if fd else kkt_solve)(dim, nel, beta, ry=ry, rl=rl)

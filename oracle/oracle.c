@@ -15,6 +15,9 @@
  */
 #include "oracle.h"
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -182,6 +185,47 @@ int or_apply_KM(int dim, const int* nel, int nrhs, const double* x, double* Kx, 
   return 0;
 }
 
+/* Sec. 2 with Dirichlet data: the stiffness rows of the interior nodes applied to a vector over all
+ * prod(nel[a]+1) grid nodes (lexicographic, axis 0 fastest; boundary values = the data y_c), i.e.
+ * out = K y + K_c y_c on the interior nodes, by the element loop over the whole grid. */
+int or_full_stiffness(int dim, const int* nel, int nrhs, const double* yfull, double* out) {
+  if (check_mesh(dim, nel) || nrhs < 0) return -1;
+  long n = or_ndof(dim, nel), nf = 1;
+  for (int a = 0; a < dim; ++a) nf *= nel[a] + 1;
+  double h[3] = {1.0, 1.0, 1.0};
+  for (int a = 0; a < dim; ++a) h[a] = 1.0 / nel[a];
+  double Ke[64], Me[64];
+  or_element(dim, h, Ke, Me);
+  int nn = 1 << dim;
+  for (int r = 0; r < nrhs; ++r) {
+    const double* yr = yfull + (long)r * nf;
+    double* o = out + (long)r * n;
+    memset(o, 0, sizeof(double) * n);
+    int e[3] = {0, 0, 0};
+    int ez = dim == 3 ? nel[2] : 1;
+    for (e[2] = 0; e[2] < ez; ++e[2])
+      for (e[1] = 0; e[1] < nel[1]; ++e[1])
+        for (e[0] = 0; e[0] < nel[0]; ++e[0]) {
+          long ip[8];
+          double ye[8];
+          for (int p = 0; p < nn; ++p) {
+            int gp[3] = {0, 0, 0};
+            for (int a = 0; a < dim; ++a) gp[a] = e[a] + ((p >> a) & 1);
+            ip[p] = node_index(dim, nel, gp);
+            long f = gp[0] + (long)(nel[0] + 1) * (gp[1] + (long)(nel[1] + 1) * gp[2]);
+            ye[p] = yr[f];
+          }
+          for (int p = 0; p < nn; ++p) {
+            if (ip[p] < 0) continue;
+            double s = 0.0;
+            for (int q = 0; q < nn; ++q) s += Ke[p * nn + q] * ye[q];
+            o[ip[p]] += s;
+          }
+        }
+  }
+  return 0;
+}
+
 /* ---------------------------------------------------------------- banded LDL^T --------- */
 /* In-place LDL^T without pivoting of a symmetric band matrix (lower-band storage, half
  * bandwidth w).  On exit band[i*(w+1)] = D_i and band[i*(w+1)+k] = L[i][i-k]. */
@@ -334,31 +378,55 @@ static double* sine_matrix(int N) {
   return V;
 }
 
-/* Apply V along axis `ax` of an array with dims m[0..dim-1] (axis 0 fastest), in place. */
+/* Apply V along axis `ax` of an array with dims m[0..dim-1] (axis 0 fastest), in place.  The
+ * lines along the axis are independent; with OpenMP they are shared out among the threads, each
+ * line's arithmetic unchanged (the same products summed in the same order), so the result does
+ * not depend on the thread count. */
 static int transform_axis(int dim, const int* m, int ax, const double* V, double* x) {
   long stride = 1;
   for (int a = 0; a < ax; ++a) stride *= m[a];
   long len = m[ax];
   long outer = 1;
   for (int a = ax + 1; a < dim; ++a) outer *= m[a];
-  double* line = (double*)malloc(sizeof(double) * len);
-  double* out = (double*)malloc(sizeof(double) * len);
-  if (!line || !out) { free(line); free(out); return -2; }
-  for (long o = 0; o < outer; ++o)
-    for (long in = 0; in < stride; ++in) {
-      long base = o * stride * len + in;
-      for (long a = 0; a < len; ++a) line[a] = x[base + a * stride];
-      for (long j = 0; j < len; ++j) {
-        double s = 0.0;
-        const double* row = V + j * len;
-        for (long a = 0; a < len; ++a) s += row[a] * line[a];
-        out[j] = s;
+  long nlines = outer * stride;
+  int fail = 0;
+#pragma omp parallel
+  {
+    double* line = (double*)malloc(sizeof(double) * len);
+    double* out = (double*)malloc(sizeof(double) * len);
+    if (!line || !out) {
+#pragma omp atomic write
+      fail = 1;
+    } else {
+#pragma omp for schedule(static)
+      for (long q = 0; q < nlines; ++q) {
+        long o = q / stride, in = q % stride;
+        long base = o * stride * len + in;
+        for (long a = 0; a < len; ++a) line[a] = x[base + a * stride];
+        for (long j = 0; j < len; ++j) {
+          double s = 0.0;
+          const double* row = V + j * len;
+          for (long a = 0; a < len; ++a) s += row[a] * line[a];
+          out[j] = s;
+        }
+        for (long a = 0; a < len; ++a) x[base + a * stride] = out[a];
       }
-      for (long a = 0; a < len; ++a) x[base + a * stride] = out[a];
     }
-  free(line);
-  free(out);
-  return 0;
+    free(line);
+    free(out);
+  }
+  return fail ? -2 : 0;
+}
+
+/* Threads of the sine transforms (OpenMP); 1 = single-threaded.  Returns the count in effect. */
+int or_set_threads(int nthreads) {
+#ifdef _OPENMP
+  if (nthreads >= 1) omp_set_num_threads(nthreads);
+  return omp_get_max_threads();
+#else
+  (void)nthreads;
+  return 1;
+#endif
 }
 
 static int sine_transform(int dim, const int* nel, double* const* Vs, double* x) {
@@ -447,6 +515,12 @@ typedef double (*mode_fn)(double kappa, double mu, double beta);
 
 static double f_schur_inv(double k, double m, double beta) { return 1.0 / (k * k / m + m / beta); }
 static double f_schur(double k, double m, double beta) { return k * k / m + m / beta; }
+/* Sec. 3.2, Eq. pearsonapproximation: S_p = (K + M/sqrt(beta)) M^{-1} (K + M/sqrt(beta)), per mode
+ * (kappa + mu/sqrt(beta))^2 / mu */
+static double f_pw_inv(double k, double m, double beta) {
+  double s = k + m / sqrt(beta);
+  return m / (s * s);
+}
 
 static int fd_diag_op(int dim, const int* nel, double beta, int nrhs, const double* x, double* y, mode_fn f) {
   fd_ctx c;
@@ -466,6 +540,11 @@ static int fd_diag_op(int dim, const int* nel, double beta, int nrhs, const doub
 int or_fd_schur_solve(int dim, const int* nel, double beta, int nrhs, const double* b, double* x) {
   if (!(beta > 0.0) || nrhs < 0) return -1;
   return fd_diag_op(dim, nel, beta, nrhs, b, x, f_schur_inv);
+}
+
+int or_fd_pw_solve(int dim, const int* nel, double beta, int nrhs, const double* b, double* x) {
+  if (!(beta > 0.0) || nrhs < 0) return -1;
+  return fd_diag_op(dim, nel, beta, nrhs, b, x, f_pw_inv);
 }
 
 int or_fd_schur_apply(int dim, const int* nel, double beta, int nrhs, const double* x, double* y) {

@@ -1,7 +1,8 @@
 /*
  * Reference oracle for the factored Schur complement solve of distributed optimal control
- * (Choi, Farhat, Murray, Saunders, arXiv 1312.5653).  TEST INFRASTRUCTURE ONLY: plain, slow,
- * single-threaded FP64 C.  Only the test suite, the smoke check and the CPU-baseline leg of the
+ * (Choi, Farhat, Murray, Saunders, arXiv 1312.5653).  TEST INFRASTRUCTURE ONLY: plain, slow
+ * FP64 C (single-threaded, except that the independent lines of the O2 sine transforms may be
+ * shared out over OpenMP threads with unchanged arithmetic; see or_set_threads).  Only the test suite, the smoke check and the CPU-baseline leg of the
  * benchmark may call it; the product library never links or loads it, and this code shares
  * nothing (no header, helper, table or constant) with the CUDA path.
  *
@@ -46,6 +47,8 @@ int or_schur_apply(int dim, const int* nel, double beta, int nrhs, const double*
 
 /* O2: x = S^{-1} b. */
 int or_fd_schur_solve(int dim, const int* nel, double beta, int nrhs, const double* b, double* x);
+/* O2: x = S_p^{-1} b, S_p = (K + M/sqrt(beta)) M^{-1} (K + M/sqrt(beta)) (Sec. 3.2). */
+int or_fd_pw_solve(int dim, const int* nel, double beta, int nrhs, const double* b, double* x);
 /* O2: y = S x. */
 int or_fd_schur_apply(int dim, const int* nel, double beta, int nrhs, const double* x, double* y);
 /* O2: z = (K + i*sgn*gamma*M)^{-1} (bre + i*bim); bim may be NULL. */
@@ -56,6 +59,12 @@ int or_fd_kkt_solve(int dim, const int* nel, double beta, int nrhs, const double
                     const double* rl, double* y, double* u, double* l);
 /* O2: eigenvalues of K and M for each sine vector (arrays of length n). */
 int or_fd_eigs(int dim, const int* nel, double* kappa, double* mu);
+/* Threads used by the O2 sine transforms (OpenMP over independent transform lines; the result
+ * does not depend on the count).  nthreads < 1 leaves it unchanged.  Returns the count in effect. */
+int or_set_threads(int nthreads);
+/* Sec. 2 with Dirichlet data: out = K y + K_c y_c on the interior nodes, from a vector over all
+ * prod(nel[a]+1) grid nodes whose boundary values are y_c (element loop over the whole grid). */
+int or_full_stiffness(int dim, const int* nel, int nrhs, const double* yfull, double* out);
 
 #ifdef __cplusplus
 }

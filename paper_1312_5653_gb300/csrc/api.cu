@@ -177,7 +177,7 @@ int ctx_ensure_outer(schur_ctx* c, int R) {
 // Relative residuals ||f - A z|| / ||f|| for R columns (synchronises).  Leaves res = f - A z.
 int ctx_residual(schur_ctx* c, const double* bre, const double* bim, int ldb, int R, cudaStream_t st, double* rel) {
   const Geom& g = c->mp->hm.g;
-  Coef27 sten = make_coef(g, c->gamma);
+  Coef27 sten = make_coef(g, c->sim, c->sre);
   prof_start(KC_RESIDUAL, st);
   k_residual<<<dim3(c->nblk, R), 256, 0, st>>>(g, sten, bre, bim, ldb, reinterpret_cast<const cx<double>*>(c->z),
                                                (int)g.n, R, reinterpret_cast<cx<double>*>(c->res), c->part, c->nblk);
@@ -200,7 +200,8 @@ int ctx_residual(schur_ctx* c, const double* bre, const double* bim, int ldb, in
 }
 
 // Outer refinement for R <= kMaxR columns: z accumulates in FP64 with z += FETI(b - A z) until
-// ||b - A z|| / ||b|| <= tol.  Output: x = -Im(z)/gamma (x != null) and/or z (zout != null).
+// ||b - A z|| / ||b|| <= tol.  Output: x (x != null) = -Im(z)/gamma for the complex factor (the
+// real-input shortcut), Re(z) for the real factor K + gamma M; and/or z itself (zout != null).
 int ctx_outer(schur_ctx* c, const double* bre, const double* bim, int ldb, int R, double* x, int ldx, double* zout,
               int ldz, cudaStream_t st, schur_stats* stats) {
   const Geom& g = c->mp->hm.g;
@@ -241,9 +242,13 @@ int ctx_outer(schur_ctx* c, const double* bre, const double* bim, int ldb, int R
     if (iters_first < 0) iters_first = ir.iters;
   }
   if (x) {
+    const dim3 grid(std::max(1, (int)std::min<long long>((g.n + 255) / 256, 4 * 152)), R);
     prof_start(KC_RESIDUAL, st);
-    k_shortcut<<<dim3(std::max(1, (int)std::min<long long>((g.n + 255) / 256, 4 * 152)), R), 256, 0, st>>>(
-        g.n, reinterpret_cast<const cx<double>*>(c->z), (int)g.n, R, 1.0 / c->gamma, x, ldx);
+    if (c->opts.factor == SCHUR_FACTOR_PW)
+      k_real_part<<<grid, 256, 0, st>>>(g.n, reinterpret_cast<const cx<double>*>(c->z), (int)g.n, R, 1.0, x, ldx);
+    else
+      k_shortcut<<<grid, 256, 0, st>>>(g.n, reinterpret_cast<const cx<double>*>(c->z), (int)g.n, R, 1.0 / c->gamma,
+                                       x, ldx);
     prof_stop(KC_RESIDUAL, st);
     API_CK(cudaGetLastError());
     ++c->launches;
@@ -261,6 +266,39 @@ int ctx_outer(schur_ctx* c, const double* bre, const double* bim, int ldb, int R
     stats->iters_first = std::max(stats->iters_first, iters_first < 0 ? 0 : iters_first);
   }
   return status;
+}
+
+// S^{-1} b by the complex factor: one outer-refined complex solve and the shortcut.  S_p^{-1} b by
+// the real factor A = K + gamma M (Sec. 3.2): w = A^{-1} b, t = M w, x = A^{-1} t, each solve
+// refined in FP64 to the context's tolerance.
+int ctx_schur_inverse(schur_ctx* c, const double* b, int ldb, int R, double* x, int ldx, cudaStream_t st,
+                      schur_stats* stats) {
+  if (c->opts.factor != SCHUR_FACTOR_PW) return ctx_outer(c, b, nullptr, ldb, R, x, ldx, nullptr, 0, st, stats);
+  const Geom& g = c->mp->hm.g;
+  const size_t n = (size_t)g.n;
+  if (!c->pw_buf) API_CK(cudaMalloc(&c->pw_buf, 2 * n * kMaxR * sizeof(double)));
+  double* w = c->pw_buf;
+  double* t = c->pw_buf + n * kMaxR;
+  schur_stats s1, s2;
+  std::memset(&s1, 0, sizeof(s1));
+  std::memset(&s2, 0, sizeof(s2));
+  int rc1 = ctx_outer(c, b, nullptr, ldb, R, w, (int)n, nullptr, 0, st, &s1);
+  if (rc1 && rc1 != SCHUR_ENOTCONV) return rc1;
+  Coef27 sten = make_coef(g, 1.0);
+  const int grid = std::max(1, (int)std::min<long long>((g.n + 255) / 256, 8 * 152));
+  k_apply_real<<<dim3(grid, R), 256, 0, st>>>(g, sten, 0, w, (int)n, t, (int)n, R, 1.0, 0.0);
+  API_CK(cudaGetLastError());
+  ++c->launches;
+  ++c->total_launches;
+  int rc2 = ctx_outer(c, t, nullptr, (int)n, R, x, ldx, nullptr, 0, st, &s2);
+  if (rc2 && rc2 != SCHUR_ENOTCONV) return rc2;
+  if (stats) {
+    stats->outer_steps = std::max(stats->outer_steps, s1.outer_steps + s2.outer_steps);
+    stats->iters_total = std::max(stats->iters_total, s1.iters_total + s2.iters_total);
+    stats->iters_first = std::max(stats->iters_first, s1.iters_first);
+    stats->rel_residual = std::max(s1.rel_residual, s2.rel_residual);
+  }
+  return rc1 ? rc1 : rc2;
 }
 
 }  // namespace schur
@@ -320,7 +358,9 @@ int schur_setup(const schur_mesh* mesh, double beta, const schur_opts* opts, voi
     return set_error(SCHUR_EINVAL, "tol must be > 0, 1 <= max_iter < 512, max_refine >= 0");
   if (opts->tc_split != 0 && opts->tc_split != 1 && opts->tc_split != 3)
     return set_error(SCHUR_EINVAL, "tc_split must be 0, 1 or 3");
-  for (int i = 0; i < 4; ++i)
+  if (opts->factor != SCHUR_FACTOR_EXACT && opts->factor != SCHUR_FACTOR_PW)
+    return set_error(SCHUR_EINVAL, "factor must be SCHUR_FACTOR_EXACT or SCHUR_FACTOR_PW");
+  for (int i = 0; i < 3; ++i)
     if (opts->reserved[i]) return set_error(SCHUR_EINVAL, "reserved option fields must be zero");
   double t0 = now_ms();
   schur_ctx* c = new (std::nothrow) schur_ctx();
@@ -329,14 +369,16 @@ int schur_setup(const schur_mesh* mesh, double beta, const schur_opts* opts, voi
   c->opts = *opts;
   c->beta = beta;
   c->gamma = 1.0 / std::sqrt(beta);
+  c->sre = opts->factor == SCHUR_FACTOR_PW ? c->gamma : 0.0;
+  c->sim = opts->factor == SCHUR_FACTOR_PW ? 0.0 : c->gamma;
   std::string msg;
   int rc = get_partition(mesh, opts, &c->mp, &msg);
   if (rc) {
     delete c;
     return set_error(rc, msg);
   }
-  c->eng = opts->precision == SCHUR_MIXED ? make_engine_f32(&c->mp->hm, &c->mp->dm, c->gamma)
-                                          : make_engine_f64(&c->mp->hm, &c->mp->dm, c->gamma);
+  c->eng = opts->precision == SCHUR_MIXED ? make_engine_f32(&c->mp->hm, &c->mp->dm, c->sim, c->sre)
+                                          : make_engine_f64(&c->mp->hm, &c->mp->dm, c->sim, c->sre);
   if (!c->eng) {
     schur_destroy(c);
     return set_error(SCHUR_ENOMEM, "engine allocation failed");
@@ -375,7 +417,7 @@ int schur_solve(schur_ctx* c, const double* b, double* x, int nrhs, int ld, void
   int status = SCHUR_OK;
   for (int r0 = 0; r0 < nrhs; r0 += kMaxR) {
     int R = std::min(kMaxR, nrhs - r0);
-    rc = ctx_outer(c, b + (size_t)r0 * ld, nullptr, ld, R, x + (size_t)r0 * ld, ld, nullptr, 0, s, st);
+    rc = ctx_schur_inverse(c, b + (size_t)r0 * ld, ld, R, x + (size_t)r0 * ld, ld, s, st);
     if (rc == SCHUR_ENOTCONV) status = rc;
     else if (rc) {
       if (st) st->status = rc;
@@ -494,6 +536,7 @@ void schur_destroy(schur_ctx* c) {
   if (c->h_part) cudaFreeHost(c->h_part);
   if (c->hb) cudaFree(c->hb);
   if (c->hx) cudaFree(c->hx);
+  if (c->pw_buf) cudaFree(c->pw_buf);
   kkt_free(c);
   delete c;
 }

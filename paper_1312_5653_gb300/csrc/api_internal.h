@@ -25,6 +25,11 @@ struct schur_ctx {
   schur_mesh mesh;
   schur_opts opts;
   double beta = 0, gamma = 0, ms_setup = 0;
+  // the factor the engine solves with: A = K + (sre + i sim) M (sim = gamma, sre = 0 for the complex
+  // factor of Sec. 4; sre = gamma, sim = 0 for the real factor of the Pearson-Wathen S_p)
+  double sre = 0, sim = 0;
+  // S_p solves: the first factor solve's result and its mass product (n x kMaxR each)
+  double* pw_buf = nullptr;
   long long launches = 0;        // kernels launched by the most recent solve call
   long long total_launches = 0;  // kernels launched through this context since setup
   // FP64 outer refinement workspace
@@ -50,6 +55,9 @@ int set_error(int code, const std::string& msg);
 int ctx_ensure_outer(schur_ctx* c, int R);
 int ctx_outer(schur_ctx* c, const double* bre, const double* bim, int ldb, int R, double* x, int ldx, double* zout,
               int ldz, cudaStream_t st, schur_stats* stats);
+// x = S^{-1} b (exact factor) or x = S_p^{-1} b (Pearson-Wathen factor) for R <= kMaxR columns
+int ctx_schur_inverse(schur_ctx* c, const double* b, int ldb, int R, double* x, int ldx, cudaStream_t st,
+                      schur_stats* stats);
 void kkt_free(schur_ctx* c);
 int get_partition(const schur_mesh* mesh, const schur_opts* opts, std::shared_ptr<MapEntry>* out, std::string* msg);
 }  // namespace schur

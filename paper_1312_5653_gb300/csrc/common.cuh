@@ -129,15 +129,17 @@ template <class R>
 struct Stencil {
   R k_one[3], k_two[3], k_off[3];  // diagonal with 1 or 2 elements, off-diagonal
   R m_one[3], m_two[3], m_off[3];
-  R gamma;
+  R gamma;  // imaginary mass shift: entries of K + i gamma M
+  R sre;    // real mass shift (0 for K + i gamma M; gamma for the real factor K + gamma M)
   int dim;
 };
 
 template <class R>
-inline Stencil<R> make_stencil(const Geom& g, double gamma) {
+inline Stencil<R> make_stencil(const Geom& g, double gamma, double sre = 0.0) {
   Stencil<R> st;
   st.dim = g.dim;
   st.gamma = (R)gamma;
+  st.sre = (R)sre;
   for (int a = 0; a < 3; ++a) {
     double h = a < g.dim ? g.h[a] : 1.0;
     st.k_one[a] = (R)(1.0 / h);
@@ -150,7 +152,7 @@ inline Stencil<R> make_stencil(const Geom& g, double gamma) {
   return st;
 }
 
-// Entry (p, q) of the subdomain Neumann matrix K + i gamma M for local node coordinates p, q
+// Entry (p, q) of the subdomain Neumann matrix K + (sre + i gamma) M for local node coordinates p, q
 // (|p_a - q_a| <= 1 assumed by callers that pass neighbours; others give 0).  s = elements per
 // axis of the segment the counts refer to; pass a huge s for interior (two-element) counts.
 template <class R>
@@ -177,7 +179,7 @@ __host__ __device__ __forceinline__ cx<R> q1_entry(const Stencil<R>& st, const i
     kk = k1[0] * m1[1] * m1[2] + m1[0] * k1[1] * m1[2] + m1[0] * m1[1] * k1[2];
     mm = m1[0] * m1[1] * m1[2];
   }
-  return mkc<R>(kk, st.gamma * mm);
+  return mkc<R>(kk + st.sre * mm, st.gamma * mm);
 }
 
 // Local node <-> coordinates on a box with `ext` nodes per axis.

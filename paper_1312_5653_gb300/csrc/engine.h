@@ -54,7 +54,9 @@ constexpr int kMaxR = 16;
 // (release threshold = unlimited), once per device.
 void configure_pool();
 
-EngineBase* make_engine_f64(const HostMaps* hm, const DevMaps* dm, double gamma);
-EngineBase* make_engine_f32(const HostMaps* hm, const DevMaps* dm, double gamma);
+// The engine solves with A = K + (sre + i gamma) M: sre = 0 for the complex factor of Sec. 4,
+// sre = gamma, gamma = 0 for the real factor K + gamma M of the Pearson-Wathen S_p (Sec. 3.2).
+EngineBase* make_engine_f64(const HostMaps* hm, const DevMaps* dm, double gamma, double sre);
+EngineBase* make_engine_f32(const HostMaps* hm, const DevMaps* dm, double gamma, double sre);
 
 }  // namespace schur

@@ -66,7 +66,8 @@ static cudaError_t launch_factor_cols(const StencilProv<T>& P, const int* codes,
 template <class T>
 class Engine : public EngineBase {
  public:
-  Engine(const HostMaps* hm, const DevMaps* dm, double gamma) : hm_(hm), dm_(dm), g_(hm->g), gamma_(gamma) {
+  Engine(const HostMaps* hm, const DevMaps* dm, double gamma, double sre)
+      : hm_(hm), dm_(dm), g_(hm->g), gamma_(gamma) {
     mv_.slot_node = dm->slot_node;
     mv_.node_slot = dm->node_slot;
     mv_.corner_node = dm->corner_node;
@@ -76,7 +77,7 @@ class Engine : public EngineBase {
     mv_.lam_side = dm->lam_side;
     mv_.sd_corner = dm->sd_corner;
     mv_.sd_minv = dm->sd_minv;
-    st_ = make_stencil<T>(g_, gamma);
+    st_ = make_stencil<T>(g_, gamma, sre);
     ncls_ = hm->ncls;
     // remainder problem: full local grid, vertices and Dirichlet nodes removed
     prr_.ly.dim = g_.dim;

@@ -62,6 +62,80 @@ __global__ void k_lin3(long long n, int R, double* y, int ldy, const double* __r
   }
 }
 
+// Full-grid node of interior node i (coordinates 1..nel-1 per axis) shifted by offset o (3^dim
+// neighbourhood), as an index into a vector over all prod(nel[a] + 1) grid nodes, boundary included.
+__device__ __forceinline__ long long full_index(const Geom& g, long long i, int o) {
+  const long long m0 = g.nel[0] - 1, m1 = g.nel[1] - 1;
+  long long G0 = i % m0 + 1, t = i / m0, G1, G2;
+  if (g.dim == 2) {
+    G1 = t + 1;
+    G2 = 0;
+  } else {
+    G1 = t % m1 + 1;
+    G2 = t / m1 + 1;
+  }
+  G0 += o % 3 - 1;
+  G1 += (o / 3) % 3 - 1;
+  if (g.dim == 3) G2 += o / 9 - 1;
+  return G0 + (long long)(g.nel[0] + 1) * (G1 + (long long)(g.nel[1] + 1) * G2);
+}
+
+__device__ __forceinline__ bool full_on_boundary(const Geom& g, long long f) {
+  const long long e0 = g.nel[0] + 1, e1 = g.nel[1] + 1;
+  const long long c0 = f % e0, c1 = (f / e0) % e1, c2 = f / (e0 * e1);
+  return c0 == 0 || c0 == g.nel[0] || c1 == 0 || c1 == g.nel[1] || (g.dim == 3 && (c2 == 0 || c2 == g.nel[2]));
+}
+
+// out = K ybar + K_c y_c on the interior nodes: the stiffness rows of the interior nodes applied to a
+// vector over the whole grid whose boundary values are the Dirichlet data (Sec. 2: the constraint
+// K y + K_c y_c = M u, and the right-hand side of Eq. schurcomplementsystem).
+__global__ void k_full_stiffness(Geom g, Coef27 cf, const double* __restrict__ yfull, int ldf, double* out, int ld,
+                                 int R) {
+  const int r = blockIdx.y;
+  const int noff = g.dim == 2 ? 9 : 27;
+  const double* yf = yfull + (size_t)r * ldf;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.n; i += (long long)gridDim.x * blockDim.x) {
+    double acc = 0;
+    for (int o = 0; o < noff; ++o) acc += cf.c[o].re * yf[full_index(g, i, o)];
+    out[(size_t)r * ld + i] = acc;
+  }
+}
+
+// y = ybar - w and u = lambda / beta on the interior nodes (Eq. updateyandu, w = M^{-1} K lambda)
+__global__ void k_control_update(Geom g, const double* __restrict__ yfull, int ldf, const double* __restrict__ w,
+                                 const double* __restrict__ lam, int ldw, double inv_beta, double* y, double* u,
+                                 int ld, int R) {
+  const int r = blockIdx.y;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.n; i += (long long)gridDim.x * blockDim.x) {
+    const double yb = yfull[(size_t)r * ldf + full_index(g, i, g.dim == 2 ? 4 : 13)];
+    y[(size_t)r * ld + i] = yb - w[(size_t)r * ldw + i];
+    u[(size_t)r * ld + i] = lam[(size_t)r * ldw + i] * inv_beta;
+  }
+}
+
+// v = K y + K_c y_c - M u (the residual of the state equation, Eq. relativeconstraintviolation):
+// interior neighbours take y, boundary neighbours the Dirichlet data of yfull
+__global__ void k_constraint(Geom g, Coef27 cf, const double* __restrict__ y, const double* __restrict__ u, int ld,
+                             const double* __restrict__ yfull, int ldf, double* v, int ldv, int R) {
+  const int r = blockIdx.y;
+  const int noff = g.dim == 2 ? 9 : 27;
+  const long long s1 = g.nel[0] - 1, s2 = s1 * (g.nel[1] - 1);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.n; i += (long long)gridDim.x * blockDim.x) {
+    double acc = 0;
+    for (int o = 0; o < noff; ++o) {
+      const long long f = full_index(g, i, o);
+      if (full_on_boundary(g, f)) {
+        acc += cf.c[o].re * yfull[(size_t)r * ldf + f];
+      } else {
+        const int d0 = o % 3 - 1, d1 = (o / 3) % 3 - 1, d2 = g.dim == 3 ? o / 9 - 1 : 0;
+        const long long q = i + d0 + s1 * d1 + s2 * d2;
+        acc += cf.c[o].re * y[(size_t)r * ld + q] - cf.c[o].im * u[(size_t)r * ld + q];
+      }
+    }
+    v[(size_t)r * ldv + i] = acc;
+  }
+}
+
 static int grid_for(long long n) { return std::max(1, (int)std::min<long long>((n + 255) / 256, 8 * 152)); }
 
 // w = M^{-1} t by `deg` Chebyshev steps (columns of length n, leading dimension ld); uses 3
@@ -200,7 +274,7 @@ static int kkt_precond_impl(schur_ctx* c, const double* r, double* z, int R, int
   std::memset(&sst, 0, sizeof(sst));
   for (int r0 = 0; r0 < R; r0 += kMaxR) {
     int RR = std::min(kMaxR, R - r0);
-    rc = ctx_outer(c, tin + (size_t)r0 * n, nullptr, (int)n, RR, tout + (size_t)r0 * n, (int)n, nullptr, 0, st, &sst);
+    rc = ctx_schur_inverse(c, tin + (size_t)r0 * n, (int)n, RR, tout + (size_t)r0 * n, (int)n, st, &sst);
     if (rc) return rc;
   }
   k_copy_cols<<<dim3(gs, R), 256, 0, st>>>(n, R, tout, (int)n, z + 2 * n, ld, 1.0);
@@ -264,6 +338,87 @@ int schur_apply_S(schur_ctx* c, const double* x, double* y, int nrhs, int ld, vo
   }
   KKT_CK(cudaStreamSynchronize(st));
   return SCHUR_OK;
+}
+
+// The range-space method of Sec. 3.1 with Dirichlet data (the thermal problem of Sec. 6.1):
+// lambda = S^{-1} (K ybar + K_c y_c), y = ybar - M^{-1} K lambda, u = lambda / beta, and the relative
+// constraint violation ||K y + K_c y_c - M u|| / ||K y|| of Eq. relativeconstraintviolation.
+int schur_control_solve(schur_ctx* c, const double* yfull, int ldf, double* y, double* u, double* lam, int nrhs,
+                        int ld, double* viol, void* stream, schur_stats* st) {
+  if (!c || nrhs < 0) return set_error(SCHUR_EINVAL, "bad arguments");
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+    st->ms_setup = c->ms_setup;
+  }
+  if (nrhs == 0) return SCHUR_OK;
+  const Geom& g = c->mp->hm.g;
+  const long long n = g.n;
+  long long nfull = 1;
+  for (int a = 0; a < g.dim; ++a) nfull *= (long long)g.nel[a] + 1;
+  if (!yfull || !y || !u) return set_error(SCHUR_EINVAL, "NULL vector");
+  if ((long long)ldf < nfull) return set_error(SCHUR_EINVAL, "ldf smaller than the number of grid nodes");
+  if ((long long)ld < n) return set_error(SCHUR_EINVAL, "ld < n");
+  if (c->opts.factor != SCHUR_FACTOR_EXACT)
+    return set_error(SCHUR_EINVAL, "the range-space solve needs the exact factor (SCHUR_FACTOR_EXACT)");
+  cudaStream_t st_ = reinterpret_cast<cudaStream_t>(stream);
+  Coef27 sten = make_coef(g, 1.0);
+  const int gs = grid_for(n);
+  const int deg = cheb_degree(g.dim, 1e-15);
+  int status = SCHUR_OK;
+  for (int r0 = 0; r0 < nrhs; r0 += kMaxR) {
+    const int R = std::min(kMaxR, nrhs - r0);
+    int rc = kkt_ws(c, R);
+    if (rc) return rc;
+    const size_t nR = (size_t)n * R;
+    double* rhs = c->kkt_buf;
+    double* lw = rhs + nR;
+    double* t = lw + nR;
+    double* w = t + nR;
+    double* scr = w + nR;  // 3 n R
+    double* v = scr + 3 * nR;
+    double* ky = v + nR;
+    const double* yf = yfull + (size_t)r0 * ldf;
+    double* yr = y + (size_t)r0 * ld;
+    double* ur = u + (size_t)r0 * ld;
+    k_full_stiffness<<<dim3(gs, R), 256, 0, st_>>>(g, sten, yf, ldf, rhs, (int)n, R);
+    KKT_CK(cudaGetLastError());
+    schur_stats sst;
+    std::memset(&sst, 0, sizeof(sst));
+    rc = ctx_schur_inverse(c, rhs, (int)n, R, lw, (int)n, st_, &sst);
+    if (rc == SCHUR_ENOTCONV) status = rc;
+    else if (rc) return rc;
+    if (st) {
+      st->outer_steps = std::max(st->outer_steps, sst.outer_steps);
+      st->iters_total = std::max(st->iters_total, sst.iters_total);
+      st->iters_first = std::max(st->iters_first, sst.iters_first);
+      st->rel_residual = std::max(st->rel_residual, sst.rel_residual);
+    }
+    // w = M^{-1} K lambda
+    k_apply_real<<<dim3(gs, R), 256, 0, st_>>>(g, sten, 1, lw, (int)n, t, (int)n, R, 1.0, 0.0);
+    KKT_CK(cudaGetLastError());
+    rc = mass_inverse(c, t, (int)n, w, (int)n, R, deg, scr, st_);
+    if (rc) return rc;
+    k_control_update<<<dim3(gs, R), 256, 0, st_>>>(g, yf, ldf, w, lw, (int)n, 1.0 / c->beta, yr, ur, ld, R);
+    KKT_CK(cudaGetLastError());
+    if (lam) {
+      k_copy_cols<<<dim3(gs, R), 256, 0, st_>>>(n, R, lw, (int)n, lam + (size_t)r0 * ld, ld, 1.0);
+      KKT_CK(cudaGetLastError());
+    }
+    if (viol) {
+      k_constraint<<<dim3(gs, R), 256, 0, st_>>>(g, sten, yr, ur, ld, yf, ldf, v, (int)n, R);
+      k_apply_real<<<dim3(gs, R), 256, 0, st_>>>(g, sten, 1, yr, ld, ky, (int)n, R, 1.0, 0.0);
+      KKT_CK(cudaGetLastError());
+      std::vector<double> vv(R), kk(R);
+      rc = dots(c, n, v, (int)n, v, (int)n, R, vv.data(), st_);
+      if (rc) return rc;
+      rc = dots(c, n, ky, (int)n, ky, (int)n, R, kk.data(), st_);
+      if (rc) return rc;
+      for (int r = 0; r < R; ++r) viol[r0 + r] = kk[r] > 0 ? std::sqrt(vv[r] / kk[r]) : std::sqrt(vv[r]);
+    }
+  }
+  KKT_CK(cudaStreamSynchronize(st_));
+  if (st) st->status = status;
+  return status;
 }
 
 // Preconditioned MINRES (Lanczos with P_mgw, Givens QR of the tridiagonal), one independent

@@ -18,10 +18,10 @@ __device__ __forceinline__ void node_crd(const Geom& g, long long gi, int* G) {
   }
 }
 
-Coef27 make_coef(const Geom& g, double gamma) {
+Coef27 make_coef(const Geom& g, double gamma, double sre) {
   // every interior node has two elements per axis, so the assembled coefficient of a neighbour
   // depends only on the offset
-  Stencil<double> st = make_stencil<double>(g, gamma);
+  Stencil<double> st = make_stencil<double>(g, gamma, sre);
   Coef27 cf;
   int G[3] = {1, 1, 1};
   for (int o = 0; o < 27; ++o) {
@@ -93,6 +93,13 @@ __global__ void k_shortcut(long long n, const cx<double>* __restrict__ z, int ld
   const int r = blockIdx.y;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     x[(size_t)r * ldx + i] = -z[(size_t)r * ldz + i].im * inv_gamma;
+}
+
+__global__ void k_real_part(long long n, const cx<double>* __restrict__ z, int ldz, int R, double scale, double* x,
+                            int ldx) {
+  const int r = blockIdx.y;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[(size_t)r * ldx + i] = z[(size_t)r * ldz + i].re * scale;
 }
 
 __global__ void k_split_complex(long long n, const cx<double>* __restrict__ z, int ldz, int R, double* out, int ldo) {

@@ -81,6 +81,9 @@ struct schur_server {
   std::deque<std::shared_ptr<Request>> queue;  // arrival order
   std::map<Key, Entry> cache;
   long long bytes_used = 0, next_ticket = 1, completed = 0;
+  // batching statistics (guarded by mu)
+  long long n_batches = 0, n_batch_cols = 0, n_shared = 0, n_setups = 0;
+  int inflight = 0, max_inflight = 0;
   bool stop = false;
   std::vector<std::thread> workers;
 
@@ -221,6 +224,11 @@ struct schur_server {
         ent->busy = 1;
       }
       const Key key = head->key;
+      ++n_batches;
+      n_batch_cols += cols;
+      if (batch.size() > 1) n_shared += (long long)batch.size();
+      if (need_setup) ++n_setups;
+      max_inflight = std::max(max_inflight, ++inflight);
       lk.unlock();
       int rc = SCHUR_OK;
       schur_ctx* ctx = ent->ctx;
@@ -267,6 +275,7 @@ struct schur_server {
         fprintf(stderr, "schur_server: batch of %d request(s) failed: %s: %s\n", (int)batch.size(), schur_strerror(rc),
                 schur_last_error());
       lk.lock();
+      --inflight;
       auto it = cache.find(key);
       if (it != cache.end()) {
         if (!it->second.ctx && ctx) it->second.ctx = ctx;
@@ -393,6 +402,12 @@ int schur_server_info(schur_server* s, schur_server_info_t* info) {
   info->queued = (int)s->queue.size();
   info->completed = s->completed;
   info->bytes_reserved = s->bytes_used;
+  info->batches = s->n_batches;
+  info->batch_columns = s->n_batch_cols;
+  info->shared_requests = s->n_shared;
+  info->setups = s->n_setups;
+  info->max_concurrent = s->max_inflight;
+  for (int i = 0; i < 3; ++i) info->reserved[i] = 0;
   return SCHUR_OK;
 }
 

@@ -106,3 +106,31 @@ def manufactured(dim, nel, beta):
     """Target whose continuum optimal state is prod_a sin(pi x_a): (I + beta Lap^2) y = y_bar and
     Lap^2 of the sine product is (dim pi^2)^2 times it."""
     return (1.0 + (dim * np.pi ** 2) ** 2 * beta) * sine_mode(dim, nel, (1,) * dim)
+
+
+def thermal_target(nel):
+    """The target temperature of the paper's thermal problem (Sec. 6.1, Eq. ex1target) on all
+    (nel+1)^2 nodes of the unit square, boundary included (lexicographic, axis 0 fastest):
+    (2 x1 - 1)^2 (2 x2 - 1)^2 on [0, 1/2]^2 and 0 elsewhere.  Its boundary values are the Dirichlet
+    data y_c (Eq. ex1boundarycondition)."""
+    nel = [int(nel)] * 2 if np.isscalar(nel) else list(nel)
+    x0 = np.arange(nel[0] + 1) / nel[0]
+    x1 = np.arange(nel[1] + 1) / nel[1]
+    X1, X0 = np.meshgrid(x1, x0, indexing="ij")  # array axis 1 = grid axis 0 (fastest)
+    y = (2 * X0 - 1) ** 2 * (2 * X1 - 1) ** 2
+    y[(X0 > 0.5) | (X1 > 0.5)] = 0.0
+    return np.ascontiguousarray(y.reshape(-1))
+
+
+def harmonic_full(dim, nel, coef=(1.0, 1.0, 2.0, 1.0)):
+    """c0 + c1 x1 + c2 x2 + c3 x1 x2 (times 1 + x3 in 3D) on all grid nodes, boundary included: a
+    target for which the state equation holds with zero control (Q1 reproduces it, and it is
+    harmonic), so the optimal control problem's solution is y = ybar, u = 0, lambda = 0."""
+    nel = [int(nel)] * dim if np.isscalar(nel) else list(nel)
+    axes = [np.arange(nel[a] + 1) / nel[a] for a in range(dim)]
+    grids = np.meshgrid(*axes[::-1], indexing="ij")[::-1]  # grids[a] varies along grid axis a
+    c0, c1, c2, c3 = coef
+    y = c0 + c1 * grids[0] + c2 * grids[1] + c3 * grids[0] * grids[1]
+    if dim == 3:
+        y = y * (1.0 + grids[2])
+    return np.ascontiguousarray(y.reshape(-1))

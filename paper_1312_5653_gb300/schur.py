@@ -22,6 +22,8 @@ SCHUR_FP64 = 0
 SCHUR_MIXED = 1
 SCHUR_LOCAL_PER_SUBDOMAIN = 0
 SCHUR_LOCAL_SHARED = 1
+SCHUR_FACTOR_EXACT = 0
+SCHUR_FACTOR_PW = 1
 
 
 class schur_mesh(ctypes.Structure):
@@ -31,7 +33,8 @@ class schur_mesh(ctypes.Structure):
 class schur_opts(ctypes.Structure):
     _fields_ = [("nsub", ctypes.c_int * 3), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
                 ("inner_tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int),
-                ("local_mode", ctypes.c_int), ("tc_split", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("local_mode", ctypes.c_int), ("tc_split", ctypes.c_int), ("factor", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 class schur_stats(ctypes.Structure):
@@ -68,7 +71,7 @@ EXPORTS = [
     "schur_apply_mass", "schur_apply_stiffness", "schur_apply_S", "schur_kkt_apply", "schur_kkt_precond_apply",
     "schur_kkt_minres", "schur_partition", "schur_partition_export", "schur_get_info", "schur_ndof",
     "schur_destroy", "schur_strerror", "schur_last_error", "schur_debug_operator", "schur_profile_begin",
-    "schur_profile_end", "schur_kernel_category_name", "schur_launch_count", "schur_apply_S_static",
+    "schur_profile_end", "schur_kernel_category_name", "schur_launch_count", "schur_apply_S_static", "schur_peak_probe", "schur_control_solve",
     "schur_server_default_opts", "schur_server_create", "schur_submit", "schur_poll", "schur_wait",
     "schur_server_info", "schur_server_destroy",
 ]
@@ -115,6 +118,8 @@ def load(build_if_missing=True):
         "schur_kernel_category_name": (ctypes.c_char_p, [I]),
         "schur_launch_count": (LL, [P]),
         "schur_apply_S_static": (I, [ctypes.POINTER(schur_mesh), D, P, P, I, I, P]),
+        "schur_peak_probe": (I, [I, I, ctypes.POINTER(D), P]),
+        "schur_control_solve": (I, [P, P, I, P, P, P, I, I, P, P, ctypes.POINTER(schur_stats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -150,6 +155,17 @@ def schur_profile_end():
     _check(load().schur_profile_end(arr, cap, ctypes.byref(cnt)), "schur_profile_end")
     return {load().schur_kernel_category_name(arr[k].category).decode(): (arr[k].launches, arr[k].total_ms)
             for k in range(cnt.value)}
+
+
+PEAK_KINDS = {0: "fp64_fma", 1: "fp32_fma", 2: "fp64_dmma", 3: "tf32_tcgen05"}
+
+
+def schur_peak_probe(kind, iters, stream=None):
+    """Measured TFLOP/s of one arithmetic peak probe (kind: see PEAK_KINDS); synchronises."""
+    out = ctypes.c_double(0.0)
+    _check(load().schur_peak_probe(int(kind), int(iters), ctypes.byref(out), _stream_ptr(stream)),
+           "schur_peak_probe")
+    return out.value
 
 
 def make_mesh(dim, nel):
@@ -304,6 +320,26 @@ class Solver:
     def schur_apply_S(self, x, y=None, stream=None):
         return self._apply(self.lib.schur_apply_S, x, y, stream, "schur_apply_S")
 
+    def schur_control_solve(self, ybar_full, stream=None, want_violation=True):
+        """Range-space solve with Dirichlet data: ybar_full (float64 CUDA tensor, (nfull,) or
+        (nrhs, nfull) over all grid nodes) -> (y, u, lambda, violation per column or None)."""
+        import numpy as np
+        import torch
+        nrhs, ldf = self._shape(ybar_full)
+        shape = (self.n,) if ybar_full.dim() == 1 else (nrhs, self.n)
+        y = torch.empty(shape, dtype=torch.float64, device=ybar_full.device)
+        u = torch.empty_like(y)
+        lam = torch.empty_like(y)
+        viol = np.zeros(max(nrhs, 1)) if want_violation else None
+        st = schur_stats()
+        rc = self.lib.schur_control_solve(self.ctx, _dptr(ybar_full, "ybar_full"), ldf, _dptr(y, "y"), _dptr(u, "u"),
+                                          _dptr(lam, "lambda"), nrhs, self.n,
+                                          None if viol is None else viol.ctypes.data_as(ctypes.c_void_p),
+                                          _stream_ptr(stream), ctypes.byref(st))
+        self.last_stats = st.as_dict()
+        _check(rc, "schur_control_solve")
+        return y, u, lam, (None if viol is None else viol[:nrhs])
+
     def schur_kkt_apply(self, v, r=None, stream=None):
         return self._apply(self.lib.schur_kkt_apply, v, r, stream, "schur_kkt_apply")
 
@@ -339,7 +375,9 @@ class schur_server_opts(ctypes.Structure):
 
 class schur_server_info_t(ctypes.Structure):
     _fields_ = [("cached_contexts", ctypes.c_int), ("queued", ctypes.c_int), ("completed", ctypes.c_longlong),
-                ("bytes_reserved", ctypes.c_longlong)]
+                ("bytes_reserved", ctypes.c_longlong), ("batches", ctypes.c_longlong),
+                ("batch_columns", ctypes.c_longlong), ("shared_requests", ctypes.c_longlong),
+                ("setups", ctypes.c_longlong), ("max_concurrent", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 def _load_server_syms(lib):
@@ -414,7 +452,7 @@ class Server:
     def info(self):
         i = schur_server_info_t()
         _check(self.lib.schur_server_info(self.srv, ctypes.byref(i)), "schur_server_info")
-        return {k: getattr(i, k) for k, _ in i._fields_}
+        return {k: getattr(i, k) for k, _ in i._fields_ if k != "reserved"}
 
     def close(self):
         if self.srv:

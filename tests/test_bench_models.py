@@ -50,3 +50,32 @@ def test_apply_models_count_packed_storage():
     assert sb == nsd * 1830 * cb + nlam * cb + nsd * 60 * cb
     _, c = bench.algorithmic("coarse_apply", info, 4)
     assert c == (125 * 126 // 2) * 1024 * cb + 2 * nco * cb
+
+
+def test_recorded_traffic_follows_the_kernel_sources(tmp_path):
+    """A recorded ncu DRAM figure is used only while the kernel's sources hash to the recorded value."""
+    k = "k_form_rr_cols<float, 17>"
+    h = bench.kernel_source_hash(k)
+    good = tmp_path / "t.md"
+    good.write_text("| kernel | launches | dram bytes per launch | source hash |\n|---|---|---|---|\n"
+                    "| `%s` | 3 | 1,234,567 | `%s` |\n" % (k, h))
+    assert bench.recorded_traffic(k, str(good)) == 1234567.0
+    stale = tmp_path / "s.md"
+    stale.write_text("| `%s` | 3 | 1234567 | `0000000000000000` |\n" % k)
+    assert bench.recorded_traffic(k, str(stale)) is None
+    assert bench.recorded_traffic("k_other", str(good)) is None
+    assert bench.recorded_traffic(k, str(tmp_path / "missing.md")) is None
+
+
+def test_category_roofline_units():
+    """HBM categories: bytes per launch / average launch time vs GB/s; ALU: flops per launch vs TFLOP/s."""
+    info = S.schur_partition(2, 1024, 64)
+    peaks = {"hbm_gbs": 6000.0, "fp32_fma": 60.0, "fp64_fma": 1.0}
+    r = bench.category_roofline("apply_F", info, 100, 2.0, 1, peaks)  # 100 launches, 20 us each
+    _, byts = bench.algorithmic("apply_F", info, 4)
+    assert r["bound"] == "hbm" and abs(r["achieved"] - byts / 20e-6 / 1e9) < 1e-6 * r["achieved"]
+    assert abs(r["frac"] - r["achieved"] / 6000.0) < 1e-12
+    f = bench.category_roofline("form", info, 2, 2.0, 2, peaks)  # one launch per step, 1 ms each
+    _, flops = bench.algorithmic("form", info, 4)
+    assert f["bound"] == "alu" and abs(f["achieved"] - flops / 1e-3 / 1e12) < 1e-9 * f["achieved"]
+    assert f["peak"] == 60.0 and f["algorithmic_bytes_per_launch"] > 0

@@ -261,3 +261,106 @@ def test_mgw_preconditioner_three_eigenvalues():
     targets = np.array([1.0, (1 + 5 ** 0.5) / 2, (1 - 5 ** 0.5) / 2])
     dist = np.abs(ev[:, None] - targets[None, :]).min(axis=1)
     assert dist.max() < 1e-8
+
+
+def test_fd_threads_do_not_change_results():
+    """The OpenMP split of the O2 sine transforms gives bitwise the same x for 1 and 4 threads."""
+    b = np.random.default_rng(11).standard_normal((2, 63 * 47))
+    prev = oracle.set_threads(0)  # the count in effect, unchanged
+    try:
+        oracle.set_threads(1)
+        x1 = oracle.fd_schur_solve(2, (64, 48), 1e-4, b)
+        oracle.set_threads(4)
+        x4 = oracle.fd_schur_solve(2, (64, 48), 1e-4, b)
+    finally:
+        oracle.set_threads(prev)
+    assert np.array_equal(x1, x4)
+
+
+# ------------------------------------------------------------ Dirichlet data, S_p (Sec. 3.2, 6.1)
+def _full_kron_K(dim, nel):
+    """Independent assembly of the stiffness on ALL grid nodes (Neumann, boundary included) as
+    Kronecker products of 1D matrices whose end rows have one element: K1 = (1/h) tridiag(-1, 2, -1)
+    with 1/h at both ends."""
+    nel = [nel] * dim if np.isscalar(nel) else nel
+    K1, M1 = [], []
+    for a in range(dim):
+        m, h = nel[a] + 1, 1.0 / nel[a]
+        E = np.eye(m, k=1) + np.eye(m, k=-1)
+        d = np.full(m, 2.0)
+        d[0] = d[-1] = 1.0
+        K1.append((np.diag(d) - E) / h)
+        M1.append(h * (np.diag(2 * d) + E) / 6)
+
+    def kron_axes(mats):
+        out = np.array([[1.0]])
+        for a in reversed(range(dim)):
+            out = np.kron(out, mats[a])
+        return out
+
+    return sum(kron_axes([K1[a] if a == t else M1[a] for a in range(dim)]) for t in range(dim))
+
+
+@pytest.mark.parametrize("dim,nel", [(2, 7), (2, (6, 9)), (3, 4), (3, (3, 5, 4))])
+def test_full_stiffness_against_kronecker_assembly(dim, nel):
+    """K y + K_c y_c (Sec. 2) equals the interior rows of an independently assembled full-grid
+    stiffness applied to the full vector; harmonic (bi/trilinear) data give zero."""
+    Kf = _full_kron_K(dim, nel)
+    inner = oracle.interior_index(dim, nel)
+    y = np.random.default_rng(3).standard_normal(oracle.nfull(dim, nel))
+    assert rel(oracle.full_stiffness(dim, nel, y), (Kf @ y)[inner]) < 1e-13
+    assert np.abs(oracle.full_stiffness(dim, nel, inputs.harmonic_full(dim, nel))).max() < 1e-12
+    # zero boundary data: the interior operator K of the homogeneous problem
+    yz = np.zeros_like(y)
+    yz[inner] = y[inner]
+    Kx, _ = oracle.apply_KM(dim, nel, y[inner])
+    assert rel(oracle.full_stiffness(dim, nel, yz), Kx) < 1e-13
+
+
+def test_control_solve_harmonic_target_is_exact():
+    """If ybar is harmonic and its boundary values are y_c, y = ybar satisfies the state equation
+    with u = 0 at zero cost: the solution is (ybar, 0, 0)."""
+    for dim, nel in [(2, 12), (3, 6)]:
+        yf = inputs.harmonic_full(dim, nel)
+        yb = oracle.interior_of(dim, nel, yf)
+        for fd in (False, True):
+            y, u, l = oracle.control_solve(dim, nel, 1e-4, yf, fd=fd)
+            assert rel(y, yb) < 1e-12
+            assert np.linalg.norm(u) < 1e-10 * np.linalg.norm(yb) and np.linalg.norm(l) < 1e-14 * np.linalg.norm(yb)
+
+
+@pytest.mark.parametrize("beta", [2e-2, 2e-5, 2e-8])
+def test_control_solve_thermal_target(beta):
+    """Sec. 6.1: the paper's target and boundary data.  O1 (banded KKT) and O2 (sine basis) agree;
+    the solution satisfies the constraint K y + K_c y_c = M u, u = lambda / beta, and
+    S lambda = K ybar + K_c y_c (Eq. schurcomplementsystem) against a dense S."""
+    N = 16
+    yf = inputs.thermal_target(N)
+    y1, u1, l1 = oracle.control_solve(2, N, beta, yf)
+    y2, u2, l2 = oracle.control_solve(2, N, beta, yf, fd=True)
+    assert rel(y2, y1) < 1e-11 and rel(u2, u1) < 1e-11 and rel(l2, l1) < 1e-11
+    K, M = kron_KM(2, N)
+    kc = oracle.boundary_coupling(2, N, yf)
+    assert np.linalg.norm(K @ y1 + kc - M @ u1) < 1e-10 * np.linalg.norm(K @ y1)
+    assert rel(u1, l1 / beta) < 1e-12
+    S = K @ np.linalg.solve(M, K) + M / beta
+    yb = oracle.interior_of(2, N, yf)
+    assert rel(S @ l1, K @ yb + kc) < 1e-9
+
+
+def test_thermal_target_values():
+    """Eq. ex1target on a 4 x 4 grid: (2x - 1)^2 (2y - 1)^2 on [0, 1/2]^2, 0 elsewhere."""
+    t = inputs.thermal_target(4).reshape(5, 5)  # [x2 index, x1 index]
+    assert t[0, 0] == 1.0 and t[0, 1] == 0.25 and t[1, 1] == 0.0625 and t[2, 2] == 0.0
+    assert t[0, 3] == 0.0 and t[3, 0] == 0.0 and t[1, 0] == 0.25
+
+
+@pytest.mark.parametrize("dim,nel", [(2, 6), (3, 4)])
+def test_pw_solve_against_dense(dim, nel):
+    """O2's S_p^{-1} b (Sec. 3.2, Eq. pearsonapproximation) against a dense (K + gM) M^-1 (K + gM)."""
+    beta = 1e-3
+    K, M = kron_KM(dim, nel)
+    g = 1.0 / np.sqrt(beta)
+    Sp = (K + g * M) @ np.linalg.solve(M, K + g * M)
+    b = np.random.default_rng(4).standard_normal((2, K.shape[0]))
+    assert rel(oracle.fd_pw_solve(dim, nel, beta, b), np.linalg.solve(Sp, b.T).T) < 1e-12
