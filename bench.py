@@ -558,8 +558,11 @@ def serve_stream(args, S, inputs, oracle):
         return np.ascontiguousarray(np.roll(pool[(dim, N)], i, axis=0)[:R])
 
     def run(prec, arrivals, count):
-        # Krylov space of at most 100 vectors per right-hand side (the FP64 form needs < 80 here)
-        srv = S.Server(budget_bytes=64 << 30, workers=4, precision=prec, tol=1e-10, max_iter=100)
+        # Krylov space of at most 100 vectors per right-hand side for the FP64 form (it needs < 80
+        # here), 60 for the mixed form (its inner solves stop at a loose tolerance, < 20 iterations);
+        # a budget that holds the contexts of all 48 (mesh, beta) keys of the stream
+        srv = S.Server(budget_bytes=160 << 30, workers=4, precision=prec, tol=1e-10,
+                       max_iter=60 if prec == S.SCHUR_MIXED else 100)
         try:
             lat, pend, nsolve, rejected = [], {}, 0, 0
             t0 = time.perf_counter()
@@ -615,7 +618,7 @@ def serve_stream(args, S, inputs, oracle):
     # spot check of served results against the oracle: the first requests of each kind (2D up to
     # 256^2, 2D 1024^2, 3D up to 64^3; first two columns of each)
     oracle.set_threads(os.cpu_count() or 1)
-    srv = S.Server(budget_bytes=16 << 30, workers=2, precision=S.SCHUR_MIXED, tol=1e-10)
+    srv = S.Server(budget_bytes=64 << 30, workers=2, precision=S.SCHUR_MIXED, tol=1e-10, max_iter=60)
     try:
         errs = []
         picks = [q for q in reqs if q[0] == 2 and q[1] <= 256][:3] + [q for q in reqs if q[1] == 1024][:1] + \

@@ -107,9 +107,12 @@ struct schur_server {
   long long estimate(const schur_mesh& m, int nrhs) const {
     if (m.dim != 2 && m.dim != 3) return -1;
     long long nsd = 1, nl = 1, ni = 1, n = 1, nco = 1, nlam = 0, L = 1;
+    long long Pa[3] = {1, 1, 1}, sa[3] = {1, 1, 1};
     for (int a = 0; a < m.dim; ++a) {
       int P = pick_nsub(m.nel[a], m.dim), s = m.nel[a] / P;
       if (s < 2) return -1;
+      Pa[a] = P;
+      sa[a] = s;
       nsd *= P;
       nl *= s + 1;
       ni *= s - 1;
@@ -118,8 +121,20 @@ struct schur_server {
       L = s + 1;
     }
     const long long nD = nl - ni - (1LL << m.dim), b = nl / L;
-    nlam = nsd * nD;  // upper bound (each slot in at most 3 multipliers, half owned)
-    if (m.dim == 3) nlam *= 2;
+    // multipliers: one per interior face node of each pair of face neighbours; in 3D also six per
+    // node of each subdomain edge line shared by four subdomains (fully redundant)
+    for (int a = 0; a < m.dim; ++a) {
+      long long f = Pa[a] - 1;
+      for (int c = 0; c < m.dim; ++c)
+        if (c != a) f *= Pa[c] * (sa[c] - 1);
+      nlam += f;
+      if (m.dim == 3) {
+        long long e = 6 * Pa[a] * (sa[a] - 1);
+        for (int c = 0; c < 3; ++c)
+          if (c != a) e *= Pa[c] - 1;
+        nlam += e;
+      }
+    }
     const long long cxb = o.precision == SCHUR_MIXED ? 8 : 16;
     long long ops = nsd * (L * b * b + 2 * nD * nD + 8 * nD) * cxb + nco * nco * cxb;
     // 3D mixed setup also holds the two layer-coupling arrays of the tensor-core formation

@@ -205,6 +205,11 @@ __global__ void __launch_bounds__(128) k_form_rr_cols(StencilProv<T> P, Geom g, 
         iu = node % b;
       }
     }
+    // first layer where this column's right-hand side is nonzero: the forward results E_K of the
+    // layers before it are zero, so they are neither stored nor read back (L: the column is zero)
+    int K0 = L;
+    if (Ku >= 0) K0 = Ku;
+    if (is_corner && !cDir[cc]) K0 = max(0, cK[cc] - 1);
     auto stage = [&](int K, int buf) {
       const cx<T>* src = Dinv + ((size_t)q * L + K) * bb;
       cx<T>* dst = Db + buf * B * SB;
@@ -218,7 +223,7 @@ __global__ void __launch_bounds__(128) k_form_rr_cols(StencilProv<T> P, Geom g, 
     for (int i = 0; i < B; ++i) prev[i] = czero<T>();
 #pragma unroll
     for (int k = 0; k < 4; ++k) kacc[k] = czero<T>();
-    auto emit = [&](int K, const cx<T>* x) {
+    auto emit = [&](int K, const cx<T>(&x)[B]) {
       if (is_unit || is_corner) {
 #pragma unroll
         for (int i = 0; i < B; ++i) {
@@ -296,7 +301,7 @@ __global__ void __launch_bounds__(128) k_form_rr_cols(StencilProv<T> P, Geom g, 
         }
         if (B & 1) cfma(prev[B - 1], Dk[mm * SB + B - 1], tm);
       }
-      if (c < ldE) {
+      if (c < ldE && K >= K0) {
 #pragma unroll
         for (int i = 0; i < B; ++i)
           if (i < b) E[((size_t)K * B + i) * ldE + c] = prev[i];
@@ -316,7 +321,7 @@ __global__ void __launch_bounds__(128) k_form_rr_cols(StencilProv<T> P, Geom g, 
       }
       cx<T> x[B];
 #pragma unroll
-      for (int i = 0; i < B; ++i) x[i] = (c < ldE && i < b) ? E[((size_t)K * B + i) * ldE + c] : czero<T>();
+      for (int i = 0; i < B; ++i) x[i] = (c < ldE && i < b && K >= K0) ? E[((size_t)K * B + i) * ldE + c] : czero<T>();
       cp_async_wait<1>();
       __syncthreads();
       cx<T> u[B];

@@ -66,10 +66,37 @@ def local_operators(dim, N, P, beta, sd):
     return F, Frc, Sd
 
 
-def dense_feti_dp(dim, N, P, beta, b):
+def face_pairs(dim, P, lam, nD):
+    """Q of the augmented coarse problem (Sec. 5, augmentation by the edge-based translational mode):
+    one column per pair of face-adjacent subdomains, ones on the multipliers between that pair.
+    Returns (Q, list of pairs)."""
+    pairs, col = [], {}
+    Q = np.zeros((len(lam), 0))
+    entries = []
+    for li, (a, bb) in enumerate(lam):
+        sa, sb = int(a) // nD, int(bb) // nD
+        ca = [(sa // P ** t) % P for t in range(dim)]
+        cb = [(sb // P ** t) % P for t in range(dim)]
+        if sum(abs(x - y) for x, y in zip(ca, cb)) != 1:
+            continue  # 3D diagonal pairs along subdomain edge lines: not a face
+        key = (min(sa, sb), max(sa, sb))
+        if key not in col:
+            col[key] = len(pairs)
+            pairs.append(key)
+        entries.append((li, col[key]))
+    Q = np.zeros((len(lam), len(pairs)))
+    for li, c in entries:
+        Q[li, c] = 1.0
+    return Q, pairs
+
+
+def dense_feti_dp(dim, N, P, beta, b, aug=False):
     """Plain dense FETI-DP for (K + i gamma M) z = b following Sec. 5: corners primal, remainder
     matrices A_rr, jump operator B from the exported maps, coarse matrix, dual problem solved
-    exactly, primal recovery by averaging the subdomain copies."""
+    exactly, primal recovery by averaging the subdomain copies.  aug=True augments the coarse
+    problem with the constraints Q^T B u = 0 (zero average jump across every subdomain face, enforced
+    by coarse unknowns mu): coarse matrix [[K_cc, -X^T], [-X, -Y]] with X = Q^T F_rc, Y = Q^T F_rr Q,
+    coupling Phi = [F_rc, F_rr Q], right-hand side [f_c; -Q^T d_r], multipliers lambda + Q mu."""
     s = N // P
     A, loc = local_neumann(dim, N, P, beta)
     nl = len(loc)
@@ -126,11 +153,26 @@ def dense_feti_dp(dim, N, P, beta, b):
             if ci not in cdone:
                 fc[ci] += b[gid(sub["G"][i])]
                 cdone.add(ci)
-    Kinv = np.linalg.inv(Kcc) if nco else np.zeros((0, 0))
-    F = Frr + Frc @ Kinv @ Frc.T
-    d = dr - Frc @ Kinv @ fc
-    lamv = np.linalg.lstsq(F, d, rcond=None)[0]
-    uc = Kinv @ (fc + Frc.T @ lamv)
+    if aug:
+        Q, _ = face_pairs(dim, P, lam, nD)
+        X = Q.T @ Frc
+        Y = Q.T @ Frr @ Q
+        Kaug = np.block([[Kcc, -X.T], [-X, -Y]])
+        Phi = np.concatenate([Frc, Frr @ Q], axis=1)
+        rhs0 = np.concatenate([fc, -Q.T @ dr])
+        Ka_inv = np.linalg.inv(Kaug)
+        F = Frr + Phi @ Ka_inv @ Phi.T
+        d = dr - Phi @ Ka_inv @ rhs0
+        lam0 = np.linalg.lstsq(F, d, rcond=None)[0]
+        w = Ka_inv @ (rhs0 + Phi.T @ lam0)
+        uc = w[:nco]
+        lamv = lam0 + Q @ w[nco:]
+    else:
+        Kinv = np.linalg.inv(Kcc) if nco else np.zeros((0, 0))
+        F = Frr + Frc @ Kinv @ Frc.T
+        d = dr - Frc @ Kinv @ fc
+        lamv = np.linalg.lstsq(F, d, rcond=None)[0]
+        uc = Kinv @ (fc + Frc.T @ lamv)
     z = np.zeros(n, complex)
     cnt = np.zeros(n)
     for sub in subs:
