@@ -530,6 +530,53 @@ def row_thermal(args, torch, S, inputs, oracle, dev, stream):
     return out
 
 
+# the paper's Table 1, FETI-DPH iterations with the rigid-body-mode augmentation on
+# K + M/(i sqrt(phi)) ("RAUG+"), for context
+TABLE1_RAUG_PLUS = {2e-2: 13, 2e-4: 13, 2e-6: 13, 2e-8: 13, 2e-10: 17, 2e-12: 26}
+
+
+def row_augmented(args, torch, S, inputs, oracle, dev, stream):
+    """The augmented coarse problem (Sec. 5, RAUG: one face-average constraint per pair of
+    face-adjacent subdomains beside the corners) at the paper's subdomain size ratio H/h = 64:
+    2D 1024^2 Q1 elements in 16 x 16 subdomains of 64^2 (the h = 1/1024 row of the paper's Table 2),
+    phi over Table 1's range.  Per phi: GMRES iterations of one FP64 FETI-DP solve to 1e-10 without
+    and with the augmentation, the mixed form's setup + solve time both ways, and at phi = 2e-8 the
+    augmented mixed result against the oracle."""
+    N, P = 1024, 16
+    n = (N - 1) ** 2
+    b = oracle.apply_M(2, N, inputs.smoothed_noise(2, N, seed=1))
+    bd = torch.from_numpy(b).to(dev)
+    out = {"workload": "2d-q1-1024^2-dirichlet-16x16sub-64x64el-smoothed-noise", "n_dofs": n,
+           "coarse_unknowns": {"corners": (P - 1) ** 2, "augmented": (P - 1) ** 2 + 2 * (P - 1) * P}, "per_phi": {}}
+    for aug in (0, 1):  # warm-up of both setups
+        S.Solver(2, N, THERMAL_PHIS[0], nsub=P, precision=S.SCHUR_MIXED, tol=OUTER_TOL, augment=aug).close()
+    for phi in THERMAL_PHIS:
+        r = {"table1_iters_plus_no_aug": TABLE1_PLUS.get(phi), "table1_iters_plus_raug": TABLE1_RAUG_PLUS.get(phi)}
+        for aug, key in ((0, "corners"), (1, "augmented")):
+            sol = S.Solver(2, N, phi, nsub=P, precision=S.SCHUR_FP64, tol=1e-3, inner_tol=1e-10, max_refine=1,
+                           augment=aug)
+            sol.schur_solve(bd)
+            r["fp64_gmres_iters_" + key] = sol.last_stats["iters_first"]
+            sol.close()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sol = S.Solver(2, N, phi, nsub=P, precision=S.SCHUR_MIXED, tol=OUTER_TOL, augment=aug)
+            t1 = time.perf_counter()
+            x = sol.schur_solve(bd)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            r["mixed_ms_setup_" + key] = 1e3 * (t1 - t0)
+            r["mixed_ms_solve_" + key] = 1e3 * (t2 - t1)
+            r["mixed_gmres_iters_" + key] = sol.last_stats["iters_total"]
+            sol.close()
+            if phi == 2e-8 and aug:
+                oracle.set_threads(os.cpu_count() or 1)
+                xr = oracle.fd_schur_solve(2, N, phi, b)
+                r["relerr_augmented_mixed_vs_oracle"] = float(np.linalg.norm(x.cpu().numpy() - xr) / np.linalg.norm(xr))
+        out["per_phi"]["%g" % phi] = r
+    return out
+
+
 def serve_stream(args, S, inputs, oracle):
     """Serving form: Poisson arrivals of mixed 2D/3D sizes, beta from 6 cached values, 1-16 seeded
     right-hand sides per request.  Capacity is measured closed-loop (the first 400 requests all
@@ -862,6 +909,7 @@ def main():
         extra["precision_form_3d"] = row_3d(args, torch, S, inputs, oracle, dev, stream, peaks)
         extra["full_space_kkt"] = row_kkt(args, torch, S, inputs, oracle, dev, stream)
         extra["thermal_range_space"] = row_thermal(args, torch, S, inputs, oracle, dev, stream)
+        extra["augmented_coarse"] = row_augmented(args, torch, S, inputs, oracle, dev, stream)
         extra["serving"] = serve_stream(args, S, inputs, oracle)
 
     if rank == 0:

@@ -80,7 +80,12 @@ typedef struct {
                         complex FETI-DP solve with K + i gamma M and x = -Im(z)/gamma) or
                         SCHUR_FACTOR_PW (S_p, by two real FETI-DP solves with K + gamma M and
                         one M product: x = (K + gamma M)^{-1} M (K + gamma M)^{-1} b)          */
-  int reserved[3];   /* must be zero                                                      */
+  int augment;       /* 1: augmented coarse problem (Sec. 5): besides the corners, one coarse
+                        unknown per pair of face-adjacent subdomains enforcing a zero average
+                        jump across that face at every iteration (the translational edge mode
+                        of the paper's RAUG; a face in 3D); the coarse matrix is inverted
+                        densely in FP64, so at most 4096 coarse unknowns (EINVAL beyond)      */
+  int reserved[2];   /* must be zero                                                      */
 } schur_opts;
 
 typedef struct {
@@ -299,8 +304,10 @@ const char* schur_last_error(void);
  * which = 0: F  = (A_rr^{-1}) restricted to the interface slots      (n_delta x n_delta)
  *         1: Frc = (A_rr^{-1} A_rc) on the interface slots           (n_delta x 2^d)
  *         2: S_bb = A_DD - A_Di A_ii^{-1} A_iD (Dirichlet precond.)  (n_delta x n_delta)
- *         3: the assembled coarse matrix, dense                      (n_coarse x n_coarse)
+ *         3: the assembled coarse matrix, dense (corner-only coarse)  (n_coarse x n_coarse)
  *         4: the coarse inverse actually applied                     (n_coarse x n_coarse)
+ *         5: the coupling columns [Frc | F Q] of the augmented coarse problem
+ *            (n_delta x (2^d + 2d); without augmentation Frc alone)
  * Row-major.  `cap` = capacity of out in complex entries.  Synchronises. */
 int schur_debug_operator(schur_ctx* ctx, int which, int cls, double* out_host, long long cap);
 

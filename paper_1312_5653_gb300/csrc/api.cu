@@ -58,6 +58,10 @@ int upload_maps(const HostMaps& hm, DevMaps* dm, std::string* msg) {
   if (e == cudaSuccess) e = upload(&dm->lam_side, hm.lam_side);
   if (e == cudaSuccess) e = upload(&dm->sd_corner, hm.sd_corner);
   if (e == cudaSuccess) e = upload(&dm->sd_minv, hm.sd_minv);
+  if (e == cudaSuccess) e = upload(&dm->sd_coarse, hm.sd_coarse);
+  if (e == cudaSuccess) e = upload(&dm->face_sd, hm.face_sd);
+  if (e == cudaSuccess) e = upload(&dm->lam_face, hm.lam_face);
+  if (e == cudaSuccess) e = upload(&dm->slot_faces, hm.slot_faces);
   if (e != cudaSuccess) {
     if (msg) *msg = std::string("uploading index maps: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? SCHUR_ENOMEM : SCHUR_ECUDA;
@@ -67,7 +71,8 @@ int upload_maps(const HostMaps& hm, DevMaps* dm, std::string* msg) {
 
 void free_maps(DevMaps* dm) {
   void* ps[] = {dm->slot_node, dm->node_slot, dm->corner_node, dm->sd_code, dm->sd_cls,
-                dm->cls_code,  dm->sd_lam,    dm->lam_side,    dm->sd_corner, dm->sd_minv};
+                dm->cls_code,  dm->sd_lam,    dm->lam_side,    dm->sd_corner, dm->sd_minv,
+                dm->sd_coarse, dm->face_sd,   dm->lam_face,    dm->slot_faces};
   for (void* p : ps)
     if (p) cudaFree(p);
   *dm = DevMaps();
@@ -126,8 +131,9 @@ int get_partition(const schur_mesh* mesh, const schur_opts* opts, std::shared_pt
   if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
   char key[160];
   const int d = mesh->dim;
-  snprintf(key, sizeof(key), "%d|%d|%d,%d,%d|%d,%d,%d|%d", dev, d, mesh->nel[0], mesh->nel[1], d == 3 ? mesh->nel[2] : 1,
-           opts->nsub[0], opts->nsub[1], d == 3 ? opts->nsub[2] : 1, opts->local_mode);
+  snprintf(key, sizeof(key), "%d|%d|%d,%d,%d|%d,%d,%d|%d|%d", dev, d, mesh->nel[0], mesh->nel[1],
+           d == 3 ? mesh->nel[2] : 1, opts->nsub[0], opts->nsub[1], d == 3 ? opts->nsub[2] : 1, opts->local_mode,
+           opts->augment);
   std::lock_guard<std::mutex> lk(g_part_mu);
   for (size_t i = 0; i < g_parts.size(); ++i)
     if (g_parts[i].first == key) {
@@ -139,7 +145,7 @@ int get_partition(const schur_mesh* mesh, const schur_opts* opts, std::shared_pt
     }
   auto e = std::make_shared<MapEntry>();
   e->device = dev;
-  std::string m = build_maps(mesh->dim, mesh->nel, opts->nsub, opts->local_mode, &e->hm);
+  std::string m = build_maps(mesh->dim, mesh->nel, opts->nsub, opts->local_mode, &e->hm, opts->augment);
   if (!m.empty()) {
     if (msg) *msg = m;
     return SCHUR_EINVAL;
@@ -360,7 +366,8 @@ int schur_setup(const schur_mesh* mesh, double beta, const schur_opts* opts, voi
     return set_error(SCHUR_EINVAL, "tc_split must be 0, 1 or 3");
   if (opts->factor != SCHUR_FACTOR_EXACT && opts->factor != SCHUR_FACTOR_PW)
     return set_error(SCHUR_EINVAL, "factor must be SCHUR_FACTOR_EXACT or SCHUR_FACTOR_PW");
-  for (int i = 0; i < 3; ++i)
+  if (opts->augment != 0 && opts->augment != 1) return set_error(SCHUR_EINVAL, "augment must be 0 or 1");
+  for (int i = 0; i < 2; ++i)
     if (opts->reserved[i]) return set_error(SCHUR_EINVAL, "reserved option fields must be zero");
   double t0 = now_ms();
   schur_ctx* c = new (std::nothrow) schur_ctx();
@@ -510,7 +517,7 @@ int schur_get_info(const schur_ctx* c, schur_info_t* info) {
   info->n_sub = g.nsd;
   info->n_classes = c->mp->hm.ncls;
   info->n_lambda = g.nlam;
-  info->n_coarse = g.ncor;
+  info->n_coarse = g.nco;
   info->n_delta = g.nD;
   info->n_local = g.nl;
   info->bytes_operators = c->eng ? c->eng->op_bytes() : 0;

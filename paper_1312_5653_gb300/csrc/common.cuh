@@ -116,9 +116,14 @@ struct Geom {
   long long n;    // global interior nodes
   int nlam;       // dual unknowns
   int ncg[3];     // coarse grid per axis
-  int ncor;       // coarse unknowns
-  int cb, cL;     // coarse layered structure
+  int ncor;       // primal corners (coarse unknowns of the unaugmented coarse problem)
+  int cb, cL;     // coarse layered structure of the corners
   int maxdeg;     // multipliers per interface slot at most (1 in 2D, 3 in 3D)
+  // coarse couplings per subdomain (nq) and coarse unknowns (nco): the corners, plus with the
+  // augmented coarse problem one average constraint per pair of face-adjacent subdomains, faces
+  // numbered after the corners (nface of them); a subdomain's face slot f = 2a + side (side 1 =
+  // the face at l_a = s_a) follows its corner slots
+  int nq, nco, nface;
 };
 
 // Per-axis assembled 1D factors of the Q1 stiffness (k) and mass (m), in the working precision.

@@ -20,6 +20,10 @@ struct DevMaps {
   int* lam_side = nullptr;
   int* sd_corner = nullptr;
   double* sd_minv = nullptr;
+  int* sd_coarse = nullptr;
+  int* face_sd = nullptr;
+  int* lam_face = nullptr;
+  int* slot_faces = nullptr;
 };
 
 int upload_maps(const HostMaps& hm, DevMaps* dm, std::string* msg);
@@ -49,6 +53,8 @@ class EngineBase {
 };
 
 constexpr int kMaxR = 16;
+// Largest augmented coarse problem (corners + faces): inverted densely in FP64.
+constexpr int kMaxAugCoarse = 4096;
 
 // Keeps freed blocks of the current device's default memory pool cached in the process
 // (release threshold = unlimited), once per device.

@@ -77,6 +77,10 @@ class Engine : public EngineBase {
     mv_.lam_side = dm->lam_side;
     mv_.sd_corner = dm->sd_corner;
     mv_.sd_minv = dm->sd_minv;
+    mv_.sd_coarse = dm->sd_coarse;
+    mv_.face_sd = dm->face_sd;
+    mv_.lam_face = dm->lam_face;
+    mv_.slot_faces = dm->slot_faces;
     st_ = make_stencil<T>(g_, gamma, sre);
     ncls_ = hm->ncls;
     // remainder problem: full local grid, vertices and Dirichlet nodes removed
@@ -153,10 +157,20 @@ class Engine : public EngineBase {
     }
     // ---- local operator storage
     ENG_CK(alloc(&F_, (size_t)ncls_ * sym_ld(g.nD) * cxT));  // packed symmetric
-    ENG_CK(alloc(&Frc_, (size_t)ncls_ * g.nD * g.nc * cxT));
+    // coupling columns: the corners' from the formation; with the augmented coarse problem the
+    // formation writes them to a temporary and Frc_ receives [Frc | F Q] (k_aug_local)
+    const bool aug = g.nq > g.nc;
+    if (aug && g.nco > kMaxAugCoarse) {
+      if (msg) *msg = "augmented coarse problem larger than " + std::to_string(kMaxAugCoarse) + " unknowns";
+      return SCHUR_EINVAL;
+    }
+    cx<T>* Frc0 = nullptr;
+    ENG_CK(alloc(&Frc_, (size_t)ncls_ * g.nD * g.nq * cxT));
+    if (aug) ENG_CK(alloc(&Frc0, (size_t)ncls_ * g.nD * g.nc * cxT));
+    cx<T>* FrcF = aug ? Frc0 : Frc_;
     ENG_CK(alloc(&Sd_, (size_t)ncls_ * sym_ld(g.nD) * cxT));  // packed symmetric
     ENG_CK(alloc(&Kcc_, (size_t)ncls_ * g.nc * g.nc * sizeof(cx<double>)));
-    op_bytes_ += (long long)ncls_ * (2 * sym_ld(g.nD) + (long long)g.nD * g.nc) * cxT;
+    op_bytes_ += (long long)ncls_ * (2 * sym_ld(g.nD) + (long long)g.nD * g.nq) * cxT;
     // ---- interior branch on a second stream: the interior problem is independent of the
     // remainder problems, so its factor and the Dirichlet S run beside the remainder factors and F
     const int C = 32;
@@ -311,7 +325,7 @@ class Engine : public EngineBase {
           ENG_CK(alloc(&Xws, (size_t)grid * g.nl * kTcCols * cxT));
           ENG_CK(smem_attr((const void*)k_form_rr_tc<T>, (int)smem));
           prof_start(KC_FORM, st);
-          k_form_rr_tc<T><<<grid, kTcThreads, smem, st>>>(prr_, g, mv_, Dinv_, Gc, Hc, ncls_, Xws, F_, Frc_, Kcc_,
+          k_form_rr_tc<T><<<grid, kTcThreads, smem, st>>>(prr_, g, mv_, Dinv_, Gc, Hc, ncls_, Xws, F_, FrcF, Kcc_,
                                                           err_ + 3, tc_terms, ncol_tc);
           prof_stop(KC_FORM, st);
           ENG_LAUNCH();
@@ -323,7 +337,7 @@ class Engine : public EngineBase {
             const size_t smem2 = 2 * (size_t)g.lb * Cr * cxT;
             ENG_CK(smem_attr((const void*)k_form_rr<T>, (int)smem2));
             prof_start(KC_FORM, st);
-            k_form_rr<T><<<grid2, 256, smem2, st>>>(prr_, g, mv_, Dinv_, ncls_, Cr, Xr, F_, Frc_, Kcc_, ncol_tc);
+            k_form_rr<T><<<grid2, 256, smem2, st>>>(prr_, g, mv_, Dinv_, ncls_, Cr, Xr, F_, FrcF, Kcc_, ncol_tc);
             prof_stop(KC_FORM, st);
             ENG_LAUNCH();
             free_one(Xr);
@@ -338,7 +352,7 @@ class Engine : public EngineBase {
           prof_start(KC_FORM, st);
           cudaError_t fe = cudaErrorInvalidValue;
 #define FC_CASE(BV) \
-  case BV: fe = launch_form_cols<T, BV>(prr_, g, mv_, Dinv_, ncls_, F_, Frc_, Kcc_, Xws, grid, ldE, st); break
+  case BV: fe = launch_form_cols<T, BV>(prr_, g, mv_, Dinv_, ncls_, F_, FrcF, Kcc_, Xws, grid, ldE, st); break
           switch (Bp) {
             FC_CASE(8);
             FC_CASE(9);
@@ -365,7 +379,7 @@ class Engine : public EngineBase {
         ENG_CK(alloc(&Xws, (size_t)grid * wpb * g.nl * CW * cxT));
         ENG_CK(smem_attr((const void*)k_form_rr_warp<T, CW>, (int)smem));
         prof_start(KC_FORM, st);
-        k_form_rr_warp<T, CW><<<grid, 32 * wpb, smem, st>>>(prr_, g, mv_, Dinv_, ncls_, F_, Frc_, Kcc_, Xws);
+        k_form_rr_warp<T, CW><<<grid, 32 * wpb, smem, st>>>(prr_, g, mv_, Dinv_, ncls_, F_, FrcF, Kcc_, Xws);
         prof_stop(KC_FORM, st);
         ENG_LAUNCH();
       } else {
@@ -375,7 +389,7 @@ class Engine : public EngineBase {
         size_t smem = 2 * (size_t)g.lb * C * cxT;
         ENG_CK(smem_attr((const void*)k_form_rr<T>, (int)smem));
         prof_start(KC_FORM, st);
-        k_form_rr<T><<<grid, 256, smem, st>>>(prr_, g, mv_, Dinv_, ncls_, C, Xws, F_, Frc_, Kcc_, 0);
+        k_form_rr<T><<<grid, 256, smem, st>>>(prr_, g, mv_, Dinv_, ncls_, C, Xws, F_, FrcF, Kcc_, 0);
         prof_stop(KC_FORM, st);
         ENG_LAUNCH();
       }
@@ -390,8 +404,46 @@ class Engine : public EngineBase {
       free_one(Sbase);
       free_one(Dii);
     }
-    // ---- coarse problem (FP64 factorisation, inverse stored in T)
-    if (g.ncor > 0) {
+    if (aug) {
+      // ---- augmented coarse problem: class couplings [Frc | F Q] and coarse blocks, the dense
+      // coarse matrix (FP64), its inverse (FP64 Gauss-Jordan), kept as packed tiles in precision T
+      const int nq = g.nq;
+      cx<double>* Kq = nullptr;
+      cx<double>* Kd = nullptr;
+      ENG_CK(alloc(&Kq, (size_t)ncls_ * nq * nq * sizeof(cx<double>)));
+      const size_t smem = (size_t)g.nD * (nq - g.nc) * cxT + (size_t)g.nD * sizeof(int);
+      ENG_CK(smem_attr((const void*)k_aug_local<T>, (int)smem));
+      prof_start(KC_COARSE_SETUP, st);
+      k_aug_local<T><<<std::max(1, std::min(ncls_, 8 * nsm_)), 256, smem, st>>>(prr_, g, mv_, F_, Frc0, Kcc_, ncls_,
+                                                                                 Frc_, Kq);
+      ENG_LAUNCH();
+      const size_t nn = (size_t)g.nco * g.nco;
+      ENG_CK(alloc(&Kd, nn * sizeof(cx<double>)));
+      k_aug_assemble<<<(int)std::min<size_t>((nn + 255) / 256, 64 * nsm_), 256, 0, st>>>(g, mv_, Kq, Kd);
+      ENG_LAUNCH();
+      int crc = dense_gj_inverse(Kd, g.nco, err_ + 2, st, msg, &launches);
+      prof_stop(KC_COARSE_SETUP, st);
+      if (crc) return crc;
+      ldk_ = (g.nco + 1) & ~1;
+      nct_ = (g.nco + kCT - 1) / kCT;
+      ENG_CK(alloc(&Kinv_, (size_t)g.nco * ldk_ * cxT));
+      ENG_CK(alloc(&Kt_, (size_t)ctile_count(nct_) * kCT * kCT * cxT));
+      op_bytes_ += (long long)ctile_count(nct_) * kCT * kCT * cxT;
+      prof_start(KC_COARSE_INV, st);
+      k_convert_rows<T><<<(int)std::min<size_t>(((size_t)g.nco * ldk_ + 255) / 256, 64 * nsm_), 256, 0, st>>>(
+          Kd, g.nco, Kinv_, ldk_);
+      ENG_LAUNCH();
+      k_pack_ctiles<T><<<(int)std::min<long long>(ctile_count(nct_), 8 * nsm_), 256, 0, st>>>(Kinv_, g.nco, ldk_,
+                                                                                            nct_, Kt_);
+      prof_stop(KC_COARSE_INV, st);
+      ENG_LAUNCH();
+      free_one(Kinv_);
+      Kinv_ = nullptr;
+      free_one(Kd);
+      free_one(Kq);
+      free_one(Frc0);
+    } else if (g.ncor > 0) {
+      // ---- coarse problem (FP64 factorisation, inverse stored in T)
       const int nt = nbr_count(g.dim), cbb = g.cb * g.cb;
       ENG_CK(alloc(&CA_, (size_t)g.cL * g.cb * nt * sizeof(cx<double>)));
       ENG_CK(alloc(&CB_, (size_t)std::max(1, g.cL) * g.cb * nt * sizeof(cx<double>)));
@@ -456,14 +508,21 @@ class Engine : public EngineBase {
     const cx<double>* fc = reinterpret_cast<const cx<double>*>(f);
     cx<double>* zc = reinterpret_cast<cx<double>*>(z);
     const size_t cxT = sizeof(cx<T>);
-    const bool coarse = g.ncor > 0;
+    const bool coarse = g.nco > 0, aug = g.nq > g.nc;
     // ---- local right-hand sides
     rc = local_solves(fc, ldf, nullptr, nullptr, R, true, st, msg);
     if (rc) return rc;
-    if (coarse) {
-      int tot = R * g.ncor;
+    if (aug) {  // face part of the coarse right-hand side: Q_s^T d_r^s
+      const long long nw = (long long)g.nsd * R;
       prof_start(KC_CORNER, st);
-      k_corner_gather<T><<<(tot + 255) / 256, 256, 0, st>>>(g, Tc_, R, fc, ldf, nullptr, T(-1), ftc_);
+      k_face_sums<T><<<(int)((nw * 32 + 255) / 256), 256, 0, st>>>(g, mv_, VD_, R, Tc_);
+      prof_stop(KC_CORNER, st);
+      ENG_LAUNCH();
+    }
+    if (coarse) {
+      int tot = R * g.nco;
+      prof_start(KC_CORNER, st);
+      k_corner_gather<T><<<(tot + 255) / 256, 256, 0, st>>>(g, mv_, Tc_, R, fc, ldf, nullptr, T(-1), ftc_);
       prof_stop(KC_CORNER, st);
       ENG_LAUNCH();
       rc = coarse_apply(ftc_, R, nullptr, wc_, st, msg);
@@ -487,10 +546,10 @@ class Engine : public EngineBase {
       if (rc) return rc;
     }
     if (coarse) {
-      int tot = R * g.ncor;
+      int tot = R * g.nco;
       if (g.nlam > 0) {
         prof_start(KC_CORNER, st);
-        k_corner_gather<T><<<(tot + 255) / 256, 256, 0, st>>>(g, Tc_, R, nullptr, 0, ftc_, T(1), gc_);
+        k_corner_gather<T><<<(tot + 255) / 256, 256, 0, st>>>(g, mv_, Tc_, R, nullptr, 0, ftc_, T(1), gc_);
         prof_stop(KC_CORNER, st);
         ENG_LAUNCH();
         rc = coarse_apply(gc_, R, nullptr, uc_, st, msg);
@@ -498,6 +557,13 @@ class Engine : public EngineBase {
         rc = coarse_apply(ftc_, R, nullptr, uc_, st, msg);
       }
       if (rc) return rc;
+      if (aug && g.nlam > 0) {  // multipliers of the local problems: lambda + Q mu
+        long long tl = (long long)R * g.nlam;
+        prof_start(KC_CORNER, st);
+        k_lam_aug<T><<<(int)((tl + 255) / 256), 256, 0, st>>>(g, mv_, uc_, R, lam_);
+        prof_stop(KC_CORNER, st);
+        ENG_LAUNCH();
+      }
     }
     {
       rc = local_solves(fc, ldf, g.nlam > 0 ? lam_ : nullptr, coarse ? uc_ : nullptr, R, false, st, msg);
@@ -536,7 +602,7 @@ class Engine : public EngineBase {
       return 0;
     };
     int rc = 0;
-    if (which <= 2 && (cls < 0 || cls >= ncls_)) return SCHUR_EINVAL;
+    if ((which <= 2 || which == 5) && (cls < 0 || cls >= ncls_)) return SCHUR_EINVAL;
     auto unpack = [&]() {  // packed upper triangle -> full symmetric matrix
       std::vector<cx<double>> full((size_t)g.nD * g.nD);
       for (int i = 0; i < g.nD; ++i)
@@ -546,24 +612,31 @@ class Engine : public EngineBase {
     if (which == 0) {
       rc = fetch(F_ + (size_t)cls * sym_ld(g.nD), (size_t)sym_ld(g.nD));
       if (!rc) unpack();
-    } else if (which == 1) {
-      rc = fetch(Frc_ + (size_t)cls * g.nD * g.nc, (size_t)g.nD * g.nc);
+    } else if (which == 1 || which == 5) {
+      // coupling columns of the class (nD x nq); which = 1 keeps the corner columns
+      rc = fetch(Frc_ + (size_t)cls * g.nD * g.nq, (size_t)g.nD * g.nq);
+      if (!rc && which == 1 && g.nq != g.nc) {
+        std::vector<cx<double>> fr((size_t)g.nD * g.nc);
+        for (int j = 0; j < g.nD; ++j)
+          for (int c = 0; c < g.nc; ++c) fr[(size_t)j * g.nc + c] = host[(size_t)j * g.nq + c];
+        host.swap(fr);
+      }
     } else if (which == 2) {
       rc = fetch(Sd_ + (size_t)cls * sym_ld(g.nD), (size_t)sym_ld(g.nD));
       if (!rc) unpack();
     }
     else if (which == 3 || which == 4) {
-      if (g.ncor == 0) return SCHUR_EINVAL;
+      if (g.nco == 0 || (which == 3 && g.nq != g.nc)) return SCHUR_EINVAL;
       if (which == 4) {
         rc = fetch(Kt_, (size_t)ctile_count(nct_) * kCT * kCT);
         if (!rc) {  // upper tiles -> full symmetric matrix (lower tiles are the transposes)
-          std::vector<cx<double>> full((size_t)g.ncor * g.ncor);
-          for (int i = 0; i < g.ncor; ++i)
-            for (int j = 0; j < g.ncor; ++j) {
+          std::vector<cx<double>> full((size_t)g.nco * g.nco);
+          for (int i = 0; i < g.nco; ++i)
+            for (int j = 0; j < g.nco; ++j) {
               const int I = i / kCT, J = j / kCT;
               const size_t e = I <= J ? (size_t)ctile_idx(I, J, nct_) * kCT * kCT + (i % kCT) * kCT + j % kCT
                                       : (size_t)ctile_idx(J, I, nct_) * kCT * kCT + (j % kCT) * kCT + i % kCT;
-              full[(size_t)i * g.ncor + j] = host[e];
+              full[(size_t)i * g.nco + j] = host[e];
             }
           host.swap(full);
         }
@@ -635,11 +708,11 @@ class Engine : public EngineBase {
       if (e == cudaSuccess) ws_.push_back((void*)*p);
       return e;
     };
-    const size_t nl = std::max(1, g.nlam), nco = std::max(1, g.ncor);
+    const size_t nl = std::max(1, g.nlam), nco = std::max(1, g.nco);
     ENG_CK(wa(&Xs_, (size_t)g.nsd * g.nl * R * cxT));
     ENG_CK(wa(&VD_, (size_t)g.nsd * R * g.nD * cxT));
     ENG_CK(wa(&Y_, (size_t)g.nsd * R * g.nD * cxT));
-    ENG_CK(wa(&Tc_, (size_t)g.nsd * R * g.nc * cxT));
+    ENG_CK(wa(&Tc_, (size_t)g.nsd * R * g.nq * cxT));
     ENG_CK(wa(&d_, nl * R * cxT));
     ENG_CK(wa(&zv_, nl * R * cxT));
     ENG_CK(wa(&lam_, nl * R * cxT));
@@ -648,7 +721,7 @@ class Engine : public EngineBase {
     ENG_CK(wa(&gc_, nco * R * cxT));
     ENG_CK(wa(&wc_, nco * R * cxT));
     ENG_CK(wa(&uc_, nco * R * cxT));
-    if (g.ncor > 0) {
+    if (g.nco > 0) {
       const size_t np = (size_t)ctile_count(nct_) * kCT * R;
       ENG_CK(wa(&cpu_, np * cxT));
       ENG_CK(wa(&cpv_, np * cxT));
@@ -731,9 +804,9 @@ class Engine : public EngineBase {
   int coarse_apply(const cx<T>* gv, int R, const int* active, cx<T>* w, cudaStream_t st, std::string* msg) {
     const long long ntile = ctile_count(nct_);
     prof_start(KC_COARSE_APPLY, st);
-    ENG_CK(launch_pdl(k_coarse_tiles<T>, dim3((unsigned)((ntile + 3) / 4)), dim3(128), 0, st, Kt_, nct_, g_.ncor, gv, R,
+    ENG_CK(launch_pdl(k_coarse_tiles<T>, dim3((unsigned)((ntile + 3) / 4)), dim3(128), 0, st, Kt_, nct_, g_.nco, gv, R,
                       active, cpu_, cpv_));
-    ENG_CK(launch_pdl(k_coarse_reduce<T>, dim3(nct_ * R), dim3(512), 0, st, cpu_, cpv_, nct_, g_.ncor, R, active, w));
+    ENG_CK(launch_pdl(k_coarse_reduce<T>, dim3(nct_ * R), dim3(512), 0, st, cpu_, cpv_, nct_, g_.nco, R, active, w));
     prof_stop(KC_COARSE_APPLY, st);
     ENG_LAUNCH();
     ENG_LAUNCH();
@@ -816,13 +889,13 @@ class Engine : public EngineBase {
   // against the Krylov basis (k_scatter_orth_dots)
   int dual_apply(const cx<T>* v, int R, const int* active, cx<T>* out, cudaStream_t st, std::string* msg,
                  const OrthArgs* oa = nullptr) {
-    const bool coarse = g_.ncor > 0;
+    const bool coarse = g_.nco > 0;
     int rc = local_apply(false, F_, v, R, active, coarse, st, msg);
     if (rc) return rc;
     if (coarse) {
-      int tot = R * g_.ncor;
+      int tot = R * g_.nco;
       prof_start(KC_CORNER, st);
-      ENG_CK(launch_pdl(k_corner_gather<T>, dim3((tot + 255) / 256), dim3(256), 0, st, g_, Tc_, R,
+      ENG_CK(launch_pdl(k_corner_gather<T>, dim3((tot + 255) / 256), dim3(256), 0, st, g_, mv_, Tc_, R,
                         (const cx<double>*)nullptr, 0, (const cx<T>*)nullptr, T(1), gc_));
       prof_stop(KC_CORNER, st);
       ENG_LAUNCH();

@@ -26,6 +26,10 @@ struct MapsView {
   const int* lam_side;
   const int* sd_corner;
   const double* sd_minv;
+  const int* sd_coarse;   // [nsd][nq] coarse unknown of each coupling slot or -1
+  const int* face_sd;     // [nface][2] lower and higher subdomain of each face (augmented only)
+  const int* lam_face;    // [nlam] face of the multiplier's pair or -1 (augmented only)
+  const int* slot_faces;  // [nD] local faces of each slot, bit f = 2a + side (augmented only)
 };
 
 __device__ __forceinline__ void local_ext(const Geom& g, int* ext) {
@@ -417,20 +421,35 @@ __global__ void k_local_rhs(StencilProv<T> P, Geom g, MapsView m, const cx<T>* _
         cfma(v, q1_entry(P.st, g.s, lc, lp), X[(size_t)crd2idx(lp, ext, dim) * R + c]);
       }
     }
-    Tc[((size_t)sd * R + c) * nc + cc] = v;
+    Tc[((size_t)sd * R + c) * g.nq + cc] = v;
   }
 }
 
 // g[r][C] = (add ? add[r][C] : 0) + sign * sum over subdomains holding corner C of Tc; with
 // f != null also adds f at the corner node (f~_c = f_c - sum A_cr A_rr^{-1} f_r uses sign -1).
 template <class T>
-__global__ void k_corner_gather(Geom g, const cx<T>* __restrict__ Tc, int R, const cx<double>* __restrict__ f, int ldf,
+__global__ void k_corner_gather(Geom g, MapsView m, const cx<T>* __restrict__ Tc, int R, const cx<double>* __restrict__ f, int ldf,
                                 const cx<T>* __restrict__ add, T sign, cx<T>* out) {
   pdl_wait();
   pdl_trigger();
   int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= R * g.ncor) return;
-  int r = e / g.ncor, cI = e - r * g.ncor, dim = g.dim;
+  if (e >= R * g.nco) return;
+  int r = e / g.nco, cI = e - r * g.nco, dim = g.dim;
+  if (cI >= g.ncor) {
+    // face unknown (augmented coarse problem): its two subdomains, at their high and low face slot
+    const int f = cI - g.ncor;
+    const int lo = m.face_sd[2 * f + 1], hi = m.face_sd[2 * f];
+    int A[3], B[3], a = 0;
+    idx2crd(lo, g.nsub, dim, A);
+    idx2crd(hi, g.nsub, dim, B);
+    for (int t = 0; t < dim; ++t)
+      if (A[t] != B[t]) a = t;
+    cx<T> sum = cadd(Tc[((size_t)lo * R + r) * g.nq + g.nc + 2 * a + 1], Tc[((size_t)hi * R + r) * g.nq + g.nc + 2 * a]);
+    cx<T> v = cscale(sum, sign);
+    if (add) v = cadd(v, add[(size_t)r * g.nco + cI]);
+    out[(size_t)r * g.nco + cI] = v;
+    return;
+  }
   int C[3];
   idx2crd(cI, g.ncg, dim, C);
   cx<T> sum = czero<T>();
@@ -440,16 +459,16 @@ __global__ void k_corner_gather(Geom g, const cx<T>* __restrict__ Tc, int R, con
     int S[3] = {0, 0, 0};
     for (int a = 0; a < dim; ++a) S[a] = C[a] + 1 - ((bits >> a) & 1);
     int sd = crd2idx(S, g.nsub, dim);
-    sum = cadd(sum, Tc[((size_t)sd * R + r) * g.nc + bits]);
+    sum = cadd(sum, Tc[((size_t)sd * R + r) * g.nq + bits]);
   }
   cx<T> v = cscale(sum, sign);
-  if (add) v = cadd(v, add[(size_t)r * g.ncor + cI]);
+  if (add) v = cadd(v, add[(size_t)r * g.nco + cI]);
   if (f) {
     int G[3] = {(C[0] + 1) * g.s[0], (C[1] + 1) * g.s[1], dim == 3 ? (C[2] + 1) * g.s[2] : 1};
     cx<double> fv = f[(size_t)r * ldf + gidx(g, G)];
     v = cadd(v, mkc<T>((T)fv.re, (T)fv.im));
   }
-  out[(size_t)r * g.ncor + cI] = v;
+  out[(size_t)r * g.nco + cI] = v;
 }
 
 // ------------------------------------------------------------------ coarse inverse, packed tiles
@@ -597,16 +616,17 @@ __global__ void __launch_bounds__(512) k_coarse_reduce(const cx<T>* __restrict__
   }
 }
 
-// Frc^s w_s on slot j of subdomain sd (w: coarse vector of one right-hand side).
+// Frc^s w_s on slot j of subdomain sd (w: coarse vector of one right-hand side; Frc: the nq
+// coupling columns of the class, the corners' and with the augmented coarse problem the faces').
 template <class T>
 __device__ __forceinline__ cx<T> frc_corr(const Geom& g, const MapsView& m, const cx<T>* __restrict__ Frc,
                                           const cx<T>* __restrict__ w, int sd, int j) {
   cx<T> acc = czero<T>();
   if (!w) return acc;
   const int q = m.sd_cls[sd];
-  for (int c = 0; c < g.nc; ++c) {
-    int ci = m.sd_corner[(size_t)sd * g.nc + c];
-    if (ci >= 0) cfma(acc, Frc[((size_t)q * g.nD + j) * g.nc + c], w[ci]);
+  for (int c = 0; c < g.nq; ++c) {
+    int ci = m.sd_coarse[(size_t)sd * g.nq + c];
+    if (ci >= 0) cfma(acc, Frc[((size_t)q * g.nD + j) * g.nq + c], w[ci]);
   }
   return acc;
 }
@@ -622,7 +642,7 @@ __global__ void k_dual_rhs(Geom g, MapsView m, const cx<T>* __restrict__ VD, con
   for (int side = 0; side < 2; ++side) {
     int code = m.lam_side[2 * lam + side];
     int sd = code / g.nD, j = code - sd * g.nD;
-    cx<T> t = csub(VD[((size_t)sd * R + r) * g.nD + j], frc_corr(g, m, Frc, w0 ? w0 + (size_t)r * g.ncor : nullptr, sd, j));
+    cx<T> t = csub(VD[((size_t)sd * R + r) * g.nD + j], frc_corr(g, m, Frc, w0 ? w0 + (size_t)r * g.nco : nullptr, sd, j));
     v = side == 0 ? cadd(v, t) : csub(v, t);
   }
   d[(size_t)r * g.nlam + lam] = v;
@@ -692,11 +712,11 @@ __global__ void k_local_apply(Geom g, MapsView m, const cx<T>* __restrict__ Op, 
     // Tc[r][c] = sum_j Frc[j][c] x[r][j]: per-thread partials over j, warp shuffles, then warps
     __shared__ cx<T> red[32];
     const int lane = tid & 31, warp = tid >> 5, nw = (nthr + 31) >> 5;
-    const cx<T>* Fr = Frc + (size_t)q * nD * g.nc;
-    for (int rc = 0; rc < R * g.nc; ++rc) {
-      const int r = rc / g.nc, c = rc - r * g.nc;
+    const cx<T>* Fr = Frc + (size_t)q * nD * g.nq;
+    for (int rc = 0; rc < R * g.nq; ++rc) {
+      const int r = rc / g.nq, c = rc - r * g.nq;
       cx<T> p = czero<T>();
-      for (int j = tid; j < nD; j += nthr) cfma(p, Fr[(size_t)j * g.nc + c], x[r * nD + j]);
+      for (int j = tid; j < nD; j += nthr) cfma(p, Fr[(size_t)j * g.nq + c], x[r * nD + j]);
       for (int o = 16; o > 0; o >>= 1) {
         p.re += __shfl_xor_sync(0xffffffffu, p.re, o);
         p.im += __shfl_xor_sync(0xffffffffu, p.im, o);
@@ -707,7 +727,7 @@ __global__ void k_local_apply(Geom g, MapsView m, const cx<T>* __restrict__ Op, 
       if (tid == 0) {
         cx<T> s = czero<T>();
         for (int w = 0; w < nw; ++w) s = cadd(s, red[w]);
-        Tc[((size_t)sd * R + r) * g.nc + c] = s;
+        Tc[((size_t)sd * R + r) * g.nq + c] = s;
       }
     }
   }
@@ -776,16 +796,16 @@ __global__ void __launch_bounds__(512) k_local_apply_rows(Geom g, MapsView m, co
     Y[(size_t)sd * nD + j] = s;
   }
   if (Tc) {
-    // Tc[c] = sum_j Frc[j][c] x[j]: one warp per corner column
-    const cx<T>* Fr = Frc + (size_t)q * nD * g.nc;
-    for (int c = warp; c < g.nc; c += nw) {
+    // Tc[c] = sum_j Frc[j][c] x[j]: one warp per coupling column
+    const cx<T>* Fr = Frc + (size_t)q * nD * g.nq;
+    for (int c = warp; c < g.nq; c += nw) {
       cx<T> p = czero<T>();
-      for (int j = lane; j < nD; j += 32) cfma(p, Fr[(size_t)j * g.nc + c], x[j]);
+      for (int j = lane; j < nD; j += 32) cfma(p, Fr[(size_t)j * g.nq + c], x[j]);
       for (int o = 16; o > 0; o >>= 1) {
         p.re += __shfl_xor_sync(0xffffffffu, p.re, o);
         p.im += __shfl_xor_sync(0xffffffffu, p.im, o);
       }
-      if (lane == 0) Tc[(size_t)sd * g.nc + c] = p;
+      if (lane == 0) Tc[(size_t)sd * g.nq + c] = p;
     }
   }
 }
@@ -806,7 +826,7 @@ __global__ void k_scatter(Geom g, MapsView m, const cx<T>* __restrict__ Y, const
     int code = m.lam_side[2 * lam + side];
     int sd = code / g.nD, j = code - sd * g.nD;
     cx<T> t = Y[((size_t)sd * R + r) * g.nD + j];
-    if (wc) t = cadd(t, frc_corr(g, m, Frc, wc + (size_t)r * g.ncor, sd, j));
+    if (wc) t = cadd(t, frc_corr(g, m, Frc, wc + (size_t)r * g.nco, sd, j));
     if (SCALE) t = cscale(t, (T)m.sd_minv[(size_t)sd * g.nD + j]);
     v = side == 0 ? cadd(v, t) : csub(v, t);
   }
@@ -947,7 +967,7 @@ __global__ void __launch_bounds__(256) k_scatter_orth_dots(Geom g, MapsView m, c
       const int code = m.lam_side[2 * lam + side];
       const int sd = code / g.nD, j = code - sd * g.nD;
       cx<T> t = Y[((size_t)sd * R + r) * g.nD + j];
-      if (wc) t = cadd(t, frc_corr(g, m, Frc, wc + (size_t)r * g.ncor, sd, j));
+      if (wc) t = cadd(t, frc_corr(g, m, Frc, wc + (size_t)r * g.nco, sd, j));
       v = side == 0 ? cadd(v, t) : csub(v, t);
     }
     w[(size_t)r * a.nlam + lam] = v;
@@ -1111,12 +1131,172 @@ __global__ void k_recover(StencilProv<T> P, Geom g, MapsView m, const cx<T>* __r
         if (ci < 0) continue;
         int lc[3];
         idx2crd(m.corner_node[cc], ext, dim, lc);
-        cfms(v, q1_entry(P.st, g.s, l, lc), uc[(size_t)c * g.ncor + ci]);
+        cfms(v, q1_entry(P.st, g.s, l, lc), uc[(size_t)c * g.nco + ci]);
       }
     }
     return v;
   };
   layered_solve<T>(P, Dinv + (size_t)q * L * b * b, R, rhs, X, R, sm);
+}
+
+// ------------------------------------------------------------------ augmented coarse problem
+// Besides the corners, one coarse unknown per pair of face-adjacent subdomains carries the
+// constraint that the average jump across that face vanishes, Q^T B u = 0 (Q: one column per face,
+// ones on the multipliers between its two subdomains; in the slot space of subdomain s the column
+// restricted to its local face f = 2a + side is sigma_f = +1 on the high side, -1 on the low side,
+// on the face's non-Dirichlet slots).  With Phi = [F_rc, F_rr Q] the coarse system is
+//   [K_cc  -X^T] [u_c]   [f~_c    ]
+//   [-X    -Y  ] [mu ] = [-Q^T d_r] + Phi^T lambda,   X = Q^T F_rc,  Y = Q^T F_rr Q,
+// the dual operator F_rr + Phi K^{-1} Phi^T keeps the form of the corner-only one, and the
+// multipliers of the local problems are lambda + Q mu.
+
+// Per operator class: the coupling columns Phi = [Frc | G], G = F Q_s (G[j][f] = sigma_f * sum of
+// F[j][j'] over the active slots j' of face f), and the class's coarse block [[Kcc, -X^T], [-X, -Y]]
+// with X = Q_s^T Frc and Y = Q_s^T G, sums accumulated in FP64.  One block per class at a time.
+template <class T>
+__global__ void k_aug_local(StencilProv<T> P, Geom g, MapsView m, const cx<T>* __restrict__ F,
+                            const cx<T>* __restrict__ Frc0, const cx<double>* __restrict__ Kcc, int ncls, cx<T>* Phi,
+                            cx<double>* Kq) {
+  extern __shared__ __align__(16) unsigned char smaug[];
+  const int nD = g.nD, nc = g.nc, nq = g.nq, ne = nq - nc, b = P.ly.b;
+  cx<T>* Gs = reinterpret_cast<cx<T>*>(smaug);         // [nD][ne]
+  int* act = reinterpret_cast<int*>(Gs + (size_t)nD * ne);  // [nD] slot active (not Dirichlet)
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const long long ld = sym_ld(nD);
+  for (int q = blockIdx.x; q < ncls; q += gridDim.x) {
+    P.select(q, m.cls_code);
+    for (int j = tid; j < nD; j += nthr) {
+      const int node = m.slot_node[j];
+      act[j] = P.removed_node(node / b, node % b) ? 0 : 1;
+    }
+    __syncthreads();
+    const cx<T>* Fq = F + (size_t)q * ld;
+    for (int e = tid; e < nD * ne; e += nthr) {
+      const int j = e / ne, f = e - j * ne;
+      double re = 0, im = 0;
+      if (act[j])
+        for (int j2 = 0; j2 < nD; ++j2)
+          if (act[j2] && ((m.slot_faces[j2] >> f) & 1)) {
+            const cx<T> v = Fq[sym_idx(j, j2, nD)];
+            re += (double)v.re;
+            im += (double)v.im;
+          }
+      const double sg = (f & 1) ? 1.0 : -1.0;
+      const cx<T> gv = mkc<T>((T)(sg * re), (T)(sg * im));
+      Gs[e] = gv;
+      Phi[((size_t)q * nD + j) * nq + nc + f] = gv;
+    }
+    for (int e = tid; e < nD * nc; e += nthr) {
+      const int j = e / nc, c = e - j * nc;
+      Phi[((size_t)q * nD + j) * nq + c] = Frc0[((size_t)q * nD + j) * nc + c];
+    }
+    __syncthreads();
+    for (int e = tid; e < nq * nq; e += nthr) {
+      const int a = e / nq, c = e - a * nq;
+      cx<double> v = mkc<double>(0, 0);
+      if (a < nc && c < nc) {
+        v = Kcc[((size_t)q * nc + a) * nc + c];
+      } else {
+        // -X[f][corner] = -sigma_f sum_{j in f} Frc[j][corner];  -Y[f][f2] = -sigma_f sum_{j in f} G[j][f2]
+        const int f = a >= nc ? a - nc : c - nc, other = a >= nc ? c : a;
+        double re = 0, im = 0;
+        for (int j = 0; j < nD; ++j)
+          if (act[j] && ((m.slot_faces[j] >> f) & 1)) {
+            const cx<T> x = other < nc ? Frc0[((size_t)q * nD + j) * nc + other] : Gs[(size_t)j * ne + (other - nc)];
+            re += (double)x.re;
+            im += (double)x.im;
+          }
+        const double sg = (f & 1) ? -1.0 : 1.0;  // -sigma_f
+        v = mkc<double>(sg * re, sg * im);
+      }
+      Kq[((size_t)q * nq + a) * nq + c] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// Right-hand-side split, face part: Tc[sd][r][nc + f] = sigma_f * sum of VD over the active slots of
+// local face f (Q_s^T d_r^s; the coarse gather with sign -1 then gives -Q^T d_r).  One warp per
+// (subdomain, right-hand side).
+template <class T>
+__global__ void k_face_sums(Geom g, MapsView m, const cx<T>* __restrict__ VD, int R, cx<T>* Tc) {
+  const int lane = threadIdx.x & 31;
+  const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  if (wid >= (long long)g.nsd * R) return;
+  const int sd = (int)(wid / R), r = (int)(wid - (long long)sd * R), ne = g.nq - g.nc;
+  cx<T> acc[6];
+#pragma unroll
+  for (int f = 0; f < 6; ++f) acc[f] = czero<T>();
+  const cx<T>* v = VD + ((size_t)sd * R + r) * g.nD;
+  for (int j = lane; j < g.nD; j += 32) {
+    if (m.sd_minv[(size_t)sd * g.nD + j] == 0.0) continue;  // Dirichlet slot
+    const int bits = m.slot_faces[j];
+    const cx<T> x = v[j];
+#pragma unroll
+    for (int f = 0; f < 6; ++f)
+      if ((bits >> f) & 1) acc[f] = cadd(acc[f], x);
+  }
+#pragma unroll
+  for (int f = 0; f < 6; ++f)
+    for (int o = 16; o > 0; o >>= 1) acc[f] = cadd(acc[f], shfl_xor_cx(acc[f], o));
+  if (lane == 0)
+    for (int f = 0; f < ne; ++f)
+      Tc[((size_t)sd * R + r) * g.nq + g.nc + f] = (f & 1) ? acc[f] : mkc<T>(-acc[f].re, -acc[f].im);
+}
+
+// lambda += Q mu: each multiplier between face neighbours takes its face's coarse unknown
+template <class T>
+__global__ void k_lam_aug(Geom g, MapsView m, const cx<T>* __restrict__ w, int R, cx<T>* lam) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)R * g.nlam) return;
+  const int r = (int)(e / g.nlam), li = (int)(e - (long long)r * g.nlam);
+  const int f = m.lam_face[li];
+  if (f >= 0) lam[e] = cadd(lam[e], w[(size_t)r * g.nco + g.ncor + f]);
+}
+
+// Dense augmented coarse matrix K (nco x nco, FP64, row-major): entry (I, J) is the sum of the class
+// blocks Kq of the subdomains holding both unknowns, visited in a fixed order (deterministic).
+static __global__ void k_aug_assemble(Geom g, MapsView m, const cx<double>* __restrict__ Kq, cx<double>* K) {
+  const long long tot = (long long)g.nco * g.nco;
+  const int dim = g.dim, nq = g.nq;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(e / g.nco), J = (int)(e - (long long)I * g.nco);
+    int own[8], nown = 0;
+    if (I < g.ncor) {
+      int C[3];
+      idx2crd(I, g.ncg, dim, C);
+      for (int bits = 0; bits < (1 << dim); ++bits) {
+        int S[3] = {0, 0, 0};
+        for (int a = 0; a < dim; ++a) S[a] = C[a] + 1 - ((bits >> a) & 1);
+        own[nown++] = crd2idx(S, g.nsub, dim);
+      }
+    } else {
+      own[nown++] = m.face_sd[2 * (I - g.ncor) + 1];
+      own[nown++] = m.face_sd[2 * (I - g.ncor)];
+    }
+    cx<double> sum = mkc<double>(0, 0);
+    for (int k = 0; k < nown; ++k) {
+      const int sd = own[k];
+      const int* sc = m.sd_coarse + (size_t)sd * nq;
+      int a = -1, c = -1;
+      for (int t = 0; t < nq; ++t) {
+        if (sc[t] == I) a = t;
+        if (sc[t] == J) c = t;
+      }
+      if (a >= 0 && c >= 0) sum = cadd(sum, Kq[((size_t)m.sd_cls[sd] * nq + a) * nq + c]);
+    }
+    K[e] = sum;
+  }
+}
+
+// Copy of an FP64 n x n matrix (row stride n) into precision T with row stride ld.
+template <class T>
+__global__ void k_convert_rows(const cx<double>* __restrict__ A, int n, cx<T>* B, int ld) {
+  const long long tot = (long long)n * ld;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / ld), j = (int)(e - (long long)i * ld);
+    B[e] = j < n ? ccast<T>(A[(size_t)i * n + j]) : czero<T>();
+  }
 }
 
 // z[gi][r] += value of node gi: the coarse unknown at corners, else the mean of its subdomain
@@ -1155,7 +1335,7 @@ __global__ void k_assemble_z(Geom g, const cx<T>* __restrict__ Xs, const cx<T>* 
   cx<double> val;
   if (nshared == dim) {
     int C[3] = {S0[0] - 1, S0[1] - 1, dim == 3 ? S0[2] - 1 : 0};
-    val = uc ? ccast<double>(uc[(size_t)r * g.ncor + crd2idx(C, g.ncg, dim)]) : mkc<double>(0, 0);
+    val = uc ? ccast<double>(uc[(size_t)r * g.nco + crd2idx(C, g.ncg, dim)]) : mkc<double>(0, 0);
   } else {
     int ext[3] = {g.s[0] + 1, g.s[1] + 1, dim == 3 ? g.s[2] + 1 : 1};
     cx<double> sum = mkc<double>(0, 0);

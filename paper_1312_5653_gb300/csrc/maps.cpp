@@ -7,11 +7,12 @@
 #include "maps.h"
 
 #include <algorithm>
+#include <cstdlib>
 #include <map>
 
 namespace schur {
 
-std::string build_maps(int dim, const int* nel, const int* nsub, int local_mode, HostMaps* m) {
+std::string build_maps(int dim, const int* nel, const int* nsub, int local_mode, HostMaps* m, int augment) {
   if (dim != 2 && dim != 3) return "dim must be 2 or 3";
   Geom& g = m->g;
   g = Geom();
@@ -200,6 +201,87 @@ std::string build_maps(int dim, const int* nel, const int* nsub, int local_mode,
     }
   }
   g.nlam = (int)(m->lam_side.size() / 2);
+
+  // coarse couplings: corners, and with the augmentation the faces between subdomains
+  g.nq = g.nc;
+  g.nco = g.ncor;
+  g.nface = 0;
+  m->sd_coarse.clear();
+  m->face_sd.clear();
+  m->lam_face.clear();
+  m->slot_faces.clear();
+  if (augment) {
+    const int ne = 2 * dim;
+    g.nq = g.nc + ne;
+    // faces normal to axis a: between S and S + e_a, S_a < nsub[a] - 1; numbered axis by axis,
+    // lexicographically over the lower subdomain's coordinates
+    int foff[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) {
+      foff[a] = g.nface;
+      int cnt = g.nsub[a] - 1;
+      for (int b = 0; b < dim; ++b)
+        if (b != a) cnt *= g.nsub[b];
+      g.nface += cnt;
+    }
+    g.nco = g.ncor + g.nface;
+    auto face_of = [&](const int* S, int a) {  // face between S and S + e_a
+      int idx = 0, stride = 1;
+      for (int b = 0; b < dim; ++b) {
+        const int ext = b == a ? g.nsub[b] - 1 : g.nsub[b];
+        idx += S[b] * stride;
+        stride *= ext;
+      }
+      return foff[a] + idx;
+    };
+    m->face_sd.assign((size_t)2 * g.nface, -1);
+    m->sd_coarse.assign((size_t)g.nsd * g.nq, -1);
+    for (int sd = 0; sd < g.nsd; ++sd) {
+      int S[3];
+      idx2crd(sd, g.nsub, dim, S);
+      for (int c = 0; c < g.nc; ++c) m->sd_coarse[(size_t)sd * g.nq + c] = m->sd_corner[(size_t)sd * g.nc + c];
+      for (int a = 0; a < dim; ++a)
+        for (int side = 0; side < 2; ++side) {
+          int T[3] = {S[0], S[1], S[2]};
+          if (side == 0) {
+            if (S[a] == 0) continue;
+            T[a] = S[a] - 1;  // the face lies between T = S - e_a and S
+          } else if (S[a] == g.nsub[a] - 1) {
+            continue;
+          }
+          const int f = face_of(T, a);
+          m->sd_coarse[(size_t)sd * g.nq + g.nc + 2 * a + side] = g.ncor + f;
+          m->face_sd[2 * f + side] = sd;  // side 1: S is the lower subdomain
+        }
+    }
+    // the face slots of every subdomain's local grid
+    m->slot_faces.assign(g.nD, 0);
+    for (int j = 0; j < g.nD; ++j) {
+      int l[3];
+      idx2crd(m->slot_node[j], ext, dim, l);
+      int bits = 0;
+      for (int a = 0; a < dim; ++a) {
+        if (l[a] == 0) bits |= 1 << (2 * a);
+        if (l[a] == g.s[a]) bits |= 1 << (2 * a + 1);
+      }
+      m->slot_faces[j] = bits;
+    }
+    // multipliers between face neighbours belong to that face's average constraint
+    m->lam_face.assign(g.nlam, -1);
+    for (int li = 0; li < g.nlam; ++li) {
+      const int sp = m->lam_side[2 * li] / g.nD, sm = m->lam_side[2 * li + 1] / g.nD;
+      int A[3], B[3];
+      idx2crd(sp, g.nsub, dim, A);
+      idx2crd(sm, g.nsub, dim, B);
+      int axis = -1, dist = 0;
+      for (int a = 0; a < dim; ++a) {
+        dist += std::abs(A[a] - B[a]);
+        if (A[a] != B[a]) axis = a;
+      }
+      if (dist == 1) m->lam_face[li] = face_of(A, axis);  // the plus side is the lower subdomain
+    }
+  } else {
+    m->sd_coarse = m->sd_corner;
+  }
   return "";
 }
 

@@ -19,10 +19,17 @@ struct HostMaps {
   std::vector<double> sd_minv;   // [nsd][nD] 1/multiplicity, 0 for Dirichlet slots
   std::vector<int> lam_side;     // [nlam][2] plus side, minus side as (subdomain*nD + slot)
   std::vector<int> sd_corner;    // [nsd][nc] coarse unknown or -1 (Dirichlet)
+  // coarse couplings: sd_coarse always (the corners alone without the augmentation); the rest
+  // only with the augmented coarse problem
+  std::vector<int> sd_coarse;    // [nsd][nq] coarse unknown of each coupling slot (corners, faces) or -1
+  std::vector<int> face_sd;      // [nface][2] the lower and the higher subdomain of each face
+  std::vector<int> lam_face;     // [nlam] face of the multiplier's subdomain pair, -1 for other pairs
+  std::vector<int> slot_faces;   // [nD] bit f set: slot lies on local face f = 2a + side
   int ncls = 0;
 };
 
 // Fills maps for the mesh; returns "" on success or a message describing the invalid input.
-std::string build_maps(int dim, const int* nel, const int* nsub, int local_mode, HostMaps* m);
+// augment: also number the faces between subdomains as coarse unknowns (augmented coarse problem).
+std::string build_maps(int dim, const int* nel, const int* nsub, int local_mode, HostMaps* m, int augment = 0);
 
 }  // namespace schur

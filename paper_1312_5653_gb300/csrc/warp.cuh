@@ -613,7 +613,7 @@ __device__ __forceinline__ cx<T> remainder_rhs(const StencilProv<T>& P, const Ge
       if (ci < 0) continue;
       int lc[3];
       idx2crd(m.corner_node[cc], ext, dim, lc);
-      cfms(v, q1_entry(P.st, g.s, l, lc), uc[(size_t)c * g.ncor + ci]);
+      cfms(v, q1_entry(P.st, g.s, l, lc), uc[(size_t)c * g.nco + ci]);
     }
   }
   return v;
@@ -683,7 +683,7 @@ __global__ void k_local_solve_warp(StencilProv<T> P, Geom g, MapsView m, const c
         cfma(v, q1_entry(P.st, g.s, lc, lp), X[(size_t)crd2idx(lp, ext, dim) * R + c]);
       }
     }
-    Tc[((size_t)sd * R + c) * nc + cc] = v;
+    Tc[((size_t)sd * R + c) * g.nq + cc] = v;
   }
 }
 

@@ -34,7 +34,7 @@ class schur_opts(ctypes.Structure):
     _fields_ = [("nsub", ctypes.c_int * 3), ("precision", ctypes.c_int), ("tol", ctypes.c_double),
                 ("inner_tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("max_refine", ctypes.c_int),
                 ("local_mode", ctypes.c_int), ("tc_split", ctypes.c_int), ("factor", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("augment", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class schur_stats(ctypes.Structure):
