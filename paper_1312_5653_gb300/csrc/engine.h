@@ -24,6 +24,8 @@ struct DevMaps {
   int* face_sd = nullptr;
   int* lam_face = nullptr;
   int* slot_faces = nullptr;
+  int* face_lam_ptr = nullptr;
+  int* face_lam = nullptr;
 };
 
 int upload_maps(const HostMaps& hm, DevMaps* dm, std::string* msg);

@@ -81,6 +81,8 @@ class Engine : public EngineBase {
     mv_.face_sd = dm->face_sd;
     mv_.lam_face = dm->lam_face;
     mv_.slot_faces = dm->slot_faces;
+    mv_.face_lam_ptr = dm->face_lam_ptr;
+    mv_.face_lam = dm->face_lam;
     st_ = make_stencil<T>(g_, gamma, sre);
     ncls_ = hm->ncls;
     // remainder problem: full local grid, vertices and Dirichlet nodes removed
@@ -537,6 +539,13 @@ class Engine : public EngineBase {
       k_dual_rhs<T><<<(int)((tot + 255) / 256), 256, 0, st>>>(g, mv_, VD_, Frc_, coarse ? wc_ : nullptr, R, d_);
       prof_stop(KC_SCATTER, st);
       ENG_LAUNCH();
+      if (aug && g.nface > 0) {
+        const long long nw = (long long)g.nface * R;
+        prof_start(KC_SCATTER, st);
+        k_dual_project<T><<<(int)((nw * 32 + 255) / 256), 256, 0, st>>>(g, mv_, R, d_);
+        prof_stop(KC_SCATTER, st);
+        ENG_LAUNCH();
+      }
       rc = gmres(R, m, tol, st, &iters, &conv, msg);
       if (rc) return rc;
     }

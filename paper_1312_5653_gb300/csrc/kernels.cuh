@@ -30,6 +30,8 @@ struct MapsView {
   const int* face_sd;     // [nface][2] lower and higher subdomain of each face (augmented only)
   const int* lam_face;    // [nlam] face of the multiplier's pair or -1 (augmented only)
   const int* slot_faces;  // [nD] local faces of each slot, bit f = 2a + side (augmented only)
+  const int* face_lam_ptr;  // [nface + 1] CSR offsets of the multipliers of each face (augmented only)
+  const int* face_lam;      // multipliers of each face (augmented only)
 };
 
 __device__ __forceinline__ void local_ext(const Geom& g, int* ext) {
@@ -1242,6 +1244,37 @@ __global__ void k_face_sums(Geom g, MapsView m, const cx<T>* __restrict__ VD, in
   if (lane == 0)
     for (int f = 0; f < ne; ++f)
       Tc[((size_t)sd * R + r) * g.nq + g.nc + f] = (f & 1) ? acc[f] : mkc<T>(-acc[f].re, -acc[f].im);
+}
+
+// d <- (I - Q (Q^T Q)^{-1} Q^T) d: subtracts from the multipliers of every face their mean.  In exact
+// arithmetic the augmented dual right-hand side satisfies Q^T d = 0 (the augmented dual operator
+// vanishes on the columns of Q, so the system is consistent only on that complement); in FP32 the
+// cancellations in d_r - Phi w leave a component along Q that the Krylov iteration cannot remove
+// (its residual would stall near it), so it is projected out.  One warp per (face, column).
+template <class T>
+__global__ void k_dual_project(Geom g, MapsView m, int R, cx<T>* d) {
+  const int lane = threadIdx.x & 31;
+  const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  if (wid >= (long long)g.nface * R) return;
+  const int f = (int)(wid % g.nface), r = (int)(wid / g.nface);
+  const int p0 = m.face_lam_ptr[f], p1 = m.face_lam_ptr[f + 1];
+  if (p1 <= p0) return;
+  cx<T>* dr = d + (size_t)r * g.nlam;
+  double sre = 0, sim = 0;
+  for (int k = p0 + lane; k < p1; k += 32) {
+    const cx<T> v = dr[m.face_lam[k]];
+    sre += (double)v.re;
+    sim += (double)v.im;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sre += __shfl_xor_sync(0xffffffffu, sre, o);
+    sim += __shfl_xor_sync(0xffffffffu, sim, o);
+  }
+  const T mre = (T)(sre / (p1 - p0)), mim = (T)(sim / (p1 - p0));
+  for (int k = p0 + lane; k < p1; k += 32) {
+    cx<T>& v = dr[m.face_lam[k]];
+    v = mkc<T>(v.re - mre, v.im - mim);
+  }
 }
 
 // lambda += Q mu: each multiplier between face neighbours takes its face's coarse unknown

@@ -209,6 +209,8 @@ std::string build_maps(int dim, const int* nel, const int* nsub, int local_mode,
   m->sd_coarse.clear();
   m->face_sd.clear();
   m->lam_face.clear();
+  m->face_lam_ptr.clear();
+  m->face_lam.clear();
   m->slot_faces.clear();
   if (augment) {
     const int ne = 2 * dim;
@@ -279,6 +281,14 @@ std::string build_maps(int dim, const int* nel, const int* nsub, int local_mode,
       }
       if (dist == 1) m->lam_face[li] = face_of(A, axis);  // the plus side is the lower subdomain
     }
+    m->face_lam_ptr.assign(g.nface + 1, 0);
+    for (int li = 0; li < g.nlam; ++li)
+      if (m->lam_face[li] >= 0) ++m->face_lam_ptr[m->lam_face[li] + 1];
+    for (int f = 0; f < g.nface; ++f) m->face_lam_ptr[f + 1] += m->face_lam_ptr[f];
+    m->face_lam.assign(m->face_lam_ptr[g.nface], 0);
+    std::vector<int> fill(m->face_lam_ptr.begin(), m->face_lam_ptr.end() - 1);
+    for (int li = 0; li < g.nlam; ++li)
+      if (m->lam_face[li] >= 0) m->face_lam[fill[m->lam_face[li]]++] = li;
   } else {
     m->sd_coarse = m->sd_corner;
   }

@@ -24,6 +24,8 @@ struct HostMaps {
   std::vector<int> sd_coarse;    // [nsd][nq] coarse unknown of each coupling slot (corners, faces) or -1
   std::vector<int> face_sd;      // [nface][2] the lower and the higher subdomain of each face
   std::vector<int> lam_face;     // [nlam] face of the multiplier's subdomain pair, -1 for other pairs
+  std::vector<int> face_lam_ptr; // [nface + 1] CSR offsets of the multipliers of each face
+  std::vector<int> face_lam;     // multipliers of each face, in increasing order
   std::vector<int> slot_faces;   // [nD] bit f set: slot lies on local face f = 2a + side
   int ncls = 0;
 };

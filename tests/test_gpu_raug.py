@@ -137,3 +137,31 @@ def test_augmented_coarse_size_limit():
         S.Solver(2, 256, 1e-4, nsub=64, augment=1)  # 63^2 + 2 * 63 * 64 > 4096 coarse unknowns
     with pytest.raises(S.SchurError):
         S.Solver(2, 64, 1e-4, nsub=4, augment=2)
+
+
+@pytest.mark.parametrize("prec", [S.SCHUR_FP64, S.SCHUR_MIXED])
+def test_augmented_1024_all_betas(prec):
+    """2D 1024^2 Q1 elements in 16 x 16 subdomains of 64^2 (H/h = 64, the paper's ratio; 705 coarse
+    unknowns with the augmentation): all four betas of the 1024^2 workload against the oracle."""
+    N, P = 1024, 16
+    b = oracle.apply_M(2, N, inputs.smoothed_noise(2, N, seed=1))
+    bd = torch.from_numpy(b).cuda()
+    oracle.set_threads(0)
+    for beta in (1e-2, 1e-4, 1e-6, 1e-8):
+        sol = S.Solver(2, N, beta, nsub=P, precision=prec, tol=1e-12, augment=1)
+        x = sol.schur_solve(bd).cpu().numpy()
+        sol.close()
+        ref = oracle.fd_schur_solve(2, N, beta, b)
+        assert rel(x, ref) <= TOL[prec], (beta, rel(x, ref))
+
+
+def test_augmented_128cube_mixed():
+    """3D 128^3 Q1 elements in 8^3 subdomains of 16^3 (1687 coarse unknowns with the augmentation),
+    mixed precision refined to 1e-10, against the oracle."""
+    N, P, beta = 128, 8, 1e-6
+    b = oracle.apply_M(3, N, inputs.random_modes_3d(N, count=8, seed=2))
+    sol = S.Solver(3, N, beta, nsub=P, precision=S.SCHUR_MIXED, tol=1e-10, augment=1)
+    x = sol.schur_solve(torch.from_numpy(b).cuda()).cpu().numpy()
+    sol.close()
+    ref = oracle.fd_schur_solve(3, N, beta, b)
+    assert rel(x, ref) <= 1e-8, rel(x, ref)
