@@ -278,7 +278,7 @@ KERNEL_OF = {"form": "k_form_rr_cols<float, 17>", "apply_F": "k_local_apply<floa
              "apply_S": "k_local_apply<float, 1, 1>", "assemble_z": "k_assemble_z<float>"}
 # source files whose contents determine each kernel (a recorded DRAM traffic figure is used only
 # while their hash is the one recorded with it)
-KERNEL_SOURCES = {"k_form_rr_cols<float, 17>": ["warp.cuh", "common.cuh"],
+KERNEL_SOURCES = {"k_form_rr_cols<float, 17>": ["warp.cuh", "layered.cuh", "common.cuh"],
                   "k_local_apply<float, 0, 1>": ["kernels.cuh", "common.cuh"],
                   "k_local_apply<float, 1, 1>": ["kernels.cuh", "common.cuh"],
                   "k_assemble_z<float>": ["kernels.cuh", "common.cuh"]}
