@@ -64,6 +64,8 @@ int upload_maps(const HostMaps& hm, DevMaps* dm, std::string* msg) {
   if (e == cudaSuccess) e = upload(&dm->slot_faces, hm.slot_faces);
   if (e == cudaSuccess) e = upload(&dm->face_lam_ptr, hm.face_lam_ptr);
   if (e == cudaSuccess) e = upload(&dm->face_lam, hm.face_lam);
+  if (e == cudaSuccess) e = upload(&dm->grp_sd, hm.grp_sd);
+  if (e == cudaSuccess) e = upload(&dm->grp_ptr, hm.grp_ptr);
   if (e != cudaSuccess) {
     if (msg) *msg = std::string("uploading index maps: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? SCHUR_ENOMEM : SCHUR_ECUDA;
@@ -74,7 +76,8 @@ int upload_maps(const HostMaps& hm, DevMaps* dm, std::string* msg) {
 void free_maps(DevMaps* dm) {
   void* ps[] = {dm->slot_node, dm->node_slot, dm->corner_node, dm->sd_code, dm->sd_cls,
                 dm->cls_code,  dm->sd_lam,    dm->lam_side,    dm->sd_corner, dm->sd_minv,
-                dm->sd_coarse, dm->face_sd,   dm->lam_face,    dm->slot_faces, dm->face_lam_ptr, dm->face_lam};
+                dm->sd_coarse, dm->face_sd,   dm->lam_face,    dm->slot_faces, dm->face_lam_ptr, dm->face_lam,
+                dm->grp_sd,    dm->grp_ptr};
   for (void* p : ps)
     if (p) cudaFree(p);
   *dm = DevMaps();

@@ -601,6 +601,17 @@ __global__ void k_bcr_identity(cx<T>* X, int n, int ld) {
     X[e] = mkc<T>((e / ld) == (e % ld) ? T(1) : T(0), T(0));
 }
 
+// dst block k = src block list[k] (count blocks of bb entries)
+template <class T>
+__global__ void k_bcr_gather_blocks(const cx<T>* __restrict__ src, const int* __restrict__ list, int count, size_t bb,
+                                    cx<T>* dst) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)count * bb;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t k = e / bb;
+    dst[e] = src[(size_t)list[k] * bb + (e - k * bb)];
+  }
+}
+
 // ------------------------------------------------------------------ host orchestration
 // Levels: lists of (j, p, q) with p, q = remaining neighbours of j (-1 if none).
 static void bcr_schedule(int L, std::vector<std::vector<int>>* lev_j, std::vector<std::vector<int>>* lev_p,
@@ -623,6 +634,37 @@ static void bcr_schedule(int L, std::vector<std::vector<int>>* lev_j, std::vecto
     lev_q->push_back(Q);
     rem.swap(next);
   }
+}
+
+void bcr_level0_maps(int L, std::vector<int>* tgt, std::vector<int>* elim, std::vector<int>* rem) {
+  std::vector<std::vector<int>> lj, lp, lq;
+  bcr_schedule(L, &lj, &lp, &lq);
+  tgt->clear();
+  elim->clear();
+  rem->clear();
+  if (lj.empty()) return;
+  std::vector<int> cm(L, -1);  // compact index of the layers that survive level 0
+  std::vector<char> gone(L, 0);
+  for (int j : lj[0]) gone[j] = 1;
+  for (int t = 0; t < L; ++t)
+    if (!gone[t]) {
+      cm[t] = (int)rem->size();
+      rem->push_back(t);
+    }
+  std::vector<int> jr(L, -1), kr(L, -1), jl(L, -1), kl(L, -1);
+  for (size_t k = 0; k < lj[0].size(); ++k) {
+    const int j = lj[0][k], p = lp[0][k], q = lq[0][k];
+    elim->insert(elim->end(), {j, p >= 0 ? cm[p] : -1, q >= 0 ? cm[q] : -1});
+    if (p >= 0) {  // j is the right neighbour of p
+      jr[p] = j;
+      kr[p] = (int)k;
+    }
+    if (q >= 0) {  // j is the left neighbour of q
+      jl[q] = j;
+      kl[q] = (int)k;
+    }
+  }
+  for (int t : *rem) tgt->insert(tgt->end(), {t, jr[t], kr[t], jl[t], kl[t]});
 }
 
 // The whole reduction as a list of launches over task arrays that are built on the host and
@@ -734,12 +776,26 @@ static cudaError_t run_plan(const BcrPlan<S>& plan, GemmTask<S>* dG, CopyTask<S>
 }
 
 template <class T>
-int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int ldk, int* err, cudaStream_t st, std::string* msg,
-               long long* launches) {
+int coarse_bcr(const StoredProv<double>& P, const BcrLevel0<T>* split, cx<T>* Kinv, int ldk, int* err, cudaStream_t st,
+               std::string* msg, long long* launches) {
   const int b = P.ly.b, L = P.ly.L;
-  const size_t bb = (size_t)b * b, n = (size_t)b * L;
+  const size_t bb = (size_t)b * b;
   std::vector<std::vector<int>> lj, lp, lq;
   bcr_schedule(L, &lj, &lp, &lq);
+  // with the level-0 split the explicit inverse covers the layers that survive level 0 (compact
+  // numbering cm), and levels 1.. of the reduction
+  const size_t lv0 = split ? 1 : 0;
+  std::vector<int> cm(L);
+  int Lx = L;
+  if (split) {
+    std::vector<char> gone(L, 0);
+    for (int j : lj[0]) gone[j] = 1;
+    Lx = 0;
+    for (int t = 0; t < L; ++t) cm[t] = gone[t] ? -1 : Lx++;
+  } else {
+    for (int t = 0; t < L; ++t) cm[t] = t;
+  }
+  const size_t n = (size_t)b * Lx;
   auto fail = [&](cudaError_t e, const char* where) {
     if (msg) *msg = std::string("coarse reduction (") + where + "): " + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? SCHUR_ENOMEM : SCHUR_ECUDA;
@@ -852,10 +908,11 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int ldk, int* err, cuda
   const size_t bN = (size_t)b * ldk;  // one block row of X (row stride ldk)
   const int N = (int)n;
   auto tb = [&](cx<T>* base, int K) { return base + (size_t)K * bb; };
-  auto xb = [&](cx<T>* base, int K, int c0) { return base + (size_t)K * bN + (size_t)c0 * b; };
+  // row block of layer K (compact numbering), block column c0
+  auto xb = [&](cx<T>* base, int K, int c0) { return base + (size_t)cm[K] * bN + (size_t)c0 * b; };
   std::vector<int> lo(L), hi(L);
-  for (int i = 0; i < L; ++i) lo[i] = hi[i] = i;
-  for (size_t lv = 0; lv < lj.size(); ++lv) {
+  for (int i = 0; i < L; ++i) lo[i] = hi[i] = cm[i];
+  for (size_t lv = lv0; lv < lj.size(); ++lv) {
     std::vector<int> left_of(L, -1), right_of(L, -1);
     for (size_t k = 0; k < lj[lv].size(); ++k) {
       if (lp[lv][k] >= 0) right_of[lp[lv][k]] = lj[lv][k];
@@ -894,7 +951,7 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int ldk, int* err, cuda
       }
     }
   }
-  for (int lv = (int)lj.size() - 1; lv >= 0; --lv) {
+  for (int lv = (int)lj.size() - 1; lv >= (int)lv0; --lv) {
     // X_j = Dinv_j X_j - Lp_j^T X_p - Lq_j X_q
     for (size_t k = 0; k < lj[lv].size(); ++k) {
       const int j = lj[lv][k], p = lp[lv][k], q = lq[lv][k];
@@ -938,6 +995,19 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int ldk, int* err, cuda
     BCR_CK(cudaGetLastError(), "convert");
     *launches += 3;
   }
+  if (split) {
+    // the level-0 blocks for the per-apply forward and backward steps
+    const std::vector<int>& J0 = lj[0];
+    int* dJ = nullptr;
+    BCR_CK(mal(&dJ, J0.size() * sizeof(int)), "alloc");
+    BCR_CK(cudaMemcpyAsync(dJ, J0.data(), J0.size() * sizeof(int), cudaMemcpyHostToDevice, st), "upload");
+    const int gg = (int)std::min<size_t>((J0.size() * bb + 255) / 256, 4096);
+    k_bcr_gather_blocks<T><<<gg, 256, 0, st>>>(DinvT, dJ, (int)J0.size(), bb, split->D0);
+    k_bcr_gather_blocks<T><<<gg, 256, 0, st>>>(LpT, dJ, (int)J0.size(), bb, split->Lp0);
+    k_bcr_gather_blocks<T><<<gg, 256, 0, st>>>(LqT, dJ, (int)J0.size(), bb, split->Lq0);
+    BCR_CK(cudaGetLastError(), "level-0 blocks");
+    *launches += 3;
+  }
   k_bcr_identity<T><<<(int)std::min<size_t>((n * ldk + 255) / 256, 8192), 256, 0, st>>>(Kinv, (int)n, ldk);
   BCR_CK(cudaGetLastError(), "identity");
   ++*launches;
@@ -948,7 +1018,9 @@ int coarse_bcr(const StoredProv<double>& P, cx<T>* Kinv, int ldk, int* err, cuda
 #undef BCR_CK
 }
 
-template int coarse_bcr<float>(const StoredProv<double>&, cx<float>*, int, int*, cudaStream_t, std::string*, long long*);
-template int coarse_bcr<double>(const StoredProv<double>&, cx<double>*, int, int*, cudaStream_t, std::string*, long long*);
+template int coarse_bcr<float>(const StoredProv<double>&, const BcrLevel0<float>*, cx<float>*, int, int*, cudaStream_t,
+                                std::string*, long long*);
+template int coarse_bcr<double>(const StoredProv<double>&, const BcrLevel0<double>*, cx<double>*, int, int*,
+                                 cudaStream_t, std::string*, long long*);
 
 }  // namespace schur

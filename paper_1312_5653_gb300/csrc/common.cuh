@@ -15,6 +15,7 @@ cudaError_t smem_attr(const void* func, int bytes);
 
 constexpr int kMaxRdev = 16;   // right-hand sides per FETI-DP solve
 constexpr int kMaxKdev = 512;  // Krylov basis size bound (max_iter < kMaxKdev)
+constexpr int kApplyGroup = 8;  // subdomains of one class that share a staged local operator
 
 // Programmatic dependent launch: a kernel launched by launch_pdl may start while its predecessor
 // in the stream is still running; it calls pdl_wait() before anything else (which returns once the

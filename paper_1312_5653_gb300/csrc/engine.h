@@ -26,6 +26,8 @@ struct DevMaps {
   int* slot_faces = nullptr;
   int* face_lam_ptr = nullptr;
   int* face_lam = nullptr;
+  int* grp_sd = nullptr;
+  int* grp_ptr = nullptr;
 };
 
 int upload_maps(const HostMaps& hm, DevMaps* dm, std::string* msg);

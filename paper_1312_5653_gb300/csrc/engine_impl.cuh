@@ -83,6 +83,9 @@ class Engine : public EngineBase {
     mv_.slot_faces = dm->slot_faces;
     mv_.face_lam_ptr = dm->face_lam_ptr;
     mv_.face_lam = dm->face_lam;
+    mv_.grp_sd = dm->grp_sd;
+    mv_.grp_ptr = dm->grp_ptr;
+    ngrp_ = (int)hm->grp_ptr.size() - 1;
     st_ = make_stencil<T>(g_, gamma, sre);
     ncls_ = hm->ncls;
     // remainder problem: full local grid, vertices and Dirichlet nodes removed
@@ -426,6 +429,7 @@ class Engine : public EngineBase {
       int crc = dense_gj_inverse(Kd, g.nco, err_ + 2, st, msg, &launches);
       prof_stop(KC_COARSE_SETUP, st);
       if (crc) return crc;
+      ncr_ = g.nco;
       ldk_ = (g.nco + 1) & ~1;
       nct_ = (g.nco + kCT - 1) / kCT;
       ENG_CK(alloc(&Kinv_, (size_t)g.nco * ldk_ * cxT));
@@ -463,18 +467,45 @@ class Engine : public EngineBase {
       cprov_.ly.L = g.cL;
       cprov_.CA = CA_;
       cprov_.CB = CB_;
-      // FP64 block cyclic reduction over the coarse layers, explicit inverse in precision T
-      ldk_ = (g.ncor + 1) & ~1;  // even row stride of the full inverse (temporary)
-      nct_ = (g.ncor + kCT - 1) / kCT;
-      ENG_CK(alloc(&Kinv_, (size_t)g.ncor * ldk_ * cxT));
+      // FP64 block cyclic reduction over the coarse layers.  With at least two layers, level 0 is
+      // kept as blocks (applied by k_bcr_fwd0 / k_bcr_bwd0 around each coarse solve) and the
+      // explicit inverse in precision T covers only the reduced matrix on the surviving layers
+      split_ = g.cL >= 2;
+      BcrLevel0<T> l0{nullptr, nullptr, nullptr};
+      ncr_ = g.ncor;
+      if (split_) {
+        std::vector<int> tgt, elim, rem;
+        bcr_level0_maps(g.cL, &tgt, &elim, &rem);
+        nj0_ = (int)elim.size() / 3;
+        nr0_ = (int)rem.size();
+        ncr_ = g.cb * nr0_;
+        auto up = [&](int** d, const std::vector<int>& h) -> cudaError_t {
+          cudaError_t e = alloc(d, std::max<size_t>(h.size(), 1) * sizeof(int));
+          if (e == cudaSuccess && !h.empty())
+            e = cudaMemcpyAsync(*d, h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+          return e;
+        };
+        ENG_CK(up(&bcr_tgt_, tgt));
+        ENG_CK(up(&bcr_elim_, elim));
+        ENG_CK(up(&bcr_rem_, rem));
+        ENG_CK(cudaStreamSynchronize(st));  // the host tables leave scope
+        const size_t nb0 = (size_t)nj0_ * cbb;
+        ENG_CK(alloc(&D0_, nb0 * cxT));
+        ENG_CK(alloc(&Lp0_, nb0 * cxT));
+        ENG_CK(alloc(&Lq0_, nb0 * cxT));
+        op_bytes_ += 3 * (long long)nb0 * cxT;
+        l0 = BcrLevel0<T>{D0_, Lp0_, Lq0_};
+      }
+      ldk_ = (ncr_ + 1) & ~1;  // even row stride of the explicit inverse (temporary)
+      nct_ = (ncr_ + kCT - 1) / kCT;
+      ENG_CK(alloc(&Kinv_, (size_t)ncr_ * ldk_ * cxT));
       ENG_CK(alloc(&Kt_, (size_t)ctile_count(nct_) * kCT * kCT * cxT));
       op_bytes_ += (long long)ctile_count(nct_) * kCT * kCT * cxT;
-      (void)cbb;
-      int crc = coarse_bcr<T>(cprov_, Kinv_, ldk_, err_ + 2, st, msg, &launches);
+      int crc = coarse_bcr<T>(cprov_, split_ ? &l0 : nullptr, Kinv_, ldk_, err_ + 2, st, msg, &launches);
       if (crc) return crc;
       // keep the upper 32 x 32 tiles of the symmetric inverse; the full matrix is released
       prof_start(KC_COARSE_INV, st);
-      k_pack_ctiles<T><<<(int)std::min<long long>(ctile_count(nct_), 8 * nsm_), 256, 0, st>>>(Kinv_, g.ncor, ldk_,
+      k_pack_ctiles<T><<<(int)std::min<long long>(ctile_count(nct_), 8 * nsm_), 256, 0, st>>>(Kinv_, ncr_, ldk_,
                                                                                             nct_, Kt_);
       prof_stop(KC_COARSE_INV, st);
       ENG_LAUNCH();
@@ -636,7 +667,26 @@ class Engine : public EngineBase {
     }
     else if (which == 3 || which == 4) {
       if (g.nco == 0 || (which == 3 && g.nq != g.nc)) return SCHUR_EINVAL;
-      if (which == 4) {
+      if (which == 4 && split_) {
+        // the coarse solve applied to the identity, kMaxRdev columns at a time
+        int erc = ensure_ws(kMaxRdev, std::max(1, wsM_), msg);
+        if (erc) return erc;
+        const int n = g.nco;
+        host.assign((size_t)n * n, mkc<double>(0, 0));
+        std::vector<cx<T>> e((size_t)kMaxRdev * n), wv((size_t)kMaxRdev * n);
+        for (int c0 = 0; c0 < n; c0 += kMaxRdev) {
+          const int R = std::min(kMaxRdev, n - c0);
+          std::fill(e.begin(), e.end(), mkc<T>(T(0), T(0)));
+          for (int r = 0; r < R; ++r) e[(size_t)r * n + c0 + r] = mkc<T>(T(1), T(0));
+          ENG_CK(cudaMemcpy(gc_, e.data(), (size_t)R * n * sizeof(cx<T>), cudaMemcpyHostToDevice));
+          erc = coarse_apply(gc_, R, nullptr, wc_, st, msg);
+          if (erc) return erc;
+          ENG_CK(cudaStreamSynchronize(st));
+          ENG_CK(cudaMemcpy(wv.data(), wc_, (size_t)R * n * sizeof(cx<T>), cudaMemcpyDeviceToHost));
+          for (int r = 0; r < R; ++r)
+            for (int i = 0; i < n; ++i) host[(size_t)i * n + c0 + r] = ccast<double>(wv[(size_t)r * n + i]);
+        }
+      } else if (which == 4) {
         rc = fetch(Kt_, (size_t)ctile_count(nct_) * kCT * kCT);
         if (!rc) {  // upper tiles -> full symmetric matrix (lower tiles are the transposes)
           std::vector<cx<double>> full((size_t)g.nco * g.nco);
@@ -735,6 +785,10 @@ class Engine : public EngineBase {
       ENG_CK(wa(&cpu_, np * cxT));
       ENG_CK(wa(&cpv_, np * cxT));
     }
+    if (split_) {
+      ENG_CK(wa(&cfr_, (size_t)ncr_ * R * cxT));
+      ENG_CK(wa(&cxr_, (size_t)ncr_ * R * cxT));
+    }
     nblk_ = std::max(1, std::min((int)((nl + 255) / 256), 2 * nsm_));
     nblk_ = std::max(nblk_, (int)((nl + 2047) / 2048));
     ENG_CK(wa(&part_, (size_t)kMaxRdev * kMaxKdev * nblk_ * sizeof(cx<double>)));
@@ -813,6 +867,27 @@ class Engine : public EngineBase {
   int coarse_apply(const cx<T>* gv, int R, const int* active, cx<T>* w, cudaStream_t st, std::string* msg) {
     const long long ntile = ctile_count(nct_);
     prof_start(KC_COARSE_APPLY, st);
+    if (split_) {
+      // level-0 forward step, reduced inverse, level-0 backward step
+      const int b = g_.cb, ns = (b + 31) / 32, nz = (R + kBcrRC - 1) / kBcrRC;
+      const size_t sm = (size_t)kBcrRC * (b + 288) * sizeof(cx<T>);
+      ENG_CK(smem_attr((const void*)k_bcr_fwd0<T>, (int)sm));
+      ENG_CK(smem_attr((const void*)k_bcr_bwd0<T>, (int)sm));
+      ENG_CK(launch_pdl(k_bcr_fwd0<T>, dim3(nr0_, ns, nz), dim3(256), sm, st, b, (const int*)bcr_tgt_,
+                        (const cx<T>*)Lp0_, (const cx<T>*)Lq0_, gv, g_.nco, cfr_, ncr_, R, active));
+      ENG_CK(launch_pdl(k_coarse_tiles<T>, dim3((unsigned)((ntile + 3) / 4)), dim3(128), 0, st, Kt_, nct_, ncr_,
+                        (const cx<T>*)cfr_, R, active, cpu_, cpv_));
+      ENG_CK(launch_pdl(k_coarse_reduce<T>, dim3(nct_ * R), dim3(512), 0, st, cpu_, cpv_, nct_, ncr_, R, active, cxr_));
+      ENG_CK(launch_pdl(k_bcr_bwd0<T>, dim3(nj0_ + nr0_, ns, nz), dim3(256), sm, st, b, nj0_, (const int*)bcr_elim_,
+                        (const int*)bcr_rem_, (const cx<T>*)D0_, (const cx<T>*)Lp0_, (const cx<T>*)Lq0_, gv, g_.nco,
+                        (const cx<T>*)cxr_, ncr_, w, g_.nco, R, active));
+      prof_stop(KC_COARSE_APPLY, st);
+      ENG_LAUNCH();
+      ENG_LAUNCH();
+      ENG_LAUNCH();
+      ENG_LAUNCH();
+      return SCHUR_OK;
+    }
     ENG_CK(launch_pdl(k_coarse_tiles<T>, dim3((unsigned)((ntile + 3) / 4)), dim3(128), 0, st, Kt_, nct_, g_.nco, gv, R,
                       active, cpu_, cpv_));
     ENG_CK(launch_pdl(k_coarse_reduce<T>, dim3(nct_ * R), dim3(512), 0, st, cpu_, cpv_, nct_, g_.nco, R, active, w));
@@ -847,6 +922,47 @@ class Engine : public EngineBase {
       }
       ENG_LAUNCH();
       return SCHUR_OK;
+    }
+    if (R <= 2 && ngrp_ > 0 && 2 * (long long)ngrp_ <= g.nsd && g.nD <= 256) {
+      // subdomains of one class in groups: each staged operator serves the whole group
+      const size_t smem = ((size_t)g.nD * g.nD + (size_t)kApplyGroup * R * g.nD +
+                           (want_tc ? (size_t)g.nD * g.nq : 0)) * sizeof(cx<T>);
+      if (smem <= ((size_t)100 << 10)) {
+        cx<T>* tc = want_tc ? Tc_ : nullptr;
+#define LG_CASE(SC)                                                                                           \
+  do {                                                                                                        \
+    ENG_CK(smem_attr((const void*)k_local_apply_grp<T, SC, 2>, (int)smem));                                  \
+    prof_start(SC ? KC_APPLY_S : KC_APPLY_F, st);                                                             \
+    ENG_CK(launch_pdl(k_local_apply_grp<T, SC, 2>, dim3(ngrp_), dim3(256), smem, st, g, mv_, Op, Frc_, v, R, \
+                      active, Y_, tc, vscale));                                                               \
+    prof_stop(SC ? KC_APPLY_S : KC_APPLY_F, st);                                                              \
+  } while (0)
+        if (precond) LG_CASE(true);
+        else LG_CASE(false);
+#undef LG_CASE
+        ENG_LAUNCH();
+        return SCHUR_OK;
+      }
+    }
+    if (R == 1 && g.nD <= 128 && g.nq <= 16) {
+      const size_t smem1 = ((size_t)sym_ld(g.nD) + (((size_t)g.nD + 1) & ~(size_t)1)) * sizeof(cx<T>);
+      if (smem1 <= ((size_t)96 << 10)) {
+        const int thr1 = ((g.nD + 31) / 32) * 32;
+        cx<T>* tc = want_tc ? Tc_ : nullptr;
+#define L1_CASE(SC)                                                                                            \
+  do {                                                                                                         \
+    ENG_CK(smem_attr((const void*)k_local_apply_1<T, SC>, (int)smem1));                                       \
+    prof_start(SC ? KC_APPLY_S : KC_APPLY_F, st);                                                              \
+    ENG_CK(launch_pdl(k_local_apply_1<T, SC>, dim3(g.nsd), dim3(thr1), smem1, st, g, mv_, Op, Frc_, v, active, \
+                      Y_, tc, vscale));                                                                        \
+    prof_stop(SC ? KC_APPLY_S : KC_APPLY_F, st);                                                               \
+  } while (0)
+        if (precond) L1_CASE(true);
+        else L1_CASE(false);
+#undef L1_CASE
+        ENG_LAUNCH();
+        return SCHUR_OK;
+      }
     }
     int thr = std::min(512, ((g.nD + 31) / 32) * 32);
     const size_t xcnt = ((size_t)R * g.nD + 1) & ~(size_t)1;
@@ -1041,12 +1157,17 @@ class Engine : public EngineBase {
   Stencil<T> st_;
   StencilProv<T> prr_, pii_;
   StoredProv<double> cprov_;
-  int ncls_ = 0, nsm_ = 152, nblk_ = 1, coarse_cluster_ = 0, ldk_ = 0, nct_ = 0;
+  int ncls_ = 0, ngrp_ = 0, nsm_ = 152, nblk_ = 1, coarse_cluster_ = 0, ldk_ = 0, nct_ = 0;
   long long op_bytes_ = 0;
   std::vector<void*> allocs_, ws_;
   int* err_ = nullptr;
   int* ones_ = nullptr;
   cx<T>*Dinv_ = nullptr, *F_ = nullptr, *Frc_ = nullptr, *Sd_ = nullptr, *Kinv_ = nullptr, *Kt_ = nullptr;
+  // coarse solve: level 0 of the reduction kept as blocks around the reduced inverse (split_)
+  bool split_ = false;
+  int ncr_ = 0, nj0_ = 0, nr0_ = 0;  // unknowns of the stored inverse; layers eliminated / kept at level 0
+  int *bcr_tgt_ = nullptr, *bcr_elim_ = nullptr, *bcr_rem_ = nullptr;
+  cx<T>*D0_ = nullptr, *Lp0_ = nullptr, *Lq0_ = nullptr, *cfr_ = nullptr, *cxr_ = nullptr;
   cx<T>*cpu_ = nullptr, *cpv_ = nullptr;  // partial products of the packed coarse inverse
   cx<double>*Kcc_ = nullptr, *CA_ = nullptr, *CB_ = nullptr, *Dc_ = nullptr;
   int wsR_ = 0, wsM_ = 0;

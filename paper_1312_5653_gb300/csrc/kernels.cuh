@@ -32,6 +32,8 @@ struct MapsView {
   const int* slot_faces;  // [nD] local faces of each slot, bit f = 2a + side (augmented only)
   const int* face_lam_ptr;  // [nface + 1] CSR offsets of the multipliers of each face (augmented only)
   const int* face_lam;      // multipliers of each face (augmented only)
+  const int* grp_sd;        // [nsd] subdomains ordered by class
+  const int* grp_ptr;       // [ngrp + 1] groups of at most kApplyGroup subdomains of one class
 };
 
 __device__ __forceinline__ void local_ext(const Geom& g, int* ext) {
@@ -618,6 +620,144 @@ __global__ void __launch_bounds__(512) k_coarse_reduce(const cx<T>* __restrict__
   }
 }
 
+// ------------------------------------------------------------------ coarse solve around level 0
+// The coarse solve w = K_cc^{-1} g with level 0 of the block cyclic reduction applied explicitly
+// around the stored inverse of the reduced matrix on the layers that survive level 0:
+//   forward:  f_t = g_t - Lp_jr g_jr - Lq_jl^T g_jl        (every surviving layer t, compact order)
+//   reduced:  x_r = K_r^{-1} f_r                            (packed tiles, k_coarse_tiles/reduce)
+//   backward: x_j = D_j^{-1} g_j - Lp_j^T x_p - Lq_j x_q    (every layer j eliminated at level 0)
+// CTA (layer, 32-row slice, kBcrRC right-hand sides); 256 threads = 32 rows x 8 k-groups.
+constexpr int kBcrRC = 4;
+
+// v[k][c] = src[(r0 + c) ld + off + k] for k < b, c < nc (zero past nc)
+template <class T>
+__device__ __forceinline__ void bcr_stage(const cx<T>* __restrict__ src, int ld, size_t off, int b, int r0, int nc,
+                                          cx<T>* v) {
+  for (int e = threadIdx.x; e < b * kBcrRC; e += blockDim.x) {
+    const int k = e / kBcrRC, c = e - k * kBcrRC;
+    v[e] = c < nc ? src[(size_t)(r0 + c) * ld + off + k] : czero<T>();
+  }
+}
+
+// acc[il][c] += alpha sum_k op(M)[i0 + il][k] v[k][c] for the rows i0 + il < b; op(M) = M (thread
+// il = tid / 8, kg = tid % 8: a warp reads four 64-byte row segments) or M^T (il = tid % 32,
+// kg = tid / 32: a warp reads one 256-byte column segment) of the b x b row-major block M.  The
+// eight k-group partials are added in order through shared memory; ends with a barrier.
+template <class T, bool TRANS>
+__device__ __forceinline__ void bcr_blk_mv(const cx<T>* __restrict__ M, int b, int i0, const cx<T>* v, int nc,
+                                           cx<T>* red, cx<T>* acc, T alpha) {
+  const int tid = threadIdx.x;
+  const int il = TRANS ? (tid & 31) : (tid >> 3), kg = TRANS ? (tid >> 5) : (tid & 7);
+  const int i = i0 + il;
+  cx<T> p[kBcrRC];
+#pragma unroll
+  for (int c = 0; c < kBcrRC; ++c) p[c] = czero<T>();
+  if (i < b) {
+#pragma unroll 4
+    for (int k = kg; k < b; k += 8) {
+      const cx<T> m = TRANS ? M[(size_t)k * b + i] : M[(size_t)i * b + k];
+#pragma unroll
+      for (int c = 0; c < kBcrRC; ++c)
+        if (c < nc) cfma(p[c], m, v[k * kBcrRC + c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kBcrRC; ++c) red[(kg * 32 + il) * kBcrRC + c] = p[c];
+  __syncthreads();
+  if (tid < 32 * kBcrRC) {
+    const int rl = tid / kBcrRC, c = tid - rl * kBcrRC;
+    cx<T> s = czero<T>();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s = cadd(s, red[(q * 32 + rl) * kBcrRC + c]);
+    acc[tid] = cadd(acc[tid], cscale(s, alpha));
+  }
+  __syncthreads();
+}
+
+// forward step of level 0 into the reduced right-hand side fr ([R][ldr], compact layer order);
+// tgt[5 c..] = (t, jr, kr, jl, kl) of the c-th surviving layer
+template <class T>
+__global__ void __launch_bounds__(256) k_bcr_fwd0(int b, const int* __restrict__ tgt, const cx<T>* __restrict__ Lp0,
+                                                  const cx<T>* __restrict__ Lq0, const cx<T>* __restrict__ g, int ldg,
+                                                  cx<T>* fr, int ldr, int R, const int* __restrict__ active) {
+  pdl_wait();
+  pdl_trigger();
+  extern __shared__ __align__(16) unsigned char smb[];
+  cx<T>* v = reinterpret_cast<cx<T>*>(smb);  // b x kBcrRC
+  cx<T>* red = v + (size_t)b * kBcrRC;         // 8 x 32 x kBcrRC
+  cx<T>* acc = red + 256 * kBcrRC;             // 32 x kBcrRC
+  const int c = blockIdx.x, i0 = blockIdx.y * 32, r0 = blockIdx.z * kBcrRC, nc = min(kBcrRC, R - r0);
+  const int t = tgt[5 * c], jr = tgt[5 * c + 1], kr = tgt[5 * c + 2], jl = tgt[5 * c + 3], kl = tgt[5 * c + 4];
+  const size_t bb = (size_t)b * b;
+  const int tid = threadIdx.x;
+  if (tid < 32 * kBcrRC) {
+    const int il = tid / kBcrRC, cc = tid - il * kBcrRC, i = i0 + il;
+    acc[tid] = (i < b && cc < nc) ? g[(size_t)(r0 + cc) * ldg + (size_t)t * b + i] : czero<T>();
+  }
+  if (kr >= 0) {
+    bcr_stage(g, ldg, (size_t)jr * b, b, r0, nc, v);
+    __syncthreads();
+    bcr_blk_mv<T, false>(Lp0 + (size_t)kr * bb, b, i0, v, nc, red, acc, T(-1));
+  }
+  if (kl >= 0) {
+    bcr_stage(g, ldg, (size_t)jl * b, b, r0, nc, v);
+    __syncthreads();
+    bcr_blk_mv<T, true>(Lq0 + (size_t)kl * bb, b, i0, v, nc, red, acc, T(-1));
+  }
+  __syncthreads();
+  if (tid < 32 * kBcrRC) {
+    const int il = tid / kBcrRC, cc = tid - il * kBcrRC, i = i0 + il;
+    if (i < b && cc < nc && (!active || active[r0 + cc])) fr[(size_t)(r0 + cc) * ldr + (size_t)c * b + i] = acc[tid];
+  }
+}
+
+// backward step of level 0: blocks x < nj solve the eliminated layers (elim[3 x..] = (j, cp, cq)),
+// blocks nj + c copy the reduced solution of the c-th surviving layer rem[c] into w ([R][ldw])
+template <class T>
+__global__ void __launch_bounds__(256) k_bcr_bwd0(int b, int nj, const int* __restrict__ elim, const int* __restrict__ rem,
+                                                  const cx<T>* __restrict__ D0, const cx<T>* __restrict__ Lp0,
+                                                  const cx<T>* __restrict__ Lq0, const cx<T>* __restrict__ g, int ldg,
+                                                  const cx<T>* __restrict__ xr, int ldr, cx<T>* w, int ldw, int R,
+                                                  const int* __restrict__ active) {
+  pdl_wait();
+  pdl_trigger();
+  extern __shared__ __align__(16) unsigned char smb[];
+  cx<T>* v = reinterpret_cast<cx<T>*>(smb);
+  cx<T>* red = v + (size_t)b * kBcrRC;
+  cx<T>* acc = red + 256 * kBcrRC;
+  const int x = blockIdx.x, i0 = blockIdx.y * 32, r0 = blockIdx.z * kBcrRC, nc = min(kBcrRC, R - r0);
+  const int tid = threadIdx.x;
+  if (x >= nj) {
+    const int cidx = x - nj, t = rem[cidx];
+    if (tid < 32 * kBcrRC) {
+      const int il = tid / kBcrRC, cc = tid - il * kBcrRC, i = i0 + il;
+      if (i < b && cc < nc && (!active || active[r0 + cc]))
+        w[(size_t)(r0 + cc) * ldw + (size_t)t * b + i] = xr[(size_t)(r0 + cc) * ldr + (size_t)cidx * b + i];
+    }
+    return;
+  }
+  const int j = elim[3 * x], cp = elim[3 * x + 1], cq = elim[3 * x + 2];
+  const size_t bb = (size_t)b * b;
+  if (tid < 32 * kBcrRC) acc[tid] = czero<T>();
+  bcr_stage(g, ldg, (size_t)j * b, b, r0, nc, v);
+  __syncthreads();
+  bcr_blk_mv<T, false>(D0 + (size_t)x * bb, b, i0, v, nc, red, acc, T(1));
+  if (cp >= 0) {
+    bcr_stage(xr, ldr, (size_t)cp * b, b, r0, nc, v);
+    __syncthreads();
+    bcr_blk_mv<T, true>(Lp0 + (size_t)x * bb, b, i0, v, nc, red, acc, T(-1));
+  }
+  if (cq >= 0) {
+    bcr_stage(xr, ldr, (size_t)cq * b, b, r0, nc, v);
+    __syncthreads();
+    bcr_blk_mv<T, false>(Lq0 + (size_t)x * bb, b, i0, v, nc, red, acc, T(-1));
+  }
+  if (tid < 32 * kBcrRC) {
+    const int il = tid / kBcrRC, cc = tid - il * kBcrRC, i = i0 + il;
+    if (i < b && cc < nc && (!active || active[r0 + cc])) w[(size_t)(r0 + cc) * ldw + (size_t)j * b + i] = acc[tid];
+  }
+}
+
 // Frc^s w_s on slot j of subdomain sd (w: coarse vector of one right-hand side; Frc: the nq
 // coupling columns of the class, the corners' and with the augmented coarse problem the faces').
 template <class T>
@@ -710,7 +850,39 @@ __global__ void k_local_apply(Geom g, MapsView m, const cx<T>* __restrict__ Op, 
     for (int r = 0; r < MR; ++r)
       if (r < R) Y[((size_t)sd * R + r) * nD + j] = acc[r];
   }
-  if (Tc) {
+  if (Tc && R * g.nq <= 16) {
+    // Tc[r][c] = sum_j Frc[j][c] x[r][j] for all (r, c) at once: per-thread partials over j, warp
+    // shuffles, one barrier, the warps' partials added in warp order
+    __shared__ cx<T> redf[16][16];
+    const int lane = tid & 31, warp = tid >> 5, nw = (nthr + 31) >> 5, nq = g.nq, nrc = R * nq;
+    const cx<T>* Fr = Frc + (size_t)q * nD * nq;
+    cx<T> p[16];
+#pragma unroll
+    for (int rc = 0; rc < 16; ++rc) p[rc] = czero<T>();
+    for (int j = tid; j < nD; j += nthr) {
+#pragma unroll
+      for (int rc = 0; rc < 16; ++rc)
+        if (rc < nrc) {
+          const int r = rc / nq, c = rc - r * nq;
+          cfma(p[rc], Fr[(size_t)j * nq + c], x[r * nD + j]);
+        }
+    }
+#pragma unroll
+    for (int rc = 0; rc < 16; ++rc)
+      if (rc < nrc)
+        for (int o = 16; o > 0; o >>= 1) p[rc] = cadd(p[rc], shfl_xor_cx(p[rc], o));
+    if (lane == 0)
+#pragma unroll
+      for (int rc = 0; rc < 16; ++rc)
+        if (rc < nrc) redf[warp][rc] = p[rc];
+    __syncthreads();
+    if (tid < nrc) {
+      cx<T> s = czero<T>();
+      for (int w = 0; w < nw; ++w) s = cadd(s, redf[w][tid]);
+      const int r = tid / nq, c = tid - r * nq;
+      Tc[((size_t)sd * R + r) * nq + c] = s;
+    }
+  } else if (Tc) {
     // Tc[r][c] = sum_j Frc[j][c] x[r][j]: per-thread partials over j, warp shuffles, then warps
     __shared__ cx<T> red[32];
     const int lane = tid & 31, warp = tid >> 5, nw = (nthr + 31) >> 5;
@@ -730,6 +902,192 @@ __global__ void k_local_apply(Geom g, MapsView m, const cx<T>* __restrict__ Op, 
         cx<T> s = czero<T>();
         for (int w = 0; w < nw; ++w) s = cadd(s, red[w]);
         Tc[((size_t)sd * R + r) * g.nq + c] = s;
+      }
+    }
+  }
+}
+
+// One right-hand side with the packed operator staged in shared memory.  The copies of Op (setup
+// data) are issued before waiting on the previous kernel.  Thread j walks two offsets into the
+// packed upper triangle: down column j (A[k][j], k < j, step nD - 1 - k) and along row j (A[j][k],
+// k >= j, step 1), one select per term, so that
+//   y_j = sum_{k<j} A[k][j] x_k + sum_{k>=j} A[j][k] x_k;
+// Tc = Frc^T x: each thread's nq products, warp shuffles, one barrier, warps added in order.
+template <class T, bool SCALE>
+__global__ void __launch_bounds__(128) k_local_apply_1(Geom g, MapsView m, const cx<T>* __restrict__ Op,
+                                                       const cx<T>* __restrict__ Frc, const cx<T>* __restrict__ lam,
+                                                       const int* __restrict__ active, cx<T>* Y, cx<T>* Tc,
+                                                       const double* __restrict__ vscale) {
+  extern __shared__ __align__(16) unsigned char smla[];
+  const int sd = blockIdx.x, nD = g.nD, tid = threadIdx.x, nthr = blockDim.x, md = g.maxdeg;
+  const int q = m.sd_cls[sd];
+  const int ld = (int)sym_ld(nD);
+  cx<T>* As = reinterpret_cast<cx<T>*>(smla);
+  cx<T>* x = As + ld;
+  {
+    const int n16 = (int)((long long)ld * sizeof(cx<T>) / 16);
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(Op + (size_t)q * ld);
+    unsigned char* dst = reinterpret_cast<unsigned char*>(As);
+    for (int i = tid; i < n16; i += nthr) cp_async16(dst + 16 * (size_t)i, src + 16 * (size_t)i);
+    cp_async_commit();
+  }
+  pdl_wait();
+  pdl_trigger();
+  const bool on = active[0] != 0;
+  for (int j = tid; j < nD; j += nthr) {
+    cx<T> v = czero<T>();
+    if (on) {
+      const int* refs = m.sd_lam + ((size_t)sd * nD + j) * md;
+      for (int k = 0; k < md; ++k) {
+        const int ref = refs[k];
+        if (ref > 0) v = cadd(v, lam[ref - 1]);
+        else if (ref < 0) v = csub(v, lam[-ref - 1]);
+      }
+      if (SCALE) v = cscale(v, (T)m.sd_minv[(size_t)sd * nD + j]);
+      if (vscale) v = cscale(v, (T)vscale[0]);
+    }
+    x[j] = v;
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  const int nq = Tc ? g.nq : 0;
+  cx<T> p[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) p[c] = czero<T>();
+  for (int j = tid; j < nD; j += nthr) {
+    cx<T> acc = czero<T>();
+    int oc = j;                        // A[k][j] for k < j
+    const int orow = sym_off(j, nD) - j;  // A[j][k] = As[orow + k] for k >= j
+#pragma unroll 4
+    for (int k = 0; k < nD; ++k) {
+      const int o = k < j ? oc : orow + k;
+      oc += nD - 1 - k;
+      cfma(acc, As[o], x[k]);
+    }
+    Y[(size_t)sd * nD + j] = acc;
+    if (nq) {
+      const cx<T>* Fr = Frc + ((size_t)q * nD + j) * nq;
+      const cx<T> xj = x[j];
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        if (c < nq) cfma(p[c], Fr[c], xj);
+    }
+  }
+  if (nq) {
+    __shared__ cx<T> red1[4][16];  // blocks of at most 128 threads
+    const int lane = tid & 31, warp = tid >> 5, nw = (nthr + 31) >> 5;
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+      if (c < nq)
+        for (int o = 16; o > 0; o >>= 1) p[c] = cadd(p[c], shfl_xor_cx(p[c], o));
+    if (lane == 0)
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        if (c < nq) red1[warp][c] = p[c];
+    __syncthreads();
+    if (tid < nq) {
+      cx<T> s = czero<T>();
+      for (int w = 0; w < nw; ++w) s = cadd(s, red1[w][tid]);
+      Tc[(size_t)sd * nq + tid] = s;
+    }
+  }
+}
+
+// The same apply for a group of subdomains that share their stored operators (one class): the CTA
+// unpacks Op[cls] into a full nD x nD array in shared memory and stages Frc[cls] (both written at
+// setup, so before waiting on the previous kernel), gathers x for every (member, right-hand side)
+// column of the group and forms Y = Op x and Tc = Frc^T x for all of them: each operator entry
+// read from L2 serves every column.  Thread (j, cc), j = tid mod TJ (TJ = nD rounded up to a warp),
+// takes the CPT consecutive columns cc CPT + s TC CPT; a warp shares cc, so x is read by broadcast
+// and Op[k][j] by consecutive j.  Shared memory: (nD^2 + kApplyGroup R nD + nD nq) entries.
+template <class T, bool SCALE, int CPT>
+__global__ void __launch_bounds__(256) k_local_apply_grp(Geom g, MapsView m, const cx<T>* __restrict__ Op,
+                                                         const cx<T>* __restrict__ Frc,
+                                                         const cx<T>* __restrict__ lam, int R,
+                                                         const int* __restrict__ active, cx<T>* Y, cx<T>* Tc,
+                                                         const double* __restrict__ vscale) {
+  extern __shared__ __align__(16) unsigned char smla[];
+  const int nD = g.nD, nq = g.nq, md = g.maxdeg, tid = threadIdx.x, nthr = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+  const int g0 = m.grp_ptr[blockIdx.x], ncol = (m.grp_ptr[blockIdx.x + 1] - g0) * R;
+  const int q = m.sd_cls[m.grp_sd[g0]];
+  cx<T>* As = reinterpret_cast<cx<T>*>(smla);   // As[k nD + j] = Op[j][k]
+  cx<T>* X = As + (size_t)nD * nD;               // X[c nD + j], column c = member R + r
+  cx<T>* Fs = X + (size_t)kApplyGroup * R * nD;  // Fs[j nq + c] = Frc[j][c]
+  {
+    // packed rows read with consecutive lanes, written to both triangles
+    const cx<T>* A = Op + (size_t)q * sym_ld(nD);
+    for (int i = warp; i < nD; i += nw) {
+      const cx<T>* row = A + sym_off(i, nD) - i;
+      for (int k = i + lane; k < nD; k += 32) {
+        const cx<T> a = row[k];
+        As[(size_t)k * nD + i] = a;
+        As[(size_t)i * nD + k] = a;
+      }
+    }
+    if (Tc) {
+      const cx<T>* F = Frc + (size_t)q * nD * nq;
+      for (int e = tid; e < nD * nq; e += nthr) Fs[e] = F[e];
+    }
+  }
+  pdl_wait();
+  pdl_trigger();
+  for (int e = tid; e < ncol * nD; e += nthr) {
+    const int c = e / nD, j = e - c * nD, mi = c / R, r = c - mi * R;
+    const int sd = m.grp_sd[g0 + mi];
+    cx<T> v = czero<T>();
+    if (active[r]) {
+      const int* refs = m.sd_lam + ((size_t)sd * nD + j) * md;
+      for (int k = 0; k < md; ++k) {
+        const int ref = refs[k];
+        if (ref > 0) v = cadd(v, lam[(size_t)r * g.nlam + ref - 1]);
+        else if (ref < 0) v = csub(v, lam[(size_t)r * g.nlam - ref - 1]);
+      }
+      if (SCALE) v = cscale(v, (T)m.sd_minv[(size_t)sd * nD + j]);
+      if (vscale) v = cscale(v, (T)vscale[r]);
+    }
+    X[e] = v;
+  }
+  __syncthreads();
+  const int TJ = (nD + 31) & ~31, TC = nthr / TJ, j = tid % TJ, cc = tid / TJ;
+  if (j < nD && cc < TC) {
+    for (int c0 = cc * CPT; c0 < ncol; c0 += TC * CPT) {
+      cx<T> acc[CPT];
+#pragma unroll
+      for (int i = 0; i < CPT; ++i) acc[i] = czero<T>();
+#pragma unroll 4
+      for (int k = 0; k < nD; ++k) {
+        const cx<T> a = As[(size_t)k * nD + j];
+#pragma unroll
+        for (int i = 0; i < CPT; ++i)
+          if (c0 + i < ncol) cfma(acc[i], a, X[(size_t)(c0 + i) * nD + k]);
+      }
+#pragma unroll
+      for (int i = 0; i < CPT; ++i)
+        if (c0 + i < ncol) {
+          const int c = c0 + i, mi = c / R, r = c - mi * R;
+          Y[((size_t)m.grp_sd[g0 + mi] * R + r) * nD + j] = acc[i];
+        }
+    }
+  }
+  if (Tc) {
+    // Tc[sd][r][c] = sum_j Frc[j][c] x[r][j]: L lanes per output, strided over j, xor shuffles
+    // within aligned groups of L lanes; every warp runs the same number of passes
+    const int nout = ncol * nq;
+    int L = 32;
+    while (L > 1 && nthr / L < nout) L >>= 1;
+    const int per = nthr / L, sub = tid % L, passes = (nout + per - 1) / per;
+    for (int p = 0; p < passes; ++p) {
+      const int o = p * per + tid / L;
+      cx<T> s = czero<T>();
+      if (o < nout) {
+        const int c = o / nq, cq = o - c * nq;
+        for (int jj = sub; jj < nD; jj += L) cfma(s, Fs[jj * nq + cq], X[(size_t)c * nD + jj]);
+      }
+      for (int off = L >> 1; off > 0; off >>= 1) s = cadd(s, shfl_xor_cx(s, off));
+      if (o < nout && sub == 0) {
+        const int c = o / nq, cq = o - c * nq, mi = c / R, r = c - mi * R;
+        Tc[((size_t)m.grp_sd[g0 + mi] * R + r) * nq + cq] = s;
       }
     }
   }

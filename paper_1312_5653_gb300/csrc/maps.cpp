@@ -108,6 +108,18 @@ std::string build_maps(int dim, const int* nel, const int* nsub, int local_mode,
     }
   }
   m->ncls = (int)m->cls_code.size();
+  // groups of subdomains that share their stored operators (class by class, increasing index)
+  {
+    std::vector<std::vector<int>> by(m->ncls);
+    for (int sd = 0; sd < g.nsd; ++sd) by[m->sd_cls[sd]].push_back(sd);
+    m->grp_sd.clear();
+    m->grp_ptr.assign(1, 0);
+    for (const auto& v : by)
+      for (size_t i = 0; i < v.size(); i += kApplyGroup) {
+        for (size_t k = i; k < v.size() && k < i + kApplyGroup; ++k) m->grp_sd.push_back(v[k]);
+        m->grp_ptr.push_back((int)m->grp_sd.size());
+      }
+  }
 
   // corners -> coarse unknowns
   m->sd_corner.assign((size_t)g.nsd * g.nc, -1);

@@ -27,6 +27,8 @@ struct HostMaps {
   std::vector<int> face_lam_ptr; // [nface + 1] CSR offsets of the multipliers of each face
   std::vector<int> face_lam;     // multipliers of each face, in increasing order
   std::vector<int> slot_faces;   // [nD] bit f set: slot lies on local face f = 2a + side
+  std::vector<int> grp_sd;       // [nsd] subdomains ordered by class
+  std::vector<int> grp_ptr;      // [ngrp + 1] groups of at most kApplyGroup subdomains of one class
   int ncls = 0;
 };
 
