@@ -493,7 +493,9 @@ class Engine : public EngineBase {
         ENG_CK(alloc(&D0_, nb0 * cxT));
         ENG_CK(alloc(&Lp0_, nb0 * cxT));
         ENG_CK(alloc(&Lq0_, nb0 * cxT));
-        op_bytes_ += 3 * (long long)nb0 * cxT;
+        ENG_CK(alloc(&LpT0_, nb0 * cxT));
+        ENG_CK(alloc(&LqT0_, nb0 * cxT));
+        op_bytes_ += 5 * (long long)nb0 * cxT;
         l0 = BcrLevel0<T>{D0_, Lp0_, Lq0_};
       }
       ldk_ = (ncr_ + 1) & ~1;  // even row stride of the explicit inverse (temporary)
@@ -503,6 +505,14 @@ class Engine : public EngineBase {
       op_bytes_ += (long long)ctile_count(nct_) * kCT * kCT * cxT;
       int crc = coarse_bcr<T>(cprov_, split_ ? &l0 : nullptr, Kinv_, ldk_, err_ + 2, st, msg, &launches);
       if (crc) return crc;
+      if (split_) {  // the blocks used transposed by the solve, stored transposed
+        const size_t nb0 = (size_t)nj0_ * cbb;
+        const int gt = (int)std::min<size_t>((nb0 + 255) / 256, 4096);
+        k_transpose_blocks<T><<<gt, 256, 0, st>>>(Lp0_, nj0_, g.cb, LpT0_);
+        ENG_LAUNCH();
+        k_transpose_blocks<T><<<gt, 256, 0, st>>>(Lq0_, nj0_, g.cb, LqT0_);
+        ENG_LAUNCH();
+      }
       // keep the upper 32 x 32 tiles of the symmetric inverse; the full matrix is released
       prof_start(KC_COARSE_INV, st);
       k_pack_ctiles<T><<<(int)std::min<long long>(ctile_count(nct_), 8 * nsm_), 256, 0, st>>>(Kinv_, ncr_, ldk_,
@@ -864,23 +874,25 @@ class Engine : public EngineBase {
     return SCHUR_OK;
   }
 
-  int coarse_apply(const cx<T>* gv, int R, const int* active, cx<T>* w, cudaStream_t st, std::string* msg) {
+  // w = K_cc^{-1} g with g = gv, or (split form only, gv null) assembled from the corner couplings Tcs
+  int coarse_apply(const cx<T>* gv, int R, const int* active, cx<T>* w, cudaStream_t st, std::string* msg,
+                   const cx<T>* Tcs = nullptr) {
     const long long ntile = ctile_count(nct_);
     prof_start(KC_COARSE_APPLY, st);
     if (split_) {
       // level-0 forward step, reduced inverse, level-0 backward step
       const int b = g_.cb, ns = (b + 31) / 32, nz = (R + kBcrRC - 1) / kBcrRC;
-      const size_t sm = (size_t)kBcrRC * (b + 288) * sizeof(cx<T>);
+      const size_t sm = (size_t)kBcrRC * (3 * (size_t)b + 256) * sizeof(cx<T>);
       ENG_CK(smem_attr((const void*)k_bcr_fwd0<T>, (int)sm));
       ENG_CK(smem_attr((const void*)k_bcr_bwd0<T>, (int)sm));
-      ENG_CK(launch_pdl(k_bcr_fwd0<T>, dim3(nr0_, ns, nz), dim3(256), sm, st, b, (const int*)bcr_tgt_,
-                        (const cx<T>*)Lp0_, (const cx<T>*)Lq0_, gv, g_.nco, cfr_, ncr_, R, active));
+      ENG_CK(launch_pdl(k_bcr_fwd0<T>, dim3(nr0_, ns, nz), dim3(256), sm, st, g_, (const int*)bcr_tgt_,
+                        (const cx<T>*)Lp0_, (const cx<T>*)LqT0_, gv, Tcs, cfr_, ncr_, R, active));
       ENG_CK(launch_pdl(k_coarse_tiles<T>, dim3((unsigned)((ntile + 3) / 4)), dim3(128), 0, st, Kt_, nct_, ncr_,
                         (const cx<T>*)cfr_, R, active, cpu_, cpv_));
       ENG_CK(launch_pdl(k_coarse_reduce<T>, dim3(nct_ * R), dim3(512), 0, st, cpu_, cpv_, nct_, ncr_, R, active, cxr_));
-      ENG_CK(launch_pdl(k_bcr_bwd0<T>, dim3(nj0_ + nr0_, ns, nz), dim3(256), sm, st, b, nj0_, (const int*)bcr_elim_,
-                        (const int*)bcr_rem_, (const cx<T>*)D0_, (const cx<T>*)Lp0_, (const cx<T>*)Lq0_, gv, g_.nco,
-                        (const cx<T>*)cxr_, ncr_, w, g_.nco, R, active));
+      ENG_CK(launch_pdl(k_bcr_bwd0<T>, dim3(nj0_ + nr0_, ns, nz), dim3(256), sm, st, g_, nj0_, (const int*)bcr_elim_,
+                        (const int*)bcr_rem_, (const cx<T>*)D0_, (const cx<T>*)LpT0_, (const cx<T>*)Lq0_, gv, Tcs,
+                        (const cx<T>*)cxr_, ncr_, w, R, active));
       prof_stop(KC_COARSE_APPLY, st);
       ENG_LAUNCH();
       ENG_LAUNCH();
@@ -1017,7 +1029,11 @@ class Engine : public EngineBase {
     const bool coarse = g_.nco > 0;
     int rc = local_apply(false, F_, v, R, active, coarse, st, msg);
     if (rc) return rc;
-    if (coarse) {
+    if (coarse && split_) {
+      // the level-0 steps of the coarse solve assemble g from the corner couplings themselves
+      rc = coarse_apply(nullptr, R, active, wc_, st, msg, Tc_);
+      if (rc) return rc;
+    } else if (coarse) {
       int tot = R * g_.nco;
       prof_start(KC_CORNER, st);
       ENG_CK(launch_pdl(k_corner_gather<T>, dim3((tot + 255) / 256), dim3(256), 0, st, g_, mv_, Tc_, R,
@@ -1167,7 +1183,8 @@ class Engine : public EngineBase {
   bool split_ = false;
   int ncr_ = 0, nj0_ = 0, nr0_ = 0;  // unknowns of the stored inverse; layers eliminated / kept at level 0
   int *bcr_tgt_ = nullptr, *bcr_elim_ = nullptr, *bcr_rem_ = nullptr;
-  cx<T>*D0_ = nullptr, *Lp0_ = nullptr, *Lq0_ = nullptr, *cfr_ = nullptr, *cxr_ = nullptr;
+  cx<T>*D0_ = nullptr, *Lp0_ = nullptr, *Lq0_ = nullptr, *LpT0_ = nullptr, *LqT0_ = nullptr, *cfr_ = nullptr,
+  *cxr_ = nullptr;
   cx<T>*cpu_ = nullptr, *cpv_ = nullptr;  // partial products of the packed coarse inverse
   cx<double>*Kcc_ = nullptr, *CA_ = nullptr, *CB_ = nullptr, *Dc_ = nullptr;
   int wsR_ = 0, wsM_ = 0;

@@ -626,135 +626,192 @@ __global__ void __launch_bounds__(512) k_coarse_reduce(const cx<T>* __restrict__
 //   forward:  f_t = g_t - Lp_jr g_jr - Lq_jl^T g_jl        (every surviving layer t, compact order)
 //   reduced:  x_r = K_r^{-1} f_r                            (packed tiles, k_coarse_tiles/reduce)
 //   backward: x_j = D_j^{-1} g_j - Lp_j^T x_p - Lq_j x_q    (every layer j eliminated at level 0)
-// CTA (layer, 32-row slice, kBcrRC right-hand sides); 256 threads = 32 rows x 8 k-groups.
+// The blocks used transposed are stored transposed, so every product is M v with M row-major.  CTA
+// (layer, 32-row slice, kBcrRC right-hand sides); 256 threads = 32 rows x 8 k-groups, thread
+// (il = tid / 8, kg = tid % 8) taking k = kg, kg + 8, ... (a warp reads four 64-byte row segments).
+// The operator entries of the first eight k-steps of every term are loaded before the vectors are
+// staged, so that their latencies overlap; the k-group partials are added in order.  g is either a
+// coarse vector or, with Tc set, assembled on the fly from the subdomains' corner couplings (the
+// per-iteration dual operator, without a separate corner gather).
 constexpr int kBcrRC = 4;
 
-// v[k][c] = src[(r0 + c) ld + off + k] for k < b, c < nc (zero past nc)
 template <class T>
-__device__ __forceinline__ void bcr_stage(const cx<T>* __restrict__ src, int ld, size_t off, int b, int r0, int nc,
-                                          cx<T>* v) {
-  for (int e = threadIdx.x; e < b * kBcrRC; e += blockDim.x) {
-    const int k = e / kBcrRC, c = e - k * kBcrRC;
-    v[e] = c < nc ? src[(size_t)(r0 + c) * ld + off + k] : czero<T>();
+struct BcrTerm {
+  const cx<T>* M;  // b x b row-major block, null: no term
+  int src;         // 0: the input g; 1: the reduced solution xr
+  int layer;       // layer of g, or compact layer of xr
+  bool neg;
+};
+
+// coarse right-hand side at corner cI: sum of the corner couplings of the subdomains that hold it
+template <class T>
+__device__ __forceinline__ cx<T> bcr_corner_sum(const Geom& g, const cx<T>* __restrict__ Tc, int R, int r, int cI) {
+  // corner coordinates (axis 0 fastest); the subdomain holding it as vertex `bits` (bit a set:
+  // high vertex) has coordinate C_a + 1 - bit_a
+  const int c0 = cI % g.ncg[0], c12 = cI / g.ncg[0];
+  const int c1 = g.dim == 3 ? c12 % g.ncg[1] : c12, c2 = g.dim == 3 ? c12 / g.ncg[1] : 0;
+  cx<T> sum = czero<T>();
+  for (int bits = 0; bits < (1 << g.dim); ++bits) {
+    const int s0 = c0 + 1 - (bits & 1), s1 = c1 + 1 - ((bits >> 1) & 1), s2 = g.dim == 3 ? c2 + 1 - ((bits >> 2) & 1) : 0;
+    const int sd = s0 + g.nsub[0] * (s1 + g.nsub[1] * s2);
+    sum = cadd(sum, Tc[((size_t)sd * R + r) * g.nq + bits]);
   }
+  return sum;
 }
 
-// acc[il][c] += alpha sum_k op(M)[i0 + il][k] v[k][c] for the rows i0 + il < b; op(M) = M (thread
-// il = tid / 8, kg = tid % 8: a warp reads four 64-byte row segments) or M^T (il = tid % 32,
-// kg = tid / 32: a warp reads one 256-byte column segment) of the b x b row-major block M.  The
-// eight k-group partials are added in order through shared memory; ends with a barrier.
-template <class T, bool TRANS>
-__device__ __forceinline__ void bcr_blk_mv(const cx<T>* __restrict__ M, int b, int i0, const cx<T>* v, int nc,
-                                           cx<T>* red, cx<T>* acc, T alpha) {
-  const int tid = threadIdx.x;
-  const int il = TRANS ? (tid & 31) : (tid >> 3), kg = TRANS ? (tid >> 5) : (tid & 7);
-  const int i = i0 + il;
+template <class T>
+__device__ __forceinline__ cx<T> bcr_g(const Geom& g, const cx<T>* __restrict__ gv, const cx<T>* __restrict__ Tc, int R,
+                                       int r, int cI) {
+  return Tc ? bcr_corner_sum(g, Tc, R, r, cI) : gv[(size_t)r * g.nco + cI];
+}
+
+// sum over the three terms of +-M_s v_s on rows i0 + il < b: threads < 32 kBcrRC return row
+// il = tid / kBcrRC, column c = tid % kBcrRC.  vs: 3 x b x kBcrRC staging, red: 8 x 32 x kBcrRC.
+template <class T>
+__device__ __forceinline__ cx<T> bcr_rows(const Geom& g, int b, int i0, const BcrTerm<T> (&tm)[3],
+                                          const cx<T>* __restrict__ gv, const cx<T>* __restrict__ Tc,
+                                          const cx<T>* __restrict__ xr, int ldr, int R, int r0, int nc, cx<T>* vs,
+                                          cx<T>* red) {
+  const int tid = threadIdx.x, il = tid >> 3, kg = tid & 7, i = i0 + il;
+  cx<T> mr[3][8];
+#pragma unroll
+  for (int s = 0; s < 3; ++s)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = kg + 8 * q;
+      mr[s][q] = (tm[s].M && i < b && k < b) ? tm[s].M[(size_t)i * b + k] : czero<T>();
+    }
+#pragma unroll
+  for (int s = 0; s < 3; ++s)
+    for (int e = tid; tm[s].M && e < b * kBcrRC; e += blockDim.x) {
+      const int k = e / kBcrRC, c = e - k * kBcrRC;
+      cx<T> v = czero<T>();
+      if (c < nc) {
+        const int r = r0 + c, cI = tm[s].layer * b + k;
+        v = tm[s].src ? xr[(size_t)r * ldr + cI] : bcr_g(g, gv, Tc, R, r, cI);
+      }
+      vs[((size_t)s * b + k) * kBcrRC + c] = v;
+    }
+  __syncthreads();
   cx<T> p[kBcrRC];
 #pragma unroll
   for (int c = 0; c < kBcrRC; ++c) p[c] = czero<T>();
-  if (i < b) {
-#pragma unroll 4
-    for (int k = kg; k < b; k += 8) {
-      const cx<T> m = TRANS ? M[(size_t)k * b + i] : M[(size_t)i * b + k];
+  for (int q0 = 0; q0 < (b + 7) / 8; q0 += 8) {
+    if (q0 > 0) {  // blocks wider than 64: the next eight k-steps
 #pragma unroll
-      for (int c = 0; c < kBcrRC; ++c)
-        if (c < nc) cfma(p[c], m, v[k * kBcrRC + c]);
+      for (int s = 0; s < 3; ++s)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int k = kg + 8 * (q0 + q);
+          mr[s][q] = (tm[s].M && i < b && k < b) ? tm[s].M[(size_t)i * b + k] : czero<T>();
+        }
     }
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+      if (tm[s].M) {
+        const cx<T>* v = vs + (size_t)s * b * kBcrRC;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int k = kg + 8 * (q0 + q);
+          if (k < b) {
+#pragma unroll
+            for (int c = 0; c < kBcrRC; ++c)
+              if (c < nc) {
+                if (tm[s].neg) cfms(p[c], mr[s][q], v[k * kBcrRC + c]);
+                else cfma(p[c], mr[s][q], v[k * kBcrRC + c]);
+              }
+          }
+        }
+      }
   }
 #pragma unroll
   for (int c = 0; c < kBcrRC; ++c) red[(kg * 32 + il) * kBcrRC + c] = p[c];
   __syncthreads();
+  cx<T> out = czero<T>();
   if (tid < 32 * kBcrRC) {
     const int rl = tid / kBcrRC, c = tid - rl * kBcrRC;
-    cx<T> s = czero<T>();
 #pragma unroll
-    for (int q = 0; q < 8; ++q) s = cadd(s, red[(q * 32 + rl) * kBcrRC + c]);
-    acc[tid] = cadd(acc[tid], cscale(s, alpha));
+    for (int q = 0; q < 8; ++q) out = cadd(out, red[(q * 32 + rl) * kBcrRC + c]);
   }
-  __syncthreads();
+  return out;
 }
 
 // forward step of level 0 into the reduced right-hand side fr ([R][ldr], compact layer order);
-// tgt[5 c..] = (t, jr, kr, jl, kl) of the c-th surviving layer
+// tgt[5 c..] = (t, jr, kr, jl, kl) of the c-th surviving layer; Lp0 = A_pj D_j^{-1},
+// LqT0 = (D_j^{-1} A_jq)^T
 template <class T>
-__global__ void __launch_bounds__(256) k_bcr_fwd0(int b, const int* __restrict__ tgt, const cx<T>* __restrict__ Lp0,
-                                                  const cx<T>* __restrict__ Lq0, const cx<T>* __restrict__ g, int ldg,
-                                                  cx<T>* fr, int ldr, int R, const int* __restrict__ active) {
-  pdl_wait();
-  pdl_trigger();
-  extern __shared__ __align__(16) unsigned char smb[];
-  cx<T>* v = reinterpret_cast<cx<T>*>(smb);  // b x kBcrRC
-  cx<T>* red = v + (size_t)b * kBcrRC;         // 8 x 32 x kBcrRC
-  cx<T>* acc = red + 256 * kBcrRC;             // 32 x kBcrRC
-  const int c = blockIdx.x, i0 = blockIdx.y * 32, r0 = blockIdx.z * kBcrRC, nc = min(kBcrRC, R - r0);
-  const int t = tgt[5 * c], jr = tgt[5 * c + 1], kr = tgt[5 * c + 2], jl = tgt[5 * c + 3], kl = tgt[5 * c + 4];
-  const size_t bb = (size_t)b * b;
-  const int tid = threadIdx.x;
-  if (tid < 32 * kBcrRC) {
-    const int il = tid / kBcrRC, cc = tid - il * kBcrRC, i = i0 + il;
-    acc[tid] = (i < b && cc < nc) ? g[(size_t)(r0 + cc) * ldg + (size_t)t * b + i] : czero<T>();
-  }
-  if (kr >= 0) {
-    bcr_stage(g, ldg, (size_t)jr * b, b, r0, nc, v);
-    __syncthreads();
-    bcr_blk_mv<T, false>(Lp0 + (size_t)kr * bb, b, i0, v, nc, red, acc, T(-1));
-  }
-  if (kl >= 0) {
-    bcr_stage(g, ldg, (size_t)jl * b, b, r0, nc, v);
-    __syncthreads();
-    bcr_blk_mv<T, true>(Lq0 + (size_t)kl * bb, b, i0, v, nc, red, acc, T(-1));
-  }
-  __syncthreads();
-  if (tid < 32 * kBcrRC) {
-    const int il = tid / kBcrRC, cc = tid - il * kBcrRC, i = i0 + il;
-    if (i < b && cc < nc && (!active || active[r0 + cc])) fr[(size_t)(r0 + cc) * ldr + (size_t)c * b + i] = acc[tid];
-  }
-}
-
-// backward step of level 0: blocks x < nj solve the eliminated layers (elim[3 x..] = (j, cp, cq)),
-// blocks nj + c copy the reduced solution of the c-th surviving layer rem[c] into w ([R][ldw])
-template <class T>
-__global__ void __launch_bounds__(256) k_bcr_bwd0(int b, int nj, const int* __restrict__ elim, const int* __restrict__ rem,
-                                                  const cx<T>* __restrict__ D0, const cx<T>* __restrict__ Lp0,
-                                                  const cx<T>* __restrict__ Lq0, const cx<T>* __restrict__ g, int ldg,
-                                                  const cx<T>* __restrict__ xr, int ldr, cx<T>* w, int ldw, int R,
+__global__ void __launch_bounds__(256) k_bcr_fwd0(Geom g, const int* __restrict__ tgt, const cx<T>* __restrict__ Lp0,
+                                                  const cx<T>* __restrict__ LqT0, const cx<T>* __restrict__ gv,
+                                                  const cx<T>* __restrict__ Tc, cx<T>* fr, int ldr, int R,
                                                   const int* __restrict__ active) {
   pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smb[];
-  cx<T>* v = reinterpret_cast<cx<T>*>(smb);
-  cx<T>* red = v + (size_t)b * kBcrRC;
-  cx<T>* acc = red + 256 * kBcrRC;
+  const int b = g.cb;
+  cx<T>* vs = reinterpret_cast<cx<T>*>(smb);  // 3 x b x kBcrRC
+  cx<T>* red = vs + 3 * (size_t)b * kBcrRC;    // 8 x 32 x kBcrRC
+  const int c = blockIdx.x, i0 = blockIdx.y * 32, r0 = blockIdx.z * kBcrRC, nc = min(kBcrRC, R - r0);
+  const int t = tgt[5 * c], jr = tgt[5 * c + 1], kr = tgt[5 * c + 2], jl = tgt[5 * c + 3], kl = tgt[5 * c + 4];
+  const size_t bb = (size_t)b * b;
+  const BcrTerm<T> tm[3] = {{kr >= 0 ? Lp0 + (size_t)kr * bb : nullptr, 0, jr, true},
+                            {kl >= 0 ? LqT0 + (size_t)kl * bb : nullptr, 0, jl, true},
+                            {nullptr, 0, 0, false}};
+  const cx<T> y = bcr_rows(g, b, i0, tm, gv, Tc, (const cx<T>*)nullptr, 0, R, r0, nc, vs, red);
+  const int tid = threadIdx.x;
+  if (tid < 32 * kBcrRC) {
+    const int il = tid / kBcrRC, cc = tid - il * kBcrRC, i = i0 + il, r = r0 + cc;
+    if (i < b && cc < nc && (!active || active[r]))
+      fr[(size_t)r * ldr + (size_t)c * b + i] = cadd(bcr_g(g, gv, Tc, R, r, t * b + i), y);
+  }
+}
+
+// backward step of level 0: blocks x < nj solve the eliminated layers (elim[3 x..] = (j, cp, cq)),
+// blocks nj + c copy the reduced solution of the c-th surviving layer rem[c] into w ([R][n_c]);
+// D0 = D_j^{-1}, LpT0 = (A_pj D_j^{-1})^T, Lq0 = D_j^{-1} A_jq
+template <class T>
+__global__ void __launch_bounds__(256) k_bcr_bwd0(Geom g, int nj, const int* __restrict__ elim, const int* __restrict__ rem,
+                                                  const cx<T>* __restrict__ D0, const cx<T>* __restrict__ LpT0,
+                                                  const cx<T>* __restrict__ Lq0, const cx<T>* __restrict__ gv,
+                                                  const cx<T>* __restrict__ Tc, const cx<T>* __restrict__ xr, int ldr,
+                                                  cx<T>* w, int R, const int* __restrict__ active) {
+  pdl_wait();
+  pdl_trigger();
+  extern __shared__ __align__(16) unsigned char smb[];
+  const int b = g.cb;
+  cx<T>* vs = reinterpret_cast<cx<T>*>(smb);
+  cx<T>* red = vs + 3 * (size_t)b * kBcrRC;
   const int x = blockIdx.x, i0 = blockIdx.y * 32, r0 = blockIdx.z * kBcrRC, nc = min(kBcrRC, R - r0);
   const int tid = threadIdx.x;
   if (x >= nj) {
     const int cidx = x - nj, t = rem[cidx];
     if (tid < 32 * kBcrRC) {
-      const int il = tid / kBcrRC, cc = tid - il * kBcrRC, i = i0 + il;
-      if (i < b && cc < nc && (!active || active[r0 + cc]))
-        w[(size_t)(r0 + cc) * ldw + (size_t)t * b + i] = xr[(size_t)(r0 + cc) * ldr + (size_t)cidx * b + i];
+      const int il = tid / kBcrRC, cc = tid - il * kBcrRC, i = i0 + il, r = r0 + cc;
+      if (i < b && cc < nc && (!active || active[r]))
+        w[(size_t)r * g.nco + (size_t)t * b + i] = xr[(size_t)r * ldr + (size_t)cidx * b + i];
     }
     return;
   }
   const int j = elim[3 * x], cp = elim[3 * x + 1], cq = elim[3 * x + 2];
   const size_t bb = (size_t)b * b;
-  if (tid < 32 * kBcrRC) acc[tid] = czero<T>();
-  bcr_stage(g, ldg, (size_t)j * b, b, r0, nc, v);
-  __syncthreads();
-  bcr_blk_mv<T, false>(D0 + (size_t)x * bb, b, i0, v, nc, red, acc, T(1));
-  if (cp >= 0) {
-    bcr_stage(xr, ldr, (size_t)cp * b, b, r0, nc, v);
-    __syncthreads();
-    bcr_blk_mv<T, true>(Lp0 + (size_t)x * bb, b, i0, v, nc, red, acc, T(-1));
-  }
-  if (cq >= 0) {
-    bcr_stage(xr, ldr, (size_t)cq * b, b, r0, nc, v);
-    __syncthreads();
-    bcr_blk_mv<T, false>(Lq0 + (size_t)x * bb, b, i0, v, nc, red, acc, T(-1));
-  }
+  const BcrTerm<T> tm[3] = {{D0 + (size_t)x * bb, 0, j, false},
+                            {cp >= 0 ? LpT0 + (size_t)x * bb : nullptr, 1, cp, true},
+                            {cq >= 0 ? Lq0 + (size_t)x * bb : nullptr, 1, cq, true}};
+  const cx<T> y = bcr_rows(g, b, i0, tm, gv, Tc, xr, ldr, R, r0, nc, vs, red);
   if (tid < 32 * kBcrRC) {
-    const int il = tid / kBcrRC, cc = tid - il * kBcrRC, i = i0 + il;
-    if (i < b && cc < nc && (!active || active[r0 + cc])) w[(size_t)(r0 + cc) * ldw + (size_t)j * b + i] = acc[tid];
+    const int il = tid / kBcrRC, cc = tid - il * kBcrRC, i = i0 + il, r = r0 + cc;
+    if (i < b && cc < nc && (!active || active[r])) w[(size_t)r * g.nco + (size_t)j * b + i] = y;
+  }
+}
+
+// dst block k = (src block k)^T for count b x b row-major blocks
+template <class T>
+__global__ void k_transpose_blocks(const cx<T>* __restrict__ src, int count, int b, cx<T>* dst) {
+  const size_t bb = (size_t)b * b;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)count * bb;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t k = e / bb;
+    const int r = (int)(e - k * bb), i = r / b, jx = r - i * b;
+    dst[k * bb + (size_t)jx * b + i] = src[e];
   }
 }
 
