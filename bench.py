@@ -242,9 +242,15 @@ def algorithmic(cat, info, prec_bytes):
         byts = nsd * packed * cb + nlam * cb + nsd * nD * cb
         return "hbm", byts
     if cat == "coarse_apply":
-        # upper 32 x 32 tiles of the symmetric coarse inverse, input and output vectors
-        nct = (nco + 31) // 32
-        return "hbm", nct * (nct + 1) // 2 * 1024 * cb + 2 * nco * cb
+        # level 0 of the reduction applied around the stored inverse of the reduced matrix: the
+        # level-0 blocks (forward: A_pj D_j^-1 and (D_j^-1 A_jq)^T per neighbour; backward: D_j^-1
+        # and both couplings), the upper 32 x 32 tiles of the reduced inverse, the corner couplings
+        # of every subdomain (read by both steps), the reduced vectors and the output
+        lev0 = bcr_tasks(cL)[0]
+        nblk = sum(p + q for p, q in lev0) * 2 + len(lev0)
+        nr = cb_ * (cL - len(lev0))
+        nct = (nr + 31) // 32
+        return "hbm", (nblk * cb_ * cb_ + nct * (nct + 1) // 2 * 1024 + 2 * nsd * nc + 2 * nr + nco) * cb
     if cat == "scatter":
         return "hbm", nlam * cb + 2 * nlam * cb
     if cat == "form":
@@ -254,9 +260,11 @@ def algorithmic(cat, info, prec_bytes):
         # per layer: explicit inverse of the b x b pivot block and the Schur update
         return "alu", nsd * b * (b ** 3 + 2 * 3 * b * b) * cmac
     if cat == "coarse_inverse":
-        # cyclic-reduction solve with the n_c columns of the identity: b x b by b x n_c products
-        ntask = sum(1 + p + q for lev in bcr_tasks(cL) for p, q in lev) * 2
-        return "alu", ntask * cb_ * cb_ * nco * cmac
+        # cyclic-reduction solve of the reduced matrix (layers surviving level 0) with its n_r
+        # identity columns: b x b by b x n_r products
+        Lr = cL - len(bcr_tasks(cL)[0])
+        ntask = sum(1 + p + q for lev in bcr_tasks(Lr) for p, q in lev) * 2
+        return "alu", ntask * cb_ * cb_ * (cb_ * Lr) * cmac
     if cat == "coarse_setup":
         # FP64 reduction: level 0 banded (2D: tridiagonal inverses and 3-term products), the
         # other levels dense (Gauss-Jordan b^3 plus the products Lp, Lq, D_p, A_pq, D_q)
@@ -274,13 +282,13 @@ CATEGORIES = ["factor", "form", "coarse_setup", "local_rhs", "apply_F", "apply_S
               "coarse_inverse", "interior"]
 # profiling categories that hold exactly one kernel on the 2D mixed workload (16^2-element
 # subdomains: layer size 17, 60 interface slots, one right-hand side)
-KERNEL_OF = {"form": "k_form_rr_cols<float, 17>", "apply_F": "k_local_apply<float, 0, 1>",
-             "apply_S": "k_local_apply<float, 1, 1>", "assemble_z": "k_assemble_z<float>"}
+KERNEL_OF = {"form": "k_form_rr_cols<float, 17>", "apply_F": "k_local_apply_1<float, 0>",
+             "apply_S": "k_local_apply_1<float, 1>", "assemble_z": "k_assemble_z<float>"}
 # source files whose contents determine each kernel (a recorded DRAM traffic figure is used only
 # while their hash is the one recorded with it)
 KERNEL_SOURCES = {"k_form_rr_cols<float, 17>": ["warp.cuh", "layered.cuh", "common.cuh"],
-                  "k_local_apply<float, 0, 1>": ["kernels.cuh", "common.cuh"],
-                  "k_local_apply<float, 1, 1>": ["kernels.cuh", "common.cuh"],
+                  "k_local_apply_1<float, 0>": ["kernels.cuh", "common.cuh"],
+                  "k_local_apply_1<float, 1>": ["kernels.cuh", "common.cuh"],
                   "k_assemble_z<float>": ["kernels.cuh", "common.cuh"]}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic_2d_1024_mixed.md")
 

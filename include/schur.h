@@ -308,6 +308,9 @@ const char* schur_last_error(void);
  *         4: the coarse inverse actually applied                     (n_coarse x n_coarse)
  *         5: the coupling columns [Frc | F Q] of the augmented coarse problem
  *            (n_delta x (2^d + 2d); without augmentation Frc alone)
+ *         6: the layer pivot inverses D_K^{-1} of the block LDL^T factorisation of the class's
+ *            remainder matrix on the full local grid of (s+1)^d nodes (layers along the last axis,
+ *            L = s+1 blocks of b = (s+1)^(d-1) nodes; removed nodes are identity rows)  (L x b x b)
  * Row-major.  `cap` = capacity of out in complex entries.  Synchronises. */
 int schur_debug_operator(schur_ctx* ctx, int which, int cls, double* out_host, long long cap);
 

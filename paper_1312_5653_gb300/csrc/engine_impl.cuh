@@ -652,7 +652,7 @@ class Engine : public EngineBase {
       return 0;
     };
     int rc = 0;
-    if ((which <= 2 || which == 5) && (cls < 0 || cls >= ncls_)) return SCHUR_EINVAL;
+    if ((which <= 2 || which == 5 || which == 6) && (cls < 0 || cls >= ncls_)) return SCHUR_EINVAL;
     auto unpack = [&]() {  // packed upper triangle -> full symmetric matrix
       std::vector<cx<double>> full((size_t)g.nD * g.nD);
       for (int i = 0; i < g.nD; ++i)
@@ -734,6 +734,10 @@ class Engine : public EngineBase {
               }
             }
       }
+    } else if (which == 6) {
+      // layer pivot inverses D_K^{-1} of the remainder factorisation (L blocks of b x b)
+      const size_t blk = (size_t)g.lL * g.lb * g.lb;
+      rc = fetch(Dinv_ + (size_t)cls * blk, blk);
     } else {
       return SCHUR_EINVAL;
     }

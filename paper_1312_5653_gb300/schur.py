@@ -360,7 +360,9 @@ class Solver:
         import numpy as np
         info = self.info()
         nD, nc, nco = info["n_delta"], 1 << self.dim, info["n_coarse"]
-        shape = {0: (nD, nD), 1: (nD, nc), 2: (nD, nD), 3: (nco, nco), 4: (nco, nco)}[which]
+        s1 = [self.nel // n for n in (self.opts.nsub[a] for a in range(self.dim))][0] + 1
+        shape = {0: (nD, nD), 1: (nD, nc), 2: (nD, nD), 3: (nco, nco), 4: (nco, nco),
+                 6: (s1, s1 ** (self.dim - 1), s1 ** (self.dim - 1))}[which]
         out = np.zeros(shape + (2,), dtype=np.float64)
         _check(self.lib.schur_debug_operator(self.ctx, which, cls, out.ctypes.data_as(ctypes.c_void_p),
                                              out.size // 2), "schur_debug_operator")

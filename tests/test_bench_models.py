@@ -39,7 +39,8 @@ def test_tc_form_executed_flops_by_enumeration(N, P):
 
 def test_apply_models_count_packed_storage():
     """The HBM models of the local and coarse applies count the stored (packed) operators: the upper
-    triangle of each symmetric nD x nD block and the upper 32 x 32 tiles of the coarse inverse."""
+    triangle of each symmetric nD x nD block, and for the coarse solve the level-0 blocks of the
+    reduction and the upper 32 x 32 tiles of the reduced inverse."""
     info = S.schur_partition(2, 1024, 64)
     nsd, nD, nlam, nco = info["n_sub"], info["n_delta"], info["n_lambda"], info["n_coarse"]
     assert (nsd, nD, nco) == (4096, 60, 63 * 63)
@@ -48,8 +49,11 @@ def test_apply_models_count_packed_storage():
     assert f == nsd * (1830 + 60 * 4) * cb + nlam * cb + nsd * 64 * cb
     _, sb = bench.algorithmic("apply_S", info, 4)
     assert sb == nsd * 1830 * cb + nlam * cb + nsd * 60 * cb
+    # coarse solve: 63 layers, level 0 eliminates the 32 even layers (two without an outer
+    # neighbour): 156 blocks of 63 x 63; the reduced matrix on 31 layers (1953 unknowns) as
+    # 62 * 63 / 2 tiles; corner couplings read twice, two reduced vectors and the output
     _, c = bench.algorithmic("coarse_apply", info, 4)
-    assert c == (125 * 126 // 2) * 1024 * cb + 2 * nco * cb
+    assert c == (156 * 63 * 63 + 62 * 63 // 2 * 1024 + 2 * nsd * 4 + 2 * 1953 + nco) * cb
 
 
 def test_recorded_traffic_follows_the_kernel_sources(tmp_path):
