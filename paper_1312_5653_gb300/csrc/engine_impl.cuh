@@ -43,11 +43,11 @@ namespace schur {
 template <class T, int B>
 static cudaError_t launch_form_cols(const StencilProv<T>& P, const Geom& g, const MapsView& mv, const cx<T>* Dinv,
                                     int ncls, cx<T>* F, cx<T>* Frc, cx<double>* Kcc, cx<T>* Ews, int grid, int ldE,
-                                    cudaStream_t st) {
+                                    int col1, cudaStream_t st) {
   const size_t smem = form_cols_smem<T, B>(g.lb, g.lL);
   cudaError_t e = smem_attr((const void*)k_form_rr_cols<T, B>, (int)smem);
   if (e != cudaSuccess) return e;
-  k_form_rr_cols<T, B><<<grid, ldE, smem, st>>>(P, g, mv, Dinv, ncls, F, Frc, Kcc, Ews, ldE);
+  k_form_rr_cols<T, B><<<grid, ldE, smem, st>>>(P, g, mv, Dinv, ncls, F, Frc, Kcc, Ews, ldE, col1);
   return cudaGetLastError();
 }
 
@@ -122,6 +122,7 @@ class Engine : public EngineBase {
     if (side_) cudaStreamDestroy(side_);
     if (fork_) cudaEventDestroy(fork_);
     if (join_) cudaEventDestroy(join_);
+    if (corner_ev_) cudaEventDestroy(corner_ev_);
   }
 
   long long op_bytes() const override { return op_bytes_; }
@@ -189,7 +190,11 @@ class Engine : public EngineBase {
     cx<T>* Dii = nullptr;
     ENG_CK(alloc(&Dii, (size_t)g.iL * ibb * cxT));
     if (!side_) {
-      ENG_CK(cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking));
+      // the second stream carries latency-bound branches (the interior factor and S, the coarse
+      // problem): its blocks are scheduled before those of the main stream
+      int lo_pri = 0, hi_pri = 0;
+      ENG_CK(cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri));
+      ENG_CK(cudaStreamCreateWithPriority(&side_, cudaStreamNonBlocking, hi_pri));
       ENG_CK(cudaEventCreateWithFlags(&fork_, cudaEventDisableTiming));
       ENG_CK(cudaEventCreateWithFlags(&join_, cudaEventDisableTiming));
     }
@@ -313,8 +318,10 @@ class Engine : public EngineBase {
       ENG_LAUNCH();
     }
     // ---- local operators
+    bool early_coarse = false;
     {
       cx<T>* Xws = nullptr;
+      cx<T>* Xc = nullptr;  // scratch of the early corner columns
       bool formed = false;
       if constexpr (sizeof(T) == 4) {
         const int ncol = g.nD + g.nc, ldE = ((ncol + 31) / 32) * 32;
@@ -350,14 +357,38 @@ class Engine : public EngineBase {
           formed = true;
         } else if (g.dim == 2 && g.lb <= 32 && ldE <= 128) {
           const int Bp = g.lb == 9 ? 9 : g.lb == 17 ? 17 : ((g.lb + 7) / 8) * 8;
+          // With the corner coarse problem (not augmented) the corner columns (Frc, Kcc) are formed
+          // first, four per warp, so that the FP64 coarse factorisation and inverse run on the
+          // second (higher-priority) stream while one CTA per class forms F
+          early_coarse = !aug && g.ncor > 0 && g.nc > 0 && g.nD > 0;
+          int col1 = g.nD + g.nc;
+          if (early_coarse) {
+            constexpr int CW = 4;
+            const int chunk0 = g.nD / CW, nrun = (g.nD + g.nc + CW - 1) / CW - chunk0, wpb = 4;
+            const int gridw = std::max(1, std::min((ncls_ * nrun + wpb - 1) / wpb, 4 * nsm_));
+            const size_t smemw = wpb * warp_solve_smem<T>(g.lb);
+            ENG_CK(alloc(&Xc, (size_t)gridw * wpb * g.nl * CW * cxT));
+            ENG_CK(smem_attr((const void*)k_form_rr_warp<T, CW>, (int)smemw));
+            prof_start(KC_FORM, st);
+            k_form_rr_warp<T, CW><<<gridw, 32 * wpb, smemw, st>>>(prr_, g, mv_, Dinv_, ncls_, F_, FrcF, Kcc_, Xc, chunk0,
+                                                                 nrun);
+            prof_stop(KC_FORM, st);
+            ENG_LAUNCH();
+            if (!corner_ev_) ENG_CK(cudaEventCreateWithFlags(&corner_ev_, cudaEventDisableTiming));
+            ENG_CK(cudaEventRecord(corner_ev_, st));
+            col1 = g.nD;
+          }
+          // one CTA per class when the coarse setup runs beside it, so that its blocks retire often
+          // and the second stream's blocks are scheduled in between; else persistent CTAs
           const size_t per_cta = (size_t)g.lL * Bp * ldE * cxT;
-          int grid = std::min(ncls_, 8 * nsm_);
-          grid = std::max(1, (int)std::min<size_t>((size_t)grid, ((size_t)256 << 20) / per_cta));
+          int grid = early_coarse ? ncls_ : std::min(ncls_, 8 * nsm_);
+          const size_t cap = early_coarse ? ((size_t)1 << 30) : ((size_t)256 << 20);
+          grid = std::max(1, (int)std::min<size_t>((size_t)grid, cap / per_cta));
           ENG_CK(alloc(&Xws, (size_t)grid * per_cta));
           prof_start(KC_FORM, st);
           cudaError_t fe = cudaErrorInvalidValue;
 #define FC_CASE(BV) \
-  case BV: fe = launch_form_cols<T, BV>(prr_, g, mv_, Dinv_, ncls_, F_, FrcF, Kcc_, Xws, grid, ldE, st); break
+  case BV: fe = launch_form_cols<T, BV>(prr_, g, mv_, Dinv_, ncls_, F_, FrcF, Kcc_, Xws, grid, ldE, col1, st); break
           switch (Bp) {
             FC_CASE(8);
             FC_CASE(9);
@@ -384,7 +415,7 @@ class Engine : public EngineBase {
         ENG_CK(alloc(&Xws, (size_t)grid * wpb * g.nl * CW * cxT));
         ENG_CK(smem_attr((const void*)k_form_rr_warp<T, CW>, (int)smem));
         prof_start(KC_FORM, st);
-        k_form_rr_warp<T, CW><<<grid, 32 * wpb, smem, st>>>(prr_, g, mv_, Dinv_, ncls_, F_, FrcF, Kcc_, Xws);
+        k_form_rr_warp<T, CW><<<grid, 32 * wpb, smem, st>>>(prr_, g, mv_, Dinv_, ncls_, F_, FrcF, Kcc_, Xws, 0, nchunk);
         prof_stop(KC_FORM, st);
         ENG_LAUNCH();
       } else {
@@ -398,11 +429,21 @@ class Engine : public EngineBase {
         prof_stop(KC_FORM, st);
         ENG_LAUNCH();
       }
-      // join the interior branch (S) before the buffers are released
+      if (early_coarse) {
+        // coarse factorisation and inverse on the second stream once the corner columns are formed
+        // (its allocations are ordered on that stream; joined below)
+        ENG_CK(cudaStreamWaitEvent(side_, corner_ev_, 0));
+        ast_ = side_;
+        const int crc = coarse_setup_bcr(side_, msg);
+        ast_ = st;
+        if (crc) return crc;
+      }
+      // join the interior branch (S) and the coarse setup before the buffers are released
       ENG_CK(cudaEventRecord(join_, side_));
       ENG_CK(cudaStreamWaitEvent(st, join_, 0));
       ENG_CK(cudaStreamSynchronize(st));
       if (Xws) free_one(Xws);
+      if (Xc) free_one(Xc);
       if (Gc) free_one(Gc);
       if (Hc) free_one(Hc);
       free_one(Xi);
@@ -448,79 +489,9 @@ class Engine : public EngineBase {
       free_one(Kd);
       free_one(Kq);
       free_one(Frc0);
-    } else if (g.ncor > 0) {
-      // ---- coarse problem (FP64 factorisation, inverse stored in T)
-      const int nt = nbr_count(g.dim), cbb = g.cb * g.cb;
-      ENG_CK(alloc(&CA_, (size_t)g.cL * g.cb * nt * sizeof(cx<double>)));
-      ENG_CK(alloc(&CB_, (size_t)std::max(1, g.cL) * g.cb * nt * sizeof(cx<double>)));
-      ENG_CK(cudaMemsetAsync(CA_, 0, (size_t)g.cL * g.cb * nt * sizeof(cx<double>), st));
-      ENG_CK(cudaMemsetAsync(CB_, 0, (size_t)std::max(1, g.cL) * g.cb * nt * sizeof(cx<double>), st));
-      const int noff = g.dim == 2 ? 9 : 27;
-      long long tot = (long long)g.ncor * noff;
-      prof_start(KC_COARSE_SETUP, st);
-      k_coarse_assemble<<<(int)((tot + 255) / 256), 256, 0, st>>>(g, Kcc_, dm_->sd_cls, CA_, CB_);
-      prof_stop(KC_COARSE_SETUP, st);
-      ENG_LAUNCH();
-      cprov_.ly.dim = g.dim;
-      for (int a = 0; a < 3; ++a) cprov_.ly.ext[a] = a < g.dim ? g.ncg[a] : 1;
-      cprov_.ly.b = g.cb;
-      cprov_.ly.L = g.cL;
-      cprov_.CA = CA_;
-      cprov_.CB = CB_;
-      // FP64 block cyclic reduction over the coarse layers.  With at least two layers, level 0 is
-      // kept as blocks (applied by k_bcr_fwd0 / k_bcr_bwd0 around each coarse solve) and the
-      // explicit inverse in precision T covers only the reduced matrix on the surviving layers
-      split_ = g.cL >= 2;
-      BcrLevel0<T> l0{nullptr, nullptr, nullptr};
-      ncr_ = g.ncor;
-      if (split_) {
-        std::vector<int> tgt, elim, rem;
-        bcr_level0_maps(g.cL, &tgt, &elim, &rem);
-        nj0_ = (int)elim.size() / 3;
-        nr0_ = (int)rem.size();
-        ncr_ = g.cb * nr0_;
-        auto up = [&](int** d, const std::vector<int>& h) -> cudaError_t {
-          cudaError_t e = alloc(d, std::max<size_t>(h.size(), 1) * sizeof(int));
-          if (e == cudaSuccess && !h.empty())
-            e = cudaMemcpyAsync(*d, h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice, st);
-          return e;
-        };
-        ENG_CK(up(&bcr_tgt_, tgt));
-        ENG_CK(up(&bcr_elim_, elim));
-        ENG_CK(up(&bcr_rem_, rem));
-        ENG_CK(cudaStreamSynchronize(st));  // the host tables leave scope
-        const size_t nb0 = (size_t)nj0_ * cbb;
-        ENG_CK(alloc(&D0_, nb0 * cxT));
-        ENG_CK(alloc(&Lp0_, nb0 * cxT));
-        ENG_CK(alloc(&Lq0_, nb0 * cxT));
-        ENG_CK(alloc(&LpT0_, nb0 * cxT));
-        ENG_CK(alloc(&LqT0_, nb0 * cxT));
-        op_bytes_ += 5 * (long long)nb0 * cxT;
-        l0 = BcrLevel0<T>{D0_, Lp0_, Lq0_};
-      }
-      ldk_ = (ncr_ + 1) & ~1;  // even row stride of the explicit inverse (temporary)
-      nct_ = (ncr_ + kCT - 1) / kCT;
-      ENG_CK(alloc(&Kinv_, (size_t)ncr_ * ldk_ * cxT));
-      ENG_CK(alloc(&Kt_, (size_t)ctile_count(nct_) * kCT * kCT * cxT));
-      op_bytes_ += (long long)ctile_count(nct_) * kCT * kCT * cxT;
-      int crc = coarse_bcr<T>(cprov_, split_ ? &l0 : nullptr, Kinv_, ldk_, err_ + 2, st, msg, &launches);
+    } else if (g.ncor > 0 && !early_coarse) {
+      const int crc = coarse_setup_bcr(st, msg);
       if (crc) return crc;
-      if (split_) {  // the blocks used transposed by the solve, stored transposed
-        const size_t nb0 = (size_t)nj0_ * cbb;
-        const int gt = (int)std::min<size_t>((nb0 + 255) / 256, 4096);
-        k_transpose_blocks<T><<<gt, 256, 0, st>>>(Lp0_, nj0_, g.cb, LpT0_);
-        ENG_LAUNCH();
-        k_transpose_blocks<T><<<gt, 256, 0, st>>>(Lq0_, nj0_, g.cb, LqT0_);
-        ENG_LAUNCH();
-      }
-      // keep the upper 32 x 32 tiles of the symmetric inverse; the full matrix is released
-      prof_start(KC_COARSE_INV, st);
-      k_pack_ctiles<T><<<(int)std::min<long long>(ctile_count(nct_), 8 * nsm_), 256, 0, st>>>(Kinv_, ncr_, ldk_,
-                                                                                            nct_, Kt_);
-      prof_stop(KC_COARSE_INV, st);
-      ENG_LAUNCH();
-      free_one(Kinv_);
-      Kinv_ = nullptr;
     }
     ENG_CK(cudaStreamSynchronize(st));
     int herr[4];
@@ -533,6 +504,86 @@ class Engine : public EngineBase {
       if (msg) *msg = "tensor-core local operator formation: completion wait timed out";
       return SCHUR_ETIMEOUT;
     }
+    return SCHUR_OK;
+  }
+
+  // Corner coarse problem: FP64 block cyclic reduction and the stored inverse in precision T, all
+  // work on stream cs (allocations follow ast_).
+  int coarse_setup_bcr(cudaStream_t cs, std::string* msg) {
+    const Geom& g = g_;
+    const size_t cxT = sizeof(cx<T>);
+    // ---- coarse problem (FP64 factorisation, inverse stored in T)
+    const int nt = nbr_count(g.dim), cbb = g.cb * g.cb;
+    ENG_CK(alloc(&CA_, (size_t)g.cL * g.cb * nt * sizeof(cx<double>)));
+    ENG_CK(alloc(&CB_, (size_t)std::max(1, g.cL) * g.cb * nt * sizeof(cx<double>)));
+    ENG_CK(cudaMemsetAsync(CA_, 0, (size_t)g.cL * g.cb * nt * sizeof(cx<double>), cs));
+    ENG_CK(cudaMemsetAsync(CB_, 0, (size_t)std::max(1, g.cL) * g.cb * nt * sizeof(cx<double>), cs));
+    const int noff = g.dim == 2 ? 9 : 27;
+    long long tot = (long long)g.ncor * noff;
+    prof_start(KC_COARSE_SETUP, cs);
+    k_coarse_assemble<<<(int)((tot + 255) / 256), 256, 0, cs>>>(g, Kcc_, dm_->sd_cls, CA_, CB_);
+    prof_stop(KC_COARSE_SETUP, cs);
+    ENG_LAUNCH();
+    cprov_.ly.dim = g.dim;
+    for (int a = 0; a < 3; ++a) cprov_.ly.ext[a] = a < g.dim ? g.ncg[a] : 1;
+    cprov_.ly.b = g.cb;
+    cprov_.ly.L = g.cL;
+    cprov_.CA = CA_;
+    cprov_.CB = CB_;
+    // FP64 block cyclic reduction over the coarse layers.  With at least two layers, level 0 is
+    // kept as blocks (applied by k_bcr_fwd0 / k_bcr_bwd0 around each coarse solve) and the
+    // explicit inverse in precision T covers only the reduced matrix on the surviving layers
+    split_ = g.cL >= 2;
+    BcrLevel0<T> l0{nullptr, nullptr, nullptr};
+    ncr_ = g.ncor;
+    if (split_) {
+      std::vector<int> tgt, elim, rem;
+      bcr_level0_maps(g.cL, &tgt, &elim, &rem);
+      nj0_ = (int)elim.size() / 3;
+      nr0_ = (int)rem.size();
+      ncr_ = g.cb * nr0_;
+      auto up = [&](int** d, const std::vector<int>& h) -> cudaError_t {
+        cudaError_t e = alloc(d, std::max<size_t>(h.size(), 1) * sizeof(int));
+        if (e == cudaSuccess && !h.empty())
+          e = cudaMemcpyAsync(*d, h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice, cs);
+        return e;
+      };
+      ENG_CK(up(&bcr_tgt_, tgt));
+      ENG_CK(up(&bcr_elim_, elim));
+      ENG_CK(up(&bcr_rem_, rem));
+      ENG_CK(cudaStreamSynchronize(cs));  // the host tables leave scope
+      const size_t nb0 = (size_t)nj0_ * cbb;
+      ENG_CK(alloc(&D0_, nb0 * cxT));
+      ENG_CK(alloc(&Lp0_, nb0 * cxT));
+      ENG_CK(alloc(&Lq0_, nb0 * cxT));
+      ENG_CK(alloc(&LpT0_, nb0 * cxT));
+      ENG_CK(alloc(&LqT0_, nb0 * cxT));
+      op_bytes_ += 5 * (long long)nb0 * cxT;
+      l0 = BcrLevel0<T>{D0_, Lp0_, Lq0_};
+    }
+    ldk_ = (ncr_ + 1) & ~1;  // even row stride of the explicit inverse (temporary)
+    nct_ = (ncr_ + kCT - 1) / kCT;
+    ENG_CK(alloc(&Kinv_, (size_t)ncr_ * ldk_ * cxT));
+    ENG_CK(alloc(&Kt_, (size_t)ctile_count(nct_) * kCT * kCT * cxT));
+    op_bytes_ += (long long)ctile_count(nct_) * kCT * kCT * cxT;
+    int crc = coarse_bcr<T>(cprov_, split_ ? &l0 : nullptr, Kinv_, ldk_, err_ + 2, cs, msg, &launches);
+    if (crc) return crc;
+    if (split_) {  // the blocks used transposed by the solve, stored transposed
+      const size_t nb0 = (size_t)nj0_ * cbb;
+      const int gt = (int)std::min<size_t>((nb0 + 255) / 256, 4096);
+      k_transpose_blocks<T><<<gt, 256, 0, cs>>>(Lp0_, nj0_, g.cb, LpT0_);
+      ENG_LAUNCH();
+      k_transpose_blocks<T><<<gt, 256, 0, cs>>>(Lq0_, nj0_, g.cb, LqT0_);
+      ENG_LAUNCH();
+    }
+    // keep the upper 32 x 32 tiles of the symmetric inverse; the full matrix is released
+    prof_start(KC_COARSE_INV, cs);
+    k_pack_ctiles<T><<<(int)std::min<long long>(ctile_count(nct_), 8 * nsm_), 256, 0, cs>>>(Kinv_, ncr_, ldk_,
+                                                                                          nct_, Kt_);
+    prof_stop(KC_COARSE_INV, cs);
+    ENG_LAUNCH();
+    free_one(Kinv_);
+    Kinv_ = nullptr;
     return SCHUR_OK;
   }
 
@@ -1200,7 +1251,7 @@ class Engine : public EngineBase {
   int* h_active_ = nullptr;
   cudaStream_t ast_ = nullptr;  // stream of the current setup / solve (stream-ordered allocations)
   cudaStream_t side_ = nullptr;  // second setup stream (interior branch)
-  cudaEvent_t fork_ = nullptr, join_ = nullptr;
+  cudaEvent_t fork_ = nullptr, join_ = nullptr, corner_ev_ = nullptr;
 };
 
 }  // namespace schur

@@ -131,6 +131,7 @@ __device__ __forceinline__ void warp_layered_solve(const Prov& P, const cx<T>* _
 // read back by the same thread in the backward sweep X_K = E_K - D_K^{-1} A_{K,K+1} X_{K+1}.
 // Outputs: rows of X on the interface slots (F, Frc) and, for the corner columns, the corner
 // Schur complement Kcc = A_cc - A_cr X_rc accumulated while the sweep passes the corner layers.
+// Only the columns below col1 are formed (col1 = nD: F alone, the corner columns formed apart).
 template <int B>
 struct ColsLayout {
   static constexpr int SB = (B + 1) & ~1;  // row stride of the staged blocks: 16-byte aligned rows
@@ -157,7 +158,7 @@ __device__ __forceinline__ void load_pair(const cx<T>* p, cx<T>& a, cx<T>& b2) {
 template <class T, int B>
 __global__ void __launch_bounds__(128) k_form_rr_cols(StencilProv<T> P, Geom g, MapsView m, const cx<T>* __restrict__ Dinv,
                                                       int ncls, cx<T>* F, cx<T>* Frc, cx<double>* Kcc, cx<T>* Ews,
-                                                      int ldE) {
+                                                      int ldE, int col1) {
   constexpr int SB = ColsLayout<B>::SB, NT = 3;
   const int b = P.ly.b, L = P.ly.L, nD = g.nD, nc = g.nc, ncol = nD + nc, bb = b * b;
   const int c = threadIdx.x, nthr = blockDim.x;
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(128) k_form_rr_cols(StencilProv<T> P, Geom g, 
   for (int e = c; e < 2 * B * SB; e += nthr) Db[e] = czero<T>();
   for (int e = c; e < L * b; e += nthr) slot_s[e] = m.node_slot[e];
   cx<T>* E = Ews + (size_t)blockIdx.x * L * B * ldE;
-  const bool is_unit = c < nD, is_corner = c >= nD && c < ncol;
+  const bool is_unit = c < nD && c < col1, is_corner = c >= nD && c < ncol && c < col1;
   const int cc = c - nD;
   for (int q = blockIdx.x; q < ncls; q += gridDim.x) {
     P.select(q, m.cls_code);
@@ -690,7 +691,7 @@ __global__ void k_local_solve_warp(StencilProv<T> P, Geom g, MapsView m, const c
 // F, Frc, Kcc of each class, one warp per (class, chunk of C columns); solution in shared memory.
 template <class T, int C>
 __global__ void k_form_rr_warp(StencilProv<T> P, Geom g, MapsView m, const cx<T>* __restrict__ Dinv, int ncls,
-                               cx<T>* F, cx<T>* Frc, cx<double>* Kcc, cx<T>* Xws) {
+                               cx<T>* F, cx<T>* Frc, cx<double>* Kcc, cx<T>* Xws, int chunk0, int nrun) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const int nD = g.nD, nc = g.nc, ncol = nD + nc, nchunk = (ncol + C - 1) / C;
   const int b = P.ly.b, L = P.ly.L, dim = g.dim;
@@ -699,8 +700,10 @@ __global__ void k_form_rr_warp(StencilProv<T> P, Geom g, MapsView m, const cx<T>
   cx<T>* X = Xws + (size_t)(blockIdx.x * wpb + wib) * g.nl * C;
   extern __shared__ unsigned char smraw[];
   cx<T>* Ds = reinterpret_cast<cx<T>*>(smraw) + (size_t)wib * 2 * P.ly.b * P.ly.b;
-  for (int w = blockIdx.x * wpb + wib; w < ncls * nchunk; w += gridDim.x * wpb) {
-  const int q = w / nchunk, col0 = (w % nchunk) * C;
+  // chunks [chunk0, chunk0 + nrun) of C columns of every class (all: 0, nchunk)
+  (void)nchunk;
+  for (int w = blockIdx.x * wpb + wib; w < ncls * nrun; w += gridDim.x * wpb) {
+  const int q = w / nrun, col0 = (chunk0 + w % nrun) * C;
   P.select(q, m.cls_code);
   const int code = P.code;
   int ext[3];
