@@ -254,8 +254,11 @@ def algorithmic(cat, info, prec_bytes):
     if cat == "scatter":
         return "hbm", nlam * cb + 2 * nlam * cb
     if cat == "form":
-        # forward and backward layer sweeps of nD + nc right-hand sides on every subdomain
-        return "alu", nsd * 2 * b * b * b * (nD + nc) * cmac
+        # forward and backward layer sweeps of the nD interface columns on every subdomain (the
+        # corner columns are formed ahead of them: form_corner)
+        return "alu", nsd * 2 * b * b * b * nD * cmac
+    if cat == "form_corner":
+        return "alu", nsd * 2 * b * b * b * nc * cmac
     if cat == "factor":
         # per layer: explicit inverse of the b x b pivot block and the Schur update
         return "alu", nsd * b * (b ** 3 + 2 * 3 * b * b) * cmac
@@ -279,7 +282,7 @@ def algorithmic(cat, info, prec_bytes):
 
 CATEGORIES = ["factor", "form", "coarse_setup", "local_rhs", "apply_F", "apply_S", "scatter", "coarse_apply",
               "corner", "gmres_dots", "gmres_update", "gmres_other", "recover", "assemble_z", "residual",
-              "coarse_inverse", "interior"]
+              "coarse_inverse", "interior", "form_corner"]
 # profiling categories that hold exactly one kernel on the 2D mixed workload (16^2-element
 # subdomains: layer size 17, 60 interface slots, one right-hand side)
 KERNEL_OF = {"form": "k_form_rr_cols<float, 17>", "apply_F": "k_local_apply_1<float, 0>",
@@ -347,11 +350,10 @@ def category_roofline(cat, info, launches, total_ms, steps, peaks):
            "algorithmic_flops_per_launch": per_launch,
            "peak_source": "measured %s FMA (schur_peak_probe)" % ("FP64" if is64 else "FP32")}
     if cat == "form":
-        # the bytes it must move: read D^-1 of every subdomain, write packed F, F_rc and K_cc
+        # the bytes it must move: read D^-1 of every subdomain, write packed F
         nsd, nD, b = info["n_sub"], info["n_delta"], int(round(info["n_local"] ** 0.5))
         packed = ((nD * (nD + 1) // 2) + 1) // 2 * 2
-        out["algorithmic_bytes_per_launch"] = (nsd * (b * b * b + packed + nD * 4) * 2 * prec_bytes +
-                                               nsd * 16 * 16) / per_step
+        out["algorithmic_bytes_per_launch"] = nsd * (b * b * b + packed) * 2 * prec_bytes / per_step
     return out
 
 
@@ -426,7 +428,7 @@ def tc_form_roofline(S, N, P, beta, peaks):
     category, against the TF32 tcgen05 peak measured by schur_peak_probe."""
     cnt = tc_form_counts(N, P)
     executed, useful = cnt["executed"], cnt["useful"]
-    S.schur_profile_begin(0x1FFFF)
+    S.schur_profile_begin(0x3FFFF)
     sol = S.Solver(3, N, beta, nsub=P, precision=S.SCHUR_MIXED, tol=OUTER_TOL)
     prof = S.schur_profile_end()
     sol.close()
@@ -792,7 +794,7 @@ def main():
 
     # untimed profiling pass, one step per beta, every category: the per-category breakdown and the
     # single kernel with the largest share (only that kernel's events are recorded while timing)
-    _, _, _, _, prof_all = timed(S.SCHUR_MIXED, 4, 0, profile_mask=0x1FFFF)
+    _, _, _, _, prof_all = timed(S.SCHUR_MIXED, 4, 0, profile_mask=0x3FFFF)
     single = [c for c in (prof_all or {}) if c in KERNEL_OF]
     dom = max(single, key=lambda c: prof_all[c][1]) if single else None
     dom_mask = (1 << CATEGORIES.index(dom)) if dom else 0

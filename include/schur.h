@@ -226,7 +226,8 @@ int schur_partition_export(const schur_mesh* mesh, const int* nsub, int local_mo
  * summed event times (ms) into out (up to cap entries; *count = categories seen) and disables
  * timing.  Categories: 0 factor, 1 form, 2 coarse_setup, 3 local_rhs, 4 apply_F, 5 apply_S,
  * 6 scatter, 7 coarse_apply, 8 corner, 9 gmres_dots, 10 gmres_update, 11 gmres_other,
- * 12 recover, 13 assemble_z, 14 residual, 15 coarse_inverse, 16 interior.
+ * 12 recover, 13 assemble_z, 14 residual, 15 coarse_inverse, 16 interior, 17 form_corner (the
+ * corner columns of the local operators, formed ahead of F on the 2D corner coarse problem).
  * schur_launch_count: kernels launched through ctx since schur_setup (setup included). */
 typedef struct {
   int category;

@@ -369,10 +369,10 @@ class Engine : public EngineBase {
             const size_t smemw = wpb * warp_solve_smem<T>(g.lb);
             ENG_CK(alloc(&Xc, (size_t)gridw * wpb * g.nl * CW * cxT));
             ENG_CK(smem_attr((const void*)k_form_rr_warp<T, CW>, (int)smemw));
-            prof_start(KC_FORM, st);
+            prof_start(KC_FORM_CORNER, st);
             k_form_rr_warp<T, CW><<<gridw, 32 * wpb, smemw, st>>>(prr_, g, mv_, Dinv_, ncls_, F_, FrcF, Kcc_, Xc, chunk0,
                                                                  nrun);
-            prof_stop(KC_FORM, st);
+            prof_stop(KC_FORM_CORNER, st);
             ENG_LAUNCH();
             if (!corner_ev_) ENG_CK(cudaEventCreateWithFlags(&corner_ev_, cudaEventDisableTiming));
             ENG_CK(cudaEventRecord(corner_ev_, st));

@@ -20,7 +20,7 @@ std::vector<cudaEvent_t> g_pool;
 const char* kNames[KC_N] = {"factor",         "form",        "coarse_setup", "local_rhs",   "apply_F",
                             "apply_S",        "scatter",     "coarse_apply", "corner",      "gmres_dots",
                             "gmres_update",   "gmres_other", "recover",      "assemble_z",  "residual",
-                            "coarse_inverse", "interior"};
+                            "coarse_inverse", "interior",    "form_corner"};
 
 cudaEvent_t take() {
   if (!g_pool.empty()) {

@@ -22,7 +22,8 @@ enum KCat {
   KC_RESIDUAL = 14,   // FP64 refinement residual and shortcut
   KC_COARSE_INV = 15, // coarse inverse columns (and precision conversion)
   KC_INTERIOR = 16,   // interior factor and Dirichlet S (second setup stream)
-  KC_N = 17
+  KC_FORM_CORNER = 17,// corner columns of the local operators formed ahead of F (2D, corner coarse)
+  KC_N = 18
 };
 
 // start/stop brackets around one launch; no-ops unless the category is enabled

@@ -143,7 +143,7 @@ def _check(code, where, allow=()):
     return code
 
 
-def schur_profile_begin(mask=0x1FFFF):
+def schur_profile_begin(mask=0x3FFFF):
     _check(load().schur_profile_begin(mask), "schur_profile_begin")
 
 
