@@ -321,7 +321,6 @@ class Engine : public EngineBase {
     bool early_coarse = false;
     {
       cx<T>* Xws = nullptr;
-      cx<T>* Xc = nullptr;  // scratch of the early corner columns
       bool formed = false;
       if constexpr (sizeof(T) == 4) {
         const int ncol = g.nD + g.nc, ldE = ((ncol + 31) / 32) * 32;
@@ -357,26 +356,34 @@ class Engine : public EngineBase {
           formed = true;
         } else if (g.dim == 2 && g.lb <= 32 && ldE <= 128) {
           const int Bp = g.lb == 9 ? 9 : g.lb == 17 ? 17 : ((g.lb + 7) / 8) * 8;
-          // With the corner coarse problem (not augmented) the corner columns (Frc, Kcc) are formed
-          // first, four per warp, so that the FP64 coarse factorisation and inverse run on the
-          // second (higher-priority) stream while one CTA per class forms F
-          early_coarse = !aug && g.ncor > 0 && g.nc > 0 && g.nD > 0;
-          int col1 = g.nD + g.nc;
+          // With the corner coarse problem (not augmented) K_cc is formed first, so that the FP64
+          // coarse factorisation and inverse run on the second (higher-priority) stream while one
+          // CTA per class forms F and F_rc
+          early_coarse = !aug && g.ncor > 0 && g.nc == 4 && g.nD > 0;
+          const int col1 = g.nD + g.nc;
           if (early_coarse) {
-            constexpr int CW = 4;
-            const int chunk0 = g.nD / CW, nrun = (g.nD + g.nc + CW - 1) / CW - chunk0, wpb = 4;
-            const int gridw = std::max(1, std::min((ncls_ * nrun + wpb - 1) / wpb, 4 * nsm_));
-            const size_t smemw = wpb * warp_solve_smem<T>(g.lb);
-            ENG_CK(alloc(&Xc, (size_t)gridw * wpb * g.nl * CW * cxT));
-            ENG_CK(smem_attr((const void*)k_form_rr_warp<T, CW>, (int)smemw));
+            // K_cc of every class from the forward sweep of its four corner columns (k_corner_kcc);
+            // F and F_rc then come from the formation below, which leaves K_cc alone
+            const int wpb = 4, gridk = std::max(1, (ncls_ + wpb - 1) / wpb);
             prof_start(KC_FORM_CORNER, st);
-            k_form_rr_warp<T, CW><<<gridw, 32 * wpb, smemw, st>>>(prr_, g, mv_, Dinv_, ncls_, F_, FrcF, Kcc_, Xc, chunk0,
-                                                                 nrun);
+            cudaError_t ke = cudaErrorInvalidValue;
+#define KC_CASE(BV) \
+  case BV: k_corner_kcc<T, BV><<<gridk, 32 * wpb, 0, st>>>(prr_, g, mv_, Dinv_, ncls_, Kcc_); ke = cudaGetLastError(); break
+            switch (Bp) {
+              KC_CASE(8);
+              KC_CASE(9);
+              KC_CASE(16);
+              KC_CASE(17);
+              KC_CASE(24);
+              KC_CASE(32);
+              default: break;
+            }
+#undef KC_CASE
+            ENG_CK(ke);
             prof_stop(KC_FORM_CORNER, st);
             ENG_LAUNCH();
             if (!corner_ev_) ENG_CK(cudaEventCreateWithFlags(&corner_ev_, cudaEventDisableTiming));
             ENG_CK(cudaEventRecord(corner_ev_, st));
-            col1 = g.nD;
           }
           // one CTA per class when the coarse setup runs beside it, so that its blocks retire often
           // and the second stream's blocks are scheduled in between; else persistent CTAs
@@ -388,7 +395,7 @@ class Engine : public EngineBase {
           prof_start(KC_FORM, st);
           cudaError_t fe = cudaErrorInvalidValue;
 #define FC_CASE(BV) \
-  case BV: fe = launch_form_cols<T, BV>(prr_, g, mv_, Dinv_, ncls_, F_, FrcF, Kcc_, Xws, grid, ldE, col1, st); break
+  case BV: fe = launch_form_cols<T, BV>(prr_, g, mv_, Dinv_, ncls_, F_, FrcF, early_coarse ? nullptr : Kcc_, Xws, grid, ldE, col1, st); break
           switch (Bp) {
             FC_CASE(8);
             FC_CASE(9);
@@ -443,7 +450,6 @@ class Engine : public EngineBase {
       ENG_CK(cudaStreamWaitEvent(st, join_, 0));
       ENG_CK(cudaStreamSynchronize(st));
       if (Xws) free_one(Xws);
-      if (Xc) free_one(Xc);
       if (Gc) free_one(Gc);
       if (Hc) free_one(Hc);
       free_one(Xi);

@@ -131,7 +131,8 @@ __device__ __forceinline__ void warp_layered_solve(const Prov& P, const cx<T>* _
 // read back by the same thread in the backward sweep X_K = E_K - D_K^{-1} A_{K,K+1} X_{K+1}.
 // Outputs: rows of X on the interface slots (F, Frc) and, for the corner columns, the corner
 // Schur complement Kcc = A_cc - A_cr X_rc accumulated while the sweep passes the corner layers.
-// Only the columns below col1 are formed (col1 = nD: F alone, the corner columns formed apart).
+// Only the columns below col1 are formed; with Kcc null the corner Schur complements are not
+// written (they come from k_corner_kcc).
 template <int B>
 struct ColsLayout {
   static constexpr int SB = (B + 1) & ~1;  // row stride of the staged blocks: 16-byte aligned rows
@@ -363,11 +364,106 @@ __global__ void __launch_bounds__(128) k_form_rr_cols(StencilProv<T> P, Geom g, 
           cx<T> v = kacc[c1];
           if (c1 == cc) v = cadd(v, q1_entry(P.st, g.s, lc2, lc2));
           if (cDir[c1] || cDir[cc]) v = czero<T>();
-          Kcc[((size_t)q * nc + c1) * nc + cc] = ccast<double>(v);
+          if (Kcc) Kcc[((size_t)q * nc + c1) * nc + cc] = ccast<double>(v);
         }
       }
     }
     __syncthreads();
+  }
+}
+
+// Corner Schur complements K_cc = A_cc - A_cr A_rr^{-1} A_rc of every class (2D, layer size b <= B)
+// from the forward layer sweep alone: with the block LDL^T factor A_rr = L D L^T by layers (pivot
+// blocks D_K, L_{K,K-1} = A_{K,K-1} D_{K-1}^{-1}) and W = L^{-1} A_rc,
+//   A_cr A_rr^{-1} A_rc = W^T D^{-1} W = sum_K W_K^T E_K,  E_K = D_K^{-1} W_K,
+//   W_K = (A_rc)_K - A_{K,K-1} E_{K-1}
+// (plain transposes: the matrices are complex symmetric).  One warp per class, lane i = row i of
+// the layer, the four corner columns in registers; D_K^{-1} read by rows (coalesced), the layer
+// couplings through shuffles.  It lets the coarse factorisation start before the local operators
+// are formed.
+template <class T, int B>
+__global__ void __launch_bounds__(128) k_corner_kcc(StencilProv<T> P, Geom g, MapsView m, const cx<T>* __restrict__ Dinv,
+                                                    int ncls, cx<double>* Kcc) {
+  constexpr int NC = 4;  // corners of a 2D subdomain
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const int b = P.ly.b, L = P.ly.L, bb = b * b;
+  const bool act = lane < b;
+  for (int q = blockIdx.x * wpb + wib; q < ncls; q += gridDim.x * wpb) {
+    P.select(q, m.cls_code);
+    int cK[NC], cI[NC], lc[NC][3];
+    bool cDir[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int node = m.corner_node[c];
+      cK[c] = node / b;
+      cI[c] = node % b;
+      P.crd(cK[c], cI[c], lc[c]);
+      cDir[c] = local_dirichlet(P.code, lc[c], g.s, 2);
+    }
+    cx<T> ep[NC], kacc[NC][NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      ep[c] = czero<T>();
+#pragma unroll
+      for (int c2 = 0; c2 < NC; ++c2) kacc[c][c2] = czero<T>();
+    }
+    for (int K = 0; K < L; ++K) {
+      const cx<T>* Dk = Dinv + ((size_t)q * L + K) * bb;
+      cx<T> d[B];
+#pragma unroll
+      for (int mm = 0; mm < B; ++mm) d[mm] = (act && mm < b) ? Dk[mm * b + lane] : czero<T>();
+      cx<T> w[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        w[c] = czero<T>();
+        if (act && !cDir[c] && abs(K - cK[c]) <= 1 && abs(lane - cI[c]) <= 1 && !P.removed_node(K, lane)) {
+          int l[3];
+          P.crd(K, lane, l);
+          w[c] = q1_entry(P.st, g.s, l, lc[c]);
+        }
+      }
+      if (K > 0) {
+        const cx<T> a0 = act ? P.Al(K - 1, lane, 0) : czero<T>();
+        const cx<T> a1 = act ? P.Al(K - 1, lane, 1) : czero<T>();
+        const cx<T> a2 = act ? P.Al(K - 1, lane, 2) : czero<T>();
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const cx<T> em = shfl_cx(ep[c], lane > 0 ? lane - 1 : 0);
+          const cx<T> en = shfl_cx(ep[c], lane < 31 ? lane + 1 : 31);
+          cfms(w[c], a0, em);
+          cfms(w[c], a1, ep[c]);
+          cfms(w[c], a2, en);
+        }
+      }
+      cx<T> e[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) e[c] = czero<T>();
+#pragma unroll
+      for (int mm = 0; mm < B; ++mm)
+        if (mm < b) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) cfma(e[c], d[mm], shfl_cx(w[c], mm));
+        }
+#pragma unroll
+      for (int c1 = 0; c1 < NC; ++c1)
+#pragma unroll
+        for (int c2 = 0; c2 < NC; ++c2) cfma(kacc[c1][c2], w[c1], e[c2]);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) ep[c] = e[c];
+    }
+#pragma unroll
+    for (int c1 = 0; c1 < NC; ++c1)
+#pragma unroll
+      for (int c2 = 0; c2 < NC; ++c2) {
+        cx<T> v = kacc[c1][c2];
+        for (int o = 16; o > 0; o >>= 1) v = cadd(v, shfl_xor_cx(v, o));
+        if (lane == 0) {
+          cx<T> r = mkc<T>(-v.re, -v.im);
+          if (c1 == c2) r = cadd(r, q1_entry(P.st, g.s, lc[c1], lc[c1]));
+          if (cDir[c1] || cDir[c2]) r = czero<T>();
+          Kcc[((size_t)q * NC + c1) * NC + c2] = ccast<double>(r);
+        }
+      }
   }
 }
 
