@@ -254,11 +254,11 @@ def algorithmic(cat, info, prec_bytes):
     if cat == "scatter":
         return "hbm", nlam * cb + 2 * nlam * cb
     if cat == "form":
-        # forward and backward layer sweeps of the nD interface columns on every subdomain (the
-        # corner columns are formed ahead of them: form_corner)
-        return "alu", nsd * 2 * b * b * b * nD * cmac
+        # forward and backward layer sweeps of nD + nc right-hand sides on every subdomain
+        return "alu", nsd * 2 * b * b * b * (nD + nc) * cmac
     if cat == "form_corner":
-        return "alu", nsd * 2 * b * b * b * nc * cmac
+        # K_cc ahead of the formation: the forward sweep of the nc corner columns
+        return "alu", nsd * b * b * b * nc * cmac
     if cat == "factor":
         # per layer: explicit inverse of the b x b pivot block and the Schur update
         return "alu", nsd * b * (b ** 3 + 2 * 3 * b * b) * cmac
@@ -350,10 +350,10 @@ def category_roofline(cat, info, launches, total_ms, steps, peaks):
            "algorithmic_flops_per_launch": per_launch,
            "peak_source": "measured %s FMA (schur_peak_probe)" % ("FP64" if is64 else "FP32")}
     if cat == "form":
-        # the bytes it must move: read D^-1 of every subdomain, write packed F
+        # the bytes it must move: read D^-1 of every subdomain, write packed F and F_rc
         nsd, nD, b = info["n_sub"], info["n_delta"], int(round(info["n_local"] ** 0.5))
         packed = ((nD * (nD + 1) // 2) + 1) // 2 * 2
-        out["algorithmic_bytes_per_launch"] = nsd * (b * b * b + packed) * 2 * prec_bytes / per_step
+        out["algorithmic_bytes_per_launch"] = nsd * (b * b * b + packed + nD * 4) * 2 * prec_bytes / per_step
     return out
 
 
