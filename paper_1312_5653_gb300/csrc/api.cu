@@ -186,12 +186,15 @@ int ctx_ensure_outer(schur_ctx* c, int R) {
 }
 
 // Relative residuals ||f - A z|| / ||f|| for R columns (synchronises).  Leaves res = f - A z.
-int ctx_residual(schur_ctx* c, const double* bre, const double* bim, int ldb, int R, cudaStream_t st, double* rel) {
+// z_zero: z is known to be zero (the first refinement step), so res = f without the stencil.
+int ctx_residual(schur_ctx* c, const double* bre, const double* bim, int ldb, int R, cudaStream_t st, double* rel,
+                 bool z_zero) {
   const Geom& g = c->mp->hm.g;
   Coef27 sten = make_coef(g, c->sim, c->sre);
   prof_start(KC_RESIDUAL, st);
   k_residual<<<dim3(c->nblk, R), 256, 0, st>>>(g, sten, bre, bim, ldb, reinterpret_cast<const cx<double>*>(c->z),
-                                               (int)g.n, R, reinterpret_cast<cx<double>*>(c->res), c->part, c->nblk);
+                                               (int)g.n, R, reinterpret_cast<cx<double>*>(c->res), c->part, c->nblk,
+                                               z_zero ? 1 : 0);
   prof_stop(KC_RESIDUAL, st);
   API_CK(cudaGetLastError());
   ++c->launches;
@@ -224,7 +227,7 @@ int ctx_outer(schur_ctx* c, const double* bre, const double* bim, int ldb, int R
   int status = SCHUR_OK;
   const double inner_tol = c->opts.inner_tol > 0 ? c->opts.inner_tol : (c->opts.precision == SCHUR_MIXED ? 3e-5 : 1e-12);
   while (true) {
-    rc = ctx_residual(c, bre, bim, ldb, R, st, rel);
+    rc = ctx_residual(c, bre, bim, ldb, R, st, rel, steps == 0);
     if (rc) return rc;
     double worst = 0;
     bool nan = false;

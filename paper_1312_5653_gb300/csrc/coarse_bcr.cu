@@ -5,12 +5,16 @@
 // (p, q: its remaining neighbours; A_pj = U_p, A_jq = U_j, symmetric blocks):
 //   Dinv_j = D_j^{-1},  Lp_j = A_pj Dinv_j,  Lq_j = Dinv_j A_jq,
 //   D_p -= Lp_j A_pj^T,  D_q -= A_jq^T Lq_j,  A_pq = -Lp_j A_jq
-// so the critical path is log2(L) levels of batched dense work.  The factor is always computed in
-// FP64.  The explicit inverse is a cyclic-reduction solve with the identity as right-hand side in
-// the working precision (FP32 copies of Dinv, Lp, Lq in the mixed form):
+// so the critical path is log2(L) levels of batched dense work.  The factor is computed in the
+// working precision: FP64 in the FP64 form, FP32 in the mixed form (whose coarse solves are FP32
+// anyway; the FP64 refinement around the inner solve corrects what the FP32 factor leaves).  The
+// explicit inverse is a cyclic-reduction solve with the identity as right-hand side in the same
+// precision:
 //   forward  X_p -= Lp_j X_j,  X_q -= Lq_j^T X_j
 //   backward X_j  = Dinv_j X_j - Lp_j^T X_p - Lq_j X_q
 #include <cooperative_groups.h>
+
+#include <type_traits>
 
 #include <algorithm>
 #include <vector>
@@ -588,8 +592,8 @@ static cudaError_t launch_gj_batch(const cx<S>* Din, cx<S>* Dout, const int* dli
   return last;
 }
 
-template <class S>
-__global__ void k_bcr_convert(const cx<double>* __restrict__ in, cx<S>* out, size_t n) {
+template <class S, class I>
+__global__ void k_bcr_convert(const cx<I>* __restrict__ in, cx<S>* out, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     out[i] = ccast<S>(in[i]);
 }
@@ -775,6 +779,11 @@ static cudaError_t run_plan(const BcrPlan<S>& plan, GemmTask<S>* dG, CopyTask<S>
   return cudaSuccess;
 }
 
+// Precision of the coarse factorisation (the block cyclic reduction's pivots and Schur updates)
+// for a solve in precision T: the working precision itself.
+template <class T>
+using BcrFactor = std::conditional_t<sizeof(T) == 4, float, double>;
+
 template <class T>
 int coarse_bcr(const StoredProv<double>& P, const BcrLevel0<T>* split, cx<T>* Kinv, int ldk, int* err, cudaStream_t st,
                std::string* msg, long long* launches) {
@@ -818,7 +827,8 @@ int coarse_bcr(const StoredProv<double>& P, const BcrLevel0<T>* split, cx<T>* Ki
       for (void* p : *m) cudaFreeAsync(p, s);
     }
   } guard{&mem, st};
-  using D64 = cx<double>;
+  using FP = BcrFactor<T>;  // precision of the factorisation
+  using D64 = cx<FP>;
   D64 *D = nullptr, *Ucur = nullptr, *Dinv = nullptr, *Lp = nullptr, *Lq = nullptr, *Unew = nullptr;
   BCR_CK(mal(&D, L * bb * sizeof(D64)), "alloc");
   BCR_CK(mal(&Ucur, L * bb * sizeof(D64)), "alloc");
@@ -827,14 +837,14 @@ int coarse_bcr(const StoredProv<double>& P, const BcrLevel0<T>* split, cx<T>* Ki
   BCR_CK(mal(&Lq, L * bb * sizeof(D64)), "alloc");
   BCR_CK(mal(&Unew, L * bb * sizeof(D64)), "alloc");
 
-  // ---- plan: FP64 factorisation.  Level 0 still sees the stencil's band (the layer blocks couple
+  // ---- plan: factorisation.  Level 0 still sees the stencil's band (the layer blocks couple
   // in-layer neighbours only): half-width 1 in 2D, a layer row + 1 in 3D, and in 2D the pivot
   // blocks are tridiagonal and are inverted by the Thomas recurrence.
   const int wband = P.ly.dim == 2 ? 1 : P.ly.ext[0] + 1;
   const bool tri0 = P.ly.dim == 2;
-  BcrPlan<double> fp;
-  std::vector<GemmTask<double>> ts;
-  std::vector<CopyTask<double>> cs;
+  BcrPlan<FP> fp;
+  std::vector<GemmTask<FP>> ts;
+  std::vector<CopyTask<FP>> cs;
   const long long lbb = (long long)bb;
   auto blk = [&](D64* base, int K) { return base + (size_t)K * bb; };
   for (size_t lv = 0; lv < lj.size(); ++lv) {
@@ -845,8 +855,8 @@ int coarse_bcr(const StoredProv<double>& P, const BcrLevel0<T>* split, cx<T>* Ki
     // Lp_j = U_p Dinv_j ; Lq_j = Dinv_j U_j
     for (size_t k = 0; k < J.size(); ++k) {
       const int j = J[k], p = lp[lv][k], q = lq[lv][k];
-      if (p >= 0) ts.push_back(task<double>(blk(Lp, j), b, 0, b, {pair<double>(blk(Ucur, p), b, 0, blk(Dinv, j), b, 0, 1.0, bA)}));
-      if (q >= 0) ts.push_back(task<double>(blk(Lq, j), b, 0, b, {pair<double>(blk(Dinv, j), b, 0, blk(Ucur, j), b, 0, 1.0, bB)}));
+      if (p >= 0) ts.push_back(task<FP>(blk(Lp, j), b, 0, b, {pair<FP>(blk(Ucur, p), b, 0, blk(Dinv, j), b, 0, FP(1), bA)}));
+      if (q >= 0) ts.push_back(task<FP>(blk(Lq, j), b, 0, b, {pair<FP>(blk(Dinv, j), b, 0, blk(Ucur, j), b, 0, FP(1), bB)}));
     }
     fp.add_gemm(ts, band);
     // remaining block t: D_t -= Lp_j U_t^T (t = p of j) and U_j'^T Lq_j' (t = q of j'), one task
@@ -860,18 +870,18 @@ int coarse_bcr(const StoredProv<double>& P, const BcrLevel0<T>* split, cx<T>* Ki
       const int jr = right_of[t], jl = left_of[t];
       if (jr < 0 && jl < 0) continue;
       if (jr >= 0 && jl >= 0)
-        ts.push_back(task<double>(blk(D, t), b, 1, b,
-                                  {pair<double>(blk(Lp, jr), b, 0, blk(Ucur, t), b, 1, -1.0, bB),
-                                   pair<double>(blk(Ucur, jl), b, 1, blk(Lq, jl), b, 0, -1.0, bA)}));
+        ts.push_back(task<FP>(blk(D, t), b, 1, b,
+                                  {pair<FP>(blk(Lp, jr), b, 0, blk(Ucur, t), b, 1, FP(-1), bB),
+                                   pair<FP>(blk(Ucur, jl), b, 1, blk(Lq, jl), b, 0, FP(-1), bA)}));
       else if (jr >= 0)
-        ts.push_back(task<double>(blk(D, t), b, 1, b, {pair<double>(blk(Lp, jr), b, 0, blk(Ucur, t), b, 1, -1.0, bB)}));
+        ts.push_back(task<FP>(blk(D, t), b, 1, b, {pair<FP>(blk(Lp, jr), b, 0, blk(Ucur, t), b, 1, FP(-1), bB)}));
       else
-        ts.push_back(task<double>(blk(D, t), b, 1, b, {pair<double>(blk(Ucur, jl), b, 1, blk(Lq, jl), b, 0, -1.0, bA)}));
+        ts.push_back(task<FP>(blk(D, t), b, 1, b, {pair<FP>(blk(Ucur, jl), b, 1, blk(Lq, jl), b, 0, FP(-1), bA)}));
     }
     for (size_t k = 0; k < J.size(); ++k) {
       const int j = J[k], p = lp[lv][k], q = lq[lv][k];
       if (p >= 0 && q >= 0)
-        ts.push_back(task<double>(blk(Unew, p), b, 0, b, {pair<double>(blk(Lp, j), b, 0, blk(Ucur, j), b, 0, -1.0, bB)}));
+        ts.push_back(task<FP>(blk(Unew, p), b, 0, b, {pair<FP>(blk(Lp, j), b, 0, blk(Ucur, j), b, 0, FP(-1), bB)}));
     }
     fp.add_gemm(ts, band);
     // the remaining p whose right neighbour j was eliminated now couples to q (or to nothing)
@@ -884,7 +894,7 @@ int coarse_bcr(const StoredProv<double>& P, const BcrLevel0<T>* split, cx<T>* Ki
 
   // ---- factor operands of the solve in precision T
   cx<T>*DinvT = nullptr, *LpT = nullptr, *LqT = nullptr, *Tmp = nullptr;
-  if (sizeof(T) == sizeof(double)) {
+  if (sizeof(T) == sizeof(FP)) {
     DinvT = reinterpret_cast<cx<T>*>(Dinv);
     LpT = reinterpret_cast<cx<T>*>(Lp);
     LqT = reinterpret_cast<cx<T>*>(Lq);
@@ -967,13 +977,13 @@ int coarse_bcr(const StoredProv<double>& P, const BcrLevel0<T>* split, cx<T>* Ki
   }
 
   // ---- device task arrays
-  GemmTask<double>* dG = nullptr;
-  CopyTask<double>* dC = nullptr;
+  GemmTask<FP>* dG = nullptr;
+  CopyTask<FP>* dC = nullptr;
   int* dL = nullptr;
   GemmTask<T>* dGi = nullptr;
   CopyTask<T>* dCi = nullptr;
-  BCR_CK(mal(&dG, fp.gemm.size() * sizeof(GemmTask<double>)), "alloc");
-  BCR_CK(mal(&dC, fp.copy.size() * sizeof(CopyTask<double>)), "alloc");
+  BCR_CK(mal(&dG, fp.gemm.size() * sizeof(GemmTask<FP>)), "alloc");
+  BCR_CK(mal(&dC, fp.copy.size() * sizeof(CopyTask<FP>)), "alloc");
   BCR_CK(mal(&dL, fp.list.size() * sizeof(int)), "alloc");
   BCR_CK(mal(&dGi, ip.gemm.size() * sizeof(GemmTask<T>)), "alloc");
   BCR_CK(mal(&dCi, ip.copy.size() * sizeof(CopyTask<T>)), "alloc");
@@ -981,14 +991,14 @@ int coarse_bcr(const StoredProv<double>& P, const BcrLevel0<T>* split, cx<T>* Ki
   // ---- run: factorisation
   const int gs = (int)std::min<size_t>((L * bb + 255) / 256, 4096);
   prof_start(KC_COARSE_SETUP, st);
-  k_bcr_densify<double><<<gs, 256, 0, st>>>(P, D, Ucur);
+  k_bcr_densify<FP><<<gs, 256, 0, st>>>(P, D, Ucur);
   BCR_CK(cudaGetLastError(), "densify");
   ++*launches;
-  BCR_CK(run_plan<double>(fp, dG, dC, dL, D, Dinv, b, wband, err, st, launches), "factorisation");
+  BCR_CK(run_plan<FP>(fp, dG, dC, dL, D, Dinv, b, wband, err, st, launches), "factorisation");
   prof_stop(KC_COARSE_SETUP, st);
   // ---- run: explicit inverse
   prof_start(KC_COARSE_INV, st);
-  if (sizeof(T) != sizeof(double)) {
+  if (sizeof(T) != sizeof(FP)) {
     k_bcr_convert<T><<<gs, 256, 0, st>>>(Dinv, DinvT, L * bb);
     k_bcr_convert<T><<<gs, 256, 0, st>>>(Lp, LpT, L * bb);
     k_bcr_convert<T><<<gs, 256, 0, st>>>(Lq, LqT, L * bb);

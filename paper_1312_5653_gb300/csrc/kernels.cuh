@@ -1441,16 +1441,19 @@ __global__ void __launch_bounds__(256) k_orth_update_norm(const cx<T>* __restric
     if (threadIdx.x == 0) a.nrm_part[(size_t)r * a.nblk + blockIdx.x] = s;
   }
   if (orth_last_block(a.cnt + r, a.nblk)) {
-    if (threadIdx.x < 32) {
-      double t = 0;
-#pragma unroll 4
-      for (int b = threadIdx.x; b < a.nblk; b += 32) t += __ldcg(a.nrm_part + (size_t)r * a.nblk + b);
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (threadIdx.x == 0) {
-        givens_step(r, a.k, a.m, sqrt(t), a.H, a.cs_c, a.cs_s, a.gvec, a.beta0, a.tol, a.active_w, a.kk, a.inv_nrm,
-                    a.resid, a.bad);
-        a.cnt[r] = 0;
-      }
+    // every thread reads its blocks' partials (one load round), warps and then the block add in order
+    __shared__ double fred[32];
+    double t = 0;
+    for (int b = threadIdx.x; b < a.nblk; b += blockDim.x) t += __ldcg(a.nrm_part + (size_t)r * a.nblk + b);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) fred[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += fred[w];
+      givens_step(r, a.k, a.m, sqrt(s), a.H, a.cs_c, a.cs_s, a.gvec, a.beta0, a.tol, a.active_w, a.kk, a.inv_nrm,
+                  a.resid, a.bad);
+      a.cnt[r] = 0;
     }
   }
 }

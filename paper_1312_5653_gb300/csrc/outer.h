@@ -11,7 +11,7 @@ Coef27 make_coef(const Geom& g, double gamma, double sre = 0.0);
 
 __global__ void k_residual(Geom g, Coef27 cf, const double* __restrict__ bre, const double* __restrict__ bim,
                            int ldb, const cx<double>* __restrict__ z, int ldz, int R, cx<double>* res,
-                           double* part, int nblk);
+                           double* part, int nblk, int zero);
 __global__ void k_shortcut(long long n, const cx<double>* __restrict__ z, int ldz, int R, double inv_gamma, double* x,
                            int ldx);
 // x = scale * Re(z) (the solution of a real factor K + gamma M; its imaginary part is zero)
