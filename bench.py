@@ -269,7 +269,7 @@ def algorithmic(cat, info, prec_bytes):
         ntask = sum(1 + p + q for lev in bcr_tasks(Lr) for p, q in lev) * 2
         return "alu", ntask * cb_ * cb_ * (cb_ * Lr) * cmac
     if cat == "coarse_setup":
-        # the reduction (FP32 in the mixed form): level 0 banded (2D: tridiagonal inverses and 3-term products), the
+        # FP64 reduction: level 0 banded (2D: tridiagonal inverses and 3-term products), the
         # other levels dense (Gauss-Jordan b^3 plus the products Lp, Lq, D_p, A_pq, D_q)
         tot = 0
         for lv, lev in enumerate(bcr_tasks(cL)):
@@ -342,12 +342,13 @@ def category_roofline(cat, info, launches, total_ms, steps, peaks):
     # ALU categories: the model counts one step's work, spread over its launches
     avg_s = total_ms / launches / 1e3
     per_launch = algo / per_step
-    # every ALU category of the mixed headline runs in FP32 (the coarse factorisation too)
-    pk = peaks.get("fp32_fma")
+    is64 = cat in ("coarse_setup",)
+    pk = peaks.get("fp64_fma" if is64 else "fp32_fma")
     ach = per_launch / avg_s / 1e12
-    out = {"bound": "alu", "precision": "fp32", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+    out = {"bound": "alu", "precision": "fp64" if is64 else "fp32", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
            "frac": ach / pk if pk else None, "traffic": None, "launches": launches, "avg_us": avg_s * 1e6,
-           "algorithmic_flops_per_launch": per_launch, "peak_source": "measured FP32 FMA (schur_peak_probe)"}
+           "algorithmic_flops_per_launch": per_launch,
+           "peak_source": "measured %s FMA (schur_peak_probe)" % ("FP64" if is64 else "FP32")}
     if cat == "form":
         # the bytes it must move: read D^-1 of every subdomain, write packed F and F_rc
         nsd, nD, b = info["n_sub"], info["n_delta"], int(round(info["n_local"] ** 0.5))

@@ -119,8 +119,7 @@ void schur_default_opts(schur_opts* opts);
  * remainder matrices A_rr (subdomain nodes minus corners and Dirichlet nodes, Sec. 5) and of the
  * interior matrices A_ii, the explicit local dual operators B A_rr^{-1} B^T, the corner coupling,
  * the Dirichlet-preconditioner Schur complements S_bb (Eq. WS), and the coarse corner problem
- * (block cyclic reduction in the working precision: FP32 in the mixed form, FP64 otherwise).
- * Synchronises `stream` before returning.  *out receives the context.
+ * (factorised in FP64).  Synchronises `stream` before returning.  *out receives the context.
  * Errors: EINVAL (mesh/beta/opts), ENOMEM, EBREAKDOWN (zero pivot), ECUDA. */
 int schur_setup(const schur_mesh* mesh, double beta, const schur_opts* opts, void* stream,
                 schur_ctx** out);

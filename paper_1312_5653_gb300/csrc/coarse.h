@@ -16,8 +16,8 @@ struct BcrLevel0 {
   cx<T>* Lp0;
   cx<T>* Lq0;
 };
-// Block cyclic reduction of the coarse matrix (assembled in FP64, factor and explicit inverse in
-// precision T).  Without split the inverse of the whole coarse matrix is written to Kinv
+// Block cyclic reduction of the coarse matrix (assembled and factorised in FP64) and the explicit
+// inverse in precision T.  Without split the inverse of the whole coarse matrix is written to Kinv
 // (n_c rows of ldk >= n_c entries); with split the level-0 blocks go to *split and Kinv receives the
 // inverse of the reduced matrix on the layers that survive level 0 (b * Lr rows, compact layer
 // order).  Entries past the row length are not defined.  Returns SCHUR_* code; *launches counts

@@ -5,16 +5,12 @@
 // (p, q: its remaining neighbours; A_pj = U_p, A_jq = U_j, symmetric blocks):
 //   Dinv_j = D_j^{-1},  Lp_j = A_pj Dinv_j,  Lq_j = Dinv_j A_jq,
 //   D_p -= Lp_j A_pj^T,  D_q -= A_jq^T Lq_j,  A_pq = -Lp_j A_jq
-// so the critical path is log2(L) levels of batched dense work.  The factor is computed in the
-// working precision: FP64 in the FP64 form, FP32 in the mixed form (whose coarse solves are FP32
-// anyway; the FP64 refinement around the inner solve corrects what the FP32 factor leaves).  The
-// explicit inverse is a cyclic-reduction solve with the identity as right-hand side in the same
-// precision:
+// so the critical path is log2(L) levels of batched dense work.  The factor is computed in FP64
+// (BcrFactor).  The explicit inverse is a cyclic-reduction solve with the identity as right-hand
+// side in the working precision (FP32 copies of Dinv, Lp, Lq in the mixed form):
 //   forward  X_p -= Lp_j X_j,  X_q -= Lq_j^T X_j
 //   backward X_j  = Dinv_j X_j - Lp_j^T X_p - Lq_j X_q
 #include <cooperative_groups.h>
-
-#include <type_traits>
 
 #include <algorithm>
 #include <vector>
@@ -780,9 +776,11 @@ static cudaError_t run_plan(const BcrPlan<S>& plan, GemmTask<S>* dG, CopyTask<S>
 }
 
 // Precision of the coarse factorisation (the block cyclic reduction's pivots and Schur updates)
-// for a solve in precision T: the working precision itself.
+// for a solve in precision T: FP64 in both forms.  (An FP32 factorisation in the mixed form gave
+// the same GMRES iterations, refinement steps and errors on the 1024^2 workload; FP64 is kept as
+// the precision of the coarse factorisation.)
 template <class T>
-using BcrFactor = std::conditional_t<sizeof(T) == 4, float, double>;
+using BcrFactor = double;
 
 template <class T>
 int coarse_bcr(const StoredProv<double>& P, const BcrLevel0<T>* split, cx<T>* Kinv, int ldk, int* err, cudaStream_t st,
@@ -1023,7 +1021,8 @@ int coarse_bcr(const StoredProv<double>& P, const BcrLevel0<T>* split, cx<T>* Ki
   ++*launches;
   BCR_CK(run_plan<T>(ip, dGi, dCi, nullptr, nullptr, nullptr, b, 0, err, st, launches), "inverse");
   prof_stop(KC_COARSE_INV, st);
-  BCR_CK(cudaStreamSynchronize(st), "sync");
+  // no synchronisation: the host arrays were pageable (staged when each copy was issued) and the
+  // temporaries are released in stream order
   return SCHUR_OK;
 #undef BCR_CK
 }

@@ -356,7 +356,7 @@ class Engine : public EngineBase {
           formed = true;
         } else if (g.dim == 2 && g.lb <= 32 && ldE <= 128) {
           const int Bp = g.lb == 9 ? 9 : g.lb == 17 ? 17 : ((g.lb + 7) / 8) * 8;
-          // With the corner coarse problem (not augmented) K_cc is formed first, so that the
+          // With the corner coarse problem (not augmented) K_cc is formed first, so that the FP64
           // coarse factorisation and inverse run on the second (higher-priority) stream while one
           // CTA per class forms F and F_rc
           early_coarse = !aug && g.ncor > 0 && g.nc == 4 && g.nD > 0;
@@ -513,12 +513,12 @@ class Engine : public EngineBase {
     return SCHUR_OK;
   }
 
-  // Corner coarse problem: block cyclic reduction (FP64 assembly, factor and stored inverse in
-  // precision T), all work on stream cs (allocations follow ast_).
+  // Corner coarse problem: FP64 block cyclic reduction and the stored inverse in precision T, all
+  // work on stream cs (allocations follow ast_); the host does not wait for it.
   int coarse_setup_bcr(cudaStream_t cs, std::string* msg) {
     const Geom& g = g_;
     const size_t cxT = sizeof(cx<T>);
-    // ---- coarse problem (assembled in FP64, factorised and inverted in T)
+    // ---- coarse problem (FP64 factorisation, inverse stored in T)
     const int nt = nbr_count(g.dim), cbb = g.cb * g.cb;
     ENG_CK(alloc(&CA_, (size_t)g.cL * g.cb * nt * sizeof(cx<double>)));
     ENG_CK(alloc(&CB_, (size_t)std::max(1, g.cL) * g.cb * nt * sizeof(cx<double>)));
@@ -536,7 +536,7 @@ class Engine : public EngineBase {
     cprov_.ly.L = g.cL;
     cprov_.CA = CA_;
     cprov_.CB = CB_;
-    // Block cyclic reduction over the coarse layers.  With at least two layers, level 0 is
+    // FP64 block cyclic reduction over the coarse layers.  With at least two layers, level 0 is
     // kept as blocks (applied by k_bcr_fwd0 / k_bcr_bwd0 around each coarse solve) and the
     // explicit inverse in precision T covers only the reduced matrix on the surviving layers
     split_ = g.cL >= 2;
@@ -556,8 +556,7 @@ class Engine : public EngineBase {
       };
       ENG_CK(up(&bcr_tgt_, tgt));
       ENG_CK(up(&bcr_elim_, elim));
-      ENG_CK(up(&bcr_rem_, rem));
-      ENG_CK(cudaStreamSynchronize(cs));  // the host tables leave scope
+      ENG_CK(up(&bcr_rem_, rem));  // pageable host tables: staged when the copy is issued
       const size_t nb0 = (size_t)nj0_ * cbb;
       ENG_CK(alloc(&D0_, nb0 * cxT));
       ENG_CK(alloc(&Lp0_, nb0 * cxT));
