@@ -303,7 +303,7 @@ struct GemmTile {
 };
 
 template <class S, int TM>
-__global__ void __launch_bounds__(256, 3) k_gemm_batch(const GemmTask<S>* __restrict__ tasks, int M, int Kd) {
+__global__ void __launch_bounds__(256) k_gemm_batch(const GemmTask<S>* __restrict__ tasks, int M, int Kd) {
   constexpr int Q = TM / 16;
   const GemmTask<S>& tk = tasks[blockIdx.z];
   const int N = tk.N;
@@ -317,62 +317,50 @@ __global__ void __launch_bounds__(256, 3) k_gemm_batch(const GemmTask<S>* __rest
   for (int a = 0; a < Q; ++a)
 #pragma unroll
     for (int c = 0; c < Q; ++c) acc[a][c] = mkc<S>(0, 0);
-  // the (pair, 16-wide K slice) steps in one sequence; each step's operand entries are loaded into
-  // registers while the previous step is multiplied, then stored to shared memory.  Operands are
-  // read along their contiguous dimension so consecutive threads touch consecutive addresses.
-  constexpr int LE = 16 * TM / 256;  // entries of each operand slice per thread
-  const int nk = (Kd + 15) / 16, nstep = tk.np * nk;
-  cx<S> ra[LE], rb[LE];
-  auto load = [&](int it) {
-    const GemmPair<S> t = tk.p[it / nk];
-    const int k0 = (it % nk) * 16;
-#pragma unroll
-    for (int u = 0; u < LE; ++u) {
-      const int e = threadIdx.x + 256 * u;
-      int r, kk;
-      if (!t.transA) r = e >> 4, kk = e & 15;
-      else kk = e / TM, r = e % TM;
-      const int gr = row0 + r, gk = k0 + kk;
-      ra[u] = (gr < M && gk < Kd) ? cscale(t.transA ? t.A[(size_t)gk * t.lda + gr] : t.A[(size_t)gr * t.lda + gk], t.alpha)
-                                  : mkc<S>(0, 0);
-      int c;
-      if (t.transB) c = e >> 4, kk = e & 15;
-      else kk = e / TM, c = e % TM;
-      const int gc = col0 + c, gk2 = k0 + kk;
-      rb[u] = (gc < N && gk2 < Kd) ? (t.transB ? t.B[(size_t)gc * t.ldb + gk2] : t.B[(size_t)gk2 * t.ldb + gc])
-                                   : mkc<S>(0, 0);
-    }
-  };
-  auto store = [&](int it) {
-    const GemmPair<S> t = tk.p[it / nk];
-#pragma unroll
-    for (int u = 0; u < LE; ++u) {
-      const int e = threadIdx.x + 256 * u;
-      if (!t.transA) As[e & 15][e >> 4] = ra[u];
-      else As[e / TM][e % TM] = ra[u];
-      if (t.transB) Bs[e & 15][e >> 4] = rb[u];
-      else Bs[e / TM][e % TM] = rb[u];
-    }
-  };
-  if (nstep > 0) load(0);
-  for (int it = 0; it < nstep; ++it) {
-    store(it);
-    __syncthreads();
-    if (it + 1 < nstep) load(it + 1);
-#pragma unroll 4
-    for (int kk = 0; kk < 16; ++kk) {
-      cx<S> a[Q], bq[Q];
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        a[q] = As[kk][ty + 16 * q];
-        bq[q] = Bs[kk][tx + 16 * q];
+  const int np = tk.np;
+  for (int s = 0; s < np; ++s) {
+    const GemmPair<S> t = tk.p[s];
+    for (int k0 = 0; k0 < Kd; k0 += 16) {
+      // operands read along their contiguous dimension so consecutive threads touch consecutive
+      // addresses
+      if (!t.transA) {
+        for (int e = threadIdx.x; e < 16 * TM; e += 256) {
+          const int r = e >> 4, kk = e & 15, gr = row0 + r, gk = k0 + kk;
+          As[kk][r] = (gr < M && gk < Kd) ? cscale(t.A[(size_t)gr * t.lda + gk], t.alpha) : mkc<S>(0, 0);
+        }
+      } else {
+        for (int e = threadIdx.x; e < 16 * TM; e += 256) {
+          const int kk = e / TM, r = e % TM, gr = row0 + r, gk = k0 + kk;
+          As[kk][r] = (gr < M && gk < Kd) ? cscale(t.A[(size_t)gk * t.lda + gr], t.alpha) : mkc<S>(0, 0);
+        }
       }
+      if (t.transB) {
+        for (int e = threadIdx.x; e < 16 * TM; e += 256) {
+          const int c = e >> 4, kk = e & 15, gc = col0 + c, gk = k0 + kk;
+          Bs[kk][c] = (gc < N && gk < Kd) ? t.B[(size_t)gc * t.ldb + gk] : mkc<S>(0, 0);
+        }
+      } else {
+        for (int e = threadIdx.x; e < 16 * TM; e += 256) {
+          const int kk = e / TM, c = e % TM, gk = k0 + kk, gc = col0 + c;
+          Bs[kk][c] = (gc < N && gk < Kd) ? t.B[(size_t)gk * t.ldb + gc] : mkc<S>(0, 0);
+        }
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < 16; ++kk) {
+        cx<S> a[Q], bq[Q];
 #pragma unroll
-      for (int q = 0; q < Q; ++q)
+        for (int q = 0; q < Q; ++q) {
+          a[q] = As[kk][ty + 16 * q];
+          bq[q] = Bs[kk][tx + 16 * q];
+        }
 #pragma unroll
-        for (int c = 0; c < Q; ++c) cfma(acc[q][c], a[q], bq[c]);
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+          for (int c = 0; c < Q; ++c) cfma(acc[q][c], a[q], bq[c]);
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 #pragma unroll
   for (int q = 0; q < Q; ++q)
